@@ -1,0 +1,388 @@
+"""Seeded synthetic QP instances for HPR-QP (problem data only).
+
+This module builds the problem data  min 1/2<x,Qx> + <c,x> + phi(x)  s.t.  l <= Ax <= u
+(the CCQP of Sec. 1, eq. (1.1); box phi is the CQP of eq. (1.2)).  It holds none of the
+solver's arithmetic: it draws random matrices and vectors and assembles CSR arrays.  Both
+the CUDA library's tests and the CPU oracle consume the same objects.
+
+Q is described as a sum of terms (``QTerm``), each one of
+  * ``diag``      Q += diag(d)
+  * ``csr``       Q += an explicit symmetric n x n CSR matrix
+  * ``dia``       Q += a symmetric banded matrix stored by its upper diagonals
+                  (offsets >= 0, diags[k][i] = Q[i, i+off_k], entries past the end are 0)
+  * ``factor``    Q += B^T B with B a p x n CSR matrix (matrix-free, Sec. 1 "no explicit Q")
+  * ``dense_factor``  Q += F^T F with F a dense row-major p x n matrix
+An empty term list means Q = 0 (the LP special case, Sec. 2.2 remark).
+
+Infinite bounds are IEEE +-inf.  phi is one of ``box`` (indicator of [L,U]), ``l1``
+(lam*||x||_1) or ``l1_box`` (both).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+PHI_BOX, PHI_L1, PHI_L1_BOX = 0, 1, 2
+_PHI_NAMES = {"box": PHI_BOX, "l1": PHI_L1, "l1_box": PHI_L1_BOX}
+
+
+@dataclass
+class QTerm:
+    kind: str                                   # diag | csr | dia | factor | dense_factor
+    p: int = 0                                  # rows of B or F
+    rowptr: Optional[np.ndarray] = None         # int32
+    colidx: Optional[np.ndarray] = None         # int32
+    vals: Optional[np.ndarray] = None           # float64
+    offsets: Optional[np.ndarray] = None        # int32, dia only
+    diags: Optional[np.ndarray] = None          # float64 [ndiag, n], dia only
+    dense: Optional[np.ndarray] = None          # float64: diag (n,) or F (p, n) row-major
+
+
+@dataclass
+class QP:
+    n: int
+    m: int
+    A_rowptr: np.ndarray
+    A_colidx: np.ndarray
+    A_vals: np.ndarray
+    c: np.ndarray
+    l: np.ndarray
+    u: np.ndarray
+    L: np.ndarray
+    U: np.ndarray
+    phi: int = PHI_BOX
+    lam: float = 0.0
+    qterms: List[QTerm] = field(default_factory=list)
+    name: str = ""
+
+    @property
+    def A_nnz(self) -> int:
+        return int(self.A_rowptr[-1]) if self.m > 0 else 0
+
+    def A_scipy(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.A_vals, self.A_colidx, self.A_rowptr), shape=(self.m, self.n))
+
+    def Q_scipy(self) -> sp.csr_matrix:
+        """Assembled Q (for small test problems and CSR comparisons only)."""
+        Q = sp.csr_matrix((self.n, self.n))
+        for t in self.qterms:
+            Q = Q + qterm_scipy(t, self.n)
+        return sp.csr_matrix(Q)
+
+
+def qterm_scipy(t: QTerm, n: int) -> sp.csr_matrix:
+    if t.kind == "diag":
+        return sp.diags(t.dense, 0, shape=(n, n), format="csr")
+    if t.kind == "csr":
+        return sp.csr_matrix((t.vals, t.colidx, t.rowptr), shape=(n, n))
+    if t.kind == "dia":
+        M = sp.csr_matrix((n, n))
+        for k, off in enumerate(t.offsets):
+            off = int(off)
+            d = t.diags[k][: n - off]
+            if off == 0:
+                M = M + sp.diags(d, 0, shape=(n, n))
+            else:
+                M = M + sp.diags(d, off, shape=(n, n)) + sp.diags(d, -off, shape=(n, n))
+        return sp.csr_matrix(M)
+    if t.kind == "factor":
+        B = sp.csr_matrix((t.vals, t.colidx, t.rowptr), shape=(t.p, n))
+        return sp.csr_matrix(B.T @ B)
+    if t.kind == "dense_factor":
+        F = np.asarray(t.dense).reshape(t.p, n)
+        return sp.csr_matrix(F.T @ F)
+    raise ValueError(t.kind)
+
+
+# --------------------------------------------------------------------------------------
+# construction helpers
+# --------------------------------------------------------------------------------------
+
+def csr_from_scipy(M) -> tuple:
+    M = sp.csr_matrix(M)
+    M.sum_duplicates()
+    M.sort_indices()
+    return (M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def _rows_k_distinct(rng: np.random.Generator, nrows: int, ncols: int, k: int) -> np.ndarray:
+    """nrows x k matrix of column indices, k distinct uniform columns per row, sorted."""
+    cols = rng.integers(0, ncols, size=(nrows, k), dtype=np.int64)
+    cols.sort(axis=1)
+    while True:
+        dup = np.any(cols[:, 1:] == cols[:, :-1], axis=1) if k > 1 else np.zeros(nrows, bool)
+        bad = np.nonzero(dup)[0]
+        if bad.size == 0:
+            return cols
+        redo = rng.integers(0, ncols, size=(bad.size, k), dtype=np.int64)
+        redo.sort(axis=1)
+        cols[bad] = redo
+
+
+def csr_k_per_row(rng, nrows, ncols, k, scale=1.0):
+    cols = _rows_k_distinct(rng, nrows, ncols, k)
+    vals = rng.standard_normal((nrows, k)) * scale
+    rowptr = (np.arange(nrows + 1, dtype=np.int64) * k).astype(np.int32)
+    return rowptr, cols.reshape(-1).astype(np.int32), vals.reshape(-1).astype(np.float64)
+
+
+def csr_bernoulli(rng, nrows, ncols, p, scale=1.0):
+    """Independent Bernoulli(p) pattern per entry, N(0, scale) values."""
+    counts = rng.binomial(ncols, p, size=nrows)
+    rowptr = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    colidx = np.empty(nnz, dtype=np.int32)
+    for i in range(nrows):
+        k = int(counts[i])
+        if k == 0:
+            continue
+        if k * 4 < ncols:
+            c = np.unique(rng.integers(0, ncols, size=k + 8 + k // 8))
+            while c.size < k:
+                c = np.unique(np.concatenate([c, rng.integers(0, ncols, size=k)]))
+            c = np.sort(rng.permutation(c)[:k])
+        else:
+            c = np.sort(rng.permutation(ncols)[:k])
+        colidx[rowptr[i]:rowptr[i + 1]] = c
+    vals = rng.standard_normal(nnz) * scale
+    if nnz >= 2 ** 31:
+        raise ValueError("nnz too large for int32 row pointers")
+    return rowptr.astype(np.int32), colidx, vals.astype(np.float64)
+
+
+def csr_bernoulli_fast(rng, nrows, ncols, p, scale=1.0):
+    """Bernoulli(p) pattern for large sparse matrices, drawn row by row in bulk."""
+    counts = rng.binomial(ncols, p, size=nrows).astype(np.int64)
+    nnz = int(counts.sum())
+    rowptr = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    rows = np.repeat(np.arange(nrows, dtype=np.int64), counts)
+    cols = rng.integers(0, ncols, size=nnz, dtype=np.int64)
+    key = rows * ncols + cols
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    # redraw duplicates until the pattern is a set (keeps the per-row counts)
+    while True:
+        dup = np.nonzero(key[1:] == key[:-1])[0] + 1
+        if dup.size == 0:
+            break
+        r = key[dup] // ncols
+        key[dup] = r * ncols + rng.integers(0, ncols, size=dup.size, dtype=np.int64)
+        key.sort()
+    colidx = (key % ncols).astype(np.int32)
+    vals = rng.standard_normal(nnz) * scale
+    return rowptr.astype(np.int32), colidx, vals.astype(np.float64)
+
+
+def _csr_matvec(rowptr, colidx, vals, x):
+    nrows = rowptr.size - 1
+    M = sp.csr_matrix((vals, colidx, rowptr), shape=(nrows, x.size))
+    return M @ x
+
+
+def _bounds_eq_then_upper(rng, Ax0, n_eq):
+    """First n_eq rows l = u = A x0; remaining rows l = -inf, u = A x0 + U(0,1)."""
+    m = Ax0.size
+    l = np.full(m, -np.inf)
+    u = Ax0 + rng.random(m)
+    l[:n_eq] = Ax0[:n_eq]
+    u[:n_eq] = Ax0[:n_eq]
+    return l, u
+
+
+# --------------------------------------------------------------------------------------
+# the five workload families
+# --------------------------------------------------------------------------------------
+
+def plain_cqp(n=1000, m=500, seed=0, a_density=0.01, q_rows=100, q_density=0.02,
+              n_eq=None, box=(0.0, 10.0)) -> QP:
+    """Plain FP64 CQP: A Bernoulli(1%) N(0,1); Q = M^T M with M q_rows x n Bernoulli(2%);
+    c ~ N(0,1); x0 ~ U(0,1); rows [0, m/2) equalities l=u=A x0, the rest l=-inf,
+    u = A x0 + U(0,1); C = [0,10]^n."""
+    rng = np.random.default_rng(seed)
+    A = csr_bernoulli(rng, m, n, a_density)
+    M = csr_bernoulli(rng, q_rows, n, q_density)
+    c = rng.standard_normal(n)
+    x0 = rng.random(n)
+    Ax0 = _csr_matvec(*A, x0) if m > 0 else np.zeros(0)
+    l, u = _bounds_eq_then_upper(rng, Ax0, m // 2 if n_eq is None else n_eq)
+    L = np.full(n, box[0])
+    U = np.full(n, box[1])
+    q = QTerm("factor", p=q_rows, rowptr=M[0], colidx=M[1], vals=M[2])
+    return QP(n, m, A[0], A[1], A[2], c, l, u, L, U, PHI_BOX, 0.0, [q],
+              name=f"plain_cqp_n{n}_m{m}_s{seed}")
+
+
+def pentadiag_terms(rng, n):
+    """Symmetric pentadiagonal P: diag U(1,2), bands +-1, +-2 U(-0.2,0.2) (row sums of
+    |off-diagonals| <= 0.8 < 1 <= diag, so P is positive definite)."""
+    d0 = 1.0 + rng.random(n)
+    d1 = rng.uniform(-0.2, 0.2, n)
+    d2 = rng.uniform(-0.2, 0.2, n)
+    d1[n - 1:] = 0.0
+    d2[max(n - 2, 0):] = 0.0
+    return QTerm("dia", offsets=np.array([0, 1, 2], np.int32), diags=np.stack([d0, d1, d2]))
+
+
+def large_cqp(n=1_000_000, m=500_000, seed=0, s_rows=None, eq_frac=0.3, a_per_row=6,
+              s_per_row=3, box=(-5.0, 5.0), q_as="sum") -> QP:
+    """Large sparse CQP: A with 6 uniform distinct columns per row, N(0,1);
+    Q = P (pentadiagonal) + S^T S with S s_rows x n, 3 nnz per row N(0,1);
+    c ~ N(0,1); 30% equality rows, the rest one-sided; C = [-5,5]^n.
+    ``q_as='sum'`` passes Q as dia + factor terms, ``'csr'`` as one assembled CSR."""
+    rng = np.random.default_rng(seed)
+    if s_rows is None:
+        s_rows = max(1, n // 100)
+    A = csr_k_per_row(rng, m, n, a_per_row)
+    P = pentadiag_terms(rng, n)
+    S = csr_k_per_row(rng, s_rows, n, s_per_row)
+    c = rng.standard_normal(n)
+    x0 = rng.random(n)
+    Ax0 = _csr_matvec(*A, x0)
+    l, u = _bounds_eq_then_upper(rng, Ax0, int(round(eq_frac * m)))
+    L = np.full(n, box[0])
+    U = np.full(n, box[1])
+    fac = QTerm("factor", p=s_rows, rowptr=S[0], colidx=S[1], vals=S[2])
+    if q_as == "sum":
+        terms = [P, fac]
+    else:
+        Q = qterm_scipy(P, n) + qterm_scipy(fac, n)
+        rp, ci, va = csr_from_scipy(Q)
+        terms = [QTerm("csr", rowptr=rp, colidx=ci, vals=va)]
+    return QP(n, m, A[0], A[1], A[2], c, l, u, L, U, PHI_BOX, 0.0, terms,
+              name=f"large_cqp_n{n}_m{m}_s{seed}_{q_as}")
+
+
+def lasso(p=50_000, q=500_000, seed=0, density=5e-4, support_frac=0.01, noise=0.01,
+          lam_frac=0.1) -> QP:
+    """Lasso min 1/2||Bx-b||^2 + lam||x||_1 as a CCQP (Sec. 4.4, original form):
+    Q = B^T B matrix-free, c = -B^T b, phi = lam||.||_1 with lam = 0.1||B^T b||_inf,
+    no A rows, C = R^n.  B is p x q Bernoulli(density), N(0, 1/sqrt(p))."""
+    rng = np.random.default_rng(seed)
+    B = csr_bernoulli_fast(rng, p, q, density, scale=1.0 / np.sqrt(p))
+    k = max(1, int(round(support_frac * q)))
+    xs = np.zeros(q)
+    xs[rng.permutation(q)[:k]] = rng.standard_normal(k)
+    Bm = sp.csr_matrix((B[2], B[1], B[0]), shape=(p, q))
+    b = Bm @ xs + noise * rng.standard_normal(p)
+    Btb = Bm.T @ b
+    c = -Btb
+    lam = lam_frac * float(np.max(np.abs(Btb)))
+    e = np.zeros(0, np.int32)
+    return QP(q, 0, np.zeros(1, np.int32), e, np.zeros(0), c, np.zeros(0), np.zeros(0),
+              np.full(q, -np.inf), np.full(q, np.inf), PHI_L1, lam,
+              [QTerm("factor", p=p, rowptr=B[0], colidx=B[1], vals=B[2])],
+              name=f"lasso_p{p}_q{q}_s{seed}")
+
+
+def portfolio(seed: int, n: Optional[int] = None, n_lo=50, n_hi=5000, sectors=10) -> QP:
+    """Portfolio-style CQP: Q = F^T F + diag(U(0.01,0.1)), F k x n dense N(0, 1/sqrt(n)),
+    k = max(5, n//20); A = [1^T; 10 sector indicator rows] with 1^T x = 1 and sector
+    sums <= 0.3; c ~ N(0, 0.1); C = [0, 0.1]^n.  Sectors are assigned round-robin and
+    then shuffled, so none is empty."""
+    rng = np.random.default_rng(seed)
+    if n is None:
+        n = int(rng.integers(n_lo, n_hi + 1))
+    k = max(5, n // 20)
+    F = rng.standard_normal((k, n)) / np.sqrt(n)
+    d = rng.uniform(0.01, 0.1, n)
+    sector = rng.permutation(np.arange(n) % sectors)
+    m = 1 + sectors
+    rows = [np.arange(n)] + [np.nonzero(sector == s)[0] for s in range(sectors)]
+    rowptr = np.zeros(m + 1, np.int64)
+    rowptr[1:] = np.cumsum([r.size for r in rows])
+    colidx = np.concatenate(rows).astype(np.int32)
+    vals = np.ones(colidx.size)
+    l = np.concatenate([[1.0], np.full(sectors, -np.inf)])
+    u = np.concatenate([[1.0], np.full(sectors, 0.3)])
+    c = 0.1 * rng.standard_normal(n)
+    terms = [QTerm("dense_factor", p=k, dense=np.ascontiguousarray(F)), QTerm("diag", dense=d)]
+    return QP(n, m, rowptr.astype(np.int32), colidx, vals, c, l, u, np.zeros(n),
+              np.full(n, 0.1), PHI_BOX, 0.0, terms, name=f"portfolio_n{n}_s{seed}")
+
+
+def param_family_base(n=100_000, m=50_000, seed=0, s_rows=None):
+    """The fixed part of the parametric family: A and Q of ``large_cqp`` at (n, m),
+    and the nominal c-bar, u-bar."""
+    base = large_cqp(n=n, m=m, seed=seed, s_rows=s_rows if s_rows is not None else max(1, n // 100))
+    return base
+
+
+def param_family_instance(base: QP, seed: int) -> QP:
+    """One member: c = c-bar + 0.1 N(0,1), u = u-bar + 0.1 U(0,1) on inequality rows."""
+    rng = np.random.default_rng(1_000_003 + seed)
+    c = base.c + 0.1 * rng.standard_normal(base.n)
+    u = base.u.copy()
+    ineq = np.isinf(base.l)
+    u[ineq] = u[ineq] + 0.1 * rng.random(int(ineq.sum()))
+    return QP(base.n, base.m, base.A_rowptr, base.A_colidx, base.A_vals, c, base.l, u,
+              base.L, base.U, base.phi, base.lam, base.qterms, name=f"{base.name}_i{seed}")
+
+
+# --------------------------------------------------------------------------------------
+# small problems for tests (closed forms, brute force, special cases)
+# --------------------------------------------------------------------------------------
+
+def random_small(n=6, m=4, seed=0, q_kind="csr", q_rank=None, phi="box", lam=0.0,
+                 eq_rows=1, box=(-1.0, 1.0), density=0.6) -> QP:
+    """Small dense-ish random CQP used by brute-force and equivalence tests."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) * (rng.random((m, n)) < density)
+    for i in range(m):
+        if not np.any(A[i]):
+            A[i, rng.integers(n)] = 1.0
+    r = n if q_rank is None else q_rank
+    Fq = rng.standard_normal((r, n))
+    Qd = Fq.T @ Fq if r > 0 else np.zeros((n, n))
+    c = rng.standard_normal(n)
+    x0 = rng.uniform(box[0] * 0.5, box[1] * 0.5, n) if np.isfinite(box[0]) else rng.standard_normal(n)
+    Ax0 = A @ x0
+    l = Ax0 - rng.random(m)
+    u = Ax0 + rng.random(m)
+    l[:eq_rows] = Ax0[:eq_rows]
+    u[:eq_rows] = Ax0[:eq_rows]
+    if m > eq_rows + 1:
+        l[eq_rows + 1::2] = -np.inf
+    rp, ci, va = csr_from_scipy(sp.csr_matrix(A))
+    terms: List[QTerm] = []
+    if r > 0:
+        if q_kind == "csr":
+            qrp, qci, qva = csr_from_scipy(sp.csr_matrix(Qd))
+            terms = [QTerm("csr", rowptr=qrp, colidx=qci, vals=qva)]
+        elif q_kind == "factor":
+            frp, fci, fva = csr_from_scipy(sp.csr_matrix(Fq))
+            terms = [QTerm("factor", p=r, rowptr=frp, colidx=fci, vals=fva)]
+        elif q_kind == "dense_factor":
+            terms = [QTerm("dense_factor", p=r, dense=np.ascontiguousarray(Fq))]
+        else:
+            raise ValueError(q_kind)
+    return QP(n, m, rp, ci, va, c, l, u, np.full(n, box[0]), np.full(n, box[1]),
+              _PHI_NAMES[phi], lam, terms, name=f"small_n{n}_m{m}_s{seed}_{q_kind}_{phi}")
+
+
+def from_dense(Q: np.ndarray, c, A=None, l=None, u=None, L=None, U=None, phi="box",
+               lam=0.0, q_kind="csr") -> QP:
+    """Wrap dense test data (Q symmetric PSD) into a QP."""
+    n = c.size
+    A = np.zeros((0, n)) if A is None else np.asarray(A, float)
+    m = A.shape[0]
+    rp, ci, va = csr_from_scipy(sp.csr_matrix(A)) if m > 0 else (np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    terms = []
+    if Q is not None and np.any(Q):
+        if q_kind == "csr":
+            qrp, qci, qva = csr_from_scipy(sp.csr_matrix(Q))
+            terms = [QTerm("csr", rowptr=qrp, colidx=qci, vals=qva)]
+        elif q_kind == "diag":
+            terms = [QTerm("diag", dense=np.diag(Q).copy())]
+        else:
+            raise ValueError(q_kind)
+    return QP(n, m, rp, ci, va, np.asarray(c, float),
+              np.zeros(0) if l is None else np.asarray(l, float),
+              np.zeros(0) if u is None else np.asarray(u, float),
+              np.full(n, -np.inf) if L is None else np.asarray(L, float),
+              np.full(n, np.inf) if U is None else np.asarray(U, float),
+              _PHI_NAMES[phi], lam, terms, name="dense")

@@ -1,0 +1,460 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: closed-form solutions,
+brute-force active-set enumeration, an LP library, the subproblem optimality conditions
+written from their definitions, the dense metric M of eq. (2.12), Algorithm 2 with an
+explicit range-space basis (Thm. 3.1), the O(1/k) bound of Thm. 3.2, and the printed
+parameter values of Sec. 4.1.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+import oracle
+import qpgen
+from tests import dense_ref as D
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _solve(qp, **kw):
+    kw.setdefault("tol", 1e-10)
+    kw.setdefault("max_iter", 400000)
+    return oracle.solve(qp, **kw)
+
+
+# ------------------------------------------------------------------ closed forms
+def test_unconstrained_closed_form():
+    # m = 0, C = R^n, Q > 0: the minimiser is -Q^{-1} c (Sec. 1, eq. (1.1) with phi = 0)
+    rng = np.random.default_rng(1)
+    n = 12
+    F = rng.standard_normal((n, n))
+    Q = F.T @ F + 0.5 * np.eye(n)
+    c = rng.standard_normal(n)
+    qp = qpgen.from_dense(Q, c)
+    s = _solve(qp)
+    assert s.status == "converged"
+    x = np.linalg.solve(Q, -c)
+    assert np.linalg.norm(s.x - x) <= 1e-7 * max(1, np.linalg.norm(x))
+
+
+def test_diag_box_closed_form():
+    # diagonal Q, box only: separable, x_j = clip(-c_j/q_j, L_j, U_j)
+    rng = np.random.default_rng(2)
+    n = 30
+    q = rng.uniform(0.5, 3.0, n)
+    c = 3 * rng.standard_normal(n)
+    L = -rng.random(n)
+    U = rng.random(n)
+    qp = qpgen.from_dense(np.diag(q), c, L=L, U=U, q_kind="diag")
+    s = _solve(qp)
+    assert s.status == "converged"
+    np.testing.assert_allclose(s.x, np.clip(-c / q, L, U), atol=1e-8)
+    # x bar lies in C exactly (it is a projection, eq. (3.2))
+    assert np.all(s.x >= L) and np.all(s.x <= U)
+
+
+def test_l1_orthonormal_design_soft_threshold():
+    # Lasso with orthonormal design (Sec. 4.4): Q = F^T F = I, c = -F^T b, the minimiser of
+    # 1/2||x||^2 - <F^T b, x> + lam||x||_1 is soft(F^T b, lam)
+    rng = np.random.default_rng(3)
+    n = 16
+    F, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    b = rng.standard_normal(n)
+    g = F.T @ b
+    lam = 0.4
+    qp = qpgen.QP(n, 0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0), -g, np.zeros(0),
+                  np.zeros(0), np.full(n, -np.inf), np.full(n, np.inf), qpgen.PHI_L1, lam,
+                  [qpgen.QTerm("dense_factor", p=n, dense=np.ascontiguousarray(F))])
+    s = _solve(qp)
+    assert s.status == "converged"
+    np.testing.assert_allclose(s.x, np.sign(g) * np.maximum(np.abs(g) - lam, 0), atol=1e-8)
+    # eq. (3.1) with the Moreau identity: zbar lies in [-lam, lam] by construction
+    assert np.all(np.abs(s.z) <= lam * (1 + 1e-12))
+
+
+def test_l1_box_separable():
+    # lam|x| + box with diagonal Q: per coordinate clip(soft(-c/q... )) -> compute by 1-D
+    # minimisation on a fine grid refined analytically: x = clip(soft(-c, lam)/q, L, U)
+    rng = np.random.default_rng(4)
+    n = 20
+    q = rng.uniform(0.5, 2.0, n)
+    c = 2 * rng.standard_normal(n)
+    L = -0.5 * rng.random(n) - 0.1
+    U = 0.5 * rng.random(n) + 0.1
+    lam = 0.3
+    qp = qpgen.from_dense(np.diag(q), c, L=L, U=U, phi="l1_box", lam=lam, q_kind="diag")
+    s = _solve(qp)
+    assert s.status == "converged"
+    soft = np.sign(-c) * np.maximum(np.abs(c) - lam, 0)
+    np.testing.assert_allclose(s.x, np.clip(soft / q, L, U), atol=1e-8)
+
+
+def test_lp_special_case_matches_linprog():
+    # Q = 0, phi = delta_C: HPR-QP reduces to HPR-LP (Sec. 2.2 remark); compare the
+    # optimal value with an LP library (HiGHS through scipy)
+    rng = np.random.default_rng(5)
+    n, m = 10, 6
+    A = rng.standard_normal((m, n))
+    x0 = rng.random(n)
+    l = A @ x0 - rng.random(m)
+    u = A @ x0 + rng.random(m)
+    l[:2] = u[:2] = (A @ x0)[:2]
+    c = rng.standard_normal(n)
+    qp = qpgen.from_dense(None, c, A=A, l=l, u=u, L=np.zeros(n), U=np.ones(n))
+    s = _solve(qp)
+    assert s.status == "converged"
+    A_ub = np.vstack([A[2:], -A[2:]])
+    b_ub = np.concatenate([u[2:], -l[2:]])
+    ref = so.linprog(c, A_ub=A_ub, b_ub=b_ub, A_eq=A[:2], b_eq=l[:2], bounds=list(zip([0] * n, [1] * n)),
+                     method="highs")
+    assert ref.status == 0
+    assert abs(s.pobj - ref.fun) <= 1e-7 * (1 + abs(ref.fun))
+    assert s.lambda_Q == 0.0
+
+
+# ------------------------------------------------------------------ brute force
+@pytest.mark.parametrize("seed,q_kind,rank", [(0, "csr", None), (1, "csr", None), (2, "factor", 2),
+                                              (3, "dense_factor", 3), (4, "factor", 1), (5, "csr", None)])
+def test_brute_force_active_sets(seed, q_kind, rank):
+    qp = qpgen.random_small(n=5, m=3, seed=seed, q_kind=q_kind, q_rank=rank)
+    best = D.brute_force(qp)
+    assert best is not None
+    obj, xs, ys, zs = best
+    s = _solve(qp, tol=1e-10)
+    assert s.status == "converged"
+    assert abs(s.pobj - obj) <= 1e-8 * (1 + abs(obj))
+    if rank is None:  # Q > 0: the minimiser is unique
+        np.testing.assert_allclose(s.x, xs, atol=1e-6)
+    # the brute-force point is a KKT point: eta vanishes there (Sec. 4.1 definitions)
+    e, _, _ = oracle.eta(qp, xs, ys, zs)
+    assert np.max(e) <= 1e-10
+
+
+def test_kkt_invariants_at_termination():
+    qp = qpgen.plain_cqp(n=200, m=100, seed=7, q_rows=20, a_density=0.05, q_density=0.1)
+    s = _solve(qp, tol=1e-8)
+    assert s.status == "converged"
+    assert max(s.eta_p, s.eta_d, s.eta_gap) <= 1e-8
+    # xbar = Prox (a projection onto C): in C exactly
+    assert np.all(s.x >= qp.L) and np.all(s.x <= qp.U)
+    # ybar of eq. (3.5): positive only at a finite lower bound, negative at a finite upper
+    assert np.all(~((s.y > 0) & ~np.isfinite(qp.l)))
+    assert np.all(~((s.y < 0) & ~np.isfinite(qp.u)))
+    # zbar of eq. (3.1): zbar_j > 0 only where xbar_j = L_j, < 0 only where xbar_j = U_j
+    assert np.all((s.z <= 0) | (s.x == qp.L))
+    assert np.all((s.z >= 0) | (s.x == qp.U))
+    # eta recomputed independently of the iteration agrees with the reported one
+    e, _, _ = oracle.eta(qp, s.x, s.y, s.z)
+    np.testing.assert_allclose(e, [s.eta_p, s.eta_d, s.eta_gap], rtol=1e-12, atol=1e-300)
+
+
+# ------------------------------------------------------------------ metric M, eq. (2.12)
+@pytest.mark.parametrize("rank", [None, 2])
+def test_mnorm_matches_dense_metric(rank):
+    qp = qpgen.random_small(n=6, m=4, seed=11, q_kind="csr" if rank is None else "factor", q_rank=rank)
+    A, Q = D.dense_of(qp)
+    lamA = 1.01 * np.linalg.eigvalsh(A @ A.T).max()
+    lamQ = 1.01 * np.linalg.eigvalsh(Q).max()
+    M = D.metric_M(A, Q, 0.7, lamA, lamQ)
+    # M is positive semidefinite on R^m x W x R^n x R^n (Assumption 2.2 / Prop. 2.3)
+    d, V = D.range_basis(Q)
+    m, n = qp.m, qp.n
+    P = np.zeros((m + 3 * n, m + d.size + 2 * n))
+    P[:m, :m] = np.eye(m)
+    P[m:m + n, m:m + d.size] = V
+    P[m + n:, m + d.size:] = np.eye(2 * n)
+    assert np.linalg.eigvalsh(P.T @ M @ P).min() >= -1e-9 * np.abs(M).max()
+    rng = np.random.default_rng(0)
+    for sigma in (0.05, 0.7, 9.0):
+        for _ in range(3):
+            dy, dw, dx = rng.standard_normal(m), rng.standard_normal(n), rng.standard_normal(n)
+            ref = D.mnorm2_dense(A, Q, sigma, lamA, lamQ, dy, dw, dx)
+            got = oracle.mnorm2(qp, sigma, lamA, lamQ, dy, dw, dx)
+            assert abs(got - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+# ------------------------------------------------------------------ one step: subproblem optimality
+def _support_subgrad_ok(s, y, lo, hi, tol):
+    """s in d delta*_K(-y): s in [lo, hi], s = lo where y > 0, s = hi where y < 0."""
+    ok = np.all(s >= lo - tol) & np.all(s <= hi + tol)
+    ok &= np.all(np.where(y > tol, np.abs(s - lo) <= tol, True))
+    ok &= np.all(np.where(y < -tol, np.abs(s - hi) <= tol, True))
+    return bool(ok)
+
+
+@pytest.mark.parametrize("seed,rank", [(21, None), (22, 2), (23, 3)])
+def test_one_step_subproblem_optimality(seed, rank):
+    """Steps 1-3 of Algorithm 3 solve the subproblems of Algorithm 2 (Prop. 3.1, eq. (2.11)):
+    each optimality condition, written from L_sigma and the proximal terms, holds."""
+    qp = qpgen.random_small(n=6, m=4, seed=seed, q_kind="csr" if rank is None else "factor", q_rank=rank)
+    A, Q = D.dense_of(qp)
+    rng = np.random.default_rng(seed)
+    lamA = 1.01 * np.linalg.eigvalsh(A @ A.T).max()
+    lamQ = 1.01 * np.linalg.eigvalsh(Q).max()
+    sigma = 0.8
+    y, w, x = rng.standard_normal(qp.m), rng.standard_normal(qp.n), rng.standard_normal(qp.n)
+    yb, wb, zb, xb, wh = oracle.step(qp, sigma, lamA, lamQ, y, w, x)
+    c = qp.c
+    tol = 1e-10
+    # Step 1: 0 in -d phi*(-zb) + x + sigma(-Qw + A^*y + zb - c); the point in the
+    # subdifferential is xbar (Step 2), so xbar must satisfy Step 2 exactly and -zb in
+    # d delta_C(xbar): xbar in C, zb > 0 only at L, zb < 0 only at U
+    np.testing.assert_allclose(xb, x + sigma * (-Q @ w + A.T @ y + zb - c), atol=1e-12)
+    assert np.all(xb >= qp.L) and np.all(xb <= qp.U)
+    assert np.all((zb <= tol) | (np.abs(xb - qp.L) <= tol))
+    assert np.all((zb >= -tol) | (np.abs(xb - qp.U) <= tol))
+    # Step 3-1 on W (gradient of the w-subproblem, all terms in Range(Q)):
+    # Q[wh - xb + sigma(Q wh - A^*y - zb + c)] + sigma Q(lamQ I - Q)(wh - w) = 0
+    g1 = Q @ (wh - xb + sigma * (Q @ wh - A.T @ y - zb + c)) + sigma * Q @ (lamQ * wh - Q @ wh - lamQ * w + Q @ w)
+    assert np.linalg.norm(g1) <= 1e-10
+    # Step 3-2: 0 in -d delta*_K(-yb) + A xb + sigma A(-Q wh + A^* yb + zb - c) + sigma S_y (yb - y)
+    s = A @ xb + sigma * A @ (-Q @ wh + A.T @ yb + zb - c) + sigma * (lamA * (yb - y) - A @ A.T @ (yb - y))
+    assert _support_subgrad_ok(s, yb, qp.l, qp.u, 1e-9)
+    # Step 3-3: like 3-1 with yb
+    g3 = Q @ (wb - xb + sigma * (Q @ wb - A.T @ yb - zb + c)) + sigma * Q @ (lamQ * wb - Q @ wb - lamQ * w + Q @ w)
+    assert np.linalg.norm(g3) <= 1e-10
+
+
+@pytest.mark.parametrize("seed,rank", [(31, None), (32, 2)])
+def test_sgs_joint_step(seed, rank):
+    """Prop. 2.3: the sGS sequence w1/2 -> y -> w solves the joint (y, w) step of
+    Algorithm 1 with T1 = S + S_sGS (eqs. (2.6)-(2.7), S_sGS from its definition)."""
+    qp = qpgen.random_small(n=6, m=4, seed=seed, q_kind="csr" if rank is None else "factor", q_rank=rank)
+    A, Q = D.dense_of(qp)
+    rng = np.random.default_rng(seed)
+    lamA = 1.01 * np.linalg.eigvalsh(A @ A.T).max()
+    lamQ = 1.01 * np.linalg.eigvalsh(Q).max()
+    sigma = 1.3
+    y, w, x = rng.standard_normal(qp.m), rng.standard_normal(qp.n), rng.standard_normal(qp.n)
+    d, V = D.range_basis(Q)
+    w = V @ (V.T @ w)  # w^k in W
+    yb, wb, zb, xb, wh = oracle.step(qp, sigma, lamA, lamQ, y, w, x)
+    wbW = V @ (V.T @ wb)  # Pi_W(wb): same Q-image (Prop. 3.1)
+    np.testing.assert_allclose(Q @ wbW, Q @ wb, atol=1e-10)
+    M = D.metric_M(A, Q, sigma, lamA, lamQ)
+    m, n = qp.m, qp.n
+    # T1 = M[yw,yw] - sigma A_Q^* A_Q
+    AQ = np.hstack([A.T, -Q])
+    T1 = M[:m + n, :m + n] - sigma * AQ.T @ AQ
+    dyw = np.concatenate([yb - y, wbW - w])
+    T1d = T1 @ dyw
+    c = qp.c
+    # y-block: 0 in -d delta*_K(-yb) + A xb + sigma A(-Q wb + A^* yb + zb - c) + (T1 d)_y
+    s = A @ xb + sigma * A @ (-Q @ wbW + A.T @ yb + zb - c) + T1d[:m]
+    assert _support_subgrad_ok(s, yb, qp.l, qp.u, 1e-9)
+    # w-block, projected on W: Q wb - Q xb - sigma Q(-Q wb + A^*yb + zb - c) + (T1 d)_w
+    gw = Q @ wbW - Q @ xb - sigma * Q @ (-Q @ wbW + A.T @ yb + zb - c) + T1d[m:]
+    assert np.linalg.norm(V.T @ gw) <= 1e-9
+
+
+# ------------------------------------------------------------------ Thm. 3.1
+@pytest.mark.parametrize("seed,rank", [(41, 2), (42, 3), (43, None)])
+def test_thm31_shadow_sequence_equals_alg2(seed, rank):
+    """Algorithm 3 (shadow w_Q, no projection) and Algorithm 2 (every w-step a minimisation
+    over W = Range(Q)) produce the same (ybar, Q wbar, zbar, xbar) from the origin."""
+    qp = qpgen.random_small(n=6, m=4, seed=seed, q_kind="csr" if rank is None else "factor", q_rank=rank)
+    A, Q = D.dense_of(qp)
+    lamA = 1.01 * np.linalg.eigvalsh(A @ A.T).max()
+    lamQ = 1.01 * np.linalg.eigvalsh(Q).max()
+    sigma = 0.6
+    K = 25
+    ref = D.alg2_run(qp, sigma, lamA, lamQ, K)
+    n, m = qp.n, qp.m
+    y, w, x = np.zeros(m), np.zeros(n), np.zeros(n)
+    for k in range(K):
+        yb, wb, zb, xb, _ = oracle.step(qp, sigma, lamA, lamQ, y, w, x)
+        ry, rQw, rz, rx = ref[k]
+        scale = 1 + np.abs(np.concatenate([ry, rQw, rz, rx])).max()
+        assert np.abs(yb - ry).max() <= 1e-9 * scale
+        assert np.abs(Q @ wb - rQw).max() <= 1e-9 * scale
+        assert np.abs(zb - rz).max() <= 1e-9 * scale
+        assert np.abs(xb - rx).max() <= 1e-9 * scale
+        a, b = 1.0 / (k + 2), (k + 1.0) / (k + 2)
+        y, w, x = b * (2 * yb - y), b * (2 * wb - w), b * (2 * xb - x)
+    # the oracle's own loop (fixed sigma, no restart) reproduces the same xbar trajectory
+    s = oracle.solve(qp, tol=1e-30, max_iter=K, lambda_A=lamA, lambda_Q=lamQ, sigma0=sigma,
+                     restart_off=1, sigma_fixed=1, trace_len=K)
+    for k in range(K):
+        np.testing.assert_allclose(s.trace["x"][k], ref[k][3], atol=1e-9 * (1 + np.abs(ref[k][3]).max()))
+
+
+# ------------------------------------------------------------------ Thm. 3.2 (O(1/k))
+@pytest.mark.parametrize("seed", [51, 52])
+def test_complexity_bound(seed):
+    """||ubar^{k+1} - u^k||_M <= ||u^0 - u*||_M / (k+1) for fixed sigma, no restarts,
+    with u* a KKT point found by brute force (Thm. 3.2, first bound)."""
+    qp = qpgen.random_small(n=5, m=3, seed=seed, q_kind="factor", q_rank=3)
+    A, Q = D.dense_of(qp)
+    obj, xs, ys, zs = D.brute_force(qp)
+    lamA = 1.01 * np.linalg.eigvalsh(A @ A.T).max()
+    lamQ = 1.01 * np.linalg.eigvalsh(Q).max()
+    sigma = 0.9
+    R0 = np.sqrt(D.mnorm2_dense(A, Q, sigma, lamA, lamQ, -ys, -xs, -xs))  # u0 = 0, w* = x*
+    K = 300
+    s = oracle.solve(qp, tol=1e-30, max_iter=K, lambda_A=lamA, lambda_Q=lamQ, sigma0=sigma,
+                     restart_off=1, sigma_fixed=1, restart_every=1, trace_len=K)
+    R = s.trace["R"]
+    assert R.size == K and np.all(np.isfinite(R))
+    k = np.arange(K)
+    assert np.all(R <= R0 / (k + 1) * (1 + 1e-9) + 1e-12)
+
+
+# ------------------------------------------------------------------ sigma update (Alg. 5)
+@pytest.mark.parametrize("t1,t2,t3,lq", [(1.0, 1.0, 0.5, 2.0), (3e-3, 7.0, 40.0, 0.1), (1e-12, 1e-12, 1e-9, 5.0),
+                                          (2.0, 0.5, 0.0, 1.0), (1e4, 1e-6, 1e3, 1e3)])
+def test_sigma_argmin(t1, t2, t3, lq):
+    f = lambda s: t1 * s + t2 / s + s * s * t3 / (1 + lq * s)
+    s_exact = oracle.sigma_argmin(t1, t2, t3, lq, golden=False)
+    s_gold = oracle.sigma_argmin(t1, t2, t3, lq, golden=True)
+    # independent minimiser: bounded Brent on log sigma
+    r = so.minimize_scalar(lambda u: f(np.exp(u)), bounds=(np.log(s_exact) - 5, np.log(s_exact) + 5),
+                           method="bounded", options={"xatol": 1e-12})
+    assert abs(np.log(s_exact) - r.x) <= 1e-5
+    assert abs(np.log(s_gold) - np.log(s_exact)) <= 1e-6
+    # first-order condition f'(s) = 0 (f strictly convex, eq. (3.10))
+    h = 1e-6 * s_exact
+    d = (f(s_exact + h) - f(s_exact - h)) / (2 * h)
+    assert abs(d) <= 1e-5 * (t1 + t2 / s_exact ** 2 + t3 / lq)
+    assert f(s_exact) <= min(f(s_exact * 1.001), f(s_exact / 1.001))
+
+
+def test_sigma_closed_form_without_theta3():
+    # theta3 = 0 (the LP case, Q = 0): f = t1 s + t2/s, argmin sqrt(t2/t1)
+    assert oracle.sigma_argmin(4.0, 9.0, 0.0, 0.0) == pytest.approx(1.5, rel=1e-15)
+
+
+def test_sigma_update_smoothing():
+    """Algorithm 5: floors at 1e-12, beta = exp(-R~_{r,tau_r-1}/R~_{0,tau_0-1}) and
+    sigma_{r+1} = exp(beta log sigma_new + (1 - beta) log sigma_r)."""
+    e = np.e
+    # theta3 = 0 and theta1 = theta2: sigma_new = 1, so log sigma_{r+1} = (1 - beta) log sigma_r
+    for ratio in (0.0, 0.05, 1.0, 3.0):
+        beta = np.exp(-ratio)
+        got = oracle.sigma_update(2.0, 2.0, 0.0, 1.0, ratio, e ** 2, False)
+        assert np.log(got) == pytest.approx((1 - beta) * 2.0, rel=1e-13, abs=1e-15)
+    # ratio 0 (first loop converged to the noise floor): beta = 1, sigma_{r+1} = sigma_new
+    assert oracle.sigma_update(4.0, 1.0, 0.0, 1.0, 0.0, 123.0, False) == pytest.approx(0.5, rel=1e-14)
+    # floors: tiny theta1, theta2 both become 1e-12, so sigma_new = 1
+    assert oracle.sigma_update(1e-30, 1e-40, 0.0, 1.0, 0.0, 7.0, False) == pytest.approx(1.0, rel=1e-14)
+    # only theta1, theta2 are floored: theta2 = 4e-12 with theta1 floored gives sqrt(4) = 2
+    assert oracle.sigma_update(0.0, 4e-12, 0.0, 1.0, 0.0, 7.0, False) == pytest.approx(2.0, rel=1e-12)
+
+
+# ------------------------------------------------------------------ power method (Sec. 4.1)
+def test_power_method_estimates():
+    qp = qpgen.plain_cqp(n=300, m=150, seed=3, q_rows=30, a_density=0.05, q_density=0.1)
+    A, Q = D.dense_of(qp)
+    la = np.linalg.eigvalsh(A @ A.T).max()
+    lq = np.linalg.eigvalsh(Q).max()
+    ea = oracle.power_A(qp, 5000, 1e-12, 1.0)
+    eq = oracle.power_Q(qp, 5000, 1e-12, 1.0)
+    assert ea <= la * (1 + 1e-9) and ea >= la * (1 - 1e-6)
+    assert eq <= lq * (1 + 1e-9) and eq >= lq * (1 - 1e-6)
+    s = oracle.solve(qp, max_iter=1)
+    assert s.lambda_A >= la and s.lambda_Q >= lq  # default safety factor keeps lambda >= lambda_1
+
+
+# ------------------------------------------------------------------ restart bookkeeping (Sec. 3.2)
+def test_restart_rules_on_trace():
+    qp = qpgen.plain_cqp(n=300, m=150, seed=5, q_rows=30, a_density=0.05, q_density=0.1)
+    K = 3000
+    s = oracle.solve(qp, tol=1e-30, max_iter=K, restart_every=1, trace_len=K)
+    R, rs = s.trace["R"], s.trace["restart"]
+    a1, a2 = 0.2, 0.8
+    a3 = 0.5
+    t = 0
+    R0 = Rprev = None
+    Rfirst = None
+    nrest = 0
+    for k in range(K - 1):
+        kd = k + 1
+        if t == 0:
+            expect = False
+            R0 = R[k]
+        else:
+            expect = (R[k] <= a1 * R0) or (R[k] <= a2 * R0 and R[k] > Rprev) or (t + 1 >= a3 * kd)
+        Rprev = R[k]
+        assert bool(rs[k]) == expect, k
+        if expect:
+            if Rfirst is None:
+                Rfirst = R[k]
+            if R[k] / Rfirst <= 0.1:
+                a3 = 0.2
+            t = 0
+            nrest += 1
+        else:
+            t += 1
+    assert nrest >= 5
+
+
+def test_restart_period_schedule():
+    # with restart tests every 10 iterations, restarts happen only at multiples of 10
+    qp = qpgen.plain_cqp(n=300, m=150, seed=6, q_rows=30, a_density=0.05, q_density=0.1)
+    s = oracle.solve(qp, tol=1e-30, max_iter=2000, restart_every=10, trace_len=2000)
+    idx = np.nonzero(s.trace["restart"])[0] + 1
+    assert idx.size > 3 and np.all(idx % 10 == 0)
+    # R~ is evaluated at multiples of 10 and at the first step of every outer loop
+    Rk = np.nonzero(np.isfinite(s.trace["R"]))[0] + 1
+    starts = set([1] + list(idx + 1))
+    assert set(Rk.tolist()) == set(k for k in range(1, 2001) if k % 10 == 0 or k in starts)
+
+
+# ------------------------------------------------------------------ printed parameters (Sec. 4.1)
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
+def test_defaults_match_paper():
+    g = _golden("paper_parameters.txt")
+    p = oracle.default_params()
+    for k in ("alpha1", "alpha2", "alpha3", "alpha3_tight", "ratio_tight", "tol"):
+        assert p[k] == g[k], k
+    assert p["check_every"] == g["check_every"]
+
+
+def test_sigma0_rule():
+    # sigma0 = ||b|| / ||c||, b = max(|l|, |u|) with infinite entries as 0 (Sec. 4.1)
+    qp = qpgen.plain_cqp(n=100, m=40, seed=9, q_rows=10, a_density=0.1, q_density=0.1)
+    s = oracle.solve(qp, max_iter=1, sigma_fixed=1)
+    b = np.maximum(np.where(np.isfinite(qp.l), np.abs(qp.l), 0), np.where(np.isfinite(qp.u), np.abs(qp.u), 0))
+    assert s.sigma == pytest.approx(np.linalg.norm(b) / np.linalg.norm(qp.c), rel=1e-14)
+    # no rows (b empty, ||b|| = 0 < 1e-16): sigma0 = 1
+    las = qpgen.lasso(p=50, q=200, density=0.05)
+    assert oracle.solve(las, max_iter=1, sigma_fixed=1).sigma == 1.0
+
+
+def test_hand_computed_iterates():
+    """Three iterations of Algorithm 4 on a 1-D problem computed by hand (golden file)."""
+    g = _golden("hand_1d_iterates.txt")
+    qp = qpgen.from_dense(np.array([[g["q"]]]), np.array([g["c"]]), L=np.array([g["L"]]), U=np.array([g["U"]]),
+                          q_kind="diag")
+    for k in range(3):
+        s = oracle.solve(qp, tol=1e-30, max_iter=k + 1, lambda_Q=g["lambda_Q"], sigma0=g["sigma"],
+                         restart_off=1, sigma_fixed=1)
+        assert s.x[0] == pytest.approx(g[f"xbar{k}"], abs=1e-15)
+        assert s.z[0] == pytest.approx(g[f"zbar{k}"], abs=1e-15)
+        assert s.w[0] == pytest.approx(g[f"wbar{k}"], abs=1e-15)
+
+
+# ------------------------------------------------------------------ invalid inputs
+def test_invalid_inputs_rejected():
+    qp = qpgen.random_small(n=4, m=2, seed=1)
+    bad = qpgen.QP(**{**qp.__dict__, "l": qp.u + 1.0})
+    assert oracle.solve(bad).status == "invalid_arg"
+    bad = qpgen.QP(**{**qp.__dict__, "L": qp.U + 1.0})
+    assert oracle.solve(bad).status == "invalid_arg"
+    c = qp.c.copy(); c[0] = np.nan
+    assert oracle.solve(qpgen.QP(**{**qp.__dict__, "c": c})).status == "invalid_arg"
+    ci = qp.A_colidx.copy(); ci[0] = qp.n
+    assert oracle.solve(qpgen.QP(**{**qp.__dict__, "A_colidx": ci})).status == "invalid_arg"
+    assert oracle.solve(qp, max_iter=0).status == "invalid_arg"
