@@ -1,0 +1,197 @@
+/* hprqp.h — C ABI of the GB300 (sm_103a) HPR-QP library.
+ *
+ * HPR-QP (arXiv 2507.02470) solves the convex composite quadratic program of Sec. 1,
+ * eq. (1.1):
+ *
+ *     min_x  1/2 <x, Q x> + <c, x> + phi(x)      s.t.   l <= A x <= u,
+ *
+ * where Q is symmetric positive semidefinite and may be given only as an operator, A is a
+ * sparse m x n matrix, and phi is the indicator of the box C = [L, U] (the CQP of eq. (1.2)),
+ * lambda * ||x||_1, or both.  The method is the dual Halpern Peaceman–Rachford iteration of
+ * Algorithm 4 with the restart rules (3.6)–(3.8) and the sigma update of Algorithm 5, run
+ * entirely in FP64 on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Pointers to problem data may point to host memory or to device memory of the current
+ *     CUDA device; the library detects which (cudaPointerGetAttributes) and copies.
+ *   - Infinite bounds are IEEE +-INFINITY.  NaN anywhere in the data is an error.
+ *   - Index arrays are int32, CSR row pointers start at 0 and are non-decreasing, column
+ *     indices lie in [0, ncols).  Row entries need not be sorted.
+ *   - Functions never abort or exit; they return a status and, on failure, record a message
+ *     readable with hprqp_last_error().  A failed call leaves the handle usable.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by the caller.
+ */
+#ifndef HPRQP_H
+#define HPRQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hprqp_status {
+  HPRQP_OK = 0,              /* converged: max(eta_p, eta_d, eta_gap) <= tol (Sec. 4.1) */
+  HPRQP_MAX_ITER = 1,        /* iteration limit reached; the last bar iterate is kept */
+  HPRQP_TIME_LIMIT = 2,      /* wall-clock limit reached */
+  HPRQP_NUMERICAL_ERROR = 3, /* NaN/Inf appeared in the iteration or its residuals */
+  HPRQP_INVALID_ARG = 4,     /* bad sizes, bounds with l > u or L > U, NaN, bad CSR */
+  HPRQP_CUDA_ERROR = 5,      /* a CUDA runtime call failed (message in last_error) */
+  HPRQP_TIMEOUT = 6,         /* a bounded device wait gave up (batched queue) */
+  HPRQP_OOM = 7              /* device allocation failed */
+} hprqp_status;
+
+/* Kinds of additive Q terms (Sec. 1: Q need not be an explicit matrix). */
+typedef enum hprqp_qkind {
+  HPRQP_Q_DIAG = 1,          /* Q += diag(dense[0..n))                                   */
+  HPRQP_Q_CSR = 2,           /* Q += n x n CSR matrix (rowptr, colidx, vals), symmetric   */
+  HPRQP_Q_DIA = 3,           /* Q += symmetric band: offsets[k] >= 0, diags is ndiag x n,
+                                diags[k*n + i] = Q[i][i + offsets[k]] (entries with
+                                i + offsets[k] >= n are ignored)                          */
+  HPRQP_Q_FACTOR = 4,        /* Q += B^T B, B a p x n CSR matrix (matrix-free)            */
+  HPRQP_Q_DENSE_FACTOR = 5   /* Q += F^T F, F a dense row-major p x n matrix              */
+} hprqp_qkind;
+
+typedef enum hprqp_phi {
+  HPRQP_PHI_BOX = 0,         /* phi = indicator of C = [L, U] (eq. (1.2))                */
+  HPRQP_PHI_L1 = 1,          /* phi = lambda ||x||_1 (Lasso, Sec. 4.4); L, U ignored     */
+  HPRQP_PHI_L1_BOX = 2       /* phi = lambda ||x||_1 + indicator of [L, U]               */
+} hprqp_phi;
+
+typedef struct hprqp_qterm {
+  int32_t kind;              /* hprqp_qkind */
+  int64_t p;                 /* FACTOR / DENSE_FACTOR: number of rows of B or F */
+  int64_t nnz;               /* CSR / FACTOR: number of stored entries */
+  const int32_t* rowptr;     /* CSR: n+1; FACTOR: p+1 */
+  const int32_t* colidx;     /* CSR / FACTOR: nnz */
+  const double* vals;        /* CSR / FACTOR: nnz */
+  int32_t ndiag;             /* DIA: number of stored diagonals (<= 8) */
+  const int32_t* offsets;    /* DIA: ndiag offsets, distinct, >= 0 */
+  const double* diags;       /* DIA: ndiag x n */
+  const double* dense;       /* DIAG: n values; DENSE_FACTOR: p x n row-major */
+} hprqp_qterm;
+
+/* Q as a sum of terms; nterms == 0 means Q = 0 (the LP case of the Sec. 2.2 remark). */
+typedef struct hprqp_qop {
+  int32_t nterms;
+  const hprqp_qterm* terms;
+} hprqp_qop;
+
+/* Allocator hooks (optional): if alloc is non-NULL all device memory of the handle is
+ * obtained from alloc(bytes, ctx, stream) and returned with free(ptr, bytes, ctx, stream). */
+typedef void* (*hprqp_alloc_fn)(size_t bytes, void* ctx, void* stream);
+typedef void (*hprqp_free_fn)(void* ptr, size_t bytes, void* ctx, void* stream);
+
+typedef struct hprqp_params {
+  void* stream;              /* cudaStream_t for all work; NULL: the handle creates one */
+  int64_t check_every;       /* termination test period, default 100 (Table 1 counts) */
+  int64_t restart_every;     /* restart test period (R~ evaluation), default 10 */
+  double alpha1, alpha2, alpha3;   /* restart parameters, defaults 0.2, 0.8, 0.5 (Sec. 4.1) */
+  double alpha3_tight;       /* alpha3 after the residual ratio drops to ratio_tight: 0.2 */
+  double ratio_tight;        /* 0.1 (Sec. 4.1) */
+  double lambda_A;           /* > 0: use as lambda_A >= lambda_1(AA^*); else power method */
+  double lambda_Q;           /* > 0: use as lambda_Q >= lambda_1(Q);    else power method */
+  double sigma0;             /* > 0: initial sigma; else ||b||/||c|| rule of Sec. 4.1 */
+  int64_t power_max_iter;    /* power method cap, default 5000 */
+  double power_tol;          /* relative change of the Rayleigh quotient, default 1e-6 */
+  double power_safety;       /* lambda = safety * estimate, default 1.01 */
+  int32_t halpern_total;     /* 1: Halpern weight 1/(k+2) from the total counter (Alg. 4
+                                as printed); 0 (default): inner counter t */
+  int32_t sigma_golden;      /* 1: golden-section search for eq. (3.12); 0: exact argmin */
+  int32_t restart_off;       /* 1: no restarts (Algorithm 3 with fixed sigma) */
+  int32_t sigma_fixed;       /* 1: keep sigma0 at restarts */
+  double time_limit;         /* seconds, <= 0: none (Sec. 4.1 uses 3600) */
+  int32_t iters_per_launch;  /* iterations captured per CUDA-graph launch, default 64 */
+  int32_t autotune;          /* 1 (default): time SpMV schedules at create and pick the best */
+  int32_t verbose;           /* 0: silent */
+  hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
+  hprqp_free_fn free;
+  void* alloc_ctx;
+} hprqp_params;
+
+/* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
+typedef struct hprqp_kkt {
+  double eta_p, eta_d, eta_gap, rel_kkt; /* rel_kkt = max of the three */
+  double pobj, dobj;         /* 1/2<x,Qx> + <c,x> + phi(x) and its dual counterpart */
+  int64_t iters, restarts;
+  double sigma, lambda_A, lambda_Q;
+  double solve_seconds;      /* wall time of the last hprqp_solve (power method included) */
+  double power_seconds;      /* part of it spent in the power method */
+  int64_t kernel_launches;   /* kernels of this library launched by the last solve */
+  int32_t status;
+} hprqp_kkt;
+
+/* Kernel kinds reported by hprqp_profile. */
+enum {
+  HPRQP_PROF_ZX = 0,         /* pending Halpern/restart update + eqs. (3.1)-(3.3), elementwise */
+  HPRQP_PROF_PRE1 = 1,       /* B_f wbar_{1/2}, F_g wbar_{1/2} (factor terms of Q) */
+  HPRQP_PROF_Q1 = 2,         /* Q wbar_{1/2} and v = what + sigma (Q w - Q wbar_{1/2}) */
+  HPRQP_PROF_A1 = 3,         /* A v, Halpern on y, eq. (3.5) */
+  HPRQP_PROF_AT = 4,         /* A^T ybar and wbar of eq. (3.3) */
+  HPRQP_PROF_PRE2 = 5,       /* B_f wbar, F_g wbar */
+  HPRQP_PROF_Q2 = 6,         /* Q wbar, R~ / stopping sums, controller */
+  HPRQP_PROF_RPRE = 7,       /* restart: B_f d, F_g d */
+  HPRQP_PROF_RESTART = 8,    /* restart: theta~ of eq. (3.11), Algorithm 5 */
+  HPRQP_PROF_KINDS = 9
+};
+
+typedef struct hprqp_handle hprqp_handle;
+
+/* Fills p with the defaults of Sec. 4.1 (alphas, tolerances) and the library defaults. */
+void hprqp_default_params(hprqp_params* p);
+
+/* Creates a solver for eq. (1.1).  n > 0 variables, m >= 0 rows.  A is CSR (m+1 row
+ * pointers; may all be NULL when m == 0).  c, L, U have n entries; l, u have m.  L, U may
+ * be NULL for phi = HPRQP_PHI_L1 (treated as -inf/+inf).  lambda >= 0 is the l1 weight.
+ * All inputs are copied (host or device, detected per pointer); the caller keeps ownership
+ * of its buffers and may free them after the call.  params may be NULL (defaults).
+ * Builds A^T (and B^T for every FACTOR term) on the device.
+ * Returns HPRQP_INVALID_ARG for inconsistent sizes, NaN, l > u, L > U, non-monotone row
+ * pointers or out-of-range column indices; HPRQP_OOM / HPRQP_CUDA_ERROR on device failure.
+ * On failure *h is set to NULL and nothing is leaked. */
+hprqp_status hprqp_create(hprqp_handle** h, int64_t n, int64_t m, const hprqp_qop* Q,
+                          const int32_t* A_rowptr, const int32_t* A_colidx, const double* A_vals,
+                          const double* c, const double* l, const double* u, const double* L,
+                          const double* U, int32_t phi, double lambda, const hprqp_params* params);
+
+/* Sets the starting point u^{0,0} of Algorithm 4: x^0 = x0 (n), y^0 = y0 (m), w^0 = x0
+ * (Q w* = Q x* at a solution, eq. (2.1)), z^0 = 0.  Either pointer may be NULL (zeros).
+ * sigma0 > 0 replaces the initial penalty parameter; <= 0 keeps the Sec. 4.1 rule.
+ * The warm start stays in effect for later solves until called again with NULLs. */
+hprqp_status hprqp_set_warm_start(hprqp_handle* h, const double* x0, const double* y0, double sigma0);
+
+/* Runs Algorithm 4 from the starting point until max(eta_p, eta_d, eta_gap) <= tol (tested
+ * every check_every iterations), max_iter iterations (>= 1), or the time limit.  Includes
+ * the power method for lambda_A, lambda_Q unless fixed in params.  Returns HPRQP_OK,
+ * HPRQP_MAX_ITER, HPRQP_TIME_LIMIT or HPRQP_NUMERICAL_ERROR (or an error status). */
+hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_iter);
+
+/* Copies the output bar iterate of Algorithm 4 (xbar: n, ybar: m, zbar: n, wbar_Q: n) into
+ * caller buffers (host or device; any may be NULL) and fills kkt (may be NULL). */
+hprqp_status hprqp_get(hprqp_handle* h, double* x, double* y, double* z, double* w, hprqp_kkt* kkt);
+
+/* Applies one linear operator of the problem to a vector (for tests and benchmarks):
+ * op 0: out = A in (in: n, out: m); 1: out = A^T in (in: m, out: n); 2: out = Q in (n -> n).
+ * in/out may be host or device pointers. */
+hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* in, double* out);
+
+/* Runs `iters` (>= 1) inner steps of Algorithm 4 from the starting point, with lambda_A,
+ * lambda_Q and sigma0 of the last hprqp_solve, as individual launches on the handle's stream
+ * bracketed by CUDA events, and writes the mean duration (milliseconds) of each kernel kind
+ * into ms[HPRQP_PROF_KINDS] (0 for kinds the problem does not use; the restart kinds are
+ * averaged over the steps that restarted).  The iterate is left in an unspecified state:
+ * call hprqp_solve again before hprqp_get.  Requires a previous hprqp_solve. */
+hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms);
+
+/* Releases all device memory of the handle.  NULL is ignored. */
+void hprqp_destroy(hprqp_handle* h);
+
+/* Message of the last failure on this handle ("" if none); h may be NULL for the last
+ * failure of hprqp_create in this thread. */
+const char* hprqp_last_error(const hprqp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPRQP_H */

@@ -361,7 +361,7 @@ void orc_default_params(orc_params* p) {
   p->tol = 1e-8;
   p->max_iter = 1000000;
   p->check_every = 100;
-  p->restart_every = 1;
+  p->restart_every = 10;
   p->alpha1 = 0.2;
   p->alpha2 = 0.8;
   p->alpha3 = 0.5;

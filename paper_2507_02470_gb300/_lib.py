@@ -1,0 +1,273 @@
+"""ctypes binding of the C ABI in include/hprqp.h (argument marshalling only).
+
+Every computation runs inside libhprqp.so on the GPU.  The library must be built first
+(``paper_2507_02470_gb300.build.build()``); loading raises if it is missing.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+_lock = threading.Lock()
+_lib = None
+
+HPRQP_OK, HPRQP_MAX_ITER, HPRQP_TIME_LIMIT, HPRQP_NUMERICAL_ERROR = 0, 1, 2, 3
+HPRQP_INVALID_ARG, HPRQP_CUDA_ERROR, HPRQP_TIMEOUT, HPRQP_OOM = 4, 5, 6, 7
+STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "time_limit", 3: "numerical_error", 4: "invalid_arg",
+                5: "cuda_error", 6: "timeout", 7: "oom"}
+QKIND = {"diag": 1, "csr": 2, "dia": 3, "factor": 4, "dense_factor": 5}
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class hprqp_qterm(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colidx", C.c_void_p), ("vals", C.c_void_p), ("ndiag", C.c_int32), ("offsets", C.c_void_p),
+                ("diags", C.c_void_p), ("dense", C.c_void_p)]
+
+
+class hprqp_qop(C.Structure):
+    _fields_ = [("nterms", C.c_int32), ("terms", C.POINTER(hprqp_qterm))]
+
+
+class hprqp_params(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("check_every", C.c_int64), ("restart_every", C.c_int64),
+                ("alpha1", C.c_double), ("alpha2", C.c_double), ("alpha3", C.c_double),
+                ("alpha3_tight", C.c_double), ("ratio_tight", C.c_double), ("lambda_A", C.c_double),
+                ("lambda_Q", C.c_double), ("sigma0", C.c_double), ("power_max_iter", C.c_int64),
+                ("power_tol", C.c_double), ("power_safety", C.c_double), ("halpern_total", C.c_int32),
+                ("sigma_golden", C.c_int32), ("restart_off", C.c_int32), ("sigma_fixed", C.c_int32),
+                ("time_limit", C.c_double), ("iters_per_launch", C.c_int32), ("autotune", C.c_int32),
+                ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class hprqp_kkt(C.Structure):
+    _fields_ = [("eta_p", C.c_double), ("eta_d", C.c_double), ("eta_gap", C.c_double), ("rel_kkt", C.c_double),
+                ("pobj", C.c_double), ("dobj", C.c_double), ("iters", C.c_int64), ("restarts", C.c_int64),
+                ("sigma", C.c_double), ("lambda_A", C.c_double), ("lambda_Q", C.c_double),
+                ("solve_seconds", C.c_double), ("power_seconds", C.c_double), ("kernel_launches", C.c_int64),
+                ("status", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status"] = STATUS_NAMES.get(d["status"], str(d["status"]))
+        return d
+
+
+# (name, restype, argtypes) of every exported symbol declared in include/hprqp.h
+_vp, _i32, _i64, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+SIGNATURES = [
+    ("hprqp_default_params", None, [C.POINTER(hprqp_params)]),
+    ("hprqp_create", C.c_int, [C.POINTER(_vp), _i64, _i64, C.POINTER(hprqp_qop), _vp, _vp, _vp, _vp, _vp, _vp,
+                               _vp, _vp, _i32, _dbl, C.POINTER(hprqp_params)]),
+    ("hprqp_set_warm_start", C.c_int, [_vp, _vp, _vp, _dbl]),
+    ("hprqp_solve", C.c_int, [_vp, _dbl, _i64]),
+    ("hprqp_get", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(hprqp_kkt)]),
+    ("hprqp_apply", C.c_int, [_vp, _i32, _vp, _vp]),
+    ("hprqp_profile", C.c_int, [_vp, _i32, _vp]),
+    ("hprqp_destroy", None, [_vp]),
+    ("hprqp_last_error", C.c_char_p, [_vp]),
+]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libhprqp.so (raises OSError/RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} (run paper_2507_02470_gb300.build.build())")
+            L = C.CDLL(path)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class HPRQPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (host or CUDA), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def default_params() -> hprqp_params:
+    p = hprqp_params()
+    lib().hprqp_default_params(C.byref(p))
+    return p
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self):
+        import torch
+
+        self.torch = torch
+
+        def _alloc(nbytes, ctx, stream):
+            try:
+                return self.torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, ctx, stream):
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _ALLOC_FN(_alloc)
+        self.free = _FREE_FN(_free)
+
+
+class Solver:
+    """One HPR-QP instance on the GPU (a handle of the C ABI).
+
+    ``qp`` is any object with the fields n, m, A_rowptr, A_colidx, A_vals, c, l, u, L, U,
+    phi, lam and qterms (a list of terms with kind, p, rowptr, colidx, vals, offsets, diags,
+    dense); arrays may be numpy (host) or torch CUDA tensors (device).
+    """
+
+    def __init__(self, qp, stream=None, torch_alloc=False, **params):
+        L = lib()
+        self._keep = []
+        p = default_params()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        if stream is not None:
+            p.stream = int(stream)
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = _TorchAllocator()
+            p.alloc = self._alloc.alloc
+            p.free = self._alloc.free
+        self.params = p
+        terms = (hprqp_qterm * max(1, len(qp.qterms)))()
+        for k, t in enumerate(qp.qterms):
+            tt = terms[k]
+            tt.kind = QKIND[t.kind]
+            tt.p = int(getattr(t, "p", 0) or 0)
+            if t.rowptr is not None:
+                rp, ci, va = self._hold(t.rowptr, np.int32), self._hold(t.colidx, np.int32), self._hold(t.vals, np.float64)
+                tt.rowptr, tt.colidx, tt.vals = _ptr(rp), _ptr(ci), _ptr(va)
+                tt.nnz = int(ci.shape[0])
+            if t.offsets is not None:
+                tt.ndiag = len(t.offsets)
+                tt.offsets = _ptr(self._hold(t.offsets, np.int32))
+                tt.diags = _ptr(self._hold(t.diags, np.float64))
+            if t.dense is not None:
+                tt.dense = _ptr(self._hold(t.dense, np.float64))
+        qop = hprqp_qop(len(qp.qterms), C.cast(terms, C.POINTER(hprqp_qterm)))
+        self.n, self.m = int(qp.n), int(qp.m)
+        h = C.c_void_p()
+        st = L.hprqp_create(C.byref(h), self.n, self.m, C.byref(qop),
+                            _ptr(self._hold(qp.A_rowptr, np.int32)) if self.m else None,
+                            _ptr(self._hold(qp.A_colidx, np.int32)) if self.m else None,
+                            _ptr(self._hold(qp.A_vals, np.float64)) if self.m else None,
+                            _ptr(self._hold(qp.c, np.float64)),
+                            _ptr(self._hold(qp.l, np.float64)) if self.m else None,
+                            _ptr(self._hold(qp.u, np.float64)) if self.m else None,
+                            _ptr(self._hold(qp.L, np.float64)) if qp.L is not None else None,
+                            _ptr(self._hold(qp.U, np.float64)) if qp.U is not None else None,
+                            int(qp.phi), float(qp.lam), C.byref(p))
+        self._keep = []  # inputs are copied by hprqp_create
+        if st != HPRQP_OK:
+            raise HPRQPError(st, L.hprqp_last_error(None).decode())
+        self.h = h
+
+    def _hold(self, a, dtype):
+        if hasattr(a, "data_ptr"):
+            import torch
+            tdt = {np.int32: torch.int32, np.float64: torch.float64}[dtype]
+            a = a.to(tdt).contiguous()
+        else:
+            a = np.ascontiguousarray(a, dtype=dtype)
+        self._keep.append(a)
+        return a
+
+    def _check(self, st, ok=(HPRQP_OK,)):
+        if st not in ok:
+            raise HPRQPError(st, lib().hprqp_last_error(self.h).decode())
+        return st
+
+    def set_warm_start(self, x0=None, y0=None, sigma0=0.0):
+        keep = [None if x0 is None else self._hold(x0, np.float64),
+                None if y0 is None else self._hold(y0, np.float64)]
+        self._check(lib().hprqp_set_warm_start(self.h, _ptr(keep[0]), _ptr(keep[1]), float(sigma0)))
+        self._keep = []
+
+    def solve(self, tol=1e-8, max_iter=1_000_000):
+        st = lib().hprqp_solve(self.h, float(tol), int(max_iter))
+        self._check(st, ok=(HPRQP_OK, HPRQP_MAX_ITER, HPRQP_TIME_LIMIT, HPRQP_NUMERICAL_ERROR))
+        return STATUS_NAMES[st]
+
+    def get(self, x=None, y=None, z=None, w=None):
+        """Copies the bar iterate into the given buffers (numpy or torch; None = allocate
+        numpy arrays) and returns (x, y, z, w, kkt dict)."""
+        x = np.empty(self.n) if x is None else x
+        y = np.empty(self.m) if y is None else y
+        z = np.empty(self.n) if z is None else z
+        w = np.empty(self.n) if w is None else w
+        k = hprqp_kkt()
+        self._check(lib().hprqp_get(self.h, _ptr(x), _ptr(y) if self.m else None, _ptr(z), _ptr(w), C.byref(k)))
+        return x, y, z, w, k.as_dict()
+
+    def kkt(self):
+        k = hprqp_kkt()
+        self._check(lib().hprqp_get(self.h, None, None, None, None, C.byref(k)))
+        return k.as_dict()
+
+    def apply(self, op, v):
+        """op 'A' (n -> m), 'AT' (m -> n) or 'Q' (n -> n) applied on the GPU."""
+        code = {"A": 0, "AT": 1, "Q": 2}[op]
+        v = np.ascontiguousarray(v, np.float64)
+        out = np.empty(self.m if code == 0 else self.n)
+        self._check(lib().hprqp_apply(self.h, code, _ptr(v), _ptr(out)))
+        return out
+
+    PROFILE_KINDS = ["zx", "pre1", "q1", "a1", "at", "pre2", "q2", "restart_pre", "restart"]
+
+    def profile(self, iters=20):
+        """Mean per-kernel durations (ms) of `iters` inner steps, timed with CUDA events."""
+        ms = np.zeros(len(self.PROFILE_KINDS))
+        self._check(lib().hprqp_profile(self.h, int(iters), _ptr(ms)))
+        return dict(zip(self.PROFILE_KINDS, ms.tolist()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hprqp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,978 @@
+// C ABI of the single-instance HPR-QP solver (include/hprqp.h).
+//
+// Host responsibilities: validate and copy the problem (host or device inputs), build the
+// stored transposes A^T and B_f^T (counting sort by column, so the row order inside each
+// transposed row is fixed), pick the SpMV schedule, run the power method of Sec. 4.1, and
+// drive Algorithm 4 as a CUDA graph of `iters_per_launch` inner steps whose kernels stop
+// themselves once the device-side controller has set the done flag.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hprqp.h"
+#include "solver.cuh"
+
+using namespace hprqp;
+
+struct hprqp_handle {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  hprqp_params prm;
+  int64_t n = 0, m = 0;
+  int phi = 0;
+  double lambda = 0.0;
+  std::vector<std::pair<void*, size_t>> allocs;
+  Args args;
+  Plan plan;
+  Ctrl* dctrl = nullptr;
+  Ctrl* hctrl = nullptr;      // pinned mirror
+  int* hflags = nullptr;      // pinned done flags
+  double nb2 = 0, nc2 = 0, b_inf = 0, c_inf = 0;
+  std::vector<double> ws_x, ws_y;
+  double ws_sigma = 0.0;
+  cudaGraphExec_t g_iter = nullptr;
+  cudaGraphExec_t g_pw[2] = {nullptr, nullptr};
+  int pw_chunk = 16;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::string err;
+  hprqp_kkt kkt;
+  int last_status = -1;
+  bool solved = false;
+  int64_t launches = 0;
+  double last_lamA = 0, last_lamQ = 0, last_sigma0 = 1;
+};
+
+static thread_local std::string g_create_err;
+
+// ------------------------------------------------------------------------------------ helpers
+static hprqp_status fail(hprqp_handle* h, hprqp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_err = buf;
+  return st;
+}
+
+#define CU(h, call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      cudaGetLastError();                                                                    \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? HPRQP_OOM : HPRQP_CUDA_ERROR, "%s: %s (%s:%d)", #call, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+    }                                                                                        \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+static hprqp_status fetch(hprqp_handle* h, std::vector<T>& out, const T* p, size_t count) {
+  out.resize(count);
+  if (count == 0) return HPRQP_OK;
+  if (!p) return fail(h, HPRQP_INVALID_ARG, "null input pointer for %zu elements", count);
+  if (is_device_ptr(p)) {
+    CU(h, cudaMemcpy(out.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(out.data(), p, count * sizeof(T));
+  }
+  return HPRQP_OK;
+}
+
+static hprqp_status dalloc(hprqp_handle* h, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  bytes = (bytes + 255) / 256 * 256;
+  if (h->prm.alloc) {
+    *p = h->prm.alloc(bytes, h->prm.alloc_ctx, h->stream);
+    if (!*p) return fail(h, HPRQP_OOM, "allocator hook returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, HPRQP_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  h->allocs.push_back({*p, bytes});
+  return HPRQP_OK;
+}
+
+template <class T>
+static hprqp_status upload(hprqp_handle* h, T** dst, const std::vector<T>& src, size_t min_count = 1) {
+  void* p = nullptr;
+  size_t cnt = std::max(src.size(), min_count);
+  hprqp_status st = dalloc(h, &p, cnt * sizeof(T));
+  if (st) return st;
+  if (!src.empty()) CU(h, cudaMemcpyAsync(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  if (cnt > src.size()) CU(h, cudaMemsetAsync((T*)p + src.size(), 0, (cnt - src.size()) * sizeof(T), h->stream));
+  *dst = (T*)p;
+  return HPRQP_OK;
+}
+
+static hprqp_status zeros(hprqp_handle* h, double** dst, size_t count) {
+  void* p = nullptr;
+  hprqp_status st = dalloc(h, &p, std::max<size_t>(count, 1) * sizeof(double));
+  if (st) return st;
+  CU(h, cudaMemsetAsync(p, 0, std::max<size_t>(count, 1) * sizeof(double), h->stream));
+  *dst = (double*)p;
+  return HPRQP_OK;
+}
+
+struct HostCsr {
+  int64_t rows = 0, cols = 0;
+  std::vector<int> rp, ci;
+  std::vector<double> v;
+};
+
+static hprqp_status check_csr(hprqp_handle* h, const HostCsr& M, const char* name) {
+  if ((int64_t)M.rp.size() != M.rows + 1) return fail(h, HPRQP_INVALID_ARG, "%s: row pointer size", name);
+  if (M.rp[0] != 0) return fail(h, HPRQP_INVALID_ARG, "%s: row pointers must start at 0", name);
+  for (int64_t i = 0; i < M.rows; i++)
+    if (M.rp[i + 1] < M.rp[i]) return fail(h, HPRQP_INVALID_ARG, "%s: row pointers decrease at row %lld", name, (long long)i);
+  const int64_t nnz = M.rp[M.rows];
+  if ((int64_t)M.ci.size() != nnz || (int64_t)M.v.size() != nnz) return fail(h, HPRQP_INVALID_ARG, "%s: nnz mismatch", name);
+  for (int64_t k = 0; k < nnz; k++) {
+    if (M.ci[k] < 0 || M.ci[k] >= M.cols)
+      return fail(h, HPRQP_INVALID_ARG, "%s: column index %d out of range at entry %lld", name, M.ci[k], (long long)k);
+    if (!std::isfinite(M.v[k])) return fail(h, HPRQP_INVALID_ARG, "%s: non-finite value at entry %lld", name, (long long)k);
+  }
+  return HPRQP_OK;
+}
+
+// deterministic transpose: entries of each transposed row in increasing original-row order
+static HostCsr transpose(const HostCsr& M) {
+  HostCsr T;
+  T.rows = M.cols;
+  T.cols = M.rows;
+  const int64_t nnz = M.rp[M.rows];
+  T.rp.assign(T.rows + 1, 0);
+  for (int64_t k = 0; k < nnz; k++) T.rp[M.ci[k] + 1]++;
+  for (int64_t i = 0; i < T.rows; i++) T.rp[i + 1] += T.rp[i];
+  std::vector<int> pos(T.rp.begin(), T.rp.end() - 1);
+  T.ci.resize(nnz);
+  T.v.resize(nnz);
+  for (int64_t r = 0; r < M.rows; r++)
+    for (int k = M.rp[r]; k < M.rp[r + 1]; k++) {
+      int c = M.ci[k];
+      T.ci[pos[c]] = (int)r;
+      T.v[pos[c]] = M.v[k];
+      pos[c]++;
+    }
+  return T;
+}
+
+static hprqp_status upload_csr(hprqp_handle* h, Csr& d, const HostCsr& M) {
+  d.rows = M.rows;
+  d.cols = M.cols;
+  d.nnz = M.rp.empty() ? 0 : M.rp[M.rows];
+  int *rp, *ci;
+  double* v;
+  hprqp_status st;
+  if ((st = upload(h, &rp, M.rp))) return st;
+  if ((st = upload(h, &ci, M.ci))) return st;
+  if ((st = upload(h, &v, M.v))) return st;
+  d.rp = rp;
+  d.ci = ci;
+  d.v = v;
+  return HPRQP_OK;
+}
+
+// ------------------------------------------------------------------------------------ defaults
+extern "C" void hprqp_default_params(hprqp_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->stream = nullptr;
+  p->check_every = 100;
+  p->restart_every = 10;
+  p->alpha1 = 0.2;
+  p->alpha2 = 0.8;
+  p->alpha3 = 0.5;
+  p->alpha3_tight = 0.2;
+  p->ratio_tight = 0.1;
+  p->lambda_A = 0.0;
+  p->lambda_Q = 0.0;
+  p->sigma0 = 0.0;
+  p->power_max_iter = 5000;
+  p->power_tol = 1e-6;
+  p->power_safety = 1.01;
+  p->time_limit = 0.0;
+  p->iters_per_launch = 64;
+  p->autotune = 1;
+}
+
+extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+static void release(hprqp_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->g_iter) cudaGraphExecDestroy(h->g_iter);
+  for (auto& g : h->g_pw)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& a : h->allocs) {
+    if (h->prm.free) h->prm.free(a.first, a.second, h->prm.alloc_ctx, h->stream);
+    else cudaFree(a.first);
+  }
+  if (h->hctrl) cudaFreeHost(h->hctrl);
+  if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  cudaGetLastError();
+  delete h;
+}
+
+extern "C" void hprqp_destroy(hprqp_handle* h) { release(h); }
+
+// ------------------------------------------------------------------------------------ autotune
+static int tune_G(hprqp_handle* h, const Csr& M, int grid, double* x, double* y, int fallback) {
+  if (M.rows == 0 || M.nnz == 0) return fallback;
+  if (!h->prm.autotune) {
+    double avg = (double)M.nnz / (double)M.rows;
+    return avg < 6 ? 1 : avg < 12 ? 2 : avg < 24 ? 4 : avg < 64 ? 8 : 32;
+  }
+  const int cand[6] = {1, 2, 4, 8, 16, 32};
+  float best = 1e30f;
+  int bestG = fallback;
+  for (int G : cand) {
+    launch_spmv_probe(M, G, grid, x, y, h->stream);
+    float tot = 0;
+    for (int r = 0; r < 3; r++) {
+      cudaEventRecord(h->ev[0], h->stream);
+      launch_spmv_probe(M, G, grid, x, y, h->stream);
+      cudaEventRecord(h->ev[1], h->stream);
+      cudaEventSynchronize(h->ev[1]);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+      tot += ms;
+    }
+    if (cudaGetLastError() != cudaSuccess) continue;
+    if (tot < best) {
+      best = tot;
+      bestG = G;
+    }
+  }
+  return bestG;
+}
+
+// ------------------------------------------------------------------------------------ create
+static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hprqp_qop* Q, const int32_t* A_rowptr,
+                                const int32_t* A_colidx, const double* A_vals, const double* c, const double* l,
+                                const double* u, const double* L, const double* U, int32_t phi, double lambda) {
+  hprqp_status st;
+  if (n <= 0 || m < 0) return fail(h, HPRQP_INVALID_ARG, "need n > 0 and m >= 0 (n=%lld, m=%lld)", (long long)n, (long long)m);
+  if (n >= (int64_t)1 << 31 || m >= (int64_t)1 << 31) return fail(h, HPRQP_INVALID_ARG, "n and m must be < 2^31");
+  if (phi < 0 || phi > 2) return fail(h, HPRQP_INVALID_ARG, "unknown phi kind %d", phi);
+  if (phi != PHI_BOX && !(lambda >= 0.0 && std::isfinite(lambda))) return fail(h, HPRQP_INVALID_ARG, "lambda must be finite and >= 0");
+  h->n = n;
+  h->m = m;
+  h->phi = phi;
+  h->lambda = phi == PHI_BOX ? 0.0 : lambda;
+
+  // ---- vectors
+  std::vector<double> hc, hl, hu, hL, hU;
+  if ((st = fetch(h, hc, c, n))) return st;
+  if ((st = fetch(h, hl, l, m))) return st;
+  if ((st = fetch(h, hu, u, m))) return st;
+  if (L) {
+    if ((st = fetch(h, hL, L, n))) return st;
+  } else {
+    if (phi != PHI_L1) return fail(h, HPRQP_INVALID_ARG, "L is required for box constraints");
+    hL.assign(n, -INFINITY);
+  }
+  if (U) {
+    if ((st = fetch(h, hU, U, n))) return st;
+  } else {
+    if (phi != PHI_L1) return fail(h, HPRQP_INVALID_ARG, "U is required for box constraints");
+    hU.assign(n, INFINITY);
+  }
+  if (phi == PHI_L1) {
+    hL.assign(n, -INFINITY);
+    hU.assign(n, INFINITY);
+  }
+  for (int64_t j = 0; j < n; j++) {
+    if (!std::isfinite(hc[j])) return fail(h, HPRQP_INVALID_ARG, "c[%lld] is not finite", (long long)j);
+    if (std::isnan(hL[j]) || std::isnan(hU[j]) || hL[j] > hU[j])
+      return fail(h, HPRQP_INVALID_ARG, "box bound %lld: need L <= U, no NaN", (long long)j);
+  }
+  double nb2 = 0, bi = 0;
+  for (int64_t i = 0; i < m; i++) {
+    if (std::isnan(hl[i]) || std::isnan(hu[i]) || hl[i] > hu[i])
+      return fail(h, HPRQP_INVALID_ARG, "row bound %lld: need l <= u, no NaN", (long long)i);
+    double bl = std::isfinite(hl[i]) ? std::fabs(hl[i]) : 0.0;
+    double bu = std::isfinite(hu[i]) ? std::fabs(hu[i]) : 0.0;
+    double b = std::max(bl, bu);
+    nb2 += b * b;
+    bi = std::max(bi, b);
+  }
+  double nc2 = 0, ci = 0;
+  for (int64_t j = 0; j < n; j++) {
+    nc2 += hc[j] * hc[j];
+    ci = std::max(ci, std::fabs(hc[j]));
+  }
+  h->nb2 = nb2;
+  h->nc2 = nc2;
+  h->b_inf = bi;
+  h->c_inf = ci;
+
+  // ---- A
+  HostCsr A;
+  A.rows = m;
+  A.cols = n;
+  if (m > 0) {
+    if ((st = fetch(h, A.rp, A_rowptr, m + 1))) return st;
+    if (A.rp[0] != 0 || A.rp[m] < 0) return fail(h, HPRQP_INVALID_ARG, "A: bad row pointers");
+    int64_t nnz = A.rp[m];
+    if ((st = fetch(h, A.ci, A_colidx, nnz))) return st;
+    if ((st = fetch(h, A.v, A_vals, nnz))) return st;
+    if ((st = check_csr(h, A, "A"))) return st;
+  }
+
+  // ---- Q terms
+  std::vector<double> qdiag;
+  HostCsr qcsr;
+  qcsr.rows = 0;
+  std::vector<int> dia_off;
+  std::vector<std::vector<double>> dia_vals;
+  std::vector<HostCsr> facs;
+  std::vector<std::pair<int64_t, std::vector<double>>> dens;
+  std::vector<HostCsr> csr_terms;
+  int nterms = Q ? Q->nterms : 0;
+  if (nterms < 0 || (nterms > 0 && !Q->terms)) return fail(h, HPRQP_INVALID_ARG, "bad Q operator");
+  for (int t = 0; t < nterms; t++) {
+    const hprqp_qterm& q = Q->terms[t];
+    if (q.kind == HPRQP_Q_DIAG) {
+      std::vector<double> d;
+      if ((st = fetch(h, d, q.dense, n))) return st;
+      for (double x : d)
+        if (!std::isfinite(x)) return fail(h, HPRQP_INVALID_ARG, "Q diag: non-finite value");
+      if (qdiag.empty()) qdiag.assign(n, 0.0);
+      for (int64_t j = 0; j < n; j++) qdiag[j] += d[j];
+    } else if (q.kind == HPRQP_Q_CSR) {
+      HostCsr M;
+      M.rows = n;
+      M.cols = n;
+      if ((st = fetch(h, M.rp, q.rowptr, n + 1))) return st;
+      if (M.rp[0] != 0 || M.rp[n] < 0) return fail(h, HPRQP_INVALID_ARG, "Q csr: bad row pointers");
+      if ((st = fetch(h, M.ci, q.colidx, M.rp[n]))) return st;
+      if ((st = fetch(h, M.v, q.vals, M.rp[n]))) return st;
+      if ((st = check_csr(h, M, "Q csr"))) return st;
+      csr_terms.push_back(std::move(M));
+    } else if (q.kind == HPRQP_Q_DIA) {
+      if (q.ndiag <= 0 || !q.offsets) return fail(h, HPRQP_INVALID_ARG, "Q dia: need ndiag > 0 and offsets");
+      std::vector<int> off;
+      std::vector<double> dv;
+      if ((st = fetch(h, off, q.offsets, q.ndiag))) return st;
+      if ((st = fetch(h, dv, q.diags, (size_t)q.ndiag * n))) return st;
+      for (int k = 0; k < q.ndiag; k++) {
+        if (off[k] < 0 || off[k] >= n) return fail(h, HPRQP_INVALID_ARG, "Q dia: offset %d out of range", off[k]);
+        auto it = std::find(dia_off.begin(), dia_off.end(), off[k]);
+        size_t slot;
+        if (it == dia_off.end()) {
+          if ((int)dia_off.size() >= kMaxDia) return fail(h, HPRQP_INVALID_ARG, "Q dia: at most %d distinct offsets", kMaxDia);
+          dia_off.push_back(off[k]);
+          dia_vals.emplace_back(n, 0.0);
+          slot = dia_off.size() - 1;
+        } else {
+          slot = it - dia_off.begin();
+        }
+        for (int64_t i = 0; i + off[k] < n; i++) {
+          double x = dv[(size_t)k * n + i];
+          if (!std::isfinite(x)) return fail(h, HPRQP_INVALID_ARG, "Q dia: non-finite value");
+          dia_vals[slot][i] += x;
+        }
+      }
+    } else if (q.kind == HPRQP_Q_FACTOR) {
+      if (q.p <= 0 || q.p >= ((int64_t)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "Q factor: bad p");
+      if ((int)facs.size() >= kMaxFac) return fail(h, HPRQP_INVALID_ARG, "at most %d factor terms", kMaxFac);
+      HostCsr B;
+      B.rows = q.p;
+      B.cols = n;
+      if ((st = fetch(h, B.rp, q.rowptr, q.p + 1))) return st;
+      if (B.rp[0] != 0 || B.rp[q.p] < 0) return fail(h, HPRQP_INVALID_ARG, "Q factor: bad row pointers");
+      if ((st = fetch(h, B.ci, q.colidx, B.rp[q.p]))) return st;
+      if ((st = fetch(h, B.v, q.vals, B.rp[q.p]))) return st;
+      if ((st = check_csr(h, B, "Q factor"))) return st;
+      facs.push_back(std::move(B));
+    } else if (q.kind == HPRQP_Q_DENSE_FACTOR) {
+      if (q.p <= 0) return fail(h, HPRQP_INVALID_ARG, "Q dense factor: bad p");
+      if ((int)dens.size() >= kMaxDense) return fail(h, HPRQP_INVALID_ARG, "at most %d dense factor terms", kMaxDense);
+      std::vector<double> F;
+      if ((st = fetch(h, F, q.dense, (size_t)q.p * n))) return st;
+      for (double x : F)
+        if (!std::isfinite(x)) return fail(h, HPRQP_INVALID_ARG, "Q dense factor: non-finite value");
+      dens.push_back({q.p, std::move(F)});
+    } else {
+      return fail(h, HPRQP_INVALID_ARG, "unknown Q term kind %d", q.kind);
+    }
+  }
+  // several explicit CSR terms: concatenate rows (duplicates are summed by the SpMV)
+  if (!csr_terms.empty()) {
+    qcsr.rows = n;
+    qcsr.cols = n;
+    qcsr.rp.assign(n + 1, 0);
+    for (int64_t i = 0; i < n; i++) {
+      int64_t cnt = 0;
+      for (auto& M : csr_terms) cnt += M.rp[i + 1] - M.rp[i];
+      qcsr.rp[i + 1] = (int)(qcsr.rp[i] + cnt);
+    }
+    qcsr.ci.reserve(qcsr.rp[n]);
+    qcsr.v.reserve(qcsr.rp[n]);
+    for (int64_t i = 0; i < n; i++)
+      for (auto& M : csr_terms)
+        for (int k = M.rp[i]; k < M.rp[i + 1]; k++) {
+          qcsr.ci.push_back(M.ci[k]);
+          qcsr.v.push_back(M.v[k]);
+        }
+  }
+
+  // ---- device problem
+  Args& a = h->args;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.m = m;
+  a.phi = phi;
+  Vec& V = a.V;
+  double *dc, *dL, *dU, *dl = nullptr, *du = nullptr;
+  if ((st = upload(h, &dc, hc))) return st;
+  if ((st = upload(h, &dL, hL))) return st;
+  if ((st = upload(h, &dU, hU))) return st;
+  if ((st = upload(h, &dl, hl))) return st;
+  if ((st = upload(h, &du, hu))) return st;
+  V.c = dc;
+  V.L = dL;
+  V.U = dU;
+  V.l = dl;
+  V.u = du;
+  if (m > 0) {
+    if ((st = upload_csr(h, a.A, A))) return st;
+    HostCsr AT = transpose(A);
+    if ((st = upload_csr(h, a.AT, AT))) return st;
+  } else {
+    a.A.cols = n;
+    a.AT.cols = 0;
+  }
+  QDev& QD = a.Q;
+  QD.n = n;
+  if (!qdiag.empty()) {
+    double* d;
+    if ((st = upload(h, &d, qdiag))) return st;
+    QD.diag = d;
+  }
+  if (qcsr.rows) {
+    if ((st = upload_csr(h, QD.csr, qcsr))) return st;
+  }
+  if (!dia_off.empty()) {
+    QD.ndia = (int)dia_off.size();
+    std::vector<double> all;
+    all.reserve((size_t)QD.ndia * n);
+    for (int k = 0; k < QD.ndia; k++) {
+      QD.dia_off[k] = dia_off[k];
+      all.insert(all.end(), dia_vals[k].begin(), dia_vals[k].end());
+    }
+    double* d;
+    if ((st = upload(h, &d, all))) return st;
+    QD.dia = d;
+  }
+  int64_t toff = 0;
+  QD.nfac = (int)facs.size();
+  for (int f = 0; f < QD.nfac; f++) {
+    if ((st = upload_csr(h, QD.fac[f], facs[f]))) return st;
+    HostCsr BT = transpose(facs[f]);
+    if ((st = upload_csr(h, QD.fact[f], BT))) return st;
+    QD.toff[f] = toff;
+    toff += facs[f].rows;
+  }
+  QD.ndense = (int)dens.size();
+  for (int g = 0; g < QD.ndense; g++) {
+    double* d;
+    if ((st = upload(h, &d, dens[g].second))) return st;
+    QD.dense[g] = d;
+    QD.dense_p[g] = dens[g].first;
+    QD.toff[QD.nfac + g] = toff;
+    toff += dens[g].first;
+  }
+  QD.tlen = toff;
+
+  // ---- work vectors (all n- and m-vectors exist; unused ones stay zero)
+  double** nvecs[] = {&V.x, &V.w, &V.Qw, &V.ATy, &V.x0, &V.w0, &V.Qw0, &V.ATy0, &V.xb, &V.wb, &V.Qwb, &V.ATyb,
+                      &V.wh, &V.Qwh, &V.v, &V.zb, &V.Qxb};
+  for (double** p : nvecs)
+    if ((st = zeros(h, p, n))) return st;
+  double** mvecs[] = {&V.y, &V.y0, &V.yb};
+  for (double** p : mvecs)
+    if ((st = zeros(h, p, m))) return st;
+  if ((st = zeros(h, &V.t1, 2 * std::max<int64_t>(toff, 1)))) return st;
+  if ((st = zeros(h, &V.t2, 2 * std::max<int64_t>(toff, 1)))) return st;
+  // the autotuner's probe gathers from ain with the column range of every B_f^T (p_f)
+  const int64_t nm = std::max(std::max(n, m), toff);
+  if ((st = zeros(h, &V.pv, nm))) return st;
+  if ((st = zeros(h, &V.pw, nm))) return st;
+  if ((st = zeros(h, &V.ptmp, nm))) return st;
+  double *ain, *aout;
+  if ((st = zeros(h, &ain, nm))) return st;
+  if ((st = zeros(h, &aout, nm))) return st;
+  V.ain = ain;
+  V.aout = aout;
+
+  // ---- launch plan
+  int dev = 0, sms = 0;
+  CU(h, cudaGetDevice(&dev));
+  CU(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  h->dev = dev;
+  Plan& P = h->plan;
+  auto chunks = [](int64_t rows) { return (int)std::max<int64_t>(1, (rows + kChunk - 1) / kChunk); };
+  const int per_sm = 4;
+  P.gridN = std::min(chunks(n), sms * per_sm);
+  P.gridM = std::min(chunks(m), sms * per_sm);
+  P.gridE = std::min(chunks(n), sms * 8);
+  P.gridPre = (int)std::min<int64_t>(std::max<int64_t>(1, (toff + 7) / 8), sms * 8);
+  a.nbM = P.gridM;
+  const int gmax = std::max(P.gridN, P.gridM);
+  if ((st = zeros(h, &a.partL, (size_t)gmax * kWL))) return st;
+  if ((st = zeros(h, &a.part3, (size_t)gmax * kW3))) return st;
+  if ((st = zeros(h, &a.partR, (size_t)gmax * kWR))) return st;
+  if ((st = zeros(h, &a.partP, (size_t)gmax * kWP))) return st;
+  {
+    void* p;
+    if ((st = dalloc(h, &p, 16 * sizeof(unsigned)))) return st;
+    CU(h, cudaMemsetAsync(p, 0, 16 * sizeof(unsigned), h->stream));
+    a.counters = (unsigned*)p;
+    if ((st = dalloc(h, &p, sizeof(Ctrl)))) return st;
+    CU(h, cudaMemsetAsync(p, 0, sizeof(Ctrl), h->stream));
+    h->dctrl = (Ctrl*)p;
+    a.C = h->dctrl;
+  }
+  CU(h, cudaMallocHost(&h->hctrl, sizeof(Ctrl)));
+  std::memset(h->hctrl, 0, sizeof(Ctrl));
+  CU(h, cudaMallocHost(&h->hflags, 8 * sizeof(int)));
+  CU(h, cudaEventCreate(&h->ev[0]));
+  CU(h, cudaEventCreate(&h->ev[1]));
+  CU(h, cudaStreamSynchronize(h->stream));
+
+  // ---- schedule autotune (lanes per row for each CSR pass)
+  {
+    CU(h, cudaMemsetAsync(ain, 0, nm * sizeof(double), h->stream));
+    P.gA = m > 0 ? tune_G(h, a.A, P.gridM, ain, aout, 1) : 1;
+    P.gAT = m > 0 ? tune_G(h, a.AT, P.gridN, ain, aout, 1) : 1;
+    const Csr* big = nullptr;
+    if (QD.csr.rows) big = &QD.csr;
+    for (int f = 0; f < QD.nfac; f++)
+      if (!big || QD.fact[f].nnz > big->nnz) big = &QD.fact[f];
+    P.gQ = big ? tune_G(h, *big, P.gridN, ain, aout, 1) : 1;
+    CU(h, cudaStreamSynchronize(h->stream));
+    CU(h, cudaGetLastError());
+  }
+  return HPRQP_OK;
+}
+
+extern "C" hprqp_status hprqp_create(hprqp_handle** out, int64_t n, int64_t m, const hprqp_qop* Q,
+                                     const int32_t* A_rowptr, const int32_t* A_colidx, const double* A_vals,
+                                     const double* c, const double* l, const double* u, const double* L,
+                                     const double* U, int32_t phi, double lambda, const hprqp_params* params) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, HPRQP_INVALID_ARG, "null handle pointer");
+  *out = nullptr;
+  hprqp_handle* h = new hprqp_handle();
+  if (params) h->prm = *params;
+  else hprqp_default_params(&h->prm);
+  if (h->prm.check_every < 1 || h->prm.restart_every < 1 || h->prm.iters_per_launch < 1 ||
+      h->prm.iters_per_launch > 4096) {
+    fail(nullptr, HPRQP_INVALID_ARG, "check_every, restart_every >= 1 and 1 <= iters_per_launch <= 4096");
+    delete h;
+    return HPRQP_INVALID_ARG;
+  }
+  if (h->prm.stream) {
+    h->stream = (cudaStream_t)h->prm.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      fail(nullptr, HPRQP_CUDA_ERROR, "cannot create a CUDA stream (no device?)");
+      delete h;
+      return HPRQP_CUDA_ERROR;
+    }
+    h->own_stream = true;
+  }
+  hprqp_status st = create_impl(h, n, m, Q, A_rowptr, A_colidx, A_vals, c, l, u, L, U, phi, lambda);
+  if (st != HPRQP_OK) {
+    if (g_create_err.empty()) g_create_err = h->err;
+    release(h);
+    return st;
+  }
+  *out = h;
+  return HPRQP_OK;
+}
+
+// ------------------------------------------------------------------------------------ warm start
+extern "C" hprqp_status hprqp_set_warm_start(hprqp_handle* h, const double* x0, const double* y0, double sigma0) {
+  if (!h) return HPRQP_INVALID_ARG;
+  hprqp_status st;
+  h->ws_x.clear();
+  h->ws_y.clear();
+  if (x0) {
+    if ((st = fetch(h, h->ws_x, x0, h->n))) return st;
+    for (double v : h->ws_x)
+      if (!std::isfinite(v)) return fail(h, HPRQP_INVALID_ARG, "warm start x0 is not finite");
+  }
+  if (y0 && h->m > 0) {
+    if ((st = fetch(h, h->ws_y, y0, h->m))) return st;
+    for (double v : h->ws_y)
+      if (!std::isfinite(v)) return fail(h, HPRQP_INVALID_ARG, "warm start y0 is not finite");
+  }
+  h->ws_sigma = sigma0 > 0 && std::isfinite(sigma0) ? sigma0 : 0.0;
+  return HPRQP_OK;
+}
+
+// ------------------------------------------------------------------------------------ graphs
+static hprqp_status build_iter_graph(hprqp_handle* h) {
+  if (h->g_iter) return HPRQP_OK;
+  cudaGraph_t g;
+  CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < h->prm.iters_per_launch && le == cudaSuccess; i++) {
+    le = launch_iteration(h->args, h->plan, h->stream);
+    if (le == cudaSuccess) le = launch_restart(h->args, h->plan, h->stream);
+  }
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    cudaGetLastError();
+    if (ce == cudaSuccess) cudaGraphDestroy(g);
+    return fail(h, HPRQP_CUDA_ERROR, "graph capture failed: %s / %s", cudaGetErrorString(le), cudaGetErrorString(ce));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->g_iter, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    h->g_iter = nullptr;
+    return fail(h, HPRQP_CUDA_ERROR, "graph instantiate failed: %s", cudaGetErrorString(ie));
+  }
+  return HPRQP_OK;
+}
+
+static hprqp_status build_pw_graph(hprqp_handle* h, int which) {
+  if (h->g_pw[which]) return HPRQP_OK;
+  cudaGraph_t g;
+  CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < h->pw_chunk && le == cudaSuccess; i++) le = launch_power_iter(h->args, h->plan, which, h->stream);
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    cudaGetLastError();
+    if (ce == cudaSuccess) cudaGraphDestroy(g);
+    return fail(h, HPRQP_CUDA_ERROR, "power graph capture failed");
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->g_pw[which], g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    h->g_pw[which] = nullptr;
+    return fail(h, HPRQP_CUDA_ERROR, "power graph instantiate failed");
+  }
+  return HPRQP_OK;
+}
+
+// Power method of Sec. 4.1 on A A^* (which = 0, R^m) or Q (which = 1, R^n); returns the
+// Rayleigh quotient at convergence times the safety factor.
+static hprqp_status power_method(hprqp_handle* h, int which, double* lam) {
+  const int64_t dim = which == 0 ? h->m : h->n;
+  hprqp_status st;
+  if ((st = build_pw_graph(h, which))) return st;
+  // host value of 1/||start||, same start vector and summation order as the CPU reference
+  double s2 = 0.0;
+  for (int64_t i = 0; i < dim; i++) {
+    uint32_t hh = (uint32_t)((uint64_t)(i + 1) * 2654435761u);
+    double v = 0.5 + (double)hh / 4294967296.0;
+    s2 += v * v;
+  }
+  Ctrl& C = *h->hctrl;
+  C.pw_it = 0;
+  C.pw_lam = 0.0;
+  C.pw_done = 0;
+  C.pw_scale = 1.0 / std::sqrt(s2);
+  C.pw_max = h->prm.power_max_iter;
+  C.pw_tol = h->prm.power_tol;
+  C.done = 1;  // keep the iteration kernels idle
+  CU(h, cudaMemcpyAsync(h->dctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+  CU(h, launch_power_init(h->args, h->plan, which, h->stream));
+  const int64_t max_launch = h->prm.power_max_iter / h->pw_chunk + 3;
+  int* flag = h->hflags;
+  h->launches += 1;
+  const int64_t pw_nodes = (int64_t)h->pw_chunk * (which == 0 ? 4 : 3 + (h->args.Q.has_pre() ? 1 : 0));
+  for (int64_t i = 0; i < max_launch; i++) {
+    CU(h, cudaGraphLaunch(h->g_pw[which], h->stream));
+    h->launches += pw_nodes;
+    CU(h, cudaMemcpyAsync(flag, &h->dctrl->pw_done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (*flag == 1) break;
+  }
+  CU(h, cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  *lam = h->prm.power_safety * h->hctrl->pw_lam;
+  return HPRQP_OK;
+}
+
+// ------------------------------------------------------------------------------------ solve
+// Starting point u^{0,0} (origin or warm start, w = x), its images, and the controller state.
+static hprqp_status init_state(hprqp_handle* h, double lamA, double lamQ, double sigma, double tol, int64_t max_iter) {
+  Args& a = h->args;
+  const bool HQ = a.Q.present(), HA = h->m > 0;
+  Vec& V = a.V;
+  const size_t nb8 = h->n * sizeof(double), mb8 = h->m * sizeof(double);
+  if (!h->ws_x.empty()) {
+    CU(h, cudaMemcpyAsync(V.x, h->ws_x.data(), nb8, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CU(h, cudaMemsetAsync(V.x, 0, nb8, h->stream));
+  }
+  CU(h, cudaMemcpyAsync(V.w, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
+  CU(h, cudaMemcpyAsync(V.x0, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
+  CU(h, cudaMemcpyAsync(V.w0, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
+  if (HA) {
+    if (!h->ws_y.empty()) CU(h, cudaMemcpyAsync(V.y, h->ws_y.data(), mb8, cudaMemcpyHostToDevice, h->stream));
+    else CU(h, cudaMemsetAsync(V.y, 0, mb8, h->stream));
+    CU(h, cudaMemcpyAsync(V.y0, V.y, mb8, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  // images Q w^0 and A^* y^0
+  if (HQ) {
+    if (!h->ws_x.empty()) {
+      CU(h, cudaMemcpyAsync((void*)V.ain, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
+      CU(h, launch_apply(a, h->plan, 2, h->stream));
+      h->launches += 1 + (a.Q.has_pre() ? 1 : 0);
+      CU(h, cudaMemcpyAsync(V.Qw, V.aout, nb8, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      CU(h, cudaMemsetAsync(V.Qw, 0, nb8, h->stream));
+    }
+    CU(h, cudaMemcpyAsync(V.Qw0, V.Qw, nb8, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if (HA) {
+    if (!h->ws_y.empty()) {
+      CU(h, cudaMemcpyAsync((void*)V.ain, V.y, mb8, cudaMemcpyDeviceToDevice, h->stream));
+      CU(h, launch_apply(a, h->plan, 1, h->stream));
+      h->launches += 1;
+      CU(h, cudaMemcpyAsync(V.ATy, V.aout, nb8, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      CU(h, cudaMemsetAsync(V.ATy, 0, nb8, h->stream));
+    }
+    CU(h, cudaMemcpyAsync(V.ATy0, V.ATy, nb8, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  CU(h, cudaMemsetAsync(a.counters, 0, 16 * sizeof(unsigned), h->stream));
+  Ctrl& C = *h->hctrl;
+  std::memset(&C, 0, sizeof(Ctrl));
+  C.lamA = lamA;
+  C.lamQ = lamQ;
+  C.lambda = h->lambda;
+  C.tol = tol;
+  C.alpha1 = h->prm.alpha1;
+  C.alpha2 = h->prm.alpha2;
+  C.alpha3 = h->prm.alpha3;
+  C.alpha3_tight = h->prm.alpha3_tight;
+  C.ratio_tight = h->prm.ratio_tight;
+  C.c_inf = h->c_inf;
+  C.b_inf = h->b_inf;
+  C.max_iter = max_iter;
+  C.check_every = h->prm.check_every;
+  C.restart_every = h->prm.restart_every;
+  C.halpern_total = h->prm.halpern_total;
+  C.restart_off = h->prm.restart_off;
+  C.sigma_fixed = h->prm.sigma_fixed;
+  C.sigma_golden = h->prm.sigma_golden;
+  C.has_A = HA;
+  C.has_Q = HQ;
+  C.phi = h->phi;
+  C.mode = 0;
+  C.k = C.t = C.r = 0;
+  C.R_first = -1.0;
+  C.rtest = !C.restart_off;
+  C.ttest = (1 % C.check_every == 0) || (1 >= max_iter);
+  C.status = 1;
+  C.done = 0;
+  C.pw_done = 1;
+  hprqp::set_sigma(C, sigma);
+  CU(h, cudaMemcpyAsync(h->dctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+  return HPRQP_OK;
+}
+
+static double initial_sigma(hprqp_handle* h) {
+  if (h->ws_sigma > 0) return h->ws_sigma;
+  if (h->prm.sigma0 > 0) return h->prm.sigma0;
+  // Sec. 4.1: sigma0 = ||b|| / ||c|| when both lie in [1e-16, 1e16], else 1
+  double nb = std::sqrt(h->nb2), nc = std::sqrt(h->nc2);
+  return (nb >= 1e-16 && nb <= 1e16 && nc >= 1e-16 && nc <= 1e16) ? nb / nc : 1.0;
+}
+
+extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_iter) {
+  if (!h) return HPRQP_INVALID_ARG;
+  h->err.clear();
+  if (!(tol > 0.0) || max_iter < 1) return fail(h, HPRQP_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+  auto t0 = std::chrono::steady_clock::now();
+  hprqp_status st;
+  Args& a = h->args;
+  const bool HQ = a.Q.present(), HA = h->m > 0;
+  CU(h, cudaSetDevice(h->dev));
+  h->launches = 0;
+  // ---- lambda_A >= lambda_1(AA^*), lambda_Q >= lambda_1(Q) (Sec. 4.1)
+  double lamA = 0.0, lamQ = 0.0;
+  if (HA) {
+    if (h->prm.lambda_A > 0) lamA = h->prm.lambda_A;
+    else if ((st = power_method(h, 0, &lamA))) return st;
+    if (!(lamA > 0.0)) lamA = 1.0;
+  }
+  if (HQ) {
+    if (h->prm.lambda_Q > 0) lamQ = h->prm.lambda_Q;
+    else if ((st = power_method(h, 1, &lamQ))) return st;
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  const double sigma = initial_sigma(h);
+  if ((st = init_state(h, lamA, lamQ, sigma, tol, max_iter))) return st;
+  if ((st = build_iter_graph(h))) return st;
+  // ---- Algorithm 4 in graph launches of iters_per_launch steps; double-buffered done poll
+  const int64_t per = h->prm.iters_per_launch;
+  const int64_t max_launch = (max_iter + per - 1) / per + 2;
+  const int64_t nodes = per * kernels_per_iteration(a);
+  bool time_up = false;
+  for (int64_t i = 0; i < max_launch; i++) {
+    CU(h, cudaGraphLaunch(h->g_iter, h->stream));
+    h->launches += nodes;
+    CU(h, cudaMemcpyAsync(&h->hflags[i & 1], &h->dctrl->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaEventRecord(h->ev[i & 1], h->stream));
+    if (i > 0) {
+      CU(h, cudaEventSynchronize(h->ev[(i - 1) & 1]));
+      if (h->hflags[(i - 1) & 1]) break;
+    }
+    if (h->prm.time_limit > 0) {
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > h->prm.time_limit) {
+        time_up = true;
+        break;
+      }
+    }
+  }
+  Ctrl& C = *h->hctrl;
+  CU(h, cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  auto t2 = std::chrono::steady_clock::now();
+  int status = C.status;
+  if (!C.done) status = time_up ? HPRQP_TIME_LIMIT : HPRQP_MAX_ITER;
+  hprqp_kkt& K = h->kkt;
+  std::memset(&K, 0, sizeof(K));
+  K.eta_p = C.eta_p;
+  K.eta_d = C.eta_d;
+  K.eta_gap = C.eta_gap;
+  K.rel_kkt = std::max(C.eta_p, std::max(C.eta_d, C.eta_gap));
+  K.pobj = C.pobj;
+  K.dobj = C.dobj;
+  K.iters = C.k;
+  K.restarts = C.r;
+  K.sigma = C.sigma;
+  K.lambda_A = lamA;
+  K.lambda_Q = lamQ;
+  K.solve_seconds = std::chrono::duration<double>(t2 - t0).count();
+  K.power_seconds = std::chrono::duration<double>(t1 - t0).count();
+  K.kernel_launches = h->launches;
+  K.status = status;
+  h->last_status = status;
+  h->solved = true;
+  h->last_lamA = lamA;
+  h->last_lamQ = lamQ;
+  h->last_sigma0 = sigma;
+  return (hprqp_status)status;
+}
+
+extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms) {
+  if (!h) return HPRQP_INVALID_ARG;
+  if (!h->solved) return fail(h, HPRQP_INVALID_ARG, "hprqp_profile before hprqp_solve");
+  if (iters < 1 || !ms) return fail(h, HPRQP_INVALID_ARG, "need iters >= 1 and an output array");
+  hprqp_status st;
+  if ((st = init_state(h, h->last_lamA, h->last_lamQ, h->last_sigma0, 1e-300, (int64_t)iters + 1))) return st;
+  cudaEvent_t ev[HPRQP_PROF_KINDS][2];
+  for (auto& e : ev) {
+    CU(h, cudaEventCreate(&e[0]));
+    CU(h, cudaEventCreate(&e[1]));
+  }
+  double tot[HPRQP_PROF_KINDS] = {0};
+  int cnt[HPRQP_PROF_KINDS] = {0};
+  cudaError_t err = cudaSuccess;
+  for (int32_t i = 0; i < iters && err == cudaSuccess; i++) {
+    // a fresh record per kind and step: events of kinds a problem lacks stay unrecorded
+    cudaEvent_t (*evp)[2] = ev;
+    for (auto& e : ev) {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+      cudaEventCreate(&e[0]);
+      cudaEventCreate(&e[1]);
+    }
+    err = launch_iteration(h->args, h->plan, h->stream, evp);
+    if (err == cudaSuccess) err = launch_restart(h->args, h->plan, h->stream, evp);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < HPRQP_PROF_KINDS && err == cudaSuccess; k++) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[k][0], ev[k][1]) == cudaSuccess) {
+        tot[k] += t;
+        cnt[k]++;
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
+  for (auto& e : ev) {
+    cudaEventDestroy(e[0]);
+    cudaEventDestroy(e[1]);
+  }
+  if (err != cudaSuccess) return fail(h, HPRQP_CUDA_ERROR, "profile: %s", cudaGetErrorString(err));
+  // restart kinds: only the steps whose gated pass did work carry weight; the gated early
+  // exits are a few microseconds and are included in the mean of all steps
+  for (int k = 0; k < HPRQP_PROF_KINDS; k++) ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
+  h->solved = false;  // the iterate no longer belongs to a solve
+  return HPRQP_OK;
+}
+
+// ------------------------------------------------------------------------------------ get / apply
+static hprqp_status copy_out(hprqp_handle* h, double* dst, const double* src, size_t count) {
+  if (!dst || count == 0) return HPRQP_OK;
+  CU(h, cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, h->stream));
+  return HPRQP_OK;
+}
+
+extern "C" hprqp_status hprqp_get(hprqp_handle* h, double* x, double* y, double* z, double* w, hprqp_kkt* kkt) {
+  if (!h) return HPRQP_INVALID_ARG;
+  if (!h->solved) return fail(h, HPRQP_INVALID_ARG, "hprqp_get before hprqp_solve");
+  hprqp_status st;
+  Vec& V = h->args.V;
+  if (z && h->last_status == HPRQP_TIME_LIMIT) CU(h, launch_zbar(h->args, h->plan, h->stream));
+  if ((st = copy_out(h, x, V.xb, h->n))) return st;
+  if ((st = copy_out(h, y, V.yb, h->m))) return st;
+  if ((st = copy_out(h, z, V.zb, h->n))) return st;
+  if ((st = copy_out(h, w, V.wb, h->n))) return st;
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (kkt) *kkt = h->kkt;
+  return HPRQP_OK;
+}
+
+extern "C" hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* in, double* out) {
+  if (!h) return HPRQP_INVALID_ARG;
+  if (op < 0 || op > 2 || !in || !out) return fail(h, HPRQP_INVALID_ARG, "bad apply arguments");
+  if (op <= 1 && h->m == 0) return fail(h, HPRQP_INVALID_ARG, "problem has no A rows");
+  const int64_t nin = op == 0 ? h->n : op == 1 ? h->m : h->n;
+  const int64_t nout = op == 0 ? h->m : h->n;
+  Vec& V = h->args.V;
+  CU(h, cudaMemcpyAsync((void*)V.ain, in, nin * sizeof(double), cudaMemcpyDefault, h->stream));
+  CU(h, launch_apply(h->args, h->plan, op, h->stream));
+  CU(h, cudaMemcpyAsync(out, V.aout, nout * sizeof(double), cudaMemcpyDefault, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return HPRQP_OK;
+}

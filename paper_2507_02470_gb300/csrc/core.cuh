@@ -1,0 +1,169 @@
+// Device-side data structures and small helpers of the HPR-QP library (sm_103a, FP64).
+//
+// On GB300 the FP64 pipe retires one warp instruction per ~19 SM cycles whatever the
+// number of active lanes, so the kernels keep every FP64 instruction on full warps and do
+// comparisons, clamps and max-reductions on the integer pipe (bit-exact with the FP64
+// operations for non-NaN inputs).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hprqp {
+
+constexpr int kMaxDia = 8;
+constexpr int kMaxFac = 4;
+constexpr int kMaxDense = 4;
+constexpr int kChunk = 256;      // rows per block pass of the row kernels (= block size)
+constexpr int kThreads = 256;
+
+enum Phi { PHI_BOX = 0, PHI_L1 = 1, PHI_L1_BOX = 2 };
+
+struct Csr {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const double* v = nullptr;
+};
+
+// Q = diag(d) + sym band + CSR + sum_f B_f^T B_f + sum_g F_g^T F_g   (Sec. 1: Q may be
+// matrix-free).  The factor intermediates t = B v, F v live in one buffer at toff[].
+struct QDev {
+  int64_t n = 0;
+  const double* diag = nullptr;
+  Csr csr;                               // rows == 0: absent
+  int ndia = 0;
+  int dia_off[kMaxDia] = {0};
+  const double* dia = nullptr;           // ndia x n, dia[k*n+i] = Q[i][i+off_k]
+  int nfac = 0;
+  Csr fac[kMaxFac];                      // B_f (p x n)
+  Csr fact[kMaxFac];                     // B_f^T (n x p)
+  int ndense = 0;
+  int64_t dense_p[kMaxDense] = {0};
+  const double* dense[kMaxDense] = {nullptr};   // F_g row-major p x n
+  int64_t toff[kMaxFac + kMaxDense] = {0};
+  int64_t tlen = 0;
+  __host__ __device__ bool present() const { return diag || csr.rows || ndia || nfac || ndense; }
+  __host__ __device__ bool has_pre() const { return nfac || ndense; }
+};
+
+// Scalars of the running iteration.  Written by the controller (the last block of the
+// last kernel of an iteration) and by the restart kernel; read by every kernel.
+struct Ctrl {
+  // per-iteration scalars
+  double sigma, inv_sigma;
+  double c1, c2, s;          // sigma lQ/(1+sigma lQ), 1/(1+sigma lQ), sigma/(1+sigma lQ)
+  double slA, inv_slA;       // sigma lA and its reciprocal
+  double tau;                // sigma * lambda (l1 threshold)
+  double ha, hb;             // pending Halpern weights 1/(i+2), (i+1)/(i+2)
+  int mode;                  // update at the start of this iteration: 0 none, 1 Halpern, 2 restart
+  int rtest, ttest;          // this iteration evaluates R~ / the stopping rule
+  int done;                  // kernels return at entry
+  int restart_pending;       // the sigma update must run before the next iteration
+  int status;
+  long long k, t, r;
+  // restart bookkeeping (Sec. 3.2)
+  double R_r0, R_prev, R_first, R_last, alpha3, ratio;
+  // constants
+  double lamA, lamQ, lambda, tol;
+  double alpha1, alpha2, alpha3_tight, ratio_tight;
+  double c_inf, b_inf;
+  long long max_iter, check_every, restart_every;
+  int halpern_total, restart_off, sigma_fixed, sigma_golden;
+  int has_A, has_Q, phi;
+  // results of the last stopping test
+  double eta_p, eta_d, eta_gap, pobj, dobj, R;
+  // power method state
+  double pw_lam, pw_scale;
+  long long pw_it, pw_max;
+  double pw_tol;
+  int pw_done;
+};
+
+// ---------------------------------------------------------------------------- int-pipe FP64 helpers
+// Monotone map of a double (non-NaN) onto a signed 64-bit key: a < b  <=>  key(a) < key(b)
+__device__ __forceinline__ long long dkey(double a) {
+  long long b = __double_as_longlong(a);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double imax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+__device__ __forceinline__ double imin(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }
+__device__ __forceinline__ double iclamp(double v, double lo, double hi) { return imin(imax(v, lo), hi); }
+__device__ __forceinline__ double iabs(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool igt0(double a) { return __double_as_longlong(a) > 0; }        // a > +0
+__device__ __forceinline__ bool ilt0(double a) {                                             // a < -0
+  return __double_as_longlong(a) < 0 && (__double_as_longlong(a) & 0x7fffffffffffffffLL) != 0;
+}
+__device__ __forceinline__ bool iisinf(double a) {
+  return (__double_as_longlong(a) & 0x7fffffffffffffffLL) == 0x7ff0000000000000LL;
+}
+
+// ---------------------------------------------------------------------------- block reductions
+// Deterministic: fixed lane/warp order.  op 0 = sum, 1 = max of non-negative values.
+template <int NT>
+__device__ __forceinline__ void block_reduce(double (&v)[NT], const unsigned maxmask, double* smem) {
+  // smem: at least NT * 32 doubles
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NT; i++) {
+    double a = v[i];
+    bool mx = (maxmask >> i) & 1u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double b = __shfl_down_sync(0xffffffffu, a, o);
+      a = mx ? imax(a, b) : a + b;
+    }
+    if (lane == 0) smem[i * 32 + warp] = a;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NT; i++) {
+      bool mx = (maxmask >> i) & 1u;
+      double a = lane < nw ? smem[i * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double b = __shfl_down_sync(0xffffffffu, a, o);
+        a = mx ? imax(a, b) : a + b;
+      }
+      if (lane == 0) v[i] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Last-block election: every block stores its partials, then the last one to arrive
+// returns true (and has visibility of all partials).
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+    if (am_last) *counter = 0;
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// Sum (or max) of `nblocks` partial rows of width W, term i at part[b*W + i]; every thread of
+// the block takes part; the result is valid in out[] of thread 0.  Fixed order.
+template <int NT>
+__device__ __forceinline__ void reduce_partials(const double* part, int nblocks, int W, unsigned maxmask,
+                                                double (&out)[NT], double* smem) {
+#pragma unroll
+  for (int i = 0; i < NT; i++) out[i] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NT; i++) {
+      double p = __ldcg(part + (size_t)b * W + i);
+      out[i] = ((maxmask >> i) & 1u) ? imax(out[i], p) : out[i] + p;
+    }
+  }
+  block_reduce<NT>(out, maxmask, smem);
+}
+
+}  // namespace hprqp

@@ -1,0 +1,75 @@
+// Kernel argument block and launch helpers of the single-instance HPR-QP solver.
+#pragma once
+#include "core.cuh"
+
+namespace hprqp {
+
+struct Vec {
+  // current iterate u = (y, w_Q, x) with the images Q w, A^* y; anchor u^{r,0}; bar iterate
+  double *x, *w, *Qw, *ATy;
+  double *x0, *w0, *Qw0, *ATy0;
+  double *xb, *wb, *Qwb, *ATyb;
+  double *wh, *Qwh, *v, *zb, *Qxb;
+  double *y, *y0, *yb;
+  const double *c, *L, *U, *l, *u;
+  double *t1, *t2;            // factor intermediates (2 * tlen each)
+  double *pv, *pw, *ptmp;     // power method vectors
+  const double* ain;          // apply input / output
+  double* aout;
+};
+
+// partial-sum regions (doubles); each kernel that reduces owns a region of gridDim.x rows
+constexpr int kWL = 12;   // width of the end-of-iteration partials
+constexpr int kW3 = 4;    // width of the y-step partials
+constexpr int kWR = 5;    // width of the restart partials
+constexpr int kWP = 2;    // width of the power-method partials
+
+struct Args {
+  int64_t n, m;
+  int phi;
+  Csr A, AT;
+  QDev Q;
+  Vec V;
+  Ctrl* C;
+  double* partL;
+  double* part3;
+  double* partR;
+  double* partP;
+  unsigned* counters;       // [0] end-of-iteration, [1] restart, [2] power
+  int nbM;                  // blocks of the m-row kernel (rows of part3)
+};
+
+// Row-kernel kinds
+enum Kind { K_Q1 = 0, K_A1 = 1, K_AT = 2, K_Q2 = 3, K_APPLY_Q = 4, K_APPLY_A = 5, K_APPLY_AT = 6,
+            K_POWER_Q = 7, K_POWER_A = 8, K_APPLY_AT_P = 9 };
+
+// Launch plan chosen at create time (lanes per row of each CSR pass, grid sizes).
+struct Plan {
+  int gQ = 1, gA = 1, gAT = 1, gPre = 32;   // lanes per row
+  int gridN = 0, gridM = 0, gridE = 0, gridPre = 0;   // blocks of the n-row, m-row, elementwise, pre kernels
+};
+
+// sigma and the scalars derived from it (host and device use the same arithmetic)
+__host__ __device__ inline void set_sigma(Ctrl& C, double sigma) {
+  C.sigma = sigma;
+  C.inv_sigma = 1.0 / sigma;
+  const double d = 1.0 + sigma * C.lamQ;
+  C.c1 = sigma * C.lamQ / d;
+  C.c2 = 1.0 / d;
+  C.s = sigma / d;
+  C.slA = sigma * C.lamA;
+  C.inv_slA = C.slA > 0.0 ? 1.0 / C.slA : 0.0;
+  C.tau = sigma * C.lambda;
+}
+
+// host-side launchers (solver.cu)
+cudaError_t launch_iteration(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
+cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
+int kernels_per_iteration(const Args& a);
+cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s);
+cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s);
+cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s);
+cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s);
+cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s);
+
+}  // namespace hprqp

@@ -1,0 +1,150 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+Bar: the first iterates agree to 1e-10 relative (||a-b|| / max(1, ||b||)), the converged
+objective to 1e-6 relative at rel-KKT <= 1e-8, operator products to 1e-13 relative.  The
+iteration trajectory depends on lambda_A, lambda_Q and sigma0 only through the data, so
+the parity runs pass the oracle's power-method estimates to both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qpgen
+
+pytestmark = pytest.mark.gpu
+
+ITER_TOL = 1e-10
+OBJ_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2507_02470_gb300 as p
+    p.build()
+    return p
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(1.0, np.linalg.norm(b)))
+
+
+def small_problems():
+    yield "plain", qpgen.plain_cqp(n=300, m=150, seed=3, q_rows=30, a_density=0.05, q_density=0.1)
+    yield "csrQ", qpgen.random_small(n=40, m=20, seed=4, q_kind="csr", density=0.3)
+    yield "dense", qpgen.portfolio(5, n=700)
+    yield "l1box", qpgen.random_small(n=30, m=10, seed=6, q_kind="factor", q_rank=10, phi="l1_box", lam=0.3)
+    yield "lasso", qpgen.lasso(p=400, q=2000, density=0.02)
+    yield "lp", qpgen.from_dense(None, np.random.default_rng(1).standard_normal(50),
+                                 A=np.random.default_rng(2).standard_normal((20, 50)),
+                                 l=np.full(20, -1.0), u=np.full(20, 1.0), L=np.zeros(50), U=np.ones(50))
+    yield "large_sum", qpgen.large_cqp(n=5000, m=2500, seed=1)
+
+
+PROBLEMS = dict(small_problems())
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_operators(pkg, name):
+    qp = PROBLEMS[name]
+    rng = np.random.default_rng(0)
+    with pkg.Solver(qp) as s:
+        v = rng.standard_normal(qp.n)
+        assert rel(s.apply("Q", v), oracle.qmul(qp, v)) <= 1e-13
+        if qp.m:
+            yv = rng.standard_normal(qp.m)
+            assert rel(s.apply("A", v), oracle.amul(qp, v)) <= 1e-13
+            assert rel(s.apply("AT", yv), oracle.atmul(qp, yv)) <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_first_iterates(pkg, name):
+    qp = PROBLEMS[name]
+    K = 50
+    ref = oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K)
+    lamA, lamQ = ref.lambda_A, ref.lambda_Q
+    with pkg.Solver(qp, lambda_A=lamA if qp.m else 0.0, lambda_Q=lamQ) as s:
+        for k in (1, 2, 3, 10, 11, 20, 21, 33, 41, 50):
+            s.solve(tol=1e-30, max_iter=k)
+            x, y, z, w, kkt = s.get()
+            assert kkt["iters"] == k
+            ex = rel(x, ref.trace["x"][k - 1])
+            assert ex <= ITER_TOL, (name, k, ex)
+            if qp.m:
+                ey = rel(y, ref.trace["y"][k - 1])
+                assert ey <= ITER_TOL, (name, k, ey)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_converged_objective(pkg, name):
+    qp = PROBLEMS[name]
+    ref = oracle.solve(qp, tol=1e-8, max_iter=500000)
+    assert ref.status == "converged"
+    with pkg.Solver(qp, lambda_A=ref.lambda_A if qp.m else 0.0, lambda_Q=ref.lambda_Q) as s:
+        st = s.solve(tol=1e-8, max_iter=500000)
+        x, y, z, w, kkt = s.get()
+    assert st == "converged", kkt
+    assert abs(kkt["pobj"] - ref.pobj) <= OBJ_TOL * (1 + abs(ref.pobj))
+    # the GPU's own stopping test is honest: recompute eta on its output with the oracle
+    e, _, _ = oracle.eta(qp, x, y, z)
+    assert np.max(e) <= 1.05e-8, e
+    assert np.all(x >= qp.L) and np.all(x <= qp.U)
+
+
+def test_power_method(pkg):
+    qp = PROBLEMS["plain"]
+    from tests import dense_ref as D
+    A, Q = D.dense_of(qp)
+    la = np.linalg.eigvalsh(A @ A.T).max()
+    lq = np.linalg.eigvalsh(Q).max()
+    with pkg.Solver(qp) as s:
+        s.solve(tol=1e-30, max_iter=1)
+        k = s.kkt()
+    assert la <= k["lambda_A"] <= 1.01 * la * (1 + 1e-6)
+    assert lq <= k["lambda_Q"] <= 1.01 * lq * (1 + 1e-6)
+    ref = oracle.solve(qp, max_iter=1)
+    assert abs(k["lambda_A"] - ref.lambda_A) <= 1e-5 * ref.lambda_A
+    assert abs(k["lambda_Q"] - ref.lambda_Q) <= 1e-5 * ref.lambda_Q
+
+
+def test_default_run_matches_oracle_objective(pkg):
+    # both sides estimate lambda themselves (power method), defaults everywhere
+    qp = qpgen.plain_cqp()
+    ref = oracle.solve(qp, tol=1e-8, max_iter=200000)
+    with pkg.Solver(qp) as s:
+        assert s.solve(tol=1e-8, max_iter=200000) == "converged"
+        k = s.kkt()
+    assert abs(k["pobj"] - ref.pobj) <= OBJ_TOL * (1 + abs(ref.pobj))
+    assert k["rel_kkt"] <= 1e-8
+
+
+def test_warm_start_and_restart_params(pkg):
+    qp = PROBLEMS["plain"]
+    x0 = np.clip(np.random.default_rng(3).random(qp.n), qp.L, qp.U)
+    y0 = np.random.default_rng(4).standard_normal(qp.m) * 0.1
+    ref = oracle.solve(qp, tol=1e-30, max_iter=40, x0=x0, y0=y0, trace_len=40, halpern_total=1, sigma_golden=1)
+    with pkg.Solver(qp, lambda_A=ref.lambda_A, lambda_Q=ref.lambda_Q, halpern_total=1, sigma_golden=1) as s:
+        s.set_warm_start(x0, y0)
+        for k in (1, 15, 40):
+            s.solve(tol=1e-30, max_iter=k)
+            x, y, *_ = s.get()
+            assert rel(x, ref.trace["x"][k - 1]) <= ITER_TOL
+            assert rel(y, ref.trace["y"][k - 1]) <= ITER_TOL
+
+
+def test_invalid_arguments(pkg):
+    qp = qpgen.random_small(n=5, m=3, seed=1)
+    bad = qpgen.QP(**{**qp.__dict__, "l": qp.u + 1})
+    with pytest.raises(pkg.HPRQPError) as e:
+        pkg.Solver(bad)
+    assert e.value.status == 4
+    c = qp.c.copy(); c[1] = np.nan
+    with pytest.raises(pkg.HPRQPError):
+        pkg.Solver(qpgen.QP(**{**qp.__dict__, "c": c}))
+    ci = qp.A_colidx.copy(); ci[-1] = 99
+    with pytest.raises(pkg.HPRQPError):
+        pkg.Solver(qpgen.QP(**{**qp.__dict__, "A_colidx": ci}))
+    with pkg.Solver(qp) as s:
+        with pytest.raises(pkg.HPRQPError):
+            s.solve(tol=1e-8, max_iter=0)
+        with pytest.raises(pkg.HPRQPError):
+            s.solve(tol=-1.0, max_iter=10)
