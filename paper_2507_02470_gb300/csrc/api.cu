@@ -46,6 +46,8 @@ struct hprqp_handle {
   bool solved = false;
   int64_t launches = 0;
   double last_lamA = 0, last_lamQ = 0, last_sigma0 = 1;
+  cudaStream_t side = nullptr;   // captures the bodies of the conditional nodes
+  bool conditional = false;      // the iteration graph selects step variants on the device
 };
 
 static thread_local std::string g_create_err;
@@ -233,6 +235,7 @@ static void release(hprqp_handle* h) {
   }
   if (h->hctrl) cudaFreeHost(h->hctrl);
   if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   cudaGetLastError();
   delete h;
@@ -543,6 +546,17 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   P.gridM = std::min(chunks(m), sms * per_sm);
   P.gridE = std::min(chunks(n), sms * 8);
   P.gridPre = (int)std::min<int64_t>(std::max<int64_t>(1, (toff + 7) / 8), sms * 8);
+  {
+    // lanes per factor row of the pre-pass: full warps only for long rows (the shuffle
+    // reduction costs FP64 instructions that short rows cannot amortise)
+    int64_t fnnz = 0, frows = 0;
+    for (auto& B : facs) {
+      fnnz += B.rp[B.rows];
+      frows += B.rows;
+    }
+    const double avg = frows ? (double)fnnz / (double)frows : 0.0;
+    P.gPre = avg < 8 ? 1 : avg < 32 ? 4 : avg < 96 ? 8 : 32;
+  }
   a.nbM = P.gridM;
   const int gmax = std::max(P.gridN, P.gridM);
   if ((st = zeros(h, &a.partL, (size_t)gmax * kWL))) return st;
@@ -643,6 +657,21 @@ extern "C" hprqp_status hprqp_set_warm_start(hprqp_handle* h, const double* x0, 
 static hprqp_status build_iter_graph(hprqp_handle* h) {
   if (h->g_iter) return HPRQP_OK;
   cudaGraph_t g;
+  // preferred: device-selected step variants through conditional nodes
+  if (!h->side) CU(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  cudaError_t be = build_conditional_graph(h->args, h->plan, h->stream, h->side, h->prm.iters_per_launch, &g);
+  if (be == cudaSuccess) {
+    cudaError_t ie = cudaGraphInstantiate(&h->g_iter, g, 0);
+    cudaGraphDestroy(g);
+    if (ie == cudaSuccess) {
+      h->conditional = true;
+      return HPRQP_OK;
+    }
+    h->g_iter = nullptr;
+  }
+  cudaGetLastError();
+  // fallback: every kernel launched each step, variants decided inside the kernels
+  h->conditional = false;
   CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int i = 0; i < h->prm.iters_per_launch && le == cudaSuccess; i++) {
@@ -843,7 +872,7 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   // ---- Algorithm 4 in graph launches of iters_per_launch steps; double-buffered done poll
   const int64_t per = h->prm.iters_per_launch;
   const int64_t max_launch = (max_iter + per - 1) / per + 2;
-  const int64_t nodes = per * kernels_per_iteration(a);
+  const int64_t nodes = h->conditional ? 1 : per * kernels_per_iteration(a);
   bool time_up = false;
   for (int64_t i = 0; i < max_launch; i++) {
     CU(h, cudaGraphLaunch(h->g_iter, h->stream));
@@ -883,6 +912,8 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   K.lambda_Q = lamQ;
   K.solve_seconds = std::chrono::duration<double>(t2 - t0).count();
   K.power_seconds = std::chrono::duration<double>(t1 - t0).count();
+  // conditional graph: only the bodies taken ran kernels (one step each, plus restarts)
+  if (h->conditional) h->launches += C.k * kernels_per_step(a) + C.r * kernels_per_restart(a);
   K.kernel_launches = h->launches;
   K.status = status;
   h->last_status = status;
@@ -907,18 +938,25 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
   double tot[HPRQP_PROF_KINDS] = {0};
   int cnt[HPRQP_PROF_KINDS] = {0};
   cudaError_t err = cudaSuccess;
+  Ctrl& C = *h->hctrl;
   for (int32_t i = 0; i < iters && err == cudaSuccess; i++) {
-    // a fresh record per kind and step: events of kinds a problem lacks stay unrecorded
-    cudaEvent_t (*evp)[2] = ev;
-    for (auto& e : ev) {
+    // the variant the device controller would select for this step
+    const int var = C.done ? 3 : C.ttest ? 2 : C.rtest ? 1 : 0;
+    if (var == 3) break;
+    for (auto& e : ev) {  // fresh events: kinds a step does not launch stay unrecorded
       cudaEventDestroy(e[0]);
       cudaEventDestroy(e[1]);
       cudaEventCreate(&e[0]);
       cudaEventCreate(&e[1]);
     }
-    err = launch_iteration(h->args, h->plan, h->stream, evp);
-    if (err == cudaSuccess) err = launch_restart(h->args, h->plan, h->stream, evp);
+    err = launch_step_var(h->args, h->plan, h->stream, var, ev);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    if (err == cudaSuccess && C.restart_pending && !C.done) {
+      err = launch_restart(h->args, h->plan, h->stream, ev);
+      if (err == cudaSuccess) err = cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    }
     for (int k = 0; k < HPRQP_PROF_KINDS && err == cudaSuccess; k++) {
       float t = 0.f;
       if (cudaEventElapsedTime(&t, ev[k][0], ev[k][1]) == cudaSuccess) {
@@ -934,8 +972,6 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
     cudaEventDestroy(e[1]);
   }
   if (err != cudaSuccess) return fail(h, HPRQP_CUDA_ERROR, "profile: %s", cudaGetErrorString(err));
-  // restart kinds: only the steps whose gated pass did work carry weight; the gated early
-  // exits are a few microseconds and are included in the mean of all steps
   for (int k = 0; k < HPRQP_PROF_KINDS; k++) ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
   h->solved = false;  // the iterate no longer belongs to a solve
   return HPRQP_OK;

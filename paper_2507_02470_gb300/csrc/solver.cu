@@ -1,616 +1,214 @@
-// Iteration kernels of HPR-QP (arXiv 2507.02470, Algorithm 4) for one problem instance.
+// Launch sequences of the single-instance HPR-QP solver and the CUDA graph that runs them.
 //
-// One inner step of Algorithm 4 is five fused passes; every vector element crosses HBM
-// once per pass and the Sec. 3.1 updates run in the epilogues of the operator products:
-//   K1  elementwise n: pending Halpern / restart update of (x, w_Q, Qw, A^*y), then
-//       eqs. (3.1)-(3.3): r_z, xbar = Prox(r_z), zbar, what = 2xbar - x, wbar_{1/2}
-//   K2  Q wbar_{1/2} (+ Q xbar on stopping tests); epilogue v = what + sigma(Qw - Qwbar_{1/2})
-//   K3  A v (+ A xbar); prologue Halpern on y; epilogue eq. (3.5): ybar = (Pi_K(r_y)-r_y)/(sigma lA)
-//   K4  A^T ybar; epilogue eq. (3.3): wbar = wbar_{1/2} + sigma/(1+sigma lQ) (A^*ybar - A^*y)
-//   K5  Q wbar; epilogue: R~ terms of the metric (2.12) and the Sec. 4.1 residuals; the last
-//       block to finish runs the controller (restart rules (3.6)-(3.8), termination).
-// The images Q w and A^* y of the Halpern iterate follow the Halpern recurrence (both maps
-// are linear), so only wbar_{1/2}, v, ybar and wbar meet an operator each step.
-// Restarts run one more gated pass for theta~ of eq. (3.11) and Algorithm 5.
+// Graph layout (one launch = iters_per_launch inner steps of Algorithm 4):
+//   dispatch -> [SWITCH step 0] -> [IF restart 0] -> [SWITCH step 1] -> [IF restart 1] -> ...
+// Each SWITCH node has four bodies: a plain step, a step that evaluates R~ (restart test,
+// Sec. 3.2), a step that evaluates the stopping rule (Sec. 4.1), and an empty body taken once
+// the solve is done.  The controller in the last block of every step sets the value of its own
+// restart IF node and of the next SWITCH node with cudaGraphSetConditional, so the host only
+// polls a done flag between launches.
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
-#include "solver.cuh"
+#include "kernels.cuh"
 
 namespace hprqp {
 
-// ------------------------------------------------------------------------------------ prox
-__device__ __forceinline__ double prox_phi(int phi, double r, double L, double U, double tau) {
-  if (phi == PHI_BOX) return iclamp(r, L, U);
-  double s = r - iclamp(r, -tau, tau);  // soft threshold
-  if (phi == PHI_L1) return s;
-  return iclamp(s, L, U);
+static RowKernel rowk(int kind, int var, int G) {
+  if (kind == K_Q1 || kind == K_Q2 || kind == K_APPLY_Q || kind == K_POWER_Q) return row_kernel_q(kind, var, G);
+  if (kind == K_A1 || kind == K_APPLY_A || kind == K_POWER_A) return row_kernel_a(kind, var, G);
+  return row_kernel_at(kind, var, G);
 }
 
-// phi^*(-z) contribution of one coordinate (0 * inf = 0; +inf when z points past an
-// infinite bound, which a Prox output cannot do)
-__device__ __forceinline__ double conj_phi_term(int phi, double z, double L, double U, double lam) {
-  if (phi == PHI_L1) return 0.0;
-  if (phi == PHI_BOX) {
-    double t = 0.0;
-    if (igt0(z)) t = -L * z;
-    else if (ilt0(z)) t = -U * z;
-    return t;
+using PreKernel = void (*)(Args, int);
+static PreKernel prek(int G, int tt) {
+#define HPRQP_PRE(GG) \
+  case GG:            \
+    return tt == 0 ? k_pre<GG, 0> : tt == 1 ? k_pre<GG, 1> : k_pre<GG, 2>;
+  switch (G) {
+    HPRQP_PRE(1)
+    HPRQP_PRE(4)
+    HPRQP_PRE(8)
+    default:
+      return tt == 0 ? k_pre<32, 0> : tt == 1 ? k_pre<32, 1> : k_pre<32, 2>;
   }
-  double best = -INFINITY;
-  if (!iisinf(L)) best = imax(best, -z * L - lam * iabs(L));
-  else if (z > lam) return INFINITY;
-  if (!iisinf(U)) best = imax(best, -z * U - lam * iabs(U));
-  else if (-z - lam > 0.0) return INFINITY;
-  if (L <= 0.0 && U >= 0.0) best = imax(best, 0.0);
-  return best;
+#undef HPRQP_PRE
 }
 
-// ------------------------------------------------------------------------------------ CSR pass
-// Row sums of a chunk of kChunk rows, G lanes per row, into shared rs0/rs1 (add: accumulate).
-template <int G, int NR>
-__device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* __restrict__ x0,
-                                          const double* __restrict__ x1, double* rs0, double* rs1, bool add) {
-  const int lane = threadIdx.x % G;
-  const int grp = threadIdx.x / G;
-  constexpr int NG = kThreads / G;
-#pragma unroll 1
-  for (int rr = grp; rr < kChunk; rr += NG) {
-    const int64_t row = row0 + rr;
-    double s0 = 0.0, s1 = 0.0;
-    if (row < M.rows) {
-      const int b = M.rp[row], e = M.rp[row + 1];
-      int k = b + lane;
-      for (; k + 3 * G < e; k += 4 * G) {
-        const int c0 = M.ci[k], c1 = M.ci[k + G], c2 = M.ci[k + 2 * G], c3 = M.ci[k + 3 * G];
-        const double v0 = M.v[k], v1 = M.v[k + G], v2 = M.v[k + 2 * G], v3 = M.v[k + 3 * G];
-        const double a0 = __ldg(x0 + c0), a1 = __ldg(x0 + c1), a2 = __ldg(x0 + c2), a3 = __ldg(x0 + c3);
-        s0 = fma(v0, a0, s0);
-        s0 = fma(v1, a1, s0);
-        s0 = fma(v2, a2, s0);
-        s0 = fma(v3, a3, s0);
-        if (NR == 2) {
-          const double b0 = __ldg(x1 + c0), b1 = __ldg(x1 + c1), b2 = __ldg(x1 + c2), b3 = __ldg(x1 + c3);
-          s1 = fma(v0, b0, s1);
-          s1 = fma(v1, b1, s1);
-          s1 = fma(v2, b2, s1);
-          s1 = fma(v3, b3, s1);
-        }
-      }
-      for (; k < e; k += G) {
-        const int c = M.ci[k];
-        const double vv = M.v[k];
-        s0 = fma(vv, __ldg(x0 + c), s0);
-        if (NR == 2) s1 = fma(vv, __ldg(x1 + c), s1);
-      }
-    }
-    if (G > 1) {
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o, G);
-        if (NR == 2) s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
-      }
-    }
-    if (lane == 0 && row < M.rows) {
-      rs0[rr] = add ? rs0[rr] + s0 : s0;
-      if (NR == 2) rs1[rr] = add ? rs1[rr] + s1 : s1;
-    }
+using ZxKernel = void (*)(Args);
+static ZxKernel zxk(int var) {
+  switch (var) {
+    case VAR_PLAIN: return k_zx<VAR_PLAIN>;
+    case VAR_R: return k_zx<VAR_R>;
+    case VAR_T: return k_zx<VAR_T>;
+    default: return k_zx<VAR_RUNTIME>;
   }
 }
 
-// All CSR-like parts of Q (explicit CSR and every B_f^T with its intermediate t_f) for a chunk.
-template <int G, int NR>
-__device__ __forceinline__ void q_csr_chunk(const QDev& Q, int64_t row0, const double* x0, const double* x1,
-                                            const double* t0, const double* t1, double* rs0, double* rs1) {
-  bool add = false;
-  if (Q.csr.rows) {
-    csr_chunk<G, NR>(Q.csr, row0, x0, x1, rs0, rs1, false);
-    add = true;
-  }
-  for (int f = 0; f < Q.nfac; f++) {
-    csr_chunk<G, NR>(Q.fact[f], row0, t0 + Q.toff[f], NR == 2 ? t1 + Q.toff[f] : nullptr, rs0, rs1, add);
-    add = true;
-  }
-  if (!add) {
-    for (int rr = threadIdx.x; rr < kChunk; rr += kThreads) {
-      rs0[rr] = 0.0;
-      if (NR == 2) rs1[rr] = 0.0;
-    }
-  }
-}
+// Optional per-kind timing: ev[kind][0/1] recorded around every launch of that kind.
+#define TIMED(kind, launch)                  \
+  do {                                       \
+    if (ev) cudaEventRecord(ev[kind][0], s); \
+    launch;                                  \
+    if (ev) cudaEventRecord(ev[kind][1], s); \
+  } while (0)
 
-// Row-local parts of (Q x)_j: diagonal, symmetric band, and F_g^T t_g of the dense factors.
-__device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double* __restrict__ x,
-                                          const double* __restrict__ t, bool with_dense) {
-  double acc = 0.0;
-  if (Q.diag) acc = Q.diag[j] * x[j];
-  for (int k = 0; k < Q.ndia; k++) {
-    const int o = Q.dia_off[k];
-    const double* d = Q.dia + (size_t)k * Q.n;
-    if (o == 0) {
-      acc = fma(d[j], x[j], acc);
-    } else {
-      if (j + o < Q.n) acc = fma(d[j], x[j + o], acc);
-      if (j - o >= 0) acc = fma(d[j - o], x[j - o], acc);
-    }
+// One inner step in variant `var`; the last kernel of the step receives the handles.
+cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, const Handles& hd,
+                        cudaEvent_t (*ev)[2]) {
+  const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
+  const Handles none;
+  const int tt = var == VAR_T ? 1 : var == VAR_RUNTIME ? 2 : 0;
+  TIMED(0, (zxk(var)<<<p.gridE, kThreads, 0, s>>>(a)));
+  if (HQ) {
+    if (pre) TIMED(1, (prek(p.gPre, tt)<<<p.gridPre, kThreads, 0, s>>>(a, 0)));
+    TIMED(2, (rowk(K_Q1, var, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, HA ? none : hd)));
   }
-  if (with_dense) {
-    for (int g = 0; g < Q.ndense; g++) {
-      const double* F = Q.dense[g];
-      const double* tg = t + Q.toff[Q.nfac + g];
-      const int64_t p = Q.dense_p[g];
-      for (int64_t r = 0; r < p; r++) acc = fma(F[(size_t)r * Q.n + j], tg[r], acc);
-    }
-  }
-  return acc;
-}
-
-// ------------------------------------------------------------------------------------ K1
-__global__ void __launch_bounds__(kThreads) k_zx(Args a) {
-  const Ctrl* __restrict__ C = a.C;
-  if (C->done) return;
-  const int mode = C->mode;
-  const double ha = C->ha, hb = C->hb, sigma = C->sigma, c1 = C->c1, c2 = C->c2, tau = C->tau,
-               inv_sigma = C->inv_sigma;
-  const bool ttest = C->ttest;
-  const bool HQ = a.Q.present(), HA = a.m > 0;
-  const int phi = a.phi;
-  const Vec& V = a.V;
-  // with m = 0 the y-step is absent and wbar = wbar_{1/2}: write it straight to wb;
-  // with Q = 0, v = what (K2 is skipped)
-  double* whout = HA ? V.wh : V.wb;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.n; j += stride) {
-    double x, w = 0.0, qw = 0.0, aty = 0.0;
-    if (mode == 1) {
-      // Halpern: u = 1/(i+2) u^{r,0} + (i+1)/(i+2) (2 ubar - u)
-      x = fma(hb, fma(2.0, V.xb[j], -V.x[j]), ha * V.x0[j]);
-      V.x[j] = x;
-      if (HQ) {
-        w = fma(hb, fma(2.0, V.wb[j], -V.w[j]), ha * V.w0[j]);
-        qw = fma(hb, fma(2.0, V.Qwb[j], -V.Qw[j]), ha * V.Qw0[j]);
-        V.w[j] = w;
-        V.Qw[j] = qw;
-      }
-      if (HA) {
-        aty = fma(hb, fma(2.0, V.ATyb[j], -V.ATy[j]), ha * V.ATy0[j]);
-        V.ATy[j] = aty;
-      }
-    } else if (mode == 2) {
-      // restart: u^{r+1,0} = ubar^{r,tau_r}
-      x = V.xb[j];
-      V.x[j] = x;
-      V.x0[j] = x;
-      if (HQ) {
-        w = V.wb[j];
-        qw = V.Qwb[j];
-        V.w[j] = w;
-        V.w0[j] = w;
-        V.Qw[j] = qw;
-        V.Qw0[j] = qw;
-      }
-      if (HA) {
-        aty = V.ATyb[j];
-        V.ATy[j] = aty;
-        V.ATy0[j] = aty;
-      }
-    } else {
-      x = V.x[j];
-      if (HQ) {
-        w = V.w[j];
-        qw = V.Qw[j];
-      }
-      if (HA) aty = V.ATy[j];
-    }
-    // eq. (3.1)-(3.2)
-    double g = -V.c[j];
-    if (HQ) g -= qw;
-    if (HA) g += aty;
-    const double rz = fma(sigma, g, x);
-    const double xbar = prox_phi(phi, rz, V.L[j], V.U[j], tau);
-    V.xb[j] = xbar;
-    if (ttest) V.zb[j] = (xbar - rz) * inv_sigma;
-    // eq. (3.3)
-    const double xh = fma(2.0, xbar, -x);
-    if (HQ) whout[j] = fma(c2, xh, c1 * w);
-    else if (HA) V.v[j] = xh;
-  }
-}
-
-// ------------------------------------------------------------------------------------ factor pre-pass
-// t = B_f x for every factor term, t = F_g x for every dense term (one warp per row).
-// which: 0 -> x = wh (and xb on stopping tests) into t1;  1 -> x = wb into t2;
-//        2 -> x = A^*ybar - A^*y^{r,0} into t2 (restart);  3 -> x = ain into t1 (apply);
-//        4 -> x = pv into t1 (power method)
-__global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) {
-  const Ctrl* __restrict__ C = a.C;
-  if (which <= 2 && C->done) return;
-  if (which == 2 && !C->restart_pending) return;
-  if (which == 4 && C->pw_done) return;
-  const QDev& Q = a.Q;
-  const Vec& V = a.V;
-  const bool two = (which == 0) && C->ttest;
-  const double* x0 = which == 0 ? (a.m > 0 ? V.wh : V.wb) : which == 1 ? V.wb : which == 3 ? a.V.ain
-                     : which == 4 ? V.pv : nullptr;
-  const double* x1 = V.xb;
-  double* t = (which == 0 || which >= 3) ? V.t1 : V.t2;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = warp; r < Q.tlen; r += nwarps) {
-    // locate the term that owns row r
-    int term = 0;
-    const int nt = Q.nfac + Q.ndense;
-    while (term + 1 < nt && r >= Q.toff[term + 1]) term++;
-    const int64_t rl = r - Q.toff[term];
-    double s0 = 0.0, s1 = 0.0;
-    if (term < Q.nfac) {
-      const Csr& B = Q.fac[term];
-      const int b = B.rp[rl], e = B.rp[rl + 1];
-      for (int k = b + lane; k < e; k += 32) {
-        const int c = B.ci[k];
-        const double bv = B.v[k];
-        double xc;
-        if (which == 2) xc = __ldg(V.ATyb + c) - __ldg(V.ATy0 + c);
-        else xc = __ldg(x0 + c);
-        s0 = fma(bv, xc, s0);
-        if (two) s1 = fma(bv, __ldg(x1 + c), s1);
-      }
-    } else {
-      const int g = term - Q.nfac;
-      const double* F = Q.dense[g] + (size_t)rl * Q.n;
-      for (int64_t j = lane; j < Q.n; j += 32) {
-        double xc;
-        if (which == 2) xc = V.ATyb[j] - V.ATy0[j];
-        else xc = x0[j];
-        s0 = fma(F[j], xc, s0);
-        if (two) s1 = fma(F[j], x1[j], s1);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_down_sync(0xffffffffu, s0, o);
-      if (two) s1 += __shfl_down_sync(0xffffffffu, s1, o);
-    }
-    if (lane == 0) {
-      t[r] = s0;
-      if (two) t[Q.tlen + r] = s1;
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------------ controller
-
-// One pass of the Sec. 3.2 / Sec. 4.1 logic after an inner step; Ls: end-of-iteration
-// sums, P3: y-step sums.  Runs on one thread.
-__device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const double* P3) {
-  const long long kd = C.k + 1;
-  bool bad = false;
-  double R = 0.0;
-  if (C.rtest) {
-    // ||u - ubar||_M^2 = sigma th1 + th2/sigma + sigma^2 th3/(1+sigma lQ) + 2<dx, A^*dy - Q dw>
-    const double th1 = C.lamA * P3[0] + C.lamQ * Ls[1] - 2.0 * Ls[2];
-    const double R2 = C.sigma * th1 + Ls[0] * C.inv_sigma + C.sigma * Ls[3] + 2.0 * Ls[4];
-    if (!isfinite(R2)) bad = true;
-    R = sqrt(fmax(R2, 0.0));
-    C.R = R;
-  }
-  if (C.ttest) {
-    const double eta_p = P3[1] / (1.0 + fmax(C.b_inf, P3[2]));
-    const double eta_d = Ls[5] / (1.0 + fmax(C.c_inf, fmax(Ls[6], Ls[7])));
-    const double pobj = 0.5 * Ls[8] + Ls[9] + (C.phi != PHI_BOX ? C.lambda * Ls[10] : 0.0);
-    const double dobj = -0.5 * Ls[8] + P3[3] - Ls[11];
-    const double eta_g = fabs(pobj - dobj) / (1.0 + fmax(fabs(pobj), fabs(dobj)));
-    C.eta_p = eta_p;
-    C.eta_d = eta_d;
-    C.eta_gap = eta_g;
-    C.pobj = pobj;
-    C.dobj = dobj;
-    if (isnan(eta_p) || isnan(eta_d) || isnan(eta_g) || isinf(pobj) || isinf(dobj)) bad = true;
-    if (bad) {
-      C.status = 3;
-      C.done = 1;
-      C.k = kd;
-      return;
-    }
-    if (fmax(eta_p, fmax(eta_d, eta_g)) <= C.tol) {
-      C.status = 0;
-      C.done = 1;
-      C.k = kd;
-      return;
-    }
-    if (kd >= C.max_iter) {
-      C.status = 1;
-      C.done = 1;
-      C.k = kd;
-      return;
-    }
-  }
-  if (bad) {
-    C.status = 3;
-    C.done = 1;
-    C.k = kd;
-    return;
-  }
-  bool restart = false;
-  if (C.rtest && !C.restart_off) {
-    if (C.t == 0) {
-      C.R_r0 = R;
-    } else {
-      restart = (R <= C.alpha1 * C.R_r0) || (R <= C.alpha2 * C.R_r0 && R > C.R_prev) ||
-                ((double)(C.t + 1) >= C.alpha3 * (double)kd);
-    }
-    C.R_prev = R;
-  }
-  if (restart) {
-    if (C.r == 0) C.R_first = R;
-    const double ratio = C.R_first > 0.0 ? R / C.R_first : 0.0;
-    C.ratio = ratio;
-    C.R_last = R;
-    if (!C.sigma_fixed) C.restart_pending = 1;
-    if (ratio <= C.ratio_tight) C.alpha3 = C.alpha3_tight;
-    C.mode = 2;
-    C.t = 0;
-    C.r++;
-  } else {
-    const double i = C.halpern_total ? (double)C.k : (double)C.t;
-    C.ha = 1.0 / (i + 2.0);
-    C.hb = (i + 1.0) / (i + 2.0);
-    C.mode = 1;
-    C.t++;
-  }
-  C.k = kd;
-  C.rtest = !C.restart_off && ((C.t == 0) || ((C.k + 1) % C.restart_every == 0));
-  C.ttest = ((C.k + 1) % C.check_every == 0) || (C.k + 1 >= C.max_iter);
-}
-
-// Per-row contributions to the R~ and stopping-rule sums (end of an inner step).
-struct EndTerms {
-  double s[kWL];
-  __device__ void zero() {
-#pragma unroll
-    for (int i = 0; i < kWL; i++) s[i] = 0.0;
-  }
-};
-constexpr unsigned kEndMax = (1u << 5) | (1u << 6) | (1u << 7);
-
-__device__ __forceinline__ void end_row(EndTerms& T, const Args& a, int64_t j, bool rtest, bool ttest, bool HQ,
-                                        bool HA, double Qwb_j) {
-  const Vec& V = a.V;
-  const double xb = V.xb[j];
-  double atyb = 0.0;
-  if (HA) atyb = V.ATyb[j];
-  if (rtest) {
-    const double dx = V.x[j] - xb;
-    double qdw = 0.0, ady = 0.0;
-    if (HQ) qdw = V.Qw[j] - Qwb_j;
-    if (HA) ady = V.ATy[j] - atyb;
-    T.s[0] = fma(dx, dx, T.s[0]);
+  if (HA) {
+    TIMED(3, (rowk(K_A1, var, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none)));
+    TIMED(4, (rowk(K_AT, var, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, HQ ? none : hd)));
     if (HQ) {
-      const double dw = V.w[j] - V.wb[j];
-      T.s[1] = fma(dw, qdw, T.s[1]);
-      if (HA) {
-        T.s[2] = fma(qdw, ady, T.s[2]);
-        T.s[3] = fma(ady, V.Qwh[j] - Qwb_j, T.s[3]);
-      }
+      if (pre) TIMED(5, (prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 1)));
+      TIMED(6, (rowk(K_Q2, var, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, hd)));
     }
-    T.s[4] = fma(dx, ady - qdw, T.s[4]);
   }
-  if (ttest) {
-    const double qxb = HQ ? V.Qxb[j] : 0.0;
-    const double cj = V.c[j];
-    const double rd = iabs(atyb - qxb + V.zb[j] - cj);
-    T.s[5] = imax(T.s[5], rd);
-    T.s[6] = imax(T.s[6], iabs(atyb));
-    T.s[7] = imax(T.s[7], iabs(qxb));
-    T.s[8] = fma(xb, qxb, T.s[8]);
-    T.s[9] = fma(cj, xb, T.s[9]);
-    if (a.phi != PHI_BOX) T.s[10] += iabs(xb);
-    T.s[11] += conj_phi_term(a.phi, V.zb[j], V.L[j], V.U[j], a.C->lambda);
+  if (!HQ && !HA) {
+    // neither operator: the controller still needs its (empty-operator) pass
+    TIMED(4, (rowk(K_AT, var, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, hd)));
   }
+  return cudaGetLastError();
 }
 
-// Reduce the end terms of this block, elect the last block, run the controller.
-__device__ __forceinline__ void end_iteration(EndTerms& T, const Args& a, bool active) {
-  __shared__ double red[kWL * 32];
-  if (active) {
-    block_reduce<kWL>(T.s, kEndMax, red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int i = 0; i < kWL; i++) a.partL[(size_t)blockIdx.x * kWL + i] = T.s[i];
-    }
-  } else if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < kWL; i++) a.partL[(size_t)blockIdx.x * kWL + i] = 0.0;
-  }
-  if (!last_block(&a.counters[0])) return;
-  double Ls[kWL], P3[kW3];
-  if (active) {
-    reduce_partials<kWL>(a.partL, gridDim.x, kWL, kEndMax, Ls, red);
-  } else {
-#pragma unroll
-    for (int i = 0; i < kWL; i++) Ls[i] = 0.0;
-  }
-  __syncthreads();
-  if (a.m > 0 && active) {
-    reduce_partials<kW3>(a.part3, a.nbM, kW3, 0x6u, P3, red);
-  } else {
-#pragma unroll
-    for (int i = 0; i < kW3; i++) P3[i] = 0.0;
-  }
-  if (threadIdx.x == 0) controller(*a.C, Ls, P3);
+cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2]) {
+  if (a.Q.present() && a.m > 0 && a.Q.has_pre()) TIMED(7, (prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 2)));
+  const int G = p.gQ;
+  void (*kr)(Args) = G == 1 ? k_restart<1> : G == 2 ? k_restart<2> : G == 4 ? k_restart<4>
+                     : G == 8 ? k_restart<8> : G == 16 ? k_restart<16> : k_restart<32>;
+  TIMED(8, (kr<<<p.gridN, kThreads, 0, s>>>(a)));
+  return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------ row kernels
-template <int G, int KIND>
-__global__ void __launch_bounds__(kThreads) k_rows(Args a) {
-  Ctrl* __restrict__ C = a.C;
-  if (KIND <= K_Q2 && C->done) return;
-  if ((KIND == K_POWER_Q || KIND == K_POWER_A || KIND == K_APPLY_AT_P) && C->pw_done) return;
-  __shared__ double rs0[kChunk];
-  __shared__ double rs1[kChunk];
-  const Vec& V = a.V;
-  const QDev& Q = a.Q;
-  const bool HQ = Q.present(), HA = a.m > 0;
-  const bool ttest = (KIND <= K_Q2) ? (bool)C->ttest : false;
-  const bool rtest = (KIND <= K_Q2) ? (bool)C->rtest : false;
-  const int64_t rows = (KIND == K_A1 || KIND == K_APPLY_A || KIND == K_POWER_A) ? a.m : a.n;
-  const int64_t nchunks = (rows + kChunk - 1) / kChunk;
-  // per-kind scalars
-  const double sigma = C->sigma, s = C->s, slA = C->slA, inv_slA = C->inv_slA;
-  const int mode = C->mode;
-  const double ha = C->ha, hb = C->hb;
-  const bool last_of_iter = (KIND == K_Q2) || (KIND == K_Q1 && !HA) || (KIND == K_AT && !HQ);
-  EndTerms T;
-  T.zero();
-  double y3[kW3] = {0.0, 0.0, 0.0, 0.0};
-  double pw[kWP] = {0.0, 0.0};
+cudaError_t launch_iteration(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2]) {
+  return launch_step(a, p, s, VAR_RUNTIME, Handles(), ev);
+}
 
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t row0 = ch * kChunk;
-    // ---- phase 1: CSR row sums into shared memory
-    if (KIND == K_Q1) {
-      if (ttest) q_csr_chunk<G, 2>(Q, row0, HA ? V.wh : V.wb, V.xb, V.t1, V.t1 + Q.tlen, rs0, rs1);
-      else q_csr_chunk<G, 1>(Q, row0, HA ? V.wh : V.wb, nullptr, V.t1, nullptr, rs0, rs1);
-    } else if (KIND == K_Q2) {
-      q_csr_chunk<G, 1>(Q, row0, V.wb, nullptr, V.t2, nullptr, rs0, rs1);
-    } else if (KIND == K_APPLY_Q) {
-      q_csr_chunk<G, 1>(Q, row0, V.ain, nullptr, V.t1, nullptr, rs0, rs1);
-    } else if (KIND == K_POWER_Q) {
-      q_csr_chunk<G, 1>(Q, row0, V.pv, nullptr, V.t1, nullptr, rs0, rs1);
-    } else if (KIND == K_A1) {
-      if (ttest) csr_chunk<G, 2>(a.A, row0, V.v, V.xb, rs0, rs1, false);
-      else csr_chunk<G, 1>(a.A, row0, V.v, nullptr, rs0, rs1, false);
-    } else if (KIND == K_APPLY_A) {
-      csr_chunk<G, 1>(a.A, row0, V.ain, nullptr, rs0, rs1, false);
-    } else if (KIND == K_POWER_A) {
-      csr_chunk<G, 1>(a.A, row0, V.ptmp, nullptr, rs0, rs1, false);
-    } else if (KIND == K_AT) {
-      csr_chunk<G, 1>(a.AT, row0, V.yb, nullptr, rs0, rs1, false);
-    } else if (KIND == K_APPLY_AT) {
-      csr_chunk<G, 1>(a.AT, row0, V.ain, nullptr, rs0, rs1, false);
-    } else if (KIND == K_APPLY_AT_P) {
-      csr_chunk<G, 1>(a.AT, row0, V.pv, nullptr, rs0, rs1, false);
-    }
-    __syncthreads();
-    // ---- phase 2: thread per row, full warps
-    const int64_t j = row0 + threadIdx.x;
-    if (j < rows) {
-      const double r0 = rs0[threadIdx.x];
-      if (KIND == K_Q1) {
-        const double* src = HA ? V.wh : V.wb;
-        const double qwh = r0 + q_local(Q, j, src, V.t1, true);
-        double qxb = 0.0;
-        if (ttest) {
-          qxb = rs1[threadIdx.x] + q_local(Q, j, V.xb, V.t1 + Q.tlen, true);
-          V.Qxb[j] = qxb;
-        }
-        if (HA) {
-          // v = what + sigma (Q w - Q wbar_{1/2})   (eq. (3.5), second form)
-          const double xh = fma(2.0, V.xb[j], -V.x[j]);
-          V.v[j] = fma(sigma, V.Qw[j] - qwh, xh);
-          if (rtest) V.Qwh[j] = qwh;
-        } else {
-          V.Qwb[j] = qwh;  // m = 0: wbar = wbar_{1/2}
-          end_row(T, a, j, rtest, ttest, HQ, HA, qwh);
-        }
-      } else if (KIND == K_Q2) {
-        const double qwb = r0 + q_local(Q, j, V.wb, V.t2, true);
-        V.Qwb[j] = qwb;
-        end_row(T, a, j, rtest, ttest, HQ, HA, qwb);
-      } else if (KIND == K_A1) {
-        // Halpern / restart on y, then eq. (3.5)
-        double y;
-        if (mode == 1) {
-          y = fma(hb, fma(2.0, V.yb[j], -V.y[j]), ha * V.y0[j]);
-          V.y[j] = y;
-        } else if (mode == 2) {
-          y = V.yb[j];
-          V.y[j] = y;
-          V.y0[j] = y;
-        } else {
-          y = V.y[j];
-        }
-        const double lo = V.l[j], hi = V.u[j];
-        const double ry = fma(-slA, y, r0);
-        const double yb = (iclamp(ry, lo, hi) - ry) * inv_slA;
-        V.yb[j] = yb;
-        if (rtest) {
-          const double dy = y - yb;
-          y3[0] = fma(dy, dy, y3[0]);
-        }
-        if (ttest) {
-          const double ax = rs1[threadIdx.x];
-          y3[1] = imax(y3[1], iabs(ax - iclamp(ax, lo, hi)));
-          y3[2] = imax(y3[2], iabs(ax));
-          double t = 0.0;
-          if (igt0(yb)) t = lo * yb;
-          else if (ilt0(yb)) t = hi * yb;
-          y3[3] += t;
-        }
-      } else if (KIND == K_AT) {
-        V.ATyb[j] = r0;
-        if (HQ) {
-          // wbar = wbar_{1/2} + sigma/(1+sigma lQ) (A^* ybar - A^* y)   (eq. (3.3))
-          V.wb[j] = fma(s, r0 - V.ATy[j], V.wh[j]);
-        } else {
-          end_row(T, a, j, rtest, ttest, HQ, HA, 0.0);
-        }
-      } else if (KIND == K_APPLY_Q) {
-        V.aout[j] = r0 + q_local(Q, j, V.ain, V.t1, true);
-      } else if (KIND == K_APPLY_A || KIND == K_APPLY_AT) {
-        V.aout[j] = r0;
-      } else if (KIND == K_APPLY_AT_P) {
-        V.ptmp[j] = r0;
-      } else if (KIND == K_POWER_Q || KIND == K_POWER_A) {
-        const double wv = KIND == K_POWER_Q ? r0 + q_local(Q, j, V.pv, V.t1, true) : r0;
-        V.pw[j] = wv;
-        pw[0] = fma(V.pv[j], wv, pw[0]);
-        pw[1] = fma(wv, wv, pw[1]);
-      }
-    }
-    __syncthreads();
-  }
+cudaError_t launch_step_var(const Args& a, const Plan& p, cudaStream_t s, int var, cudaEvent_t (*ev)[2]) {
+  return launch_step(a, p, s, var, Handles(), ev);
+}
 
-  // ---- block reductions / controllers
-  if (KIND == K_A1) {
-    __shared__ double red3[kW3 * 32];
-    if (rtest || ttest) {
-      block_reduce<kW3>(y3, 0x6u, red3);
-    }
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int i = 0; i < kW3; i++) a.part3[(size_t)blockIdx.x * kW3 + i] = y3[i];
-    }
+int kernels_per_step(const Args& a) {
+  const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
+  int k = 1;
+  if (HQ) k += 1 + (pre ? 1 : 0);
+  if (HA) k += 2 + (HQ ? 1 + (pre ? 1 : 0) : 0);
+  if (!HQ && !HA) k += 1;
+  return k;
+}
+int kernels_per_restart(const Args& a) { return 1 + ((a.Q.present() && a.m > 0 && a.Q.has_pre()) ? 1 : 0); }
+int kernels_per_iteration(const Args& a) { return kernels_per_step(a) + kernels_per_restart(a); }
+
+// ------------------------------------------------------------------------------------ dispatch
+__global__ void k_dispatch(Args a, Handles hd) {
+  if (threadIdx.x == 0 && hd.has_next) cudaGraphSetConditional(hd.sw_next, next_variant(*a.C));
+}
+
+static cudaError_t add_cond(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            unsigned size, cudaGraph_t* bodies) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = size;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, dv.data(), nullptr, dv.size(), &np);
+  if (e != cudaSuccess) return e;
+  for (unsigned b = 0; b < size; b++) bodies[b] = np.conditional.phGraph_out[b];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Builds the conditional graph of `steps` inner steps on stream s (side stream s2 captures the
+// bodies).  Returns the captured graph in *out.
+cudaError_t build_conditional_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int steps,
+                                    cudaGraph_t* out) {
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+  std::vector<cudaGraphConditionalHandle> sw(steps), rs(steps);
+  for (int i = 0; i < steps && e == cudaSuccess; i++) {
+    e = cudaGraphConditionalHandleCreate(&sw[i], g, 3u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&rs[i], g, 0u, cudaGraphCondAssignDefault);
   }
-  if (last_of_iter) end_iteration(T, a, rtest || ttest);
-  if (KIND == K_POWER_Q || KIND == K_POWER_A) {
-    __shared__ double redp[kWP * 32];
-    block_reduce<kWP>(pw, 0u, redp);
-    if (threadIdx.x == 0) {
-      a.partP[(size_t)blockIdx.x * kWP] = pw[0];
-      a.partP[(size_t)blockIdx.x * kWP + 1] = pw[1];
-    }
-    if (last_block(&a.counters[2])) {
-      double tot[kWP];
-      reduce_partials<kWP>(a.partP, gridDim.x, kWP, 0u, tot, redp);
-      if (threadIdx.x == 0) {
-        // Rayleigh quotient of the unit vector v, Sec. 4.1 power method
-        const double lnew = tot[0], nw = sqrt(tot[1]);
-        if (nw == 0.0 || !isfinite(nw)) {
-          C->pw_lam = 0.0;
-          C->pw_done = 1;
-          C->pw_scale = 0.0;
-        } else {
-          const bool conv = (C->pw_it > 0) && fabs(lnew - C->pw_lam) <= C->pw_tol * fabs(lnew);
-          C->pw_lam = lnew;
-          C->pw_scale = 1.0 / nw;
-          C->pw_it++;
-          if (conv || C->pw_it >= C->pw_max) C->pw_done = 2;  // 2: normalise once more, then stop
-        }
+  if (e == cudaSuccess) {
+    Handles h0;
+    h0.sw_next = sw[0];
+    h0.has_next = 1;
+    k_dispatch<<<1, 32, 0, s>>>(a, h0);
+    e = cudaGetLastError();
+  }
+  for (int i = 0; i < steps && e == cudaSuccess; i++) {
+    cudaGraph_t bodies[4];
+    e = add_cond(s, sw[i], cudaGraphCondTypeSwitch, 4, bodies);
+    for (int v = 0; v < 3 && e == cudaSuccess; v++) {
+      e = cudaStreamBeginCaptureToGraph(s2, bodies[v], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) break;
+      Handles hd;
+      hd.rs_cur = rs[i];
+      hd.has_rs = 1;
+      if (i + 1 < steps) {
+        hd.sw_next = sw[i + 1];
+        hd.has_next = 1;
       }
+      cudaError_t le = launch_step(a, p, s2, v, hd, nullptr);
+      cudaGraph_t tmp;
+      e = cudaStreamEndCapture(s2, &tmp);
+      if (le != cudaSuccess) e = le;
     }
+    // body 3 stays empty: nothing to do once the solve is finished
+    if (e != cudaSuccess) break;
+    cudaGraph_t rb[1];
+    e = add_cond(s, rs[i], cudaGraphCondTypeIf, 1, rb);
+    if (e != cudaSuccess) break;
+    e = cudaStreamBeginCaptureToGraph(s2, rb[0], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) break;
+    cudaError_t le = launch_restart(a, p, s2, nullptr);
+    cudaGraph_t tmp;
+    e = cudaStreamEndCapture(s2, &tmp);
+    if (le != cudaSuccess) e = le;
   }
+  cudaGraph_t gout = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(s, &gout);
+  if (e == cudaSuccess) e = ee;
+  if (e != cudaSuccess) {
+    if (gout) cudaGraphDestroy(gout);
+    cudaGetLastError();
+    return e;
+  }
+  *out = gout;
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------ apply / power
+cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s) {
+  const Handles none;
+  if (op == 0) {
+    rowk(K_APPLY_A, 0, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none);
+  } else if (op == 1) {
+    rowk(K_APPLY_AT, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
+  } else {
+    if (a.Q.has_pre()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 3);
+    rowk(K_APPLY_Q, 0, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, none);
+  }
+  return cudaGetLastError();
 }
 
 // v <- w / ||w|| (power method); dim elements
@@ -620,12 +218,10 @@ __global__ void k_pw_norm(Args a, int64_t dim) {
   const double sc = C->pw_scale;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim; j += stride) a.V.pv[j] = a.V.pw[j] * sc;
-  // the grid-wide flag flip from 2 to 1 happens in k_pw_flag
 }
 __global__ void k_pw_flag(Args a) {
   if (a.C->pw_done == 2) a.C->pw_done = 1;
 }
-
 __global__ void k_pw_start(Args a, int64_t dim) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += stride) {
@@ -635,149 +231,27 @@ __global__ void k_pw_start(Args a, int64_t dim) {
   }
 }
 
-// ------------------------------------------------------------------------------------ restart (Alg. 5)
-__device__ void sigma_argmin_dev(double t1, double t2, double t3, double lq, int golden, double* out) {
-  double hi = sqrt(t2 / t1);
-  if (t3 <= 0.0 || lq <= 0.0) {
-    *out = hi;
-    return;
-  }
-  double lo = sqrt(t2 / (t1 + t3 / lq));
-  if (!golden) {
-    for (int it = 0; it < 200 && (hi - lo) > 4.0e-16 * hi; it++) {
-      const double mid = 0.5 * (lo + hi);
-      const double d = 1.0 + lq * mid;
-      const double fp = t1 - t2 / (mid * mid) + t3 * mid * (2.0 + lq * mid) / (d * d);
-      if (fp > 0.0) hi = mid;
-      else lo = mid;
-    }
-    *out = 0.5 * (lo + hi);
-    return;
-  }
-  const double gr = 0.6180339887498949;
-  double A = log(lo), B = log(hi);
-  double x1 = B - gr * (B - A), x2 = A + gr * (B - A);
-  auto f = [&](double u) {
-    const double s = exp(u);
-    return t1 * s + t2 / s + s * s * t3 / (1.0 + lq * s);
-  };
-  double f1 = f(x1), f2 = f(x2);
-  for (int it = 0; it < 200 && (B - A) > 1e-12; it++) {
-    if (f1 < f2) {
-      B = x2; x2 = x1; f2 = f1;
-      x1 = B - gr * (B - A);
-      f1 = f(x1);
-    } else {
-      A = x1; x1 = x2; f1 = f2;
-      x2 = A + gr * (B - A);
-      f2 = f(x2);
-    }
-  }
-  *out = exp(0.5 * (A + B));
+// which 0: lambda_1(A A^*) on R^m; 1: lambda_1(Q) on R^n
+cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s) {
+  const int64_t dim = which == 0 ? a.m : a.n;
+  k_pw_start<<<p.gridE, kThreads, 0, s>>>(a, dim);
+  return cudaGetLastError();
 }
 
-constexpr unsigned kRMax = 0u;
-
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_restart(Args a) {
-  Ctrl* __restrict__ C = a.C;
-  if (C->done || !C->restart_pending) return;
-  __shared__ double rs0[kChunk];
-  __shared__ double red[kWR * 32];
-  const Vec& V = a.V;
-  const QDev& Q = a.Q;
-  const bool HQ = Q.present(), HA = a.m > 0;
-  double S[kWR] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const int64_t nchunks = (a.n + kChunk - 1) / kChunk;
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t row0 = ch * kChunk;
-    // d = A^*ybar - A^*y^{r,0}; explicit CSR part of <d, Q d> (gathered on the fly)
-    if (HQ && HA && Q.csr.rows) {
-      const int G1 = G;
-      const int lane = threadIdx.x % G1, grp = threadIdx.x / G1;
-      for (int rr = grp; rr < kChunk; rr += kThreads / G1) {
-        const int64_t row = row0 + rr;
-        double s0 = 0.0;
-        if (row < a.n) {
-          for (int k = Q.csr.rp[row] + lane; k < Q.csr.rp[row + 1]; k += G1) {
-            const int c = Q.csr.ci[k];
-            s0 = fma(Q.csr.v[k], V.ATyb[c] - V.ATy0[c], s0);
-          }
-        }
-        for (int o = G1 / 2; o > 0; o >>= 1) s0 += __shfl_down_sync(0xffffffffu, s0, o, G1);
-        if (lane == 0 && row < a.n) rs0[rr] = s0;
-      }
-    } else {
-      rs0[threadIdx.x] = 0.0;
-    }
-    __syncthreads();
-    const int64_t j = row0 + threadIdx.x;
-    if (j < a.n) {
-      const double dx = V.xb[j] - V.x0[j];
-      S[3] = fma(dx, dx, S[3]);
-      if (HQ) {
-        const double dw = V.wb[j] - V.w0[j];
-        const double qdw = V.Qwb[j] - V.Qw0[j];
-        S[1] = fma(dw, qdw, S[1]);
-        if (HA) {
-          const double d = V.ATyb[j] - V.ATy0[j];
-          S[2] = fma(qdw, d, S[2]);
-          // <d, (diag + band + CSR) d>; the factor parts come from ||t2||^2 below
-          double qd = rs0[threadIdx.x];
-          if (Q.diag) qd = fma(Q.diag[j], d, qd);
-          for (int k = 0; k < Q.ndia; k++) {
-            const int o = Q.dia_off[k];
-            const double* dg = Q.dia + (size_t)k * Q.n;
-            if (o == 0) {
-              qd = fma(dg[j], d, qd);
-            } else {
-              if (j + o < a.n) qd = fma(dg[j], V.ATyb[j + o] - V.ATy0[j + o], qd);
-              if (j - o >= 0) qd = fma(dg[j - o], V.ATyb[j - o] - V.ATy0[j - o], qd);
-            }
-          }
-          S[4] = fma(d, qd, S[4]);
-        }
-      }
-    }
-    __syncthreads();
+cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s) {
+  const int64_t dim = which == 0 ? a.m : a.n;
+  const Handles none;
+  // normalise the previous w into v (the first call normalises the start vector)
+  k_pw_norm<<<p.gridE, kThreads, 0, s>>>(a, dim);
+  k_pw_flag<<<1, 1, 0, s>>>(a);
+  if (which == 0) {
+    rowk(K_APPLY_AT_P, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
+    rowk(K_POWER_A, 0, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none);
+  } else {
+    if (a.Q.has_pre()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 4);
+    rowk(K_POWER_Q, 0, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, none);
   }
-  // ||B_f d||^2 and ||F_g d||^2 from the pre-pass, and ||ybar - y^{r,0}||^2
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
-  if (HQ && HA) {
-    for (int64_t r = gt; r < Q.tlen; r += gs) S[4] = fma(V.t2[r], V.t2[r], S[4]);
-  }
-  for (int64_t i = gt; i < a.m; i += gs) {
-    const double dy = V.yb[i] - V.y0[i];
-    S[0] = fma(dy, dy, S[0]);
-  }
-  block_reduce<kWR>(S, kRMax, red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < kWR; i++) a.partR[(size_t)blockIdx.x * kWR + i] = S[i];
-  }
-  if (!last_block(&a.counters[1])) return;
-  double tot[kWR];
-  reduce_partials<kWR>(a.partR, gridDim.x, kWR, kRMax, tot, red);
-  if (threadIdx.x == 0) {
-    // Algorithm 5: theta~ of eq. (3.11), floors, argmin of eq. (3.12), smoothing
-    double th1 = C->lamA * tot[0] + C->lamQ * tot[1] - 2.0 * tot[2];
-    double th2 = tot[3];
-    const double th3 = tot[4];
-    th1 = fmax(th1, 1e-12);
-    th2 = fmax(th2, 1e-12);
-    double snew;
-    sigma_argmin_dev(th1, th2, th3, C->lamQ, C->sigma_golden, &snew);
-    const double beta = exp(-C->ratio);
-    const double sig = exp(beta * log(snew) + (1.0 - beta) * log(C->sigma));
-    if (!isfinite(sig) || !(sig > 0.0)) {
-      C->status = 3;
-      C->done = 1;
-    } else {
-      set_sigma(*C, sig);
-    }
-    C->restart_pending = 0;
-  }
+  return cudaGetLastError();
 }
 
 // zbar = (xbar - r_z)/sigma from the stored iterate (used by hprqp_get)
@@ -793,109 +267,6 @@ __global__ void k_zbar(Args a) {
     const double rz = fma(C->sigma, g, V.x[j]);
     V.zb[j] = (V.xb[j] - rz) * C->inv_sigma;
   }
-}
-
-// ------------------------------------------------------------------------------------ launchers
-using RowKernel = void (*)(Args);
-
-template <int KIND>
-static RowKernel pick(int G) {
-  switch (G) {
-    case 1: return k_rows<1, KIND>;
-    case 2: return k_rows<2, KIND>;
-    case 4: return k_rows<4, KIND>;
-    case 8: return k_rows<8, KIND>;
-    case 16: return k_rows<16, KIND>;
-    default: return k_rows<32, KIND>;
-  }
-}
-static RowKernel pick_restart(int G) {
-  switch (G) {
-    case 1: return k_restart<1>;
-    case 2: return k_restart<2>;
-    case 4: return k_restart<4>;
-    case 8: return k_restart<8>;
-    case 16: return k_restart<16>;
-    default: return k_restart<32>;
-  }
-}
-
-// Optional per-kind timing: ev[kind][0/1] recorded around every launch of that kind.
-#define TIMED(kind, launch)                                  \
-  do {                                                       \
-    if (ev) cudaEventRecord(ev[kind][0], s);                 \
-    launch;                                                  \
-    if (ev) cudaEventRecord(ev[kind][1], s);                 \
-  } while (0)
-
-cudaError_t launch_iteration(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2]) {
-  const bool HQ = a.Q.present(), HA = a.m > 0;
-  TIMED(0, (k_zx<<<p.gridE, kThreads, 0, s>>>(a)));
-  if (HQ) {
-    if (a.Q.has_pre()) TIMED(1, (k_pre<<<p.gridPre, kThreads, 0, s>>>(a, 0)));
-    TIMED(2, (pick<K_Q1>(p.gQ)<<<p.gridN, kThreads, 0, s>>>(a)));
-  }
-  if (HA) {
-    TIMED(3, (pick<K_A1>(p.gA)<<<p.gridM, kThreads, 0, s>>>(a)));
-    TIMED(4, (pick<K_AT>(p.gAT)<<<p.gridN, kThreads, 0, s>>>(a)));
-    if (HQ) {
-      if (a.Q.has_pre()) TIMED(5, (k_pre<<<p.gridPre, kThreads, 0, s>>>(a, 1)));
-      TIMED(6, (pick<K_Q2>(p.gQ)<<<p.gridN, kThreads, 0, s>>>(a)));
-    }
-  }
-  if (!HQ && !HA) {
-    // neither operator: the controller still needs its (empty-operator) pass
-    TIMED(4, (pick<K_AT>(p.gAT)<<<p.gridN, kThreads, 0, s>>>(a)));
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2]) {
-  if (a.Q.present() && a.m > 0 && a.Q.has_pre()) TIMED(7, (k_pre<<<p.gridPre, kThreads, 0, s>>>(a, 2)));
-  TIMED(8, (pick_restart(p.gQ)<<<p.gridN, kThreads, 0, s>>>(a)));
-  return cudaGetLastError();
-}
-
-int kernels_per_iteration(const Args& a) {
-  const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
-  int k = 1;
-  if (HQ) k += 1 + (pre ? 1 : 0);
-  if (HA) k += 2 + (HQ ? 1 + (pre ? 1 : 0) : 0);
-  if (!HQ && !HA) k += 1;
-  k += 1 + ((HQ && HA && pre) ? 1 : 0);  // restart pass (gated inside the kernels)
-  return k;
-}
-
-cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s) {
-  if (op == 0) pick<K_APPLY_A>(p.gA)<<<p.gridM, kThreads, 0, s>>>(a);
-  else if (op == 1) pick<K_APPLY_AT>(p.gAT)<<<p.gridN, kThreads, 0, s>>>(a);
-  else {
-    if (a.Q.has_pre()) k_pre<<<p.gridPre, kThreads, 0, s>>>(a, 3);
-    pick<K_APPLY_Q>(p.gQ)<<<p.gridN, kThreads, 0, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-
-// which 0: lambda_1(A A^*) on R^m; 1: lambda_1(Q) on R^n
-cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s) {
-  const int64_t dim = which == 0 ? a.m : a.n;
-  k_pw_start<<<p.gridE, kThreads, 0, s>>>(a, dim);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s) {
-  const int64_t dim = which == 0 ? a.m : a.n;
-  // normalise the previous w into v (the first call normalises the start vector)
-  k_pw_norm<<<p.gridE, kThreads, 0, s>>>(a, dim);
-  k_pw_flag<<<1, 1, 0, s>>>(a);
-  if (which == 0) {
-    pick<K_APPLY_AT_P>(p.gAT)<<<p.gridN, kThreads, 0, s>>>(a);
-    pick<K_POWER_A>(p.gA)<<<p.gridM, kThreads, 0, s>>>(a);
-  } else {
-    if (a.Q.has_pre()) k_pre<<<p.gridPre, kThreads, 0, s>>>(a, 4);
-    pick<K_POWER_Q>(p.gQ)<<<p.gridN, kThreads, 0, s>>>(a);
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s) {

@@ -63,8 +63,15 @@ __host__ __device__ inline void set_sigma(Ctrl& C, double sigma) {
 }
 
 // host-side launchers (solver.cu)
+// One inner step; var: 0 plain, 1 with the R~ test, 2 with the stopping test, 3 decided on the
+// device at run time.  ev (optional) receives CUDA events around each kernel kind.
+cudaError_t launch_step_var(const Args& a, const Plan& p, cudaStream_t s, int var, cudaEvent_t (*ev)[2] = nullptr);
 cudaError_t launch_iteration(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
 cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
+cudaError_t build_conditional_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int steps,
+                                    cudaGraph_t* out);
+int kernels_per_step(const Args& a);
+int kernels_per_restart(const Args& a);
 int kernels_per_iteration(const Args& a);
 cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s);
 cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s);
