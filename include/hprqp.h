@@ -184,8 +184,33 @@ hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* in, double* 
  * call hprqp_solve again before hprqp_get.  Requires a previous hprqp_solve. */
 hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms);
 
+/* Allocation-free power method.  The paper has no counterpart to this entry point; it exists
+ * for callers that cannot allocate device memory at the moment they need lambda_A: code that
+ * runs while a stream is being captured into a CUDA graph (allocations are not allowed then),
+ * real-time loops that must not allocate after start-up, and processes whose device memory is
+ * owned entirely by another allocator.
+ *
+ * Computes lambda_A = safety * lambda_1(A A^*) exactly as hprqp_solve does (same start vector,
+ * Rayleigh quotient and stopping rule: relative change <= tol, at most max_iter steps) and
+ * writes it to *lambda_out (host pointer).  A (m x n) and its transpose A^T (n x m) are CSR
+ * arrays in device memory; stream is a cudaStream_t (NULL: the legacy default stream).
+ *
+ * Nothing is allocated: the work vectors, partial sums and control scalars live in one
+ * file-scope device array sized for m, n <= HPRQP_NOALLOC_MAX_DIM, which every GPU that loads
+ * the library keeps until the process exits (about 3.2 MB).  Larger m or n return
+ * HPRQP_INVALID_ARG.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
+ * the array; calls that overlap on the GPU race with each other.  The call returns after the
+ * estimate has been copied to the host. */
+#define HPRQP_NOALLOC_MAX_DIM 131072
+hprqp_status hprqp_power_noalloc(int64_t m, int64_t n, const int32_t* A_rowptr, const int32_t* A_colidx,
+                                 const double* A_vals, const int32_t* AT_rowptr, const int32_t* AT_colidx,
+                                 const double* AT_vals, int64_t max_iter, double tol, double safety,
+                                 void* stream, double* lambda_out);
+
 /* Releases all device memory of the handle.  NULL is ignored. */
 void hprqp_destroy(hprqp_handle* h);
+
 
 /* Message of the last failure on this handle ("" if none); h may be NULL for the last
  * failure of hprqp_create in this thread. */

@@ -72,6 +72,8 @@ SIGNATURES = [
     ("hprqp_get", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.POINTER(hprqp_kkt)]),
     ("hprqp_apply", C.c_int, [_vp, _i32, _vp, _vp]),
     ("hprqp_profile", C.c_int, [_vp, _i32, _vp]),
+    ("hprqp_power_noalloc", C.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _vp,
+                                      C.POINTER(_dbl)]),
     ("hprqp_destroy", None, [_vp]),
     ("hprqp_last_error", C.c_char_p, [_vp]),
 ]
@@ -271,3 +273,4 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
