@@ -238,6 +238,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--launch-mode", type=int, default=0,
+                    help="0 conditional CUDA graph (default), 1 flat graph, 2 stream launches (for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -264,7 +266,7 @@ def main():
     pkg.build()
     qp, desc = workload(args.workload)
     stream = torch.cuda.Stream()
-    solver = pkg.Solver(qp, stream=stream.cuda_stream)
+    solver = pkg.Solver(qp, stream=stream.cuda_stream, launch_mode=args.launch_mode)
     iters_per_step, solve_s = [], []
     for _ in range(args.warmup):
         solver.solve(tol=TOL, max_iter=1_000_000)
@@ -326,7 +328,7 @@ def main():
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        with pkg.Solver(pinned, stream=stream.cuda_stream) as s2:
+        with pkg.Solver(pinned, stream=stream.cuda_stream, launch_mode=args.launch_mode) as s2:
             s2.solve(tol=TOL, max_iter=1_000_000)
             _, _, _, _, k2 = s2.get(outx, outy if qp.m else None, outz, outw)
         torch.cuda.synchronize()

@@ -108,6 +108,12 @@ typedef struct hprqp_params {
   hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
   hprqp_free_fn free;
   void* alloc_ctx;
+  int32_t launch_mode;       /* 0 (default): CUDA graph whose conditional nodes pick each
+                                step's variant on the device; 1: graph without conditional
+                                nodes (variants read at run time inside the kernels);
+                                2: plain stream launches of the same step variants, chosen on
+                                the host after each step (for profilers that cannot follow
+                                conditional graph nodes; one host synchronisation per step) */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
@@ -211,6 +217,49 @@ hprqp_status hprqp_power_noalloc(int64_t m, int64_t n, const int32_t* A_rowptr, 
 /* Releases all device memory of the handle.  NULL is ignored. */
 void hprqp_destroy(hprqp_handle* h);
 
+/* ------------------------------------------------------------------------------------------
+ * Batched solver: many independent instances of eq. (1.1), each run through Algorithm 4 with
+ * its own sigma, restart and termination state, in one persistent kernel launch (one thread
+ * block per instance, instances taken from a work queue ordered by estimated cost).
+ * Supported Q terms per instance: at most one DIAG, one DENSE_FACTOR (p <= 1024) and one CSR.
+ * m <= HPRQP_BATCH_MAX_M rows per instance (the second Q product of a step and the theta
+ * terms of eqs. (2.12), (3.11) use Q A^T and A Q A^T, formed once per solve).
+ * ---------------------------------------------------------------------------------------- */
+#define HPRQP_BATCH_MAX_M 32
+#define HPRQP_BATCH_MAX_P 1024
+
+typedef struct hprqp_problem {
+  int64_t n, m;
+  const hprqp_qop* Q;
+  const int32_t* A_rowptr;   /* m+1 */
+  const int32_t* A_colidx;
+  const double* A_vals;
+  const double *c, *l, *u, *L, *U;   /* as in hprqp_create; L, U may be NULL for PHI_L1 */
+  int32_t phi;
+  double lambda;
+  const double* x0;          /* optional warm start (NULL: origin), w0 = x0 */
+  const double* y0;
+  double sigma0;             /* > 0: initial sigma; else the Sec. 4.1 rule */
+  double lambda_A, lambda_Q; /* > 0: use as given; else the power method of Sec. 4.1 */
+} hprqp_problem;
+
+typedef struct hprqp_batch hprqp_batch;
+
+/* Copies `count` (>= 1) problems (host or device pointers) to the device.  params: as for
+ * hprqp_create (stream, alphas, periods, power method, autotune; NULL = defaults).  The
+ * autotuner times the persistent kernel's block size on a sample of the batch at the first
+ * solve. */
+hprqp_status hprqp_batch_create(hprqp_batch** b, int32_t count, const hprqp_problem* probs,
+                                const hprqp_params* params);
+/* Solves every instance to max(eta_p, eta_d, eta_gap) <= tol or max_iter iterations.  Returns
+ * HPRQP_OK when all converged, HPRQP_MAX_ITER when some did not, an error status otherwise. */
+hprqp_status hprqp_batch_solve(hprqp_batch* b, double tol, int64_t max_iter);
+/* Bar iterate and residuals of instance i (any output may be NULL; host or device). */
+hprqp_status hprqp_batch_get(hprqp_batch* b, int32_t i, double* x, double* y, double* z, hprqp_kkt* kkt);
+/* Wall time (seconds) of the last hprqp_batch_solve and the number of kernel launches in it. */
+hprqp_status hprqp_batch_stats(hprqp_batch* b, double* seconds, int64_t* kernel_launches);
+void hprqp_batch_destroy(hprqp_batch* b);
+const char* hprqp_batch_last_error(const hprqp_batch* b);
 
 /* Message of the last failure on this handle ("" if none); h may be NULL for the last
  * failure of hprqp_create in this thread. */

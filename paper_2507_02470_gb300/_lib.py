@@ -45,7 +45,8 @@ class hprqp_params(C.Structure):
                 ("power_tol", C.c_double), ("power_safety", C.c_double), ("halpern_total", C.c_int32),
                 ("sigma_golden", C.c_int32), ("restart_off", C.c_int32), ("sigma_fixed", C.c_int32),
                 ("time_limit", C.c_double), ("iters_per_launch", C.c_int32), ("autotune", C.c_int32),
-                ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("launch_mode", C.c_int32)]
 
 
 class hprqp_kkt(C.Structure):
@@ -59,6 +60,14 @@ class hprqp_kkt(C.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["status"] = STATUS_NAMES.get(d["status"], str(d["status"]))
         return d
+
+
+class hprqp_problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("Q", C.POINTER(hprqp_qop)), ("A_rowptr", C.c_void_p),
+                ("A_colidx", C.c_void_p), ("A_vals", C.c_void_p), ("c", C.c_void_p), ("l", C.c_void_p),
+                ("u", C.c_void_p), ("L", C.c_void_p), ("U", C.c_void_p), ("phi", C.c_int32), ("lam", C.c_double),
+                ("x0", C.c_void_p), ("y0", C.c_void_p), ("sigma0", C.c_double), ("lambda_A", C.c_double),
+                ("lambda_Q", C.c_double)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/hprqp.h
@@ -75,6 +84,12 @@ SIGNATURES = [
     ("hprqp_power_noalloc", C.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _vp,
                                       C.POINTER(_dbl)]),
     ("hprqp_destroy", None, [_vp]),
+    ("hprqp_batch_create", C.c_int, [C.POINTER(_vp), _i32, C.POINTER(hprqp_problem), C.POINTER(hprqp_params)]),
+    ("hprqp_batch_solve", C.c_int, [_vp, _dbl, _i64]),
+    ("hprqp_batch_get", C.c_int, [_vp, _i32, _vp, _vp, _vp, C.POINTER(hprqp_kkt)]),
+    ("hprqp_batch_stats", C.c_int, [_vp, C.POINTER(_dbl), C.POINTER(_i64)]),
+    ("hprqp_batch_destroy", None, [_vp]),
+    ("hprqp_batch_last_error", C.c_char_p, [_vp]),
     ("hprqp_last_error", C.c_char_p, [_vp]),
 ]
 
@@ -274,3 +289,135 @@ class Solver:
     def __exit__(self, *a):
         self.close()
 
+
+def _qop_of(qp, hold):
+    terms = (hprqp_qterm * max(1, len(qp.qterms)))()
+    for k, t in enumerate(qp.qterms):
+        tt = terms[k]
+        tt.kind = QKIND[t.kind]
+        tt.p = int(getattr(t, "p", 0) or 0)
+        if t.rowptr is not None:
+            rp, ci, va = hold(t.rowptr, np.int32), hold(t.colidx, np.int32), hold(t.vals, np.float64)
+            tt.rowptr, tt.colidx, tt.vals = _ptr(rp), _ptr(ci), _ptr(va)
+            tt.nnz = int(ci.shape[0])
+        if t.offsets is not None:
+            tt.ndiag = len(t.offsets)
+            tt.offsets = _ptr(hold(t.offsets, np.int32))
+            tt.diags = _ptr(hold(t.diags, np.float64))
+        if t.dense is not None:
+            tt.dense = _ptr(hold(t.dense, np.float64))
+    hold(terms, None)
+    q = hprqp_qop(len(qp.qterms), C.cast(terms, C.POINTER(hprqp_qterm)))
+    hold(q, None)
+    return q
+
+
+class BatchSolver:
+    """Many independent QPs solved in one persistent launch (hprqp_batch_* of the C ABI).
+
+    ``problems`` is a list of QP-like objects (see ``Solver``); optional per-instance
+    ``x0``/``y0``/``sigma0``/``lambda_A``/``lambda_Q`` lists set warm starts and fixed
+    parameters."""
+
+    def __init__(self, problems, stream=None, x0=None, y0=None, sigma0=None, lambda_A=None, lambda_Q=None,
+                 **params):
+        L = lib()
+        keep = []
+
+        def hold(a, dtype):
+            if dtype is None:
+                keep.append(a)
+                return a
+            if hasattr(a, "data_ptr"):
+                import torch
+                tdt = {np.int32: torch.int32, np.float64: torch.float64}[dtype]
+                a = a.to(tdt).contiguous()
+            else:
+                a = np.ascontiguousarray(a, dtype=dtype)
+            keep.append(a)
+            return a
+
+        p = default_params()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        if stream is not None:
+            p.stream = int(stream)
+        self.params = p
+        cnt = len(problems)
+        arr = (hprqp_problem * cnt)()
+        self.ns, self.ms = [], []
+        for i, qp in enumerate(problems):
+            pr = arr[i]
+            pr.n, pr.m = int(qp.n), int(qp.m)
+            self.ns.append(int(qp.n))
+            self.ms.append(int(qp.m))
+            pr.Q = C.pointer(_qop_of(qp, hold))
+            if qp.m:
+                pr.A_rowptr = _ptr(hold(qp.A_rowptr, np.int32))
+                pr.A_colidx = _ptr(hold(qp.A_colidx, np.int32))
+                pr.A_vals = _ptr(hold(qp.A_vals, np.float64))
+                pr.l = _ptr(hold(qp.l, np.float64))
+                pr.u = _ptr(hold(qp.u, np.float64))
+            pr.c = _ptr(hold(qp.c, np.float64))
+            pr.L = _ptr(hold(qp.L, np.float64)) if qp.L is not None else None
+            pr.U = _ptr(hold(qp.U, np.float64)) if qp.U is not None else None
+            pr.phi = int(qp.phi)
+            pr.lam = float(qp.lam)
+            if x0 is not None and x0[i] is not None:
+                pr.x0 = _ptr(hold(x0[i], np.float64))
+                if y0 is not None and y0[i] is not None and qp.m:
+                    pr.y0 = _ptr(hold(y0[i], np.float64))
+            pr.sigma0 = float(sigma0[i]) if sigma0 is not None else 0.0
+            pr.lambda_A = float(lambda_A[i]) if lambda_A is not None else 0.0
+            pr.lambda_Q = float(lambda_Q[i]) if lambda_Q is not None else 0.0
+        h = C.c_void_p()
+        st = L.hprqp_batch_create(C.byref(h), cnt, arr, C.byref(p))
+        keep.clear()
+        if st != HPRQP_OK:
+            raise HPRQPError(st, L.hprqp_batch_last_error(None).decode())
+        self.h = h
+        self.count = cnt
+
+    def _check(self, st, ok=(HPRQP_OK,)):
+        if st not in ok:
+            raise HPRQPError(st, lib().hprqp_batch_last_error(self.h).decode())
+        return st
+
+    def solve(self, tol=1e-8, max_iter=1_000_000):
+        st = lib().hprqp_batch_solve(self.h, float(tol), int(max_iter))
+        self._check(st, ok=(HPRQP_OK, HPRQP_MAX_ITER))
+        return STATUS_NAMES[st]
+
+    def get(self, i):
+        x = np.empty(self.ns[i])
+        y = np.empty(max(self.ms[i], 1))
+        z = np.empty(self.ns[i])
+        k = hprqp_kkt()
+        self._check(lib().hprqp_batch_get(self.h, int(i), _ptr(x), _ptr(y) if self.ms[i] else None, _ptr(z),
+                                          C.byref(k)))
+        return x, y[:self.ms[i]], z, k.as_dict()
+
+    def stats(self):
+        sec = C.c_double()
+        n = C.c_int64()
+        self._check(lib().hprqp_batch_stats(self.h, C.byref(sec), C.byref(n)))
+        return {"seconds": sec.value, "kernel_launches": n.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hprqp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

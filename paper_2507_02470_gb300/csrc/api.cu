@@ -607,8 +607,8 @@ extern "C" hprqp_status hprqp_create(hprqp_handle** out, int64_t n, int64_t m, c
   if (params) h->prm = *params;
   else hprqp_default_params(&h->prm);
   if (h->prm.check_every < 1 || h->prm.restart_every < 1 || h->prm.iters_per_launch < 1 ||
-      h->prm.iters_per_launch > 4096) {
-    fail(nullptr, HPRQP_INVALID_ARG, "check_every, restart_every >= 1 and 1 <= iters_per_launch <= 4096");
+      h->prm.iters_per_launch > 4096 || h->prm.launch_mode < 0 || h->prm.launch_mode > 2) {
+    fail(nullptr, HPRQP_INVALID_ARG, "check_every, restart_every >= 1, 1 <= iters_per_launch <= 4096, launch_mode 0..2");
     delete h;
     return HPRQP_INVALID_ARG;
   }
@@ -659,7 +659,9 @@ static hprqp_status build_iter_graph(hprqp_handle* h) {
   cudaGraph_t g;
   // preferred: device-selected step variants through conditional nodes
   if (!h->side) CU(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-  cudaError_t be = build_conditional_graph(h->args, h->plan, h->stream, h->side, h->prm.iters_per_launch, &g);
+  cudaError_t be = h->prm.launch_mode == 0
+                       ? build_conditional_graph(h->args, h->plan, h->stream, h->side, h->prm.iters_per_launch, &g)
+                       : cudaErrorNotSupported;
   if (be == cudaSuccess) {
     cudaError_t ie = cudaGraphInstantiate(&h->g_iter, g, 0);
     cudaGraphDestroy(g);
@@ -844,6 +846,36 @@ static double initial_sigma(hprqp_handle* h) {
   return (nb >= 1e-16 && nb <= 1e16 && nc >= 1e-16 && nc <= 1e16) ? nb / nc : 1.0;
 }
 
+static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::time_point t0,
+                                 std::chrono::steady_clock::time_point t1, double lamA, double lamQ, double sigma,
+                                 bool time_up);
+
+// launch_mode 2: the same step variants as the conditional graph, launched one step at a time
+// on the stream, the host reading the controller state after each step.
+static hprqp_status solve_stream(hprqp_handle* h, std::chrono::steady_clock::time_point t0,
+                                 std::chrono::steady_clock::time_point t1, double lamA, double lamQ, double sigma) {
+  Ctrl& C = *h->hctrl;
+  bool time_up = false;
+  for (;;) {
+    const int var = C.done ? 3 : C.ttest ? 2 : C.rtest ? 1 : 0;
+    if (var == 3) break;
+    CU(h, launch_step_var(h->args, h->plan, h->stream, var));
+    CU(h, cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (C.restart_pending && !C.done) {
+      CU(h, launch_restart(h->args, h->plan, h->stream));
+      CU(h, cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+      CU(h, cudaStreamSynchronize(h->stream));
+    }
+    if (h->prm.time_limit > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > h->prm.time_limit) {
+      time_up = true;
+      break;
+    }
+  }
+  return finish_solve(h, t0, t1, lamA, lamQ, sigma, time_up);
+}
+
 extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_iter) {
   if (!h) return HPRQP_INVALID_ARG;
   h->err.clear();
@@ -868,6 +900,7 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   auto t1 = std::chrono::steady_clock::now();
   const double sigma = initial_sigma(h);
   if ((st = init_state(h, lamA, lamQ, sigma, tol, max_iter))) return st;
+  if (h->prm.launch_mode == 2) return solve_stream(h, t0, t1, lamA, lamQ, sigma);
   if ((st = build_iter_graph(h))) return st;
   // ---- Algorithm 4 in graph launches of iters_per_launch steps; double-buffered done poll
   const int64_t per = h->prm.iters_per_launch;
@@ -891,6 +924,13 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
       }
     }
   }
+  return finish_solve(h, t0, t1, lamA, lamQ, sigma, time_up);
+}
+
+static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::time_point t0,
+                                 std::chrono::steady_clock::time_point t1, double lamA, double lamQ, double sigma,
+                                 bool time_up) {
+  Args& a = h->args;
   Ctrl& C = *h->hctrl;
   CU(h, cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
@@ -912,8 +952,9 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   K.lambda_Q = lamQ;
   K.solve_seconds = std::chrono::duration<double>(t2 - t0).count();
   K.power_seconds = std::chrono::duration<double>(t1 - t0).count();
-  // conditional graph: only the bodies taken ran kernels (one step each, plus restarts)
-  if (h->conditional) h->launches += C.k * kernels_per_step(a) + C.r * kernels_per_restart(a);
+  // conditional graph and stream launches: only the variants taken ran kernels
+  if (h->conditional || h->prm.launch_mode == 2)
+    h->launches += C.k * kernels_per_step(a) + C.r * kernels_per_restart(a);
   K.kernel_launches = h->launches;
   K.status = status;
   h->last_status = status;

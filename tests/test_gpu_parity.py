@@ -170,3 +170,19 @@ def test_invalid_arguments(pkg):
             s.solve(tol=1e-8, max_iter=0)
         with pytest.raises(pkg.HPRQPError):
             s.solve(tol=-1.0, max_iter=10)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_launch_modes_agree(pkg, mode):
+    # the flat graph (variants read inside the kernels) and host-driven stream launches run the
+    # same algorithm as the conditional graph: identical iterates up to rounding
+    qp = PROBLEMS["large_sum"]
+    ref = oracle.solve(qp, tol=1e-30, max_iter=60, trace_len=60)
+    with pkg.Solver(qp, lambda_A=ref.lambda_A, lambda_Q=ref.lambda_Q, launch_mode=mode) as s:
+        for k in (7, 60):
+            s.solve(tol=1e-30, max_iter=k)
+            x, y, *_ = s.get()
+            assert rel(x, ref.trace["x"][k - 1]) <= ITER_TOL
+            assert rel(y, ref.trace["y"][k - 1]) <= ITER_TOL
+        st = s.solve(tol=1e-8, max_iter=100000)
+        assert st == "converged"
