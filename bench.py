@@ -44,6 +44,96 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def portfolio_batch(count, seed0=0):
+    import qpgen
+    return [qpgen.portfolio(seed0 + s) for s in range(count)]
+
+
+def _oracle_one(args):
+    import oracle
+    import qpgen
+    seed, tol = args
+    qp = qpgen.portfolio(seed)
+    import time as _t
+    t = _t.perf_counter()
+    s = oracle.solve(qp, tol=tol, max_iter=1_000_000)
+    return s.iters, _t.perf_counter() - t
+
+
+def run_batched(args, rank, world):
+    """Config 3: the portfolio batch in one persistent launch, against the plain solver."""
+    import torch
+    import paper_2507_02470_gb300 as pkg
+    count = args.c3_count
+    # CPU oracle sample first (spawned pool, before any GPU work in this process)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        sample = list(range(0, count, max(1, count // cores)))[:cores]
+        ctx = mp.get_context("spawn")
+        t = time.perf_counter()
+        with ctx.Pool(len(sample)) as pool:
+            outs = pool.map(_oracle_one, [(s, TOL) for s in sample])
+        dt = time.perf_counter() - t
+        its = sum(o[0] for o in outs)
+        cpu = {"value": round(its / dt, 3), "unit": UNIT, "cores": len(sample), "kind": "oracle",
+               "sample": f"{len(sample)} instances (seeds {sample[0]}..{sample[-1]}) solved to 1e-8, one per "
+                         f"process on {len(sample)} host cores, {dt:.1f} s"}
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    pkg.build()
+    seed0 = rank * count
+    probs = portfolio_batch(count, seed0)
+    stream = torch.cuda.Stream()
+    b = pkg.BatchSolver(probs, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        b.solve(tol=TOL)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = 0
+    conv = 0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = b.solve(tol=TOL)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    for i in range(count):
+        k = b.get(i)[3]
+        its += k["iters"]
+        conv += k["status"] == "converged"
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    t_step = max(dev_s, wall) / args.steps
+    # the plain single-instance solver on a sample of the same instances (create + solve each)
+    sample = list(range(0, count, max(1, count // args.plain_sample)))[:args.plain_sample]
+    plain_t, plain_its = 0.0, 0
+    for i in sample:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with pkg.Solver(probs[i], stream=stream.cuda_stream) as s:
+            s.solve(tol=TOL)
+            plain_its += s.kkt()["iters"]
+        torch.cuda.synchronize()
+        plain_t += time.perf_counter() - t
+    plain_total = plain_t / len(sample) * count
+    nsum = sum(p.n for p in probs)
+    line = {"metric": METRIC, "value": round(its / t_step, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched portfolio CQPs x{count}: n~U{{50..5000}} (sum n={nsum}), "
+                                   "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch",
+                       "tol": TOL, "l2": "F pool larger than L2"},
+            "time_to_tol_s": round(t_step, 4), "converged": conv, "instances": count,
+            "plain_solver_est_s": round(plain_total, 3), "speedup_vs_plain": round(plain_total / t_step, 2),
+            "plain_sample": f"{len(sample)} instances solved one by one (create+solve), scaled to {count}",
+            "clocks": clocks.summary(), "gpu_launches": args.steps, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -233,7 +323,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3"])
+    ap.add_argument("--c3-count", type=int, default=4096)
+    ap.add_argument("--plain-sample", type=int, default=24)
     ap.add_argument("--cpu-iters", type=int, default=30)
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -256,6 +348,11 @@ def main():
             dist.destroy_process_group()
         return
 
+    if args.workload == "c3":
+        run_batched(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
     import torch
     import paper_2507_02470_gb300 as pkg
     torch.cuda.set_device(local)
