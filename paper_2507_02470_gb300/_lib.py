@@ -91,6 +91,29 @@ SIGNATURES = [
     ("hprqp_batch_destroy", None, [_vp]),
     ("hprqp_batch_last_error", C.c_char_p, [_vp]),
     ("hprqp_last_error", C.c_char_p, [_vp]),
+    ("hprqp_set_data", C.c_int, [_vp, _vp, _vp, _vp]),
+    ("hprqp_set_lambda", C.c_int, [_vp, _dbl, _dbl]),
+    # learned warm start (include/hprqp_learn.h)
+    ("hprqp_gemm_bf16", C.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
+    ("hprqp_learn_check", C.c_int, []),
+    ("hprqp_cast_bf16_f64", C.c_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _vp, _i64, _vp, _vp]),
+    ("hprqp_cast_bf16_f32", C.c_int, [_vp, _i64, _i64, _i64, _vp, _dbl, _vp, _i64, _vp, _vp]),
+    ("hprqp_row_stats", C.c_int, [_vp, _i64, _i64, _i64, C.c_float, _vp, _vp, _vp]),
+    ("hprqp_col_mean_f64", C.c_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
+    ("hprqp_ws_standardize", C.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _i64, _vp]),
+    ("hprqp_mlp_create", C.c_int, [C.POINTER(_vp), _i32, C.POINTER(_i32), _i32, _vp]),
+    ("hprqp_mlp_set_layer", C.c_int, [_vp, _i32, _vp, _vp]),
+    ("hprqp_mlp_get_layer", C.c_int, [_vp, _i32, _vp, _vp]),
+    ("hprqp_mlp_forward", C.c_int, [_vp, _vp, _i64, _i32, _vp, _i64]),
+    ("hprqp_mlp_backward", C.c_int, [_vp, _vp, _i64]),
+    ("hprqp_mlp_get_grad", C.c_int, [_vp, _i32, _vp, _vp]),
+    ("hprqp_mlp_adam", C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float, _i64]),
+    ("hprqp_mlp_destroy", C.c_int, [_vp]),
+    ("hprqp_ws_loss", C.c_int, [_vp, _i64, _i32, _i32, _vp, _vp, _i64, _vp, _vp, C.c_float, C.c_float, C.c_float,
+                                C.c_float, C.c_float, _vp, _i64, _i32, _vp, _vp]),
+    ("hprqp_ws_decode", C.c_int, [_vp, _i64, _i64, _i32, _vp, _i64, _i32, C.c_float, C.c_float, C.c_float, _vp, _vp,
+                                  _vp, _vp, _vp, _i64, _vp, _vp]),
+    ("hprqp_learn_last_error", C.c_char_p, []),
 ]
 
 
@@ -234,6 +257,16 @@ class Solver:
                 None if y0 is None else self._hold(y0, np.float64)]
         self._check(lib().hprqp_set_warm_start(self.h, _ptr(keep[0]), _ptr(keep[1]), float(sigma0)))
         self._keep = []
+
+    def set_data(self, c=None, l=None, u=None):
+        """Replaces c and the row bounds (host numpy or CUDA tensors; None keeps them)."""
+        keep = [None if a is None else self._hold(a, np.float64) for a in (c, l, u)]
+        self._check(lib().hprqp_set_data(self.h, *[_ptr(a) for a in keep]))
+        self._keep = []
+
+    def set_lambda(self, lambda_A, lambda_Q):
+        """Fixes lambda_A, lambda_Q for later solves (0 restores the power method)."""
+        self._check(lib().hprqp_set_lambda(self.h, float(lambda_A), float(lambda_Q)))
 
     def solve(self, tol=1e-8, max_iter=1_000_000):
         st = lib().hprqp_solve(self.h, float(tol), int(max_iter))

@@ -24,7 +24,8 @@ def sources():
 
 def _deps():
     files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    files.append(os.path.join(os.path.dirname(HERE), "include", "hprqp.h"))
+    for h in ("hprqp.h", "hprqp_learn.h"):
+        files.append(os.path.join(os.path.dirname(HERE), "include", h))
     files.append(os.path.abspath(__file__))
     return files
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/hprqp.h"
+#include "../../include/hprqp_learn.h"
 #include "solver.cuh"
 
 using namespace hprqp;
@@ -275,6 +276,35 @@ static int tune_G(hprqp_handle* h, const Csr& M, int grid, double* x, double* y,
 }
 
 // ------------------------------------------------------------------------------------ create
+// Checks c (finite) and the row bounds (l <= u, no NaN) and records the norms that the
+// stopping test (Sec. 4.1: b = max(|l|, |u|) with infinite entries as 0) and the sigma0
+// rule use.
+static hprqp_status data_norms(hprqp_handle* h, const std::vector<double>& hc, const std::vector<double>& hl,
+                               const std::vector<double>& hu) {
+  for (size_t j = 0; j < hc.size(); j++)
+    if (!std::isfinite(hc[j])) return fail(h, HPRQP_INVALID_ARG, "c[%lld] is not finite", (long long)j);
+  double nb2 = 0, bi = 0;
+  for (size_t i = 0; i < hl.size(); i++) {
+    if (std::isnan(hl[i]) || std::isnan(hu[i]) || hl[i] > hu[i])
+      return fail(h, HPRQP_INVALID_ARG, "row bound %lld: need l <= u, no NaN", (long long)i);
+    double bl = std::isfinite(hl[i]) ? std::fabs(hl[i]) : 0.0;
+    double bu = std::isfinite(hu[i]) ? std::fabs(hu[i]) : 0.0;
+    double b = std::max(bl, bu);
+    nb2 += b * b;
+    bi = std::max(bi, b);
+  }
+  double nc2 = 0, ci = 0;
+  for (double v : hc) {
+    nc2 += v * v;
+    ci = std::max(ci, std::fabs(v));
+  }
+  h->nb2 = nb2;
+  h->nc2 = nc2;
+  h->b_inf = bi;
+  h->c_inf = ci;
+  return HPRQP_OK;
+}
+
 static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hprqp_qop* Q, const int32_t* A_rowptr,
                                 const int32_t* A_colidx, const double* A_vals, const double* c, const double* l,
                                 const double* u, const double* L, const double* U, int32_t phi, double lambda) {
@@ -310,29 +340,10 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     hU.assign(n, INFINITY);
   }
   for (int64_t j = 0; j < n; j++) {
-    if (!std::isfinite(hc[j])) return fail(h, HPRQP_INVALID_ARG, "c[%lld] is not finite", (long long)j);
     if (std::isnan(hL[j]) || std::isnan(hU[j]) || hL[j] > hU[j])
       return fail(h, HPRQP_INVALID_ARG, "box bound %lld: need L <= U, no NaN", (long long)j);
   }
-  double nb2 = 0, bi = 0;
-  for (int64_t i = 0; i < m; i++) {
-    if (std::isnan(hl[i]) || std::isnan(hu[i]) || hl[i] > hu[i])
-      return fail(h, HPRQP_INVALID_ARG, "row bound %lld: need l <= u, no NaN", (long long)i);
-    double bl = std::isfinite(hl[i]) ? std::fabs(hl[i]) : 0.0;
-    double bu = std::isfinite(hu[i]) ? std::fabs(hu[i]) : 0.0;
-    double b = std::max(bl, bu);
-    nb2 += b * b;
-    bi = std::max(bi, b);
-  }
-  double nc2 = 0, ci = 0;
-  for (int64_t j = 0; j < n; j++) {
-    nc2 += hc[j] * hc[j];
-    ci = std::max(ci, std::fabs(hc[j]));
-  }
-  h->nb2 = nb2;
-  h->nc2 = nc2;
-  h->b_inf = bi;
-  h->c_inf = ci;
+  if ((st = data_norms(h, hc, hl, hu))) return st;
 
   // ---- A
   HostCsr A;
@@ -650,6 +661,40 @@ extern "C" hprqp_status hprqp_set_warm_start(hprqp_handle* h, const double* x0, 
       if (!std::isfinite(v)) return fail(h, HPRQP_INVALID_ARG, "warm start y0 is not finite");
   }
   h->ws_sigma = sigma0 > 0 && std::isfinite(sigma0) ? sigma0 : 0.0;
+  return HPRQP_OK;
+}
+
+extern "C" hprqp_status hprqp_set_data(hprqp_handle* h, const double* c, const double* l, const double* u) {
+  if (!h) return HPRQP_INVALID_ARG;
+  hprqp_status st;
+  Vec& V = h->args.V;
+  const int64_t n = h->n, m = h->m;
+  std::vector<double> hc, hl, hu;
+  if ((st = fetch(h, hc, c ? c : V.c, n))) return st;
+  if ((st = fetch(h, hl, l ? l : V.l, m))) return st;
+  if ((st = fetch(h, hu, u ? u : V.u, m))) return st;
+  const double nb2 = h->nb2, nc2 = h->nc2, bi = h->b_inf, ci = h->c_inf;
+  if ((st = data_norms(h, hc, hl, hu))) {
+    h->nb2 = nb2;
+    h->nc2 = nc2;
+    h->b_inf = bi;
+    h->c_inf = ci;
+    return st;
+  }
+  if (c) CU(h, cudaMemcpyAsync((void*)V.c, hc.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (l && m) CU(h, cudaMemcpyAsync((void*)V.l, hl.data(), m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (u && m) CU(h, cudaMemcpyAsync((void*)V.u, hu.data(), m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  h->solved = false;
+  return HPRQP_OK;
+}
+
+extern "C" hprqp_status hprqp_set_lambda(hprqp_handle* h, double lambda_A, double lambda_Q) {
+  if (!h) return HPRQP_INVALID_ARG;
+  if (!(lambda_A >= 0.0 && std::isfinite(lambda_A)) || !(lambda_Q >= 0.0 && std::isfinite(lambda_Q)))
+    return fail(h, HPRQP_INVALID_ARG, "lambda_A and lambda_Q must be finite and >= 0");
+  h->prm.lambda_A = lambda_A;
+  h->prm.lambda_Q = lambda_Q;
   return HPRQP_OK;
 }
 

@@ -323,6 +323,27 @@ def param_family_instance(base: QP, seed: int) -> QP:
               base.L, base.U, base.phi, base.lam, base.qterms, name=f"{base.name}_i{seed}")
 
 
+def ws_gaussian(rows: int, cols: int, seed: int) -> np.ndarray:
+    """A rows x cols float32 matrix of independent N(0, 1) draws (seeded), the raw material
+    of the fixed random projection P and decoder basis Phi of the learned warm start; the
+    caller applies the scale."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((rows, cols), dtype=np.float32)
+
+
+def ws_family_data(base: QP, seeds) -> tuple:
+    """(c, u) of the family members with the given seeds, stacked as float64 arrays
+    (len(seeds) x n and len(seeds) x m), as ``param_family_instance`` draws them."""
+    seeds = list(seeds)
+    C = np.empty((len(seeds), base.n))
+    U = np.empty((len(seeds), base.m))
+    for k, sd in enumerate(seeds):
+        q = param_family_instance(base, sd)
+        C[k] = q.c
+        U[k] = q.u
+    return C, U
+
+
 # --------------------------------------------------------------------------------------
 # small problems for tests (closed forms, brute force, special cases)
 # --------------------------------------------------------------------------------------
