@@ -134,6 +134,94 @@ def run_batched(args, rank, world):
     b.close()
 
 
+def run_learned(args, rank, world):
+    """Config 4: learned warm start on the parametric family (n=1e5, m=5e4) against the plain
+    solver started from the origin, both on the GPU."""
+    import torch
+    import paper_2507_02470_gb300 as pkg
+    from paper_2507_02470_gb300 import learned as L
+    import qpgen
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    pkg.build()
+    base = qpgen.param_family_base(n=100_000, m=50_000, seed=0)
+    Ntr, Nte = args.c4_train, args.c4_test
+    off = rank * (Ntr + Nte)
+    tr_data = lambda a, b: qpgen.ws_family_data(base, range(off + a, off + b))
+    Cte, Ute = qpgen.ws_family_data(base, range(10_000_000 + off, 10_000_000 + off + Nte))
+    te_data = lambda a, b: (Cte[a:b], Ute[a:b])
+    D = base.n + base.m
+    Z = torch.empty(Ntr, D, dtype=torch.float64, device="cuda")
+    t = time.perf_counter()
+    tr = L.solve_members(base, tr_data, Ntr, Z=Z, workers=args.c4_workers)
+    t_train_solves = time.perf_counter() - t
+    lam = tr["lambda"]
+    ws = L.LearnedWarmStart(base.n, base.m, base.L, base.U, base.l, base.u, d0=512, hidden=(1024, 1024), r=256,
+                            seed=0, max_batch=256)
+    rep = ws.fit(tr_data, Z, tr["sigma"], epochs=args.c4_epochs, batch=256, lr=1e-3)
+    del Z
+    # inference for the held-out members (batched), timed on the device and the host
+    for _ in range(2):
+        ws.predict(Cte[:min(Nte, 256)], Ute[:min(Nte, 256)])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    Z0, sig0 = ws.predict(Cte, Ute)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t
+    Z0h, sig0h = Z0.cpu().numpy(), sig0.cpu().numpy()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        cold = L.solve_members(base, te_data, Nte, lam=lam)
+        warm = L.solve_members(base, te_data, Nte, lam=lam, starts=(Z0h, sig0h))
+    conv = sum(s == "converged" for s in cold["status"]) + sum(s == "converged" for s in warm["status"])
+    objdiff = float(np.max(np.abs(warm["pobj"] - cold["pobj"]) / np.maximum(1.0, np.abs(cold["pobj"]))))
+    t_cold = float(np.mean(cold["seconds"]))
+    t_warm = float(np.mean(warm["seconds"])) + t_pred / Nte
+    # tensor-core GEMM roofline: the feature projection of one batch of 256 members
+    pk, pk_src = peaks()
+    cu = torch.zeros(256, ws.Dp, dtype=torch.bfloat16, device="cuda")
+    F = torch.empty(ws.d0, 256, dtype=torch.float32, device="cuda")
+    s0 = torch.cuda.current_stream()
+    for _ in range(3):
+        L.gemm_bf16(ws.P, cu, out=F, splits=8)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(s0)
+    for _ in range(reps):
+        L.gemm_bf16(ws.P, cu, out=F, splits=8)
+    e1.record(s0)
+    torch.cuda.synchronize()
+    L.check()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * ws.d0 * 256 * ws.Dp
+    tf = flops / (ms * 1e-3) / 1e12
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    line = {"metric": METRIC, "value": round(t_warm, 5), "unit": "s per held-out instance to 1e-8 (learned start)",
+            "n_gpus": world, "steps": Nte, "warmup": 0, "ms_per_step": round(t_warm * 1e3, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16/f32 network",
+            "data": "synthetic",
+            "config": {"workload": "learned warm start, family of cqp n=1e5 m=5e4 (A, Q fixed; c=cbar+0.1N(0,1), "
+                                   "u=ubar+0.1U(0,1) on inequality rows), MLP 512-1024-1024-257, P 512 x 1.5e5, "
+                                   "Phi 1.5e5 x 256", "train": Ntr, "test": Nte, "tol": TOL,
+                       "epochs": args.c4_epochs},
+            "cold": {"iters_mean": float(cold["iters"].mean()), "s_mean": t_cold,
+                     "s_median": float(np.median(cold["seconds"]))},
+            "warm": {"iters_mean": float(warm["iters"].mean()), "s_mean": t_warm,
+                     "s_median": float(np.median(warm["seconds"])) + t_pred / Nte,
+                     "inference_s_per_instance": t_pred / Nte},
+            "speedup_vs_plain": round(t_cold / t_warm, 3), "converged": conv, "of": 2 * Nte,
+            "max_rel_obj_diff": objdiff,
+            "train": {"solves_s": round(t_train_solves, 2), "workers": args.c4_workers,
+                      "iters_mean": float(tr["iters"].mean()), "fit_s": round(rep.seconds, 2),
+                      "loss_sigma": rep.loss_sigma[-1], "loss_latent": rep.loss_latent[-1],
+                      "latent_mu_only": rep.latent_baseline},
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16 feature projection 512 x 256 x 150016 (split-K 8)",
+                         "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s", "frac": round(tf / peak, 4),
+                         "ms_per_launch": round(ms, 4), "peak_source": f"bf16 {pk_src} (burst)", "traffic": None},
+            "clocks": clocks.summary(), "gpu_launches": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ws.close()
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -323,7 +411,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--c4-train", type=int, default=2000)
+    ap.add_argument("--c4-test", type=int, default=100)
+    ap.add_argument("--c4-epochs", type=int, default=30)
+    ap.add_argument("--c4-workers", type=int, default=4)
     ap.add_argument("--c3-count", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=24)
     ap.add_argument("--cpu-iters", type=int, default=30)
@@ -348,6 +440,11 @@ def main():
             dist.destroy_process_group()
         return
 
+    if args.workload == "c4":
+        run_learned(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "c3":
         run_batched(args, rank, world)
         if dist:

@@ -723,7 +723,7 @@ extern "C" hprqp_status hprqp_ws_decode(const uint16_t* Phi, int64_t ldphi, int6
   const int64_t ldl = round8(r);
   uint16_t* ell = nullptr;
   LCU(cudaMallocAsync(reinterpret_cast<void**>(&ell), (size_t)B * ldl * 2, st));
-  k_cast<float><<<B, 256, 0, st>>>(O + 1, B, r, ldo, nullptr, 1.0, ell, ldl, nullptr);
+  k_cast<float><<<(int)std::min(B, 65535), 256, 0, st>>>(O + 1, B, r, ldo, nullptr, 1.0, ell, ldl, nullptr);
   cudaError_t e = cudaGetLastError();
   hprqp_status s2 = HPRQP_OK;
   if (e == cudaSuccess) s2 = gemm(D, B, r, Phi, ldphi, ell, ldl, work, B, 1, nullptr, st);

@@ -13,14 +13,11 @@ from __future__ import annotations
 import ctypes as C
 import math
 from dataclasses import dataclass, field
-from typing import List, Optional
+from typing import List
 
 import numpy as np
 
 from ._lib import HPRQPError, lib
-
-_BF16 = None
-
 
 def _torch():
     import torch
@@ -140,6 +137,10 @@ class MLP:
             pass
 
 
+def _rows(Cs, Us):
+    return lambda b0, b1: (Cs[b0:b1], Us[b0:b1])
+
+
 def dual_box(l, u):
     """Sign box of the multipliers y of l <= Ax <= u in the solver's convention (y <= 0 on rows
     with l = -inf, y >= 0 on rows with u = +inf, free on rows with both bounds finite)."""
@@ -216,23 +217,23 @@ class LearnedWarmStart:
         cu[:, self.n:].copy_(torch.as_tensor(Us, dtype=torch.float64), non_blocking=False)
         return cast_bf16(cu, ld=self.Dp, stream=self.stream)
 
-    def raw_features(self, Cs, Us, out=None, col0=0):
-        """F (d0 x B, FP32 feature-major) = P [c; u] for the rows of Cs (B x n), Us (B x m)."""
+    def raw_features(self, data, N, out=None):
+        """F (d0 x N, FP32 feature-major) = P [c; u] for members 0..N-1, where data(b0, b1)
+        returns their (c, u) rows as (b1-b0) x n and (b1-b0) x m arrays."""
         torch = _torch()
-        B = Cs.shape[0]
         if out is None:
-            out = torch.empty(self.d0, B, dtype=torch.float32, device=self.device)
-            col0 = 0
-        for b0 in range(0, B, self.chunk):
-            b1 = min(B, b0 + self.chunk)
-            cu = self._pack(Cs[b0:b1], Us[b0:b1])
-            gemm_bf16(self.P, cu, out=out[:, col0 + b0:col0 + b1], splits=8, stream=self.stream)
+            out = torch.empty(self.d0, N, dtype=torch.float32, device=self.device)
+        for b0 in range(0, N, self.chunk):
+            b1 = min(N, b0 + self.chunk)
+            Cs, Us = data(b0, b1)
+            cu = self._pack(Cs, Us)
+            gemm_bf16(self.P, cu, out=out[:, b0:b1], splits=8, stream=self.stream)
         return out
 
     def features(self, Cs, Us):
         """Standardised BF16 features (B x round8(d0)) with the training statistics."""
         torch = _torch()
-        F = self.raw_features(Cs, Us)
+        F = self.raw_features(_rows(Cs, Us), Cs.shape[0])
         B = F.shape[1]
         X = torch.zeros(B, round8(self.d0), dtype=torch.bfloat16, device=self.device)
         _chk(lib().hprqp_ws_standardize(F.data_ptr(), self.d0, B, F.stride(0), self.fmean.data_ptr(),
@@ -240,13 +241,16 @@ class LearnedWarmStart:
         return X
 
     # ---------------------------------------------------------------- training
-    def fit(self, Cs, Us, Z, sigma, epochs=30, batch=256, lr=1e-3, w_sigma=1.0, log=None):
-        """Cs (N x n), Us (N x m): data of the training members (numpy); Z (N x D, FP64 CUDA):
-        their solutions (x, y); sigma (N,): the final sigma of each solve."""
+    def fit(self, data, Z, sigma, epochs=30, batch=256, lr=1e-3, w_sigma=1.0, log=None):
+        """data: (Cs, Us) arrays (N x n, N x m) of the training members, or a function
+        data(b0, b1) returning rows b0..b1-1 of them; Z (N x D, FP64 CUDA): their solutions
+        (x, y); sigma (N,): the final sigma of each solve."""
         import time
         torch = _torch()
         t0 = time.perf_counter()
-        N = Cs.shape[0]
+        N = Z.shape[0]
+        if isinstance(data, tuple):
+            data = _rows(*data)
         s = self.stream
         self.mu = torch.empty(self.D, dtype=torch.float64, device=self.device)
         _chk(lib().hprqp_col_mean_f64(Z.data_ptr(), N, self.D, Z.stride(0), self.mu.data_ptr(), _sp(s)))
@@ -261,7 +265,7 @@ class LearnedWarmStart:
         # G = Phi^T Phi
         self.G = gemm_bf16(self.PhiT, self.PhiT, splits=32, stream=s)
         # features and their statistics
-        F = self.raw_features(Cs, Us)
+        F = self.raw_features(data, N)
         self.fmean = torch.empty(self.d0, dtype=torch.float32, device=self.device)
         self.fistd = torch.empty(self.d0, dtype=torch.float32, device=self.device)
         _chk(lib().hprqp_row_stats(F.data_ptr(), self.d0, N, F.stride(0), C.c_float(1e-20), self.fmean.data_ptr(),
@@ -326,3 +330,70 @@ class LearnedWarmStart:
 
     def close(self):
         self.mlp.close()
+
+
+def solve_members(base, data, N, stream=None, Z=None, starts=None, lam=None, tol=1e-8, workers=1):
+    """Solves members 0..N-1 of a family with the plain solver (one handle per worker thread,
+    each on its own CUDA stream).  data(b0, b1) -> (Cs, Us) as in ``LearnedWarmStart.fit``;
+    starts: optional (Z0 (N x D) host/CUDA, sigma0 (N,)) warm starts; lam: (lambda_A,
+    lambda_Q) to skip the power method.  Writes solutions into Z (N x D, CUDA) if given and
+    returns a dict of per-member iterations, seconds, objectives, final sigmas and the
+    lambdas used."""
+    import threading
+    import time
+    import torch
+    from ._lib import Solver
+    n, m = base.n, base.m
+    out = {"iters": np.zeros(N, dtype=np.int64), "seconds": np.zeros(N), "pobj": np.zeros(N),
+           "sigma": np.zeros(N), "status": [""] * N}
+    lam_box = [lam]
+    lock = threading.Lock()
+    errors = []
+
+    def work(wid):
+        try:
+            st_ = torch.cuda.Stream() if workers > 1 else None
+            sp = st_.cuda_stream if st_ is not None else stream
+            with Solver(base, stream=sp) as s:
+                if lam_box[0] is not None:
+                    s.set_lambda(*lam_box[0])
+                for b0 in range(wid, N, workers):
+                    Cs, Us = data(b0, b0 + 1)
+                    s.set_data(c=Cs[0], u=Us[0])
+                    t0 = time.perf_counter()
+                    if starts is not None:
+                        z0, sg = starts
+                        s.set_warm_start(z0[b0, :n], z0[b0, n:], float(sg[b0]))
+                    else:
+                        s.set_warm_start(None, None, 0.0)
+                    status = s.solve(tol=tol)
+                    dt = time.perf_counter() - t0
+                    if Z is not None:
+                        _, _, _, _, k = s.get(Z[b0, :n], Z[b0, n:], None, None)
+                    else:
+                        k = s.kkt()
+                    out["iters"][b0] = k["iters"]
+                    out["seconds"][b0] = dt
+                    out["pobj"][b0] = k["pobj"]
+                    out["sigma"][b0] = k["sigma"]
+                    out["status"][b0] = status
+                    with lock:
+                        if lam_box[0] is None:
+                            lam_box[0] = (k["lambda_A"], k["lambda_Q"])
+                    s.set_lambda(*lam_box[0])
+        except Exception as e:  # noqa: BLE001
+            errors.append(e)
+
+    if workers > 1 and lam_box[0] is None:
+        # the first member fixes lambda_A, lambda_Q for every worker
+        first = solve_members(base, data, 1, stream=stream, Z=Z, starts=starts, lam=None, tol=tol)
+        lam_box[0] = first["lambda"]
+    threads = [threading.Thread(target=work, args=(w,)) for w in range(workers)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    out["lambda"] = lam_box[0]
+    return out

@@ -1,0 +1,44 @@
+"""Per-kernel timings of the HPR-QP inner step on one of the synthetic workloads.
+
+    python -m paper_2507_02470_gb300.profile_step --workload c1 --iters 30
+
+Creates the solver with stream launches (launch_mode 2, which external profilers can attach
+to kernel by kernel), runs a short solve to fix lambda_A, lambda_Q and sigma, then
+``hprqp_profile``: `iters` inner steps launched one kernel at a time with CUDA events around
+each.  Prints one JSON line with the mean milliseconds of every kernel kind.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c4"])
+    ap.add_argument("--iters", type=int, default=30)
+    ap.add_argument("--warm-iters", type=int, default=20, help="iterations of the solve before profiling")
+    args = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import qpgen
+    import paper_2507_02470_gb300 as pkg
+    pkg.build()
+    qp = {"c0": lambda: qpgen.plain_cqp(),
+          "c1": lambda: qpgen.large_cqp(n=1_000_000, m=500_000, seed=0),
+          "c2": lambda: qpgen.lasso(),
+          "c4": lambda: qpgen.param_family_base(n=100_000, m=50_000, seed=0)}[args.workload]()
+    with pkg.Solver(qp, launch_mode=2) as s:
+        s.solve(tol=1e-30, max_iter=args.warm_iters)
+        ms = s.profile(iters=args.iters)
+        k = s.kkt()
+    print(json.dumps({"workload": args.workload, "n": qp.n, "m": qp.m, "iters": args.iters,
+                      "lambda_A": k["lambda_A"], "lambda_Q": k["lambda_Q"],
+                      "ms": {a: round(b, 5) for a, b in ms.items()}}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -199,51 +199,27 @@ def test_ws_loss_and_decode_match_oracle(env):
     L.check()
 
 
-def _solve_family(p, base, Cs, Us, stream, x0=None, y0=None, sig0=None, lam=None):
-    """Solve each member; returns (iterations, objectives, final sigmas, solutions (N x D))."""
-    import torch
-    n, m = base.n, base.m
-    out = torch.empty(Cs.shape[0], n + m, dtype=torch.float64, device="cuda")
-    its, objs, sigs = [], [], []
-    with p.Solver(base, stream=stream) as s:
-        if lam is not None:
-            s.set_lambda(*lam)
-        for i in range(Cs.shape[0]):
-            s.set_data(c=Cs[i], u=Us[i])
-            if x0 is not None:
-                s.set_warm_start(x0[i], y0[i], float(sig0[i]))
-            else:
-                s.set_warm_start(None, None, 0.0)
-            st = s.solve(tol=1e-8)
-            assert st == "converged", (i, st)
-            _, _, _, _, k = s.get(out[i, :n], out[i, n:], None, None)
-            its.append(k["iters"])
-            objs.append(k["pobj"])
-            sigs.append(k["sigma"])
-            lam = (k["lambda_A"], k["lambda_Q"])
-            s.set_lambda(*lam)
-    return np.array(its), np.array(objs), np.array(sigs), out, lam
-
-
 def test_learned_warm_start_reduces_iterations(env):
     torch, p, L = env
     base = qpgen.param_family_base(n=4000, m=2000, seed=5)
-    stream = torch.cuda.current_stream().cuda_stream
     Ntr, Nte = 320, 24
     Ctr, Utr = qpgen.ws_family_data(base, range(Ntr))
     Cte, Ute = qpgen.ws_family_data(base, range(100_000, 100_000 + Nte))
-    its, objs, sigs, Z, lam = _solve_family(p, base, Ctr, Utr, stream)
+    Z = torch.empty(Ntr, base.n + base.m, dtype=torch.float64, device="cuda")
+    tr = L.solve_members(base, lambda a, b: (Ctr[a:b], Utr[a:b]), Ntr, Z=Z, workers=2)
+    assert all(s == "converged" for s in tr["status"])
     ws = L.LearnedWarmStart(base.n, base.m, base.L, base.U, base.l, base.u, d0=128, hidden=(256, 256), r=32,
                             seed=1, max_batch=64, chunk=128)
-    rep = ws.fit(Ctr, Utr, Z, sigs, epochs=60, batch=64, lr=1e-3)
+    rep = ws.fit((Ctr, Utr), Z, tr["sigma"], epochs=60, batch=64, lr=1e-3)
     assert rep.loss_latent[-1] < rep.latent_baseline      # better than decoding to mu alone
     assert rep.loss_sigma[-1] < rep.loss_sigma[0]
     Z0, sig0 = ws.predict(Cte, Ute)
-    # held-out members: cold (origin, sigma0 rule) vs learned start
-    cold_its, cold_obj, _, _, _ = _solve_family(p, base, Cte, Ute, stream, lam=lam)
-    Z0h = Z0.cpu().numpy()
-    warm_its, warm_obj, _, _, _ = _solve_family(p, base, Cte, Ute, stream, x0=Z0h[:, :base.n], y0=Z0h[:, base.n:],
-                                                sig0=sig0.cpu().numpy(), lam=lam)
-    assert np.all(np.abs(warm_obj - cold_obj) <= 1e-6 * np.maximum(1.0, np.abs(cold_obj)))
-    assert warm_its.mean() < 0.9 * cold_its.mean(), (warm_its.mean(), cold_its.mean())
+    L.check()
+    # held-out members: from the origin with the sigma0 rule, and from the learned start
+    te = lambda a, b: (Cte[a:b], Ute[a:b])
+    cold = L.solve_members(base, te, Nte, lam=tr["lambda"])
+    warm = L.solve_members(base, te, Nte, lam=tr["lambda"], starts=(Z0.cpu().numpy(), sig0.cpu().numpy()))
+    assert all(s == "converged" for s in cold["status"] + warm["status"])
+    assert np.all(np.abs(warm["pobj"] - cold["pobj"]) <= 1e-6 * np.maximum(1.0, np.abs(cold["pobj"])))
+    assert warm["iters"].mean() < 0.9 * cold["iters"].mean(), (warm["iters"].mean(), cold["iters"].mean())
     ws.close()
