@@ -603,6 +603,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     P.gQ = big ? tune_G(h, *big, P.gridN, ain, aout, 1) : 1;
     CU(h, cudaStreamSynchronize(h->stream));
     CU(h, cudaGetLastError());
+    CU(h, plan_plain_grids(a, P, sms));
   }
   return HPRQP_OK;
 }

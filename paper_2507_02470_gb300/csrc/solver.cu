@@ -7,6 +7,7 @@
 // the solve is done.  The controller in the last block of every step sets the value of its own
 // restart IF node and of the next SWITCH node with cudaGraphSetConditional, so the host only
 // polls a done flag between launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -60,23 +61,41 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
   const Handles none;
   const int tt = var == VAR_T ? 1 : var == VAR_RUNTIME ? 2 : 0;
-  TIMED(0, (zxk(var)<<<p.gridE, kThreads, 0, s>>>(a)));
+  // plain steps write no partial sums, so they may run at their own (larger) grids
+  const bool pl = var == VAR_PLAIN && p.wZX > 0;
+  TIMED(0, (zxk(var)<<<pl ? p.wZX : p.gridE, kThreads, 0, s>>>(a)));
   if (HQ) {
     if (pre) TIMED(1, (prek(p.gPre, tt)<<<p.gridPre, kThreads, 0, s>>>(a, 0)));
-    TIMED(2, (rowk(K_Q1, var, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, HA ? none : hd)));
+    TIMED(2, (rowk(K_Q1, var, p.gQ)<<<pl ? p.wQ1 : p.gridN, kThreads, 0, s>>>(a, HA ? none : hd)));
   }
   if (HA) {
-    TIMED(3, (rowk(K_A1, var, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none)));
-    TIMED(4, (rowk(K_AT, var, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, HQ ? none : hd)));
+    TIMED(3, (rowk(K_A1, var, p.gA)<<<pl ? p.wA1 : p.gridM, kThreads, 0, s>>>(a, none)));
+    TIMED(4, (rowk(K_AT, var, p.gAT)<<<pl ? p.wAT : p.gridN, kThreads, 0, s>>>(a, HQ ? none : hd)));
     if (HQ) {
       if (pre) TIMED(5, (prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 1)));
-      TIMED(6, (rowk(K_Q2, var, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, hd)));
+      TIMED(6, (rowk(K_Q2, var, p.gQ)<<<pl ? p.wQ2 : p.gridN, kThreads, 0, s>>>(a, hd)));
     }
   }
   if (!HQ && !HA) {
     // neither operator: the controller still needs its (empty-operator) pass
     TIMED(4, (rowk(K_AT, var, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, hd)));
   }
+  return cudaGetLastError();
+}
+
+cudaError_t plan_plain_grids(const Args& a, Plan& p, int sms) {
+  auto wave = [sms](const void* f, int64_t units) -> int {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kThreads, 0) != cudaSuccess || occ < 1) occ = 1;
+    const int64_t need = std::max<int64_t>(1, units);
+    return (int)std::min<int64_t>(need, (int64_t)sms * occ);
+  };
+  const int64_t chN = (a.n + kChunk - 1) / kChunk, chM = (a.m + kChunk - 1) / kChunk;
+  p.wZX = wave((const void*)zxk(VAR_PLAIN), (a.n + kThreads - 1) / kThreads);
+  p.wQ1 = wave((const void*)rowk(K_Q1, VAR_PLAIN, p.gQ), chN);
+  p.wQ2 = wave((const void*)rowk(K_Q2, VAR_PLAIN, p.gQ), chN);
+  p.wAT = wave((const void*)rowk(K_AT, VAR_PLAIN, p.gAT), chN);
+  p.wA1 = wave((const void*)rowk(K_A1, VAR_PLAIN, p.gA), std::max<int64_t>(chM, 1));
   return cudaGetLastError();
 }
 

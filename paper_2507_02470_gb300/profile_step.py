@@ -33,8 +33,8 @@ def main(argv=None):
           "c4": lambda: qpgen.param_family_base(n=100_000, m=50_000, seed=0)}[args.workload]()
     with pkg.Solver(qp, launch_mode=2) as s:
         s.solve(tol=1e-30, max_iter=args.warm_iters)
-        ms = s.profile(iters=args.iters)
         k = s.kkt()
+        ms = s.profile(iters=args.iters)
     print(json.dumps({"workload": args.workload, "n": qp.n, "m": qp.m, "iters": args.iters,
                       "lambda_A": k["lambda_A"], "lambda_Q": k["lambda_Q"],
                       "ms": {a: round(b, 5) for a, b in ms.items()}}), flush=True)
