@@ -467,6 +467,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
     statuses = []
+    kkts = []
     with ClockSampler(local) as clocks:
         if dist:
             dist.barrier()
@@ -476,6 +477,7 @@ def main():
         for _ in range(args.steps):
             statuses.append(solver.solve(tol=TOL, max_iter=1_000_000))
             k = solver.kkt()
+            kkts.append(k)
             iters_per_step.append(k["iters"])
             solve_s.append(k["solve_seconds"])
             launches += k["kernel_launches"]
@@ -544,6 +546,10 @@ def main():
                        "l2": "inputs larger than L2 (working set > 129 MB), no flush needed",
                        "check_every": int(solver.params.check_every), "restart_every": int(solver.params.restart_every)},
             "time_to_tol_s": round(statistics.median(solve_s), 4),
+            "tolerance_ladder": {
+                "1e-4": {"iters": kkts[-1]["iters_1e4"], "s": round(statistics.median(k["seconds_1e4"] for k in kkts), 4)},
+                "1e-6": {"iters": kkts[-1]["iters_1e6"], "s": round(statistics.median(k["seconds_1e6"] for k in kkts), 4)},
+                "1e-8": {"iters": kkts[-1]["iters"], "s": round(statistics.median(solve_s), 4)}},
             "iters_per_solve": iters_per_step, "status": statuses,
             "rel_kkt": kk["rel_kkt"], "pobj": kk["pobj"], "power_s": round(kk["power_seconds"], 4),
             "clocks": clocks.summary(), "gpu_launches": int(launches),

@@ -126,6 +126,11 @@ typedef struct hprqp_kkt {
   double power_seconds;      /* part of it spent in the power method */
   int64_t kernel_launches;   /* kernels of this library launched by the last solve */
   int32_t status;
+  /* tolerance ladder (Sec. 4 reports 1e-4, 1e-6 and 1e-8): the first stopping test at which
+   * max(eta_p, eta_d, eta_gap) <= 1e-4 (resp. 1e-6), and the time to it (power method plus
+   * device time from the first step to that test); 0 when not reached */
+  int64_t iters_1e4, iters_1e6;
+  double seconds_1e4, seconds_1e6;
 } hprqp_kkt;
 
 /* Kernel kinds reported by hprqp_profile. */

@@ -69,7 +69,8 @@ class _Result(C.Structure):
     _fields_ = [("eta_p", C.c_double), ("eta_d", C.c_double), ("eta_gap", C.c_double),
                 ("pobj", C.c_double), ("dobj", C.c_double), ("iters", C.c_int64),
                 ("restarts", C.c_int64), ("sigma", C.c_double), ("lambda_A", C.c_double),
-                ("lambda_Q", C.c_double), ("status", C.c_int32)]
+                ("lambda_Q", C.c_double), ("status", C.c_int32), ("iters_1e4", C.c_int64),
+                ("iters_1e6", C.c_int64)]
 
 
 def lib():
@@ -169,6 +170,8 @@ class Solution:
     lambda_Q: float
     status: str
     trace: Optional[dict] = None
+    iters_1e4: int = 0
+    iters_1e6: int = 0
 
 
 def default_params() -> dict:
@@ -213,7 +216,8 @@ def solve(qp, trace_len: int = 0, x0=None, y0=None, **kw) -> Solution:
         if qp.m == 0:
             tr["y"] = tr["y"][:, :0]
     return Solution(x, y[:qp.m], z, w, r.eta_p, r.eta_d, r.eta_gap, r.pobj, r.dobj, int(r.iters),
-                    int(r.restarts), r.sigma, r.lambda_A, r.lambda_Q, STATUS.get(r.status, str(r.status)), tr)
+                    int(r.restarts), r.sigma, r.lambda_A, r.lambda_Q, STATUS.get(r.status, str(r.status)), tr,
+                    int(r.iters_1e4), int(r.iters_1e6))
 
 
 def qmul(qp, v):

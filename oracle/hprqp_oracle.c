@@ -475,6 +475,9 @@ int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, doub
         k = kd;
         break;
       }
+      /* tolerance ladder of Sec. 4: the first test at which 1e-4 and 1e-6 are met */
+      if (res->iters_1e4 == 0 && fmax(eta3[0], fmax(eta3[1], eta3[2])) <= 1e-4) res->iters_1e4 = kd;
+      if (res->iters_1e6 == 0 && fmax(eta3[0], fmax(eta3[1], eta3[2])) <= 1e-6) res->iters_1e6 = kd;
       if (fmax(eta3[0], fmax(eta3[1], eta3[2])) <= prm->tol) {
         status = ORC_CONVERGED;
         k = kd;

@@ -75,6 +75,7 @@ typedef struct {
   int64_t iters, restarts;
   double sigma, lambda_A, lambda_Q;
   int32_t status;
+  int64_t iters_1e4, iters_1e6;  /* first stopping test with max(eta) <= 1e-4 / 1e-6 (0: none) */
 } orc_result;
 
 void orc_default_params(orc_params* p);

@@ -54,7 +54,8 @@ class hprqp_kkt(C.Structure):
                 ("pobj", C.c_double), ("dobj", C.c_double), ("iters", C.c_int64), ("restarts", C.c_int64),
                 ("sigma", C.c_double), ("lambda_A", C.c_double), ("lambda_Q", C.c_double),
                 ("solve_seconds", C.c_double), ("power_seconds", C.c_double), ("kernel_launches", C.c_int64),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("iters_1e4", C.c_int64), ("iters_1e6", C.c_int64),
+                ("seconds_1e4", C.c_double), ("seconds_1e6", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -946,6 +946,8 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   auto t1 = std::chrono::steady_clock::now();
   const double sigma = initial_sigma(h);
   if ((st = init_state(h, lamA, lamQ, sigma, tol, max_iter))) return st;
+  CU(h, launch_stamp(a, h->stream));
+  h->launches += 1;
   if (h->prm.launch_mode == 2) return solve_stream(h, t0, t1, lamA, lamQ, sigma);
   if ((st = build_iter_graph(h))) return st;
   // ---- Algorithm 4 in graph launches of iters_per_launch steps; double-buffered done poll
@@ -1003,6 +1005,18 @@ static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::tim
     h->launches += C.k * kernels_per_step(a) + C.r * kernels_per_restart(a);
   K.kernel_launches = h->launches;
   K.status = status;
+  // tolerance ladder: iterations and time (power method + device time since the first step)
+  const int64_t lk[2] = {C.ladder_k[0], C.ladder_k[1]};
+  for (int q = 0; q < 2; q++) {
+    const double sec = lk[q] > 0 ? K.power_seconds + 1e-9 * (double)(C.ladder_ns[q] - C.t0_ns) : 0.0;
+    if (q == 0) {
+      K.iters_1e4 = lk[0];
+      K.seconds_1e4 = sec;
+    } else {
+      K.iters_1e6 = lk[1];
+      K.seconds_1e6 = sec;
+    }
+  }
   h->last_status = status;
   h->solved = true;
   h->last_lamA = lamA;

@@ -72,6 +72,10 @@ struct Ctrl {
   int has_A, has_Q, phi;
   // results of the last stopping test
   double eta_p, eta_d, eta_gap, pobj, dobj, R;
+  // tolerance ladder (Sec. 4 reports 1e-4, 1e-6, 1e-8): first stopping test meeting 1e-4 / 1e-6,
+  // with the device time stamp (%globaltimer, ns) of that test and of the first step
+  long long ladder_k[2];
+  unsigned long long ladder_ns[2], t0_ns;
   // power method state
   double pw_lam, pw_scale;
   long long pw_it, pw_max;
@@ -84,6 +88,11 @@ struct Ctrl {
 __device__ __forceinline__ long long dkey(double a) {
   long long b = __double_as_longlong(a);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 __device__ __forceinline__ double imax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
 __device__ __forceinline__ double imin(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }

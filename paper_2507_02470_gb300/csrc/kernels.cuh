@@ -357,7 +357,16 @@ __device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const doub
     C.pobj = pobj;
     C.dobj = dobj;
     if (isnan(eta_p) || isnan(eta_d) || isnan(eta_g) || isinf(pobj) || isinf(dobj)) bad = true;
-    if (!bad && fmax(eta_p, fmax(eta_d, eta_g)) <= C.tol) {
+    const double rk = fmax(eta_p, fmax(eta_d, eta_g));
+    if (!bad && C.ladder_k[0] == 0 && rk <= 1e-4) {
+      C.ladder_k[0] = kd;
+      C.ladder_ns[0] = global_ns();
+    }
+    if (!bad && C.ladder_k[1] == 0 && rk <= 1e-6) {
+      C.ladder_k[1] = kd;
+      C.ladder_ns[1] = global_ns();
+    }
+    if (!bad && rk <= C.tol) {
       C.status = 0;
       C.done = 1;
       C.k = kd;

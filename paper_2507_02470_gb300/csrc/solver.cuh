@@ -81,6 +81,8 @@ cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStrea
 cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s);
 cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s);
 cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s);
+// Records the device time stamp of the start of the iteration (tolerance ladder).
+cudaError_t launch_stamp(const Args& a, cudaStream_t s);
 // Fills the plain-variant grids of p from the occupancy of those kernels (after gQ, gA, gAT).
 cudaError_t plan_plain_grids(const Args& a, Plan& p, int sms);
 

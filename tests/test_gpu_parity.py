@@ -186,3 +186,19 @@ def test_launch_modes_agree(pkg, mode):
             assert rel(y, ref.trace["y"][k - 1]) <= ITER_TOL
         st = s.solve(tol=1e-8, max_iter=100000)
         assert st == "converged"
+
+
+def test_tolerance_ladder(pkg):
+    """Iterations and time to 1e-4 and 1e-6 recorded during a 1e-8 solve (Sec. 4 reports the
+    three tolerances): they are where looser solves stop, and the oracle's."""
+    qp = PROBLEMS["plain"]
+    ref = oracle.solve(qp, tol=1e-8, max_iter=500000)
+    with pkg.Solver(qp, lambda_A=ref.lambda_A, lambda_Q=ref.lambda_Q) as s:
+        assert s.solve(tol=1e-8, max_iter=500000) == "converged"
+        k = s.kkt()
+        assert 0 < k["iters_1e4"] <= k["iters_1e6"] <= k["iters"]
+        assert 0 < k["seconds_1e4"] <= k["seconds_1e6"] <= k["solve_seconds"] * 1.01 + 1e-3
+        assert (k["iters_1e4"], k["iters_1e6"]) == (ref.iters_1e4, ref.iters_1e6)
+        for tol, key in ((1e-4, "iters_1e4"), (1e-6, "iters_1e6")):
+            assert s.solve(tol=tol, max_iter=500000) == "converged"
+            assert s.kkt()["iters"] == k[key]

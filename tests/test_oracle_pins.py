@@ -458,3 +458,15 @@ def test_invalid_inputs_rejected():
     ci = qp.A_colidx.copy(); ci[0] = qp.n
     assert oracle.solve(qpgen.QP(**{**qp.__dict__, "A_colidx": ci})).status == "invalid_arg"
     assert oracle.solve(qp, max_iter=0).status == "invalid_arg"
+
+
+def test_tolerance_ladder_marks_where_looser_solves_stop():
+    """The ladder iterations are the stopping points of solves run to 1e-4 and 1e-6 (Sec. 4
+    reports all three tolerances): the first stopping test that meets each threshold."""
+    qp = qpgen.plain_cqp(n=300, m=150, seed=1, q_rows=30, a_density=0.05, q_density=0.1)
+    full = oracle.solve(qp, tol=1e-8)
+    assert 0 < full.iters_1e4 <= full.iters_1e6 <= full.iters
+    assert full.iters_1e4 % 100 == 0 and full.iters_1e6 % 100 == 0
+    for tol, k in ((1e-4, full.iters_1e4), (1e-6, full.iters_1e6)):
+        s = oracle.solve(qp, tol=tol, lambda_A=full.lambda_A, lambda_Q=full.lambda_Q)
+        assert s.status == "converged" and s.iters == k
