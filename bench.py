@@ -309,7 +309,7 @@ def algorithmic(qp):
     zx_vec = (15 if HA else 11) if qp.qterms else 8
     zx_out = 6 if HA else 5
     out = {
-        "zx": (8 * n * (zx_vec + zx_out), 20 * n),
+        "zx": (8 * n * (zx_vec + zx_out), 18 * n),
         "pre1": (pre_bytes + 8 * n, pre_flops),
         "q1": (q_bytes + 8 * n * (1 + 3 + 1), q_flops + 3 * n),
         "a1": (12 * nnzA + 4 * m + 8 * n + 8 * m * 6, nnzA + 6 * m),

@@ -114,6 +114,12 @@ typedef struct hprqp_params {
                                 2: plain stream launches of the same step variants, chosen on
                                 the host after each step (for profilers that cannot follow
                                 conditional graph nodes; one host synchronisation per step) */
+  int32_t scaling;           /* 1 (default): the Sec. 4.1 preconditioning (10 Ruiz passes, then
+                                Pock-Chambolle with alpha = 1, on K = [Q A^T; A 0]) when Q is
+                                explicit (DIAG, CSR and DIA terms only) and phi is the box
+                                indicator; the iteration runs on the scaled problem while the
+                                stopping test, hprqp_get, hprqp_apply and warm starts stay in
+                                the original variables.  0: never scale. */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */

@@ -60,7 +60,7 @@ class _Params(C.Structure):
                 ("lambda_A", C.c_double), ("lambda_Q", C.c_double), ("sigma0", C.c_double),
                 ("power_max_iter", C.c_int64), ("power_tol", C.c_double), ("power_safety", C.c_double),
                 ("halpern_total", C.c_int32), ("sigma_golden", C.c_int32), ("restart_off", C.c_int32),
-                ("sigma_fixed", C.c_int32), ("x0", C.c_void_p), ("y0", C.c_void_p),
+                ("sigma_fixed", C.c_int32), ("scaling", C.c_int32), ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("trace_len", C.c_int64), ("trace_x", C.c_void_p), ("trace_y", C.c_void_p),
                 ("trace_R", C.c_void_p), ("trace_sigma", C.c_void_p), ("trace_restart", C.c_void_p)]
 
@@ -83,6 +83,8 @@ def lib():
             L.orc_default_params.argtypes = [C.POINTER(_Params)]
             L.orc_solve.argtypes = [C.POINTER(_Problem), C.POINTER(_Params), C.POINTER(_Result), vp, vp, vp, vp]
             L.orc_solve.restype = C.c_int
+            L.orc_scaling.argtypes = [C.POINTER(_Problem), vp, vp]
+            L.orc_scaling.restype = C.c_int
             for f in (L.orc_qmul, L.orc_amul, L.orc_atmul):
                 f.argtypes = [C.POINTER(_Problem), vp, vp]
             for f in (L.orc_power_A, L.orc_power_Q):
@@ -218,6 +220,15 @@ def solve(qp, trace_len: int = 0, x0=None, y0=None, **kw) -> Solution:
     return Solution(x, y[:qp.m], z, w, r.eta_p, r.eta_d, r.eta_gap, r.pobj, r.dobj, int(r.iters),
                     int(r.restarts), r.sigma, r.lambda_A, r.lambda_Q, STATUS.get(r.status, str(r.status)), tr,
                     int(r.iters_1e4), int(r.iters_1e6))
+
+
+def scaling(qp):
+    """(d, e, applied): the Sec. 4.1 preconditioning of qp (x = D xs, y = E ys)."""
+    P = Problem(qp)
+    d = np.ones(qp.n)
+    e = np.ones(max(qp.m, 1))
+    ok = lib().orc_scaling(P.ref, d.ctypes.data, e.ctypes.data)
+    return d, e[:qp.m], bool(ok)
 
 
 def qmul(qp, v):

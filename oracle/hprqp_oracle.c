@@ -373,6 +373,7 @@ void orc_default_params(orc_params* p) {
   p->power_max_iter = 5000;
   p->power_tol = 1e-6;
   p->power_safety = 1.01;
+  p->scaling = 1;
 }
 
 static int bad_double(double v) { return isnan(v); }
@@ -395,14 +396,89 @@ static int validate(const orc_problem* P, const orc_params* prm) {
   return 1;
 }
 
-/* ------------------------------------------------------------------ Algorithm 4 */
-int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, double* xout,
-              double* yout, double* zout, double* wout) {
-  memset(res, 0, sizeof(*res));
-  if (!validate(P, prm)) {
-    res->status = ORC_INVALID;
-    return ORC_INVALID;
+
+/* ------------------------------------------------------------------ preconditioning (Sec. 4.1)
+ * The matrix that is equilibrated is K = [Q A^T; A 0] (symmetric, order n + m), scaled as
+ * diag(s) K diag(s) with s = (d, e).  One pass computes the norm of every column of the
+ * scaled K (the infinity norm in the 10 Ruiz passes, the 1-norm in the Pock-Chambolle pass
+ * with alpha = 1) and divides s_j by the square root of it (columns of norm 0 keep s_j). */
+static int scaling_eligible(const orc_problem* P) {
+  if (P->phi != ORC_PHI_BOX) return 0;
+  for (int32_t t = 0; t < P->nq; t++) {
+    int32_t kd = P->q[t].kind;
+    if (kd != ORC_Q_DIAG && kd != ORC_Q_CSR && kd != ORC_Q_DIA) return 0;
   }
+  return 1;
+}
+
+/* accumulate |v| into the column norm (inf: max, one: sum) */
+static void acc_norm(double* nrm, int64_t j, double v, int inf) {
+  v = fabs(v);
+  if (inf) nrm[j] = fmax(nrm[j], v);
+  else nrm[j] += v;
+}
+
+static void scaled_col_norms(const orc_problem* P, const double* d, const double* e, int inf, double* cn,
+                             double* rn) {
+  int64_t n = P->n, m = P->m;
+  for (int64_t j = 0; j < n; j++) cn[j] = 0.0;
+  for (int64_t i = 0; i < m; i++) rn[i] = 0.0;
+  for (int32_t t = 0; t < P->nq; t++) {
+    const orc_qterm* T = &P->q[t];
+    if (T->kind == ORC_Q_DIAG) {
+      for (int64_t j = 0; j < n; j++) acc_norm(cn, j, T->dense[j] * d[j] * d[j], inf);
+    } else if (T->kind == ORC_Q_CSR) {
+      /* Q symmetric: the column norm of column j equals the norm of row j */
+      for (int64_t i = 0; i < n; i++)
+        for (int32_t k = T->rowptr[i]; k < T->rowptr[i + 1]; k++)
+          acc_norm(cn, i, T->vals[k] * d[i] * d[T->colidx[k]], inf);
+    } else { /* DIA: Q[i][i+o] and its mirror Q[i+o][i] */
+      for (int32_t kk = 0; kk < T->ndiag; kk++) {
+        int64_t o = T->offsets[kk];
+        for (int64_t i = 0; i + o < n; i++) {
+          double v = T->diags[(int64_t)kk * n + i] * d[i] * d[i + o];
+          acc_norm(cn, i, v, inf);
+          if (o != 0) acc_norm(cn, i + o, v, inf);
+        }
+      }
+    }
+  }
+  /* A block (rows n..n+m of K) and its transpose (columns n..n+m) */
+  for (int64_t i = 0; i < m; i++)
+    for (int32_t k = P->A_rowptr[i]; k < P->A_rowptr[i + 1]; k++) {
+      int64_t j = P->A_colidx[k];
+      double v = P->A_vals[k] * e[i] * d[j];
+      acc_norm(cn, j, v, inf);
+      acc_norm(rn, i, v, inf);
+    }
+}
+
+int orc_scaling(const orc_problem* P, double* d, double* e) {
+  int64_t n = P->n, m = P->m;
+  for (int64_t j = 0; j < n; j++) d[j] = 1.0;
+  for (int64_t i = 0; i < m; i++) e[i] = 1.0;
+  if (!scaling_eligible(P)) return 0;
+  double *cn = vnew(n), *rn = vnew(m);
+  for (int pass = 0; pass < 11; pass++) {
+    int inf = pass < 10; /* 10 Ruiz passes, then Pock-Chambolle (alpha = 1) */
+    scaled_col_norms(P, d, e, inf, cn, rn);
+    for (int64_t j = 0; j < n; j++)
+      if (cn[j] > 0.0) d[j] /= sqrt(cn[j]);
+    for (int64_t i = 0; i < m; i++)
+      if (rn[i] > 0.0) e[i] /= sqrt(rn[i]);
+  }
+  free(cn);
+  free(rn);
+  return 1;
+}
+
+/* ------------------------------------------------------------------ Algorithm 4 */
+/* P: the problem the iteration runs on.  With preconditioning, P is the scaled problem and
+ * P0, d, e the original and the scaling (x = D xs, y = E ys, z = D^{-1} zs): warm starts,
+ * traces, the stopping test of Sec. 4.1 and the outputs are in the original space. */
+static int solve_core(const orc_problem* P, const orc_params* prm, orc_result* res, double* xout,
+                      double* yout, double* zout, double* wout, const orc_problem* P0, const double* d,
+                      const double* e) {
   int64_t n = P->n, m = P->m;
   /* Sec. 4.1: lambda_A >= lambda_1(AA^*), lambda_Q >= lambda_1(Q) by the power method */
   double lamA = prm->lambda_A > 0.0 ? prm->lambda_A
@@ -432,10 +508,11 @@ int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, doub
   double *dx = vnew(n), *dw = vnew(n), *dy = vnew(m);
   /* Sec. 4.1: start at the origin; a warm start sets x, y and w = x (Q w* = Q x*) */
   if (prm->x0) {
-    memcpy(x, prm->x0, sizeof(double) * n);
-    memcpy(w, prm->x0, sizeof(double) * n);
+    for (int64_t j = 0; j < n; j++) x[j] = w[j] = d ? prm->x0[j] / d[j] : prm->x0[j];
   }
-  if (prm->y0 && m > 0) memcpy(y, prm->y0, sizeof(double) * m);
+  if (prm->y0 && m > 0)
+    for (int64_t i = 0; i < m; i++) y[i] = e ? prm->y0[i] / e[i] : prm->y0[i];
+  double *ux = vnew(n), *uy = vnew(m), *uz = vnew(n); /* original-space bar iterate */
   memcpy(x0, x, sizeof(double) * n);
   memcpy(w0, w, sizeof(double) * n);
   if (m > 0) memcpy(y0, y, sizeof(double) * m);
@@ -462,14 +539,25 @@ int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, doub
       R = sqrt(fmax(0.0, orc_mnorm2(P, sigma, lamA, lamQ, dy, dw, dx)));
     }
     if (k < prm->trace_len) {
-      if (prm->trace_x) memcpy(prm->trace_x + k * n, xb, sizeof(double) * n);
-      if (prm->trace_y && m > 0) memcpy(prm->trace_y + k * m, yb, sizeof(double) * m);
+      if (prm->trace_x)
+        for (int64_t j = 0; j < n; j++) prm->trace_x[k * n + j] = d ? d[j] * xb[j] : xb[j];
+      if (prm->trace_y && m > 0)
+        for (int64_t i = 0; i < m; i++) prm->trace_y[k * m + i] = e ? e[i] * yb[i] : yb[i];
       if (prm->trace_R) prm->trace_R[k] = R;
       if (prm->trace_sigma) prm->trace_sigma[k] = sigma;
       if (prm->trace_restart) prm->trace_restart[k] = 0;
     }
     if (ttest) {
-      orc_eta(P, xb, yb, zb, eta3, &pobj, &dobj);
+      if (d) {
+        for (int64_t j = 0; j < n; j++) {
+          ux[j] = d[j] * xb[j];
+          uz[j] = zb[j] / d[j];
+        }
+        for (int64_t i = 0; i < m; i++) uy[i] = e[i] * yb[i];
+        orc_eta(P0, ux, uy, uz, eta3, &pobj, &dobj);
+      } else {
+        orc_eta(P, xb, yb, zb, eta3, &pobj, &dobj);
+      }
       if (isnan(eta3[0]) || isnan(eta3[1]) || isnan(eta3[2]) || isinf(pobj) || isinf(dobj)) {
         status = ORC_NUMERICAL;
         k = kd;
@@ -560,12 +648,80 @@ int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, doub
   res->restarts = r;
   res->sigma = sigma;
   res->status = status;
-  if (xout) memcpy(xout, xb, sizeof(double) * n);
-  if (yout && m > 0) memcpy(yout, yb, sizeof(double) * m);
-  if (zout) memcpy(zout, zb, sizeof(double) * n);
-  if (wout) memcpy(wout, wb, sizeof(double) * n);
+  for (int64_t j = 0; j < n; j++) {
+    if (xout) xout[j] = d ? d[j] * xb[j] : xb[j];
+    if (zout) zout[j] = d ? zb[j] / d[j] : zb[j];
+    if (wout) wout[j] = d ? d[j] * wb[j] : wb[j];
+  }
+  if (yout)
+    for (int64_t i = 0; i < m; i++) yout[i] = e ? e[i] * yb[i] : yb[i];
+  free(ux); free(uy); free(uz);
   free(x); free(w); free(y); free(x0); free(w0); free(y0);
   free(xb); free(wb); free(yb); free(zb); free(wh);
   free(dx); free(dw); free(dy);
   return status;
+}
+
+/* Algorithm 4, on the preconditioned problem when prm->scaling applies (Sec. 4.1): with
+ * x = D xs and y = E ys the scaled data are A_s = E A D, Q_s = D Q D, c_s = D c,
+ * [l_s, u_s] = E [l, u], [L_s, U_s] = D^{-1} [L, U]. */
+int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, double* xout,
+              double* yout, double* zout, double* wout) {
+  memset(res, 0, sizeof(*res));
+  if (!validate(P, prm)) {
+    res->status = ORC_INVALID;
+    return ORC_INVALID;
+  }
+  if (!prm->scaling || !scaling_eligible(P)) return solve_core(P, prm, res, xout, yout, zout, wout, NULL, NULL, NULL);
+  int64_t n = P->n, m = P->m;
+  double *d = vnew(n), *e = vnew(m);
+  orc_scaling(P, d, e);
+  int64_t nnzA = m > 0 ? P->A_rowptr[m] : 0;
+  double *Av = vnew(nnzA), *c = vnew(n), *L = vnew(n), *U = vnew(n), *l = vnew(m), *u = vnew(m);
+  for (int64_t i = 0; i < m; i++)
+    for (int32_t k = P->A_rowptr[i]; k < P->A_rowptr[i + 1]; k++) Av[k] = e[i] * P->A_vals[k] * d[P->A_colidx[k]];
+  for (int64_t j = 0; j < n; j++) {
+    c[j] = d[j] * P->c[j];
+    L[j] = P->L[j] / d[j];
+    U[j] = P->U[j] / d[j];
+  }
+  for (int64_t i = 0; i < m; i++) {
+    l[i] = e[i] * P->l[i];
+    u[i] = e[i] * P->u[i];
+  }
+  orc_qterm* q = (orc_qterm*)calloc((size_t)(P->nq > 0 ? P->nq : 1), sizeof(orc_qterm));
+  double** qv = (double**)calloc((size_t)(P->nq > 0 ? P->nq : 1), sizeof(double*));
+  for (int32_t t = 0; t < P->nq; t++) {
+    const orc_qterm* T = &P->q[t];
+    q[t] = *T;
+    if (T->kind == ORC_Q_DIAG) {
+      qv[t] = vnew(n);
+      for (int64_t j = 0; j < n; j++) qv[t][j] = d[j] * T->dense[j] * d[j];
+      q[t].dense = qv[t];
+    } else if (T->kind == ORC_Q_CSR) {
+      qv[t] = vnew(T->rowptr[n]);
+      for (int64_t i = 0; i < n; i++)
+        for (int32_t k = T->rowptr[i]; k < T->rowptr[i + 1]; k++) qv[t][k] = d[i] * T->vals[k] * d[T->colidx[k]];
+      q[t].vals = qv[t];
+    } else {
+      qv[t] = vnew((int64_t)T->ndiag * n);
+      for (int32_t kk = 0; kk < T->ndiag; kk++)
+        for (int64_t i = 0; i + T->offsets[kk] < n; i++)
+          qv[t][(int64_t)kk * n + i] = d[i] * T->diags[(int64_t)kk * n + i] * d[i + T->offsets[kk]];
+      q[t].diags = qv[t];
+    }
+  }
+  orc_problem S = *P;
+  S.q = q;
+  S.A_vals = Av;
+  S.c = c;
+  S.L = L;
+  S.U = U;
+  S.l = l;
+  S.u = u;
+  int st = solve_core(&S, prm, res, xout, yout, zout, wout, P, d, e);
+  for (int32_t t = 0; t < P->nq; t++) free(qv[t]);
+  free(qv); free(q);
+  free(Av); free(c); free(L); free(U); free(l); free(u); free(d); free(e);
+  return st;
 }

@@ -59,6 +59,8 @@ typedef struct {
   int32_t sigma_golden;      /* 1: golden-section search instead of the exact argmin */
   int32_t restart_off;       /* 1: never restart (plain Algorithm 3) */
   int32_t sigma_fixed;       /* 1: keep sigma0 at restarts */
+  int32_t scaling;           /* 1: Ruiz + Pock-Chambolle preconditioning of Sec. 4.1 when Q is
+                                explicit (DIAG/CSR/DIA terms only) and phi is the box indicator */
   const double* x0;          /* optional warm start (n); w0 = x0 */
   const double* y0;          /* optional warm start (m) */
   /* optional per-iteration trace (first trace_len iterations), any may be NULL */
@@ -79,6 +81,10 @@ typedef struct {
 } orc_result;
 
 void orc_default_params(orc_params* p);
+/* Sec. 4.1 preconditioning: 10 Ruiz passes, then Pock-Chambolle with alpha = 1, on
+ * K = [Q A^T; A 0]; writes the column scaling d (n) and row scaling e (m) of
+ * x = D xs, y = E ys.  Returns 0 (d = e = 1) when the problem is not eligible. */
+int orc_scaling(const orc_problem* P, double* d, double* e);
 
 /* Algorithm 4.  x, y, z, w receive the final bar iterate (any may be NULL). */
 int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res,

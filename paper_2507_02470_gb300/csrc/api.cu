@@ -49,6 +49,11 @@ struct hprqp_handle {
   double last_lamA = 0, last_lamQ = 0, last_sigma0 = 1;
   cudaStream_t side = nullptr;   // captures the bodies of the conditional nodes
   bool conditional = false;      // the iteration graph selects step variants on the device
+  // preconditioning (Sec. 4.1): x = D xs, y = E ys; host copies of d, e and scratch for the
+  // unscaled outputs of hprqp_get
+  bool scaled = false;
+  std::vector<double> hd, he;
+  double *ux = nullptr, *uy = nullptr, *uz = nullptr, *uw = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -216,6 +221,7 @@ extern "C" void hprqp_default_params(hprqp_params* p) {
   p->time_limit = 0.0;
   p->iters_per_launch = 64;
   p->autotune = 1;
+  p->scaling = 1;
 }
 
 extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
@@ -303,6 +309,64 @@ static hprqp_status data_norms(hprqp_handle* h, const std::vector<double>& hc, c
   h->b_inf = bi;
   h->c_inf = ci;
   return HPRQP_OK;
+}
+
+// Sec. 4.1 preconditioning: ten Ruiz passes (infinity norms), then one Pock-Chambolle pass
+// with alpha = 1 (1-norms), on the symmetric K = [Q A^T; A 0] scaled as diag(s) K diag(s),
+// s = (d, e); every pass divides s_j by the square root of the norm of column j of the
+// currently scaled K (norm 0: s_j unchanged).  Q given by its diagonal, merged CSR and bands.
+static void precondition(int64_t n, int64_t m, const std::vector<double>& qdiag, const HostCsr& qcsr,
+                         const std::vector<int>& dia_off, const std::vector<std::vector<double>>& dia_vals,
+                         const HostCsr& A, std::vector<double>& d, std::vector<double>& e) {
+  d.assign(n, 1.0);
+  e.assign(m, 1.0);
+  std::vector<double> cn(n), rn(m);
+  for (int pass = 0; pass < 11; pass++) {
+    const bool ruiz = pass < 10;
+    std::fill(cn.begin(), cn.end(), 0.0);
+    std::fill(rn.begin(), rn.end(), 0.0);
+    auto put = [ruiz](double& acc, double v) { acc = ruiz ? std::max(acc, std::fabs(v)) : acc + std::fabs(v); };
+    if (!qdiag.empty())
+      for (int64_t j = 0; j < n; j++) put(cn[j], qdiag[j] * d[j] * d[j]);
+    if (qcsr.rows)
+      for (int64_t i = 0; i < n; i++)        // symmetric: column i has the norm of row i
+        for (int k = qcsr.rp[i]; k < qcsr.rp[i + 1]; k++) put(cn[i], qcsr.v[k] * d[i] * d[qcsr.ci[k]]);
+    for (size_t b = 0; b < dia_off.size(); b++) {
+      const int64_t o = dia_off[b];
+      for (int64_t i = 0; i + o < n; i++) {
+        const double v = dia_vals[b][i] * d[i] * d[i + o];
+        put(cn[i], v);
+        if (o != 0) put(cn[i + o], v);
+      }
+    }
+    for (int64_t i = 0; i < m; i++)
+      for (int k = A.rp[i]; k < A.rp[i + 1]; k++) {
+        const double v = A.v[k] * e[i] * d[A.ci[k]];
+        put(cn[A.ci[k]], v);
+        put(rn[i], v);
+      }
+    for (int64_t j = 0; j < n; j++)
+      if (cn[j] > 0.0) d[j] /= std::sqrt(cn[j]);
+    for (int64_t i = 0; i < m; i++)
+      if (rn[i] > 0.0) e[i] /= std::sqrt(rn[i]);
+  }
+}
+
+// c_s = D c, [l_s, u_s] = E [l, u] (in place) and the norms of the sigma0 rule on them
+static void scale_data(hprqp_handle* h, std::vector<double>& hc, std::vector<double>& hl, std::vector<double>& hu) {
+  for (size_t j = 0; j < hc.size(); j++) hc[j] *= h->hd[j];
+  for (size_t i = 0; i < hl.size(); i++) {
+    hl[i] *= h->he[i];
+    hu[i] *= h->he[i];
+  }
+  double nb2 = 0.0, nc2 = 0.0;
+  for (size_t i = 0; i < hl.size(); i++) {
+    const double b = std::max(std::isfinite(hl[i]) ? std::fabs(hl[i]) : 0.0, std::isfinite(hu[i]) ? std::fabs(hu[i]) : 0.0);
+    nb2 += b * b;
+  }
+  for (double v : hc) nc2 += v * v;
+  h->nb2 = nb2;
+  h->nc2 = nc2;
 }
 
 static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hprqp_qop* Q, const int32_t* A_rowptr,
@@ -456,6 +520,29 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
         }
   }
 
+  // ---- preconditioning (Sec. 4.1: only when Q is explicit; the box-only phi keeps the
+  // prox a plain clip in the scaled variables).  b_inf, c_inf of the stopping test stay those
+  // of the original data; the sigma0 norms become those of the scaled data.
+  h->scaled = h->prm.scaling && phi == PHI_BOX && facs.empty() && dens.empty();
+  if (h->scaled) {
+    precondition(n, m, qdiag, qcsr, dia_off, dia_vals, A, h->hd, h->he);
+    const std::vector<double>& d = h->hd;
+    const std::vector<double>& e = h->he;
+    for (int64_t i = 0; i < m; i++)
+      for (int k = A.rp[i]; k < A.rp[i + 1]; k++) A.v[k] *= e[i] * d[A.ci[k]];
+    for (size_t j = 0; j < qdiag.size(); j++) qdiag[j] *= d[j] * d[j];
+    if (qcsr.rows)
+      for (int64_t i = 0; i < n; i++)
+        for (int k = qcsr.rp[i]; k < qcsr.rp[i + 1]; k++) qcsr.v[k] *= d[i] * d[qcsr.ci[k]];
+    for (size_t b = 0; b < dia_off.size(); b++)
+      for (int64_t i = 0; i + dia_off[b] < n; i++) dia_vals[b][i] *= d[i] * d[i + dia_off[b]];
+    for (int64_t j = 0; j < n; j++) {
+      hL[j] /= d[j];
+      hU[j] /= d[j];
+    }
+    scale_data(h, hc, hl, hu);
+  }
+
   // ---- device problem
   Args& a = h->args;
   std::memset(&a, 0, sizeof(a));
@@ -474,6 +561,23 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   V.U = dU;
   V.l = dl;
   V.u = du;
+  V.sd = V.se = V.isd = V.ise = nullptr;
+  if (h->scaled) {
+    std::vector<double> id(n), ie(m);
+    for (int64_t j = 0; j < n; j++) id[j] = 1.0 / h->hd[j];
+    for (int64_t i = 0; i < m; i++) ie[i] = 1.0 / h->he[i];
+    double *p1, *p2, *p3, *p4;
+    if ((st = upload(h, &p1, h->hd)) || (st = upload(h, &p2, h->he)) || (st = upload(h, &p3, id)) ||
+        (st = upload(h, &p4, ie)))
+      return st;
+    V.sd = p1;
+    V.se = p2;
+    V.isd = p3;
+    V.ise = p4;
+    if ((st = zeros(h, &h->ux, n)) || (st = zeros(h, &h->uy, m)) || (st = zeros(h, &h->uz, n)) ||
+        (st = zeros(h, &h->uw, n)))
+      return st;
+  }
   if (m > 0) {
     if ((st = upload_csr(h, a.A, A))) return st;
     HostCsr AT = transpose(A);
@@ -567,6 +671,12 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     }
     const double avg = frows ? (double)fnnz / (double)frows : 0.0;
     P.gPre = avg < 8 ? 1 : avg < 32 ? 4 : avg < 96 ? 8 : 32;
+    // the pre-pass is a grid-stride loop over factor rows: launch only the blocks its rows
+    // need (a short factor such as S with 1e4 rows needs 40 blocks, not a full wave)
+    int64_t drows = 0;   // dense factor rows take one warp each
+    for (auto& F : dens) drows += F.first;
+    P.gridPre = (int)std::min<int64_t>(
+        std::max<int64_t>(1, (frows * P.gPre + drows * 32 + kThreads - 1) / kThreads), (int64_t)sms * 8);
   }
   a.nbM = P.gridM;
   const int gmax = std::max(P.gridN, P.gridM);
@@ -674,6 +784,14 @@ extern "C" hprqp_status hprqp_set_data(hprqp_handle* h, const double* c, const d
   if ((st = fetch(h, hc, c ? c : V.c, n))) return st;
   if ((st = fetch(h, hl, l ? l : V.l, m))) return st;
   if ((st = fetch(h, hu, u ? u : V.u, m))) return st;
+  if (h->scaled) {   // the kept pieces are stored scaled: back to the original data first
+    if (!c)
+      for (int64_t j = 0; j < n; j++) hc[j] /= h->hd[j];
+    if (!l)
+      for (int64_t i = 0; i < m; i++) hl[i] /= h->he[i];
+    if (!u)
+      for (int64_t i = 0; i < m; i++) hu[i] /= h->he[i];
+  }
   const double nb2 = h->nb2, nc2 = h->nc2, bi = h->b_inf, ci = h->c_inf;
   if ((st = data_norms(h, hc, hl, hu))) {
     h->nb2 = nb2;
@@ -682,6 +800,7 @@ extern "C" hprqp_status hprqp_set_data(hprqp_handle* h, const double* c, const d
     h->c_inf = ci;
     return st;
   }
+  if (h->scaled) scale_data(h, hc, hl, hu);
   if (c) CU(h, cudaMemcpyAsync((void*)V.c, hc.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   if (l && m) CU(h, cudaMemcpyAsync((void*)V.l, hl.data(), m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   if (u && m) CU(h, cudaMemcpyAsync((void*)V.u, hu.data(), m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -816,12 +935,14 @@ static hprqp_status init_state(hprqp_handle* h, double lamA, double lamQ, double
   } else {
     CU(h, cudaMemsetAsync(V.x, 0, nb8, h->stream));
   }
+  if (h->scaled && !h->ws_x.empty()) CU(h, launch_vmul(V.x, V.isd, h->n, h->stream));   // xs = D^{-1} x0
   CU(h, cudaMemcpyAsync(V.w, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
   CU(h, cudaMemcpyAsync(V.x0, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
   CU(h, cudaMemcpyAsync(V.w0, V.x, nb8, cudaMemcpyDeviceToDevice, h->stream));
   if (HA) {
     if (!h->ws_y.empty()) CU(h, cudaMemcpyAsync(V.y, h->ws_y.data(), mb8, cudaMemcpyHostToDevice, h->stream));
     else CU(h, cudaMemsetAsync(V.y, 0, mb8, h->stream));
+    if (h->scaled && !h->ws_y.empty()) CU(h, launch_vmul(V.y, V.ise, h->m, h->stream));   // ys = E^{-1} y0
     CU(h, cudaMemcpyAsync(V.y0, V.y, mb8, cudaMemcpyDeviceToDevice, h->stream));
   }
   // images Q w^0 and A^* y^0
@@ -1091,10 +1212,22 @@ extern "C" hprqp_status hprqp_get(hprqp_handle* h, double* x, double* y, double*
   hprqp_status st;
   Vec& V = h->args.V;
   if (z && h->last_status == HPRQP_TIME_LIMIT) CU(h, launch_zbar(h->args, h->plan, h->stream));
-  if ((st = copy_out(h, x, V.xb, h->n))) return st;
-  if ((st = copy_out(h, y, V.yb, h->m))) return st;
-  if ((st = copy_out(h, z, V.zb, h->n))) return st;
-  if ((st = copy_out(h, w, V.wb, h->n))) return st;
+  const double *xs = V.xb, *ys = V.yb, *zs = V.zb, *ws = V.wb;
+  if (h->scaled) {
+    // back to the original variables: x = D xs, y = E ys, z = D^{-1} zs, w = D ws
+    CU(h, launch_vmul_to(h->ux, V.xb, V.sd, h->n, h->stream));
+    CU(h, launch_vmul_to(h->uy, V.yb, V.se, h->m, h->stream));
+    CU(h, launch_vmul_to(h->uz, V.zb, V.isd, h->n, h->stream));
+    CU(h, launch_vmul_to(h->uw, V.wb, V.sd, h->n, h->stream));
+    xs = h->ux;
+    ys = h->uy;
+    zs = h->uz;
+    ws = h->uw;
+  }
+  if ((st = copy_out(h, x, xs, h->n))) return st;
+  if ((st = copy_out(h, y, ys, h->m))) return st;
+  if ((st = copy_out(h, z, zs, h->n))) return st;
+  if ((st = copy_out(h, w, ws, h->n))) return st;
   CU(h, cudaStreamSynchronize(h->stream));
   if (kkt) *kkt = h->kkt;
   return HPRQP_OK;
@@ -1108,7 +1241,11 @@ extern "C" hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* i
   const int64_t nout = op == 0 ? h->m : h->n;
   Vec& V = h->args.V;
   CU(h, cudaMemcpyAsync((void*)V.ain, in, nin * sizeof(double), cudaMemcpyDefault, h->stream));
+  // with preconditioning the stored operators are E A D, D A^T E, D Q D: map the input into
+  // the scaled variables and the output back (A x = E^{-1} A_s D^{-1} x, and so on)
+  if (h->scaled) CU(h, launch_vmul((double*)V.ain, op == 1 ? V.ise : V.isd, nin, h->stream));
   CU(h, launch_apply(h->args, h->plan, op, h->stream));
+  if (h->scaled) CU(h, launch_vmul(V.aout, op == 0 ? V.ise : V.isd, nout, h->stream));
   CU(h, cudaMemcpyAsync(out, V.aout, nout * sizeof(double), cudaMemcpyDefault, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   return HPRQP_OK;

@@ -457,10 +457,13 @@ __device__ __forceinline__ void end_row(EndTerms& T, const Args& a, int64_t j, b
   if (ttest) {
     const double qxb = HQ ? V.Qxb[j] : 0.0;
     const double cj = V.c[j];
-    const double rd = iabs(atyb - qxb + V.zb[j] - cj);
+    // infinity norms in the original variables: every term of the dual residual is D^{-1}
+    // times its scaled counterpart (x = D xs, y = E ys, z = D^{-1} zs)
+    const double sc = V.isd ? V.isd[j] : 1.0;
+    const double rd = iabs(atyb - qxb + V.zb[j] - cj) * sc;
     T.s[5] = imax(T.s[5], rd);
-    T.s[6] = imax(T.s[6], iabs(atyb));
-    T.s[7] = imax(T.s[7], iabs(qxb));
+    T.s[6] = imax(T.s[6], iabs(atyb) * sc);
+    T.s[7] = imax(T.s[7], iabs(qxb) * sc);
     T.s[8] = fma(xb, qxb, T.s[8]);
     T.s[9] = fma(cj, xb, T.s[9]);
     if (a.phi != PHI_BOX) T.s[10] += iabs(xb);
@@ -593,8 +596,9 @@ __global__ void __launch_bounds__(kThreads) k_rows(Args a, Handles hd) {
         }
         if (RED && ttest) {
           const double ax = rs1[threadIdx.x];
-          y3[1] = imax(y3[1], iabs(ax - iclamp(ax, lo, hi)));
-          y3[2] = imax(y3[2], iabs(ax));
+          const double sc = V.ise ? V.ise[j] : 1.0;   // A x = E^{-1} (A_s xs)
+          y3[1] = imax(y3[1], iabs(ax - iclamp(ax, lo, hi)) * sc);
+          y3[2] = imax(y3[2], iabs(ax) * sc);
           double t = 0.0;
           if (igt0(yb)) t = lo * yb;
           else if (ilt0(yb)) t = hi * yb;

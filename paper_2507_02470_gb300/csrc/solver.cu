@@ -83,6 +83,23 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   return cudaGetLastError();
 }
 
+__global__ void k_vmul(double* __restrict__ out, const double* __restrict__ v, const double* __restrict__ sc,
+                       int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) out[i] = v[i] * sc[i];
+}
+
+cudaError_t launch_vmul_to(double* out, const double* v, const double* sc, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+  k_vmul<<<blocks, kThreads, 0, st>>>(out, v, sc, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vmul(double* v, const double* sc, int64_t n, cudaStream_t st) {
+  return launch_vmul_to(v, v, sc, n, st);
+}
+
 __global__ void k_stamp(Ctrl* C) {
   if (threadIdx.x == 0 && blockIdx.x == 0) C->t0_ns = global_ns();
 }

@@ -16,6 +16,8 @@ struct Vec {
   double *pv, *pw, *ptmp;     // power method vectors
   const double* ain;          // apply input / output
   double* aout;
+  // preconditioning (x = D xs, y = E ys): d, e and their reciprocals; null when not scaled
+  const double *sd, *se, *isd, *ise;
 };
 
 // partial-sum regions (doubles); each kernel that reduces owns a region of gridDim.x rows
@@ -81,6 +83,10 @@ cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStrea
 cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s);
 cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s);
 cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s);
+// v[i] *= s[i] for i < n
+cudaError_t launch_vmul(double* v, const double* s, int64_t n, cudaStream_t st);
+// out[i] = v[i] * s[i] for i < n
+cudaError_t launch_vmul_to(double* out, const double* v, const double* s, int64_t n, cudaStream_t st);
 // Records the device time stamp of the start of the iteration (tolerance ladder).
 cudaError_t launch_stamp(const Args& a, cudaStream_t s);
 // Fills the plain-variant grids of p from the occupancy of those kernels (after gQ, gA, gAT).

@@ -49,7 +49,7 @@ def test_oracle_and_library_share_the_defaults(lib):
     o = oracle.default_params()
     p = pkg.default_params()
     for k in ("check_every", "restart_every", "alpha1", "alpha2", "alpha3", "alpha3_tight", "ratio_tight",
-              "power_max_iter", "power_tol", "power_safety", "halpern_total", "sigma_golden"):
+              "power_max_iter", "power_tol", "power_safety", "halpern_total", "sigma_golden", "scaling"):
         assert o[k] == getattr(p, k), k
 
 

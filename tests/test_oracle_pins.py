@@ -276,7 +276,7 @@ def test_thm31_shadow_sequence_equals_alg2(seed, rank):
         y, w, x = b * (2 * yb - y), b * (2 * wb - w), b * (2 * xb - x)
     # the oracle's own loop (fixed sigma, no restart) reproduces the same xbar trajectory
     s = oracle.solve(qp, tol=1e-30, max_iter=K, lambda_A=lamA, lambda_Q=lamQ, sigma0=sigma,
-                     restart_off=1, sigma_fixed=1, trace_len=K)
+                     restart_off=1, sigma_fixed=1, trace_len=K, scaling=0)
     for k in range(K):
         np.testing.assert_allclose(s.trace["x"][k], ref[k][3], atol=1e-9 * (1 + np.abs(ref[k][3]).max()))
 
@@ -440,7 +440,7 @@ def test_hand_computed_iterates():
                           q_kind="diag")
     for k in range(3):
         s = oracle.solve(qp, tol=1e-30, max_iter=k + 1, lambda_Q=g["lambda_Q"], sigma0=g["sigma"],
-                         restart_off=1, sigma_fixed=1)
+                         restart_off=1, sigma_fixed=1, scaling=0)
         assert s.x[0] == pytest.approx(g[f"xbar{k}"], abs=1e-15)
         assert s.z[0] == pytest.approx(g[f"zbar{k}"], abs=1e-15)
         assert s.w[0] == pytest.approx(g[f"wbar{k}"], abs=1e-15)
@@ -470,3 +470,53 @@ def test_tolerance_ladder_marks_where_looser_solves_stop():
     for tol, k in ((1e-4, full.iters_1e4), (1e-6, full.iters_1e6)):
         s = oracle.solve(qp, tol=tol, lambda_A=full.lambda_A, lambda_Q=full.lambda_Q)
         assert s.status == "converged" and s.iters == k
+
+
+# ------------------------------------------------------------------ preconditioning (Sec. 4.1)
+def _scaled_K(qp, d, e):
+    A, Q = D.dense_of(qp)
+    n, m = qp.n, qp.m
+    K = np.zeros((n + m, n + m))
+    K[:n, :n] = Q
+    K[n:, :n] = A
+    K[:n, n:] = A.T
+    s = np.concatenate([d, e])
+    return s[:, None] * K * s[None, :], K
+
+
+@pytest.mark.parametrize("seed,kind", [(61, "csr"), (62, "csr"), (63, "csr")])
+def test_pock_chambolle_pass_bounds_the_scaled_norm(seed, kind):
+    """After the Pock-Chambolle pass (alpha = 1) the scaled K = [Q A^T; A 0] has spectral
+    norm <= 1 (Pock and Chambolle's diagonal preconditioning lemma)."""
+    qp = qpgen.random_small(n=7, m=4, seed=seed, q_kind=kind)
+    d, e, ok = oracle.scaling(qp)
+    assert ok and np.all(d > 0) and np.all(e > 0)
+    Ks, K = _scaled_K(qp, d, e)
+    assert np.linalg.norm(Ks, 2) <= 1.0 + 1e-12
+    # the scaling is not the identity on these badly scaled matrices
+    assert not np.allclose(d, 1.0)
+
+
+def test_scaling_skipped_when_q_is_matrix_free_or_l1():
+    assert not oracle.scaling(qpgen.random_small(n=6, m=3, seed=64, q_kind="factor", q_rank=3))[2]
+    assert not oracle.scaling(qpgen.random_small(n=6, m=3, seed=65, q_kind="csr", phi="l1", lam=0.3))[2]
+
+
+@pytest.mark.parametrize("seed", [66, 68, 69])
+def test_scaled_solve_returns_the_unscaled_solution(seed):
+    """Solving the preconditioned problem and mapping back (x = D xs, y = E ys, z = zs / D)
+    gives a point that meets the stopping rule of the original problem and has its
+    optimal objective (the unscaled solve as reference)."""
+    qp = qpgen.random_small(n=8, m=5, seed=seed, q_kind="csr", box=(-1.0, 1.0))
+    # stretch the problem's scales so that the preconditioning matters
+    rng = np.random.default_rng(seed)
+    col = 10.0 ** rng.uniform(-2, 2, qp.n)
+    qp.A_vals = qp.A_vals * col[qp.A_colidx]
+    a = oracle.solve(qp, tol=1e-10, scaling=1, max_iter=200000)
+    b = oracle.solve(qp, tol=1e-10, scaling=0, max_iter=200000)
+    assert a.status == b.status == "converged"
+    assert a.pobj == pytest.approx(b.pobj, rel=1e-8, abs=1e-9)
+    e3, _, _ = oracle.eta(qp, a.x, a.y, a.z)
+    assert np.max(e3) <= 1.01e-10
+    assert np.all(a.x >= qp.L - 1e-12) and np.all(a.x <= qp.U + 1e-12)
+    assert a.iters < b.iters          # on these stretched columns the preconditioning pays
