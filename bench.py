@@ -344,24 +344,34 @@ def roofline(prof, qp, pk, pk_src, traffic):
     return r
 
 
+TRAFFIC_FILES = {"c1": "traffic_cqp_n1e6.txt"}
+
+
 def traffic_table(wname):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current
-    kernel sources; null otherwise."""
-    path = os.path.join(ROOT, "profiles", f"traffic_{wname}.json")
+    """Per-launch DRAM bytes (read + write) of each step kernel from the committed ncu summary,
+    if it was taken on the current step-kernel sources; None otherwise."""
+    name = TRAFFIC_FILES.get(wname)
+    if not name:
+        return None
     try:
-        with open(path) as f:
-            t = json.load(f)
-    except Exception:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    except OSError:
         return None
-    if t.get("source_sha") != source_sha():
+    table = {r[0]: r[1] for r in rows if len(r) >= 2}
+    if table.get("source_sha") != source_sha():
         return None
-    return t.get("bytes_per_launch")
+    return {k: float(v) for k, v in table.items() if k != "source_sha"}
+
+
+STEP_SOURCES = ("core.cuh", "solver.cuh", "kernels.cuh", "solver.cu", "rows_q.cu", "rows_a.cu", "rows_at.cu")
 
 
 def source_sha():
+    """Hash of the sources of the step kernels (a change to them voids recorded traffic)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2507_02470_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in STEP_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

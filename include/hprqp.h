@@ -113,7 +113,10 @@ typedef struct hprqp_params {
                                 nodes (variants read at run time inside the kernels);
                                 2: plain stream launches of the same step variants, chosen on
                                 the host after each step (for profilers that cannot follow
-                                conditional graph nodes; one host synchronisation per step) */
+                                conditional graph nodes; one host synchronisation per step);
+                                3: persistent solver, all passes of up to 4096 inner steps in
+                                one cooperative launch with grid barriers between passes (for
+                                small and mid-sized problems, where launch latency dominates) */
   int32_t scaling;           /* 1 (default): the Sec. 4.1 preconditioning (10 Ruiz passes, then
                                 Pock-Chambolle with alpha = 1, on K = [Q A^T; A 0]) when Q is
                                 explicit (DIAG, CSR and DIA terms only) and phi is the box
@@ -259,7 +262,8 @@ typedef struct hprqp_batch hprqp_batch;
 /* Copies `count` (>= 1) problems (host or device pointers) to the device.  params: as for
  * hprqp_create (stream, alphas, periods, power method, autotune; NULL = defaults).  The
  * autotuner times the persistent kernel's block size on a sample of the batch at the first
- * solve. */
+ * solve.  Batched instances are solved without the Sec. 4.1 preconditioning (params.scaling
+ * is ignored). */
 hprqp_status hprqp_batch_create(hprqp_batch** b, int32_t count, const hprqp_problem* probs,
                                 const hprqp_params* params);
 /* Solves every instance to max(eta_p, eta_d, eta_gap) <= tol or max_iter iterations.  Returns

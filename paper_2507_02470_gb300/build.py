@@ -16,6 +16,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhprqp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# the persistent solver reads data that other blocks of the same launch wrote: global loads
+# default to the L2-coherent path there
+PER_FILE = {"persist.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def sources():
@@ -53,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     def comp(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

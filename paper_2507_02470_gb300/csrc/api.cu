@@ -679,7 +679,14 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
         std::max<int64_t>(1, (frows * P.gPre + drows * 32 + kThreads - 1) / kThreads), (int64_t)sms * 8);
   }
   a.nbM = P.gridM;
-  const int gmax = std::max(P.gridN, P.gridM);
+  if (h->prm.launch_mode == 3) {
+    // persistent solver: one block per row chunk of the larger dimension, at most the
+    // co-resident blocks of its kernel
+    const int cap = persist_max_blocks(sms);
+    if (cap < 1) return fail(h, HPRQP_CUDA_ERROR, "persistent solver: no co-resident blocks");
+    P.gridP = (int)std::min<int64_t>(std::max(chunks(n), chunks(std::max<int64_t>(m, 1))), cap);
+  }
+  const int gmax = std::max(std::max(P.gridN, P.gridM), P.gridP);
   if ((st = zeros(h, &a.partL, (size_t)gmax * kWL))) return st;
   if ((st = zeros(h, &a.part3, (size_t)gmax * kW3))) return st;
   if ((st = zeros(h, &a.partR, (size_t)gmax * kWR))) return st;
@@ -729,8 +736,8 @@ extern "C" hprqp_status hprqp_create(hprqp_handle** out, int64_t n, int64_t m, c
   if (params) h->prm = *params;
   else hprqp_default_params(&h->prm);
   if (h->prm.check_every < 1 || h->prm.restart_every < 1 || h->prm.iters_per_launch < 1 ||
-      h->prm.iters_per_launch > 4096 || h->prm.launch_mode < 0 || h->prm.launch_mode > 2) {
-    fail(nullptr, HPRQP_INVALID_ARG, "check_every, restart_every >= 1, 1 <= iters_per_launch <= 4096, launch_mode 0..2");
+      h->prm.iters_per_launch > 4096 || h->prm.launch_mode < 0 || h->prm.launch_mode > 3) {
+    fail(nullptr, HPRQP_INVALID_ARG, "check_every, restart_every >= 1, 1 <= iters_per_launch <= 4096, launch_mode 0..3");
     delete h;
     return HPRQP_INVALID_ARG;
   }
@@ -1043,6 +1050,32 @@ static hprqp_status solve_stream(hprqp_handle* h, std::chrono::steady_clock::tim
   return finish_solve(h, t0, t1, lamA, lamQ, sigma, time_up);
 }
 
+// launch_mode 3: every pass of many inner steps in one cooperative launch (persist.cu);
+// the host checks the done flag (and the time limit) between launches.
+static hprqp_status solve_persist(hprqp_handle* h, std::chrono::steady_clock::time_point t0,
+                                  std::chrono::steady_clock::time_point t1, double lamA, double lamQ, double sigma) {
+  Args& a = h->args;
+  unsigned* bar = a.counters + 8;
+  int* err = reinterpret_cast<int*>(a.counters + 10);
+  const long long per = 4096;
+  bool time_up = false;
+  for (;;) {
+    CU(h, launch_persist(a, h->plan, h->plan.gridP, per, bar, err, h->stream));
+    h->launches += 1;
+    CU(h, cudaMemcpyAsync(h->hflags, &h->dctrl->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(h->hflags + 1, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (h->hflags[1]) return fail(h, HPRQP_TIMEOUT, "persistent solver: a grid barrier wait gave up");
+    if (h->hflags[0]) break;
+    if (h->prm.time_limit > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > h->prm.time_limit) {
+      time_up = true;
+      break;
+    }
+  }
+  return finish_solve(h, t0, t1, lamA, lamQ, sigma, time_up);
+}
+
 extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_iter) {
   if (!h) return HPRQP_INVALID_ARG;
   h->err.clear();
@@ -1070,6 +1103,7 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   CU(h, launch_stamp(a, h->stream));
   h->launches += 1;
   if (h->prm.launch_mode == 2) return solve_stream(h, t0, t1, lamA, lamQ, sigma);
+  if (h->prm.launch_mode == 3) return solve_persist(h, t0, t1, lamA, lamQ, sigma);
   if ((st = build_iter_graph(h))) return st;
   // ---- Algorithm 4 in graph launches of iters_per_launch steps; double-buffered done poll
   const int64_t per = h->prm.iters_per_launch;

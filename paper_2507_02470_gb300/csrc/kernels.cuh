@@ -22,6 +22,18 @@
 
 #include "solver.cuh"
 
+// Loads of vectors that other blocks wrote.  Separate launches may read them through the
+// read-only cache (__ldg) and with restrict-qualified pointers; the persistent solver, which
+// runs every pass inside one launch separated by grid barriers, compiles these bodies with
+// HPRQP_COHERENT so that such loads go to L2 (__ldcg) and no pointer claims read-only data.
+#ifdef HPRQP_COHERENT
+#define HPRQP_LDG(p) __ldcg(p)
+#define HPRQP_RESTRICT
+#else
+#define HPRQP_LDG(p) __ldg(p)
+#define HPRQP_RESTRICT __restrict__
+#endif
+
 namespace hprqp {
 
 // Conditional-node handles set by the controller (graph mode); zero flags when unused.
@@ -77,8 +89,8 @@ __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, dou
 // ------------------------------------------------------------------------------------ CSR pass
 // Row sums of a chunk of kChunk rows, G lanes per row, into shared rs0/rs1 (add: accumulate).
 template <int G, int NR>
-__device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* __restrict__ x0,
-                                          const double* __restrict__ x1, double* rs0, double* rs1, bool add) {
+__device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
+                                          const double* HPRQP_RESTRICT x1, double* rs0, double* rs1, bool add) {
   const int lane = threadIdx.x % G;
   const int grp = threadIdx.x / G;
   constexpr int NG = kThreads / G;
@@ -92,13 +104,13 @@ __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const doub
       for (; k + 3 * G < e; k += 4 * G) {
         const int c0 = M.ci[k], c1 = M.ci[k + G], c2 = M.ci[k + 2 * G], c3 = M.ci[k + 3 * G];
         const double v0 = M.v[k], v1 = M.v[k + G], v2 = M.v[k + 2 * G], v3 = M.v[k + 3 * G];
-        const double a0 = __ldg(x0 + c0), a1 = __ldg(x0 + c1), a2 = __ldg(x0 + c2), a3 = __ldg(x0 + c3);
+        const double a0 = HPRQP_LDG(x0 + c0), a1 = HPRQP_LDG(x0 + c1), a2 = HPRQP_LDG(x0 + c2), a3 = HPRQP_LDG(x0 + c3);
         s0 = fma(v0, a0, s0);
         s0 = fma(v1, a1, s0);
         s0 = fma(v2, a2, s0);
         s0 = fma(v3, a3, s0);
         if (NR == 2) {
-          const double b0 = __ldg(x1 + c0), b1 = __ldg(x1 + c1), b2 = __ldg(x1 + c2), b3 = __ldg(x1 + c3);
+          const double b0 = HPRQP_LDG(x1 + c0), b1 = HPRQP_LDG(x1 + c1), b2 = HPRQP_LDG(x1 + c2), b3 = HPRQP_LDG(x1 + c3);
           s1 = fma(v0, b0, s1);
           s1 = fma(v1, b1, s1);
           s1 = fma(v2, b2, s1);
@@ -108,8 +120,8 @@ __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const doub
       for (; k < e; k += G) {
         const int c = M.ci[k];
         const double vv = M.v[k];
-        s0 = fma(vv, __ldg(x0 + c), s0);
-        if (NR == 2) s1 = fma(vv, __ldg(x1 + c), s1);
+        s0 = fma(vv, HPRQP_LDG(x0 + c), s0);
+        if (NR == 2) s1 = fma(vv, HPRQP_LDG(x1 + c), s1);
       }
     }
     if (G > 1) {
@@ -148,8 +160,8 @@ __device__ __forceinline__ void q_csr_chunk(const QDev& Q, int64_t row0, const d
 }
 
 // Row-local parts of (Q x)_j: diagonal, symmetric band, and F_g^T t_g of the dense factors.
-__device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double* __restrict__ x,
-                                          const double* __restrict__ t, bool with_dense) {
+__device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double* HPRQP_RESTRICT x,
+                                          const double* HPRQP_RESTRICT t, bool with_dense) {
   double acc = 0.0;
   if (Q.diag) acc = Q.diag[j] * x[j];
   for (int k = 0; k < Q.ndia; k++) {
@@ -175,8 +187,8 @@ __device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double
 
 // ------------------------------------------------------------------------------------ K1
 template <int VAR>
-__global__ void __launch_bounds__(kThreads) k_zx(Args a) {
-  const Ctrl* __restrict__ C = a.C;
+__device__ __forceinline__ void zx_body(const Args& a) {
+  const Ctrl* HPRQP_RESTRICT C = a.C;
   if (C->done) return;
   const int mode = C->mode;
   const double ha = C->ha, hb = C->hb, sigma = C->sigma, c1 = C->c1, c2 = C->c2, tau = C->tau,
@@ -246,14 +258,17 @@ __global__ void __launch_bounds__(kThreads) k_zx(Args a) {
   }
 }
 
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) k_zx(Args a) { zx_body<VAR>(a); }
+
 // ------------------------------------------------------------------------------------ factor pre-pass
 // t = B_f x for every factor term (G lanes per row), t = F_g x for every dense term (one warp
 // per row).  which: 0 -> x = wbar_{1/2} (and xbar on stopping tests) into t1; 1 -> x = wbar into
 // t2; 2 -> x = A^*ybar - A^*y^{r,0} into t2 (restart); 3 -> x = ain into t1 (apply);
 // 4 -> x = pv into t1 (power method).  TT: 0 one vector, 1 two (stopping test), 2 read C->ttest.
 template <int G, int TT>
-__global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) {
-  const Ctrl* __restrict__ C = a.C;
+__device__ __forceinline__ void pre_body(const Args& a, int which) {
+  const Ctrl* HPRQP_RESTRICT C = a.C;
   if (which <= 2 && C->done) return;
   if (which == 2 && !C->restart_pending) return;
   if (which == 4 && C->pw_done) return;
@@ -284,9 +299,9 @@ __global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) {
         for (int k = b + lane; k < e; k += G) {
           const int c = B.ci[k];
           const double bv = B.v[k];
-          const double xc = which == 2 ? __ldg(V.ATyb + c) - __ldg(V.ATy0 + c) : __ldg(x0 + c);
+          const double xc = which == 2 ? HPRQP_LDG(V.ATyb + c) - HPRQP_LDG(V.ATy0 + c) : HPRQP_LDG(x0 + c);
           s0 = fma(bv, xc, s0);
-          if (two) s1 = fma(bv, __ldg(x1 + c), s1);
+          if (two) s1 = fma(bv, HPRQP_LDG(x1 + c), s1);
         }
       }
       if (G > 1) {
@@ -329,6 +344,9 @@ __global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) {
     }
   }
 }
+
+template <int G, int TT>
+__global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) { pre_body<G, TT>(a, which); }
 
 // ------------------------------------------------------------------------------------ controller
 // One pass of the Sec. 3.2 / Sec. 4.1 logic after an inner step; Ls: end-of-step sums,
@@ -501,8 +519,8 @@ __device__ __forceinline__ void end_iteration(EndTerms& T, const Args& a, const 
 
 // ------------------------------------------------------------------------------------ row kernels
 template <int G, int KIND, int VAR>
-__global__ void __launch_bounds__(kThreads) k_rows(Args a, Handles hd) {
-  Ctrl* __restrict__ C = a.C;
+__device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
+  Ctrl* HPRQP_RESTRICT C = a.C;
   if (KIND <= K_Q2 && C->done) return;
   if ((KIND == K_POWER_Q || KIND == K_POWER_A || KIND == K_APPLY_AT_P) && C->pw_done) return;
   __shared__ double rs0[kChunk];
@@ -669,6 +687,9 @@ __global__ void __launch_bounds__(kThreads) k_rows(Args a, Handles hd) {
   }
 }
 
+template <int G, int KIND, int VAR>
+__global__ void __launch_bounds__(kThreads) k_rows(Args a, Handles hd) { rows_body<G, KIND, VAR>(a, hd); }
+
 // ------------------------------------------------------------------------------------ restart (Alg. 5)
 __device__ __forceinline__ void sigma_argmin_dev(double t1, double t2, double t3, double lq, int golden,
                                                  double* out) {
@@ -712,8 +733,8 @@ __device__ __forceinline__ void sigma_argmin_dev(double t1, double t2, double t3
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_restart(Args a) {
-  Ctrl* __restrict__ C = a.C;
+__device__ __forceinline__ void restart_body(const Args& a) {
+  Ctrl* HPRQP_RESTRICT C = a.C;
   if (C->done || !C->restart_pending) return;
   __shared__ double rs0[kChunk];
   __shared__ double red[kWR * 32];
@@ -811,6 +832,9 @@ __global__ void __launch_bounds__(kThreads) k_restart(Args a) {
     C->restart_pending = 0;
   }
 }
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_restart(Args a) { restart_body<G>(a); }
 
 using RowKernel = void (*)(Args, Handles);
 

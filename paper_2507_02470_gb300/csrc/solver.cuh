@@ -52,6 +52,7 @@ struct Plan {
   // blocks of the plain (non-reducing) step variants: one full wave at the occupancy of each
   // kernel; the reducing variants keep gridN/gridM/gridE, which size the partial-sum regions
   int wZX = 0, wQ1 = 0, wA1 = 0, wAT = 0, wQ2 = 0;
+  int gridP = 0;   // blocks of the persistent (cooperative) solver
 };
 
 // sigma and the scalars derived from it (host and device use the same arithmetic)
@@ -87,6 +88,11 @@ cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, do
 cudaError_t launch_vmul(double* v, const double* s, int64_t n, cudaStream_t st);
 // out[i] = v[i] * s[i] for i < n
 cudaError_t launch_vmul_to(double* out, const double* v, const double* s, int64_t n, cudaStream_t st);
+// Persistent solver (persist.cu): co-resident blocks of its kernel on `sms` SMs, and one
+// cooperative launch running at most `steps` inner steps (bar: 2 zeroed words; err: flag).
+int persist_max_blocks(int sms);
+cudaError_t launch_persist(const Args& a, const Plan& p, int grid, long long steps, unsigned* bar, int* err,
+                           cudaStream_t s);
 // Records the device time stamp of the start of the iteration (tolerance ladder).
 cudaError_t launch_stamp(const Args& a, cudaStream_t s);
 // Fills the plain-variant grids of p from the occupancy of those kernels (after gQ, gA, gAT).

@@ -1,5 +1,8 @@
 """Parity of the batched persistent solver (hprqp_batch_*) with the CPU oracle.
 
+The batched solver runs every instance unpreconditioned, so its references run with
+scaling=0 (the Sec. 4.1 preconditioning would apply to the explicit-Q instance).
+
 Every instance of a batch runs Algorithm 4 with its own sigma, restart and termination state
 inside one launch; each must reproduce the oracle's iterates (1e-10 relative at the checked
 steps, same lambda_A, lambda_Q) and its converged objective (1e-6 relative at rel-KKT 1e-8).
@@ -36,7 +39,7 @@ def mixed_batch():
 def test_batch_first_iterates(pkg):
     probs = mixed_batch()
     K = 40
-    refs = [oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K) for qp in probs]
+    refs = [oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K, scaling=0) for qp in probs]
     lamA = [r.lambda_A for r in refs]
     lamQ = [r.lambda_Q for r in refs]
     for k in (1, 2, 11, 21, 40):
@@ -52,7 +55,7 @@ def test_batch_first_iterates(pkg):
 
 def test_batch_converged(pkg):
     probs = mixed_batch()
-    refs = [oracle.solve(qp, tol=1e-8, max_iter=400000) for qp in probs]
+    refs = [oracle.solve(qp, tol=1e-8, max_iter=400000, scaling=0) for qp in probs]
     with pkg.BatchSolver(probs, lambda_A=[r.lambda_A for r in refs], lambda_Q=[r.lambda_Q for r in refs]) as b:
         assert b.solve(tol=1e-8, max_iter=400000) == "converged"
         for i, (qp, ref) in enumerate(zip(probs, refs)):
@@ -69,7 +72,7 @@ def test_batch_power_method_and_defaults(pkg):
     with pkg.BatchSolver(probs) as b:
         assert b.solve(tol=1e-8, max_iter=400000) == "converged"
         for i, qp in enumerate(probs):
-            ref = oracle.solve(qp, tol=1e-8, max_iter=400000)
+            ref = oracle.solve(qp, tol=1e-8, max_iter=400000, scaling=0)
             x, y, z, kkt = b.get(i)
             assert abs(kkt["lambda_Q"] - ref.lambda_Q) <= 1e-5 * ref.lambda_Q
             assert abs(kkt["lambda_A"] - ref.lambda_A) <= 1e-5 * ref.lambda_A
@@ -82,7 +85,7 @@ def test_batch_matches_single_instance_solver(pkg):
         b.solve(tol=1e-8)
         outs = [b.get(i) for i in range(len(probs))]
     for qp, (x, y, z, kkt) in zip(probs, outs):
-        with pkg.Solver(qp) as s:
+        with pkg.Solver(qp, scaling=0) as s:
             s.solve(tol=1e-8)
             x1, y1, z1, w1, k1 = s.get()
         assert abs(kkt["pobj"] - k1["pobj"]) <= 1e-6 * (1 + abs(k1["pobj"]))

@@ -172,7 +172,7 @@ def test_invalid_arguments(pkg):
             s.solve(tol=-1.0, max_iter=10)
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_launch_modes_agree(pkg, mode):
     # the flat graph (variants read inside the kernels) and host-driven stream launches run the
     # same algorithm as the conditional graph: identical iterates up to rounding
@@ -202,3 +202,27 @@ def test_tolerance_ladder(pkg):
         for tol, key in ((1e-4, "iters_1e4"), (1e-6, "iters_1e6")):
             assert s.solve(tol=tol, max_iter=500000) == "converged"
             assert s.kkt()["iters"] == k[key]
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_persistent_solver_matches_oracle(pkg, name):
+    """launch_mode 3 (every pass of many steps in one cooperative launch, grid barriers between
+    passes) reproduces the oracle's iterates and converged objective on every family."""
+    qp = PROBLEMS[name]
+    K = 50
+    ref = oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K)
+    lam = dict(lambda_A=ref.lambda_A if qp.m else 0.0, lambda_Q=ref.lambda_Q)
+    with pkg.Solver(qp, launch_mode=3, **lam) as s:
+        for k in (1, 2, 11, 21, 50):
+            s.solve(tol=1e-30, max_iter=k)
+            x, y, *_ = s.get()
+            assert rel(x, ref.trace["x"][k - 1]) <= ITER_TOL, k
+            if qp.m:
+                assert rel(y, ref.trace["y"][k - 1]) <= ITER_TOL, k
+    full = oracle.solve(qp, tol=1e-8, max_iter=500000)
+    with pkg.Solver(qp, launch_mode=3, lambda_A=full.lambda_A if qp.m else 0.0, lambda_Q=full.lambda_Q) as s:
+        assert s.solve(tol=1e-8, max_iter=500000) == "converged"
+        x, y, z, w, kkt = s.get()
+    assert abs(kkt["pobj"] - full.pobj) <= OBJ_TOL * (1 + abs(full.pobj))
+    e, _, _ = oracle.eta(qp, x, y, z)
+    assert np.max(e) <= 1.05e-8, e
