@@ -175,25 +175,33 @@ def run_learned(args, rank, world):
     objdiff = float(np.max(np.abs(warm["pobj"] - cold["pobj"]) / np.maximum(1.0, np.abs(cold["pobj"]))))
     t_cold = float(np.mean(cold["seconds"]))
     t_warm = float(np.mean(warm["seconds"])) + t_pred / Nte
-    # tensor-core GEMM roofline: the feature projection of one batch of 256 members
+    # tensor-core GEMM roofline: the feature projection P [c; u] (512 x 150016 BF16) of a
+    # block of 4096 training members (compute-bound shape), and of one inference batch of 256
+    # members (memory-bound shape), timed alone with CUDA events
     pk, pk_src = peaks()
-    cu = torch.zeros(256, ws.Dp, dtype=torch.bfloat16, device="cuda")
-    F = torch.empty(ws.d0, 256, dtype=torch.float32, device="cuda")
     s0 = torch.cuda.current_stream()
-    for _ in range(3):
-        L.gemm_bf16(ws.P, cu, out=F, splits=8)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    e0.record(s0)
-    for _ in range(reps):
-        L.gemm_bf16(ws.P, cu, out=F, splits=8)
-    e1.record(s0)
-    torch.cuda.synchronize()
+
+    def time_gemm(nb, reps=10):
+        cu = torch.zeros(nb, ws.Dp, dtype=torch.bfloat16, device="cuda")
+        F = torch.empty(ws.d0, nb, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            L.gemm_bf16(ws.P, cu, out=F)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s0)
+        for _ in range(reps):
+            L.gemm_bf16(ws.P, cu, out=F)
+        e1.record(s0)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        flops = 2.0 * ws.d0 * nb * ws.Dp
+        byts = 2.0 * (ws.d0 + nb) * ws.Dp + 4.0 * ws.d0 * nb
+        return ms, flops / (ms * 1e-3) / 1e12, byts / (ms * 1e-3) / 1e9, L.auto_splits(ws.d0, nb, ws.Dp)
+
+    ms_big, tf_big, gb_big, sp_big = time_gemm(4096)
+    ms_inf, tf_inf, gb_inf, sp_inf = time_gemm(256, reps=20)
     L.check()
-    ms = e0.elapsed_time(e1) / reps
-    flops = 2.0 * ws.d0 * 256 * ws.Dp
-    tf = flops / (ms * 1e-3) / 1e12
     peak = float(pk.get("bf16_tflops", 1900.0))
+    hbm = float(pk.get("hbm_gbs", 6800.0))
     line = {"metric": METRIC, "value": round(t_warm, 5), "unit": "s per held-out instance to 1e-8 (learned start)",
             "n_gpus": world, "steps": Nte, "warmup": 0, "ms_per_step": round(t_warm * 1e3, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve, bf16/f32 network",
@@ -211,11 +219,18 @@ def run_learned(args, rank, world):
             "max_rel_obj_diff": objdiff,
             "train": {"solves_s": round(t_train_solves, 2), "workers": args.c4_workers,
                       "iters_mean": float(tr["iters"].mean()), "fit_s": round(rep.seconds, 2),
+                      "adam_steps": rep.steps, "train_steps_s": round(rep.train_seconds, 2),
                       "loss_sigma": rep.loss_sigma[-1], "loss_latent": rep.loss_latent[-1],
                       "latent_mu_only": rep.latent_baseline},
-            "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16 feature projection 512 x 256 x 150016 (split-K 8)",
-                         "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s", "frac": round(tf / peak, 4),
-                         "ms_per_launch": round(ms, 4), "peak_source": f"bf16 {pk_src} (burst)", "traffic": None},
+            "roofline": {"bound": "tensor",
+                         "kernel": f"k_gemm_bf16 feature projection 512 x 4096 x 150016 (split-K {sp_big})",
+                         "achieved": round(tf_big, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tf_big / peak, 4), "hbm_frac": round(gb_big / hbm, 4),
+                         "ms_per_launch": round(ms_big, 4), "peak_source": f"bf16 {pk_src} (burst)",
+                         "traffic": None,
+                         "inference_batch": {"shape": f"512 x 256 x 150016 (split-K {sp_inf})", "ms": round(ms_inf, 4),
+                                             "TFLOP/s": round(tf_inf, 1), "GB/s": round(gb_inf, 1),
+                                             "hbm_frac": round(gb_inf / hbm, 4)}},
             "clocks": clocks.summary(), "gpu_launches": None, "cpu_baseline": None}
     if rank == 0:
         print(json.dumps(line), flush=True)

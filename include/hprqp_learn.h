@@ -42,7 +42,7 @@ extern "C" {
  * order (deterministic); work must then hold splits * M * N floats.  Entries of A, B past
  * M, N, K are never read.  Requirements: lda, ldb multiples of 8 and >= K; A and B 16-byte
  * aligned; ldc >= N.  Returns HPRQP_INVALID_ARG when they fail, HPRQP_CUDA_ERROR on a
- * launch failure. */
+ * launch failure.  Tiles are 128 x BN with BN = 64 (N <= 64), 128 (N < 512) or 256. */
 hprqp_status hprqp_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
                              int64_t ldb, float* C, int64_t ldc, int32_t splits, float* work, void* stream);
 

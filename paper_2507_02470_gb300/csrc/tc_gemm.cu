@@ -318,7 +318,9 @@ cudaError_t gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, int64_t ld
   splits = (kb_total + kb_per - 1) / kb_per;   // no empty split
   if (splits > 1 && !work) return bad("splits > 1 needs a work buffer of splits*M*N floats");
   if (splits > 65535) return bad("too many splits");
-  const int BN = N <= 64 ? 64 : 128;
+  // tile width: 256 columns (128 x 256 accumulator, 256 TMEM columns) when N is wide enough
+  // to keep many tiles, else 128 or 64
+  const int BN = N <= 64 ? 64 : N < 512 ? 128 : 256;
   CUtensorMap ta, tb;
   cudaError_t e;
   if ((e = make_map(&ta, A, M, K, lda, kBM)) != cudaSuccess) return e;
@@ -326,8 +328,9 @@ cudaError_t gemm_bf16(int64_t M, int64_t N, int64_t K, const void* A, int64_t ld
   float* out = splits > 1 ? work : C;
   const int64_t ld = splits > 1 ? N : ldc;
   const int vec = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && ld % 4 == 0) ? 1 : 0;
-  e = BN == 64 ? launch<64>(ta, tb, out, ld, M * N, M, N, kb_total, kb_per, splits, vec, stream)
-               : launch<128>(ta, tb, out, ld, M * N, M, N, kb_total, kb_per, splits, vec, stream);
+  e = BN == 64    ? launch<64>(ta, tb, out, ld, M * N, M, N, kb_total, kb_per, splits, vec, stream)
+      : BN == 128 ? launch<128>(ta, tb, out, ld, M * N, M, N, kb_total, kb_per, splits, vec, stream)
+                  : launch<256>(ta, tb, out, ld, M * N, M, N, kb_total, kb_per, splits, vec, stream);
   if (e != cudaSuccess || splits == 1) return e;
   const int64_t total = M * N;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);

@@ -39,14 +39,27 @@ def round8(x: int) -> int:
     return (int(x) + 7) // 8 * 8
 
 
-def gemm_bf16(A, B, out=None, splits=1, stream=None):
+def auto_splits(M, N, K, device=None):
+    """K-splits that give about one CTA per SM (the library's tile rule: 128 x BN tiles with
+    BN = 64, 128 or 256 by N)."""
+    torch = _torch()
+    sms = torch.cuda.get_device_properties(device or torch.cuda.current_device()).multi_processor_count
+    bn = 64 if N <= 64 else 128 if N < 512 else 256
+    tiles = -(-M // 128) * -(-N // bn)
+    kb = -(-K // 64)
+    return int(max(1, min(kb, round(sms / tiles))))
+
+
+def gemm_bf16(A, B, out=None, splits=0, stream=None):
     """out (M x N, FP32) = A @ B^T for CUDA bfloat16 tensors A (M x K) and B (N x K) whose rows
-    are contiguous (any row stride that is a multiple of 8)."""
+    are contiguous (any row stride that is a multiple of 8).  splits <= 0: ``auto_splits``."""
     torch = _torch()
     M, K = A.shape
     N, K2 = B.shape
     if K2 != K or A.stride(1) != 1 or B.stride(1) != 1:
         raise ValueError("A (M x K) and B (N x K) need unit column stride")
+    if splits <= 0:
+        splits = auto_splits(M, N, K, A.device)
     if out is None:
         out = torch.empty(M, N, dtype=torch.float32, device=A.device)
     work = None
@@ -157,7 +170,9 @@ class FitReport:
     loss_sigma: List[float] = field(default_factory=list)
     loss_latent: List[float] = field(default_factory=list)
     latent_baseline: float = 0.0      # latent loss of ell = 0 (decoding to mu)
-    seconds: float = 0.0
+    seconds: float = 0.0              # whole fit (targets, features, statistics, training)
+    train_seconds: float = 0.0        # the Adam steps alone
+    steps: int = 0
 
 
 class LearnedWarmStart:
@@ -227,7 +242,7 @@ class LearnedWarmStart:
             b1 = min(N, b0 + self.chunk)
             Cs, Us = data(b0, b1)
             cu = self._pack(Cs, Us)
-            gemm_bf16(self.P, cu, out=out[:, b0:b1], splits=8, stream=self.stream)
+            gemm_bf16(self.P, cu, out=out[:, b0:b1], stream=self.stream)
         return out
 
     def features(self, Cs, Us):
@@ -260,10 +275,10 @@ class LearnedWarmStart:
         for b0 in range(0, N, self.chunk):
             b1 = min(N, b0 + self.chunk)
             dz = cast_bf16(Z[b0:b1], sub=self.mu, ld=self.Dp, rownorm2=self.dd[b0:b1], stream=s)
-            gemm_bf16(self.PhiT, dz, out=self.R[:, b0:b1], splits=8, stream=s)
+            gemm_bf16(self.PhiT, dz, out=self.R[:, b0:b1], stream=s)
             del dz
         # G = Phi^T Phi
-        self.G = gemm_bf16(self.PhiT, self.PhiT, splits=32, stream=s)
+        self.G = gemm_bf16(self.PhiT, self.PhiT, stream=s)
         # features and their statistics
         F = self.raw_features(data, N)
         self.fmean = torch.empty(self.d0, dtype=torch.float32, device=self.device)
@@ -286,6 +301,8 @@ class LearnedWarmStart:
         B = min(batch, self.max_batch)
         dO = torch.zeros(B, self.dims[-1], dtype=torch.float32, device=self.device)
         loss = torch.zeros(2, dtype=torch.float32, device=self.device)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter()
         for ep in range(epochs):
             acc = torch.zeros(2, dtype=torch.float64, device=self.device)
             nb = 0
@@ -306,6 +323,8 @@ class LearnedWarmStart:
             if log:
                 log(f"epoch {ep}: sigma {acc[0]:.4g} latent {acc[1]:.4g} (mu only {rep.latent_baseline:.4g})")
         check()
+        rep.train_seconds = time.perf_counter() - t_train
+        rep.steps = self.mlp.t
         rep.seconds = time.perf_counter() - t0
         return rep
 

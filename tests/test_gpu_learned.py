@@ -46,7 +46,8 @@ def normrel(a, b):
 
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (256, 384, 1024, 1), (200, 100, 150, 1),
-                                          (300, 50, 700, 3), (1, 1, 1, 1), (129, 65, 8, 1), (640, 256, 4096, 16)])
+                                          (300, 50, 700, 3), (1, 1, 1, 1), (129, 65, 8, 1), (640, 256, 4096, 16),
+                                          (256, 640, 192, 1), (300, 1000, 300, 2), (130, 513, 4000, 0)])
 def test_gemm_matches_exact_product(env, M, N, K, splits):
     torch, p, L = env
     rng = np.random.default_rng(M * 7 + N * 3 + K)
