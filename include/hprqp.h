@@ -123,6 +123,11 @@ typedef struct hprqp_params {
                                 indicator; the iteration runs on the scaled problem while the
                                 stopping test, hprqp_get, hprqp_apply and warm starts stay in
                                 the original variables.  0: never scale. */
+  int32_t method;            /* 0 (default): HPR-QP, Algorithm 4.  1, 2: the primal HPR methods of
+                                Appendix A (Algorithm 6 on reformulation (1.3), Algorithm 7 on
+                                (1.4)), for ablations: fixed sigma (sigma0 or the Sec. 4.1 rule),
+                                no restarts, stopping rule of Sec. 4.1 every check_every steps;
+                                they need scaling = 0 and run as stream launches */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */

@@ -60,7 +60,7 @@ class _Params(C.Structure):
                 ("lambda_A", C.c_double), ("lambda_Q", C.c_double), ("sigma0", C.c_double),
                 ("power_max_iter", C.c_int64), ("power_tol", C.c_double), ("power_safety", C.c_double),
                 ("halpern_total", C.c_int32), ("sigma_golden", C.c_int32), ("restart_off", C.c_int32),
-                ("sigma_fixed", C.c_int32), ("scaling", C.c_int32), ("x0", C.c_void_p), ("y0", C.c_void_p),
+                ("sigma_fixed", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32), ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("trace_len", C.c_int64), ("trace_x", C.c_void_p), ("trace_y", C.c_void_p),
                 ("trace_R", C.c_void_p), ("trace_sigma", C.c_void_p), ("trace_restart", C.c_void_p)]
 

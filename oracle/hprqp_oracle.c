@@ -662,6 +662,141 @@ static int solve_core(const orc_problem* P, const orc_params* prm, orc_result* r
   return status;
 }
 
+
+/* ------------------------------------------------------------------ primal HPR (Appendix A)
+ * Algorithm 6 (method 1) on min 1/2<x,Qx> + <c,x> + phi(x) + delta_K(s) s.t. Ax = s, with
+ * S_x = lambda_Q I - Q + sigma (lambda_A I - A^*A), and Algorithm 7 (method 2) on the
+ * reformulation with v = x, S_v = lambda_Q I - Q, S_x = sigma (lambda_A I - A^*A); both with
+ * the Halpern step of Step 5, fixed sigma and no restarts, as printed.  The proximal terms
+ * make the x-step separable:
+ *   method 1:  tau = lambda_Q + sigma lambda_A,
+ *              xbar = Prox_{phi/tau}(x - (Qx + c - A^*(2 ybar - y)) / tau)
+ *   method 2:  vbar = (lambda_Q v - Qv + sigma x - t) / (lambda_Q + sigma),
+ *              tau = sigma (1 + lambda_A),
+ *              xbar = Prox_{phi/tau}(x - (c - A^*(2 ybar - y) - tbar + sigma (x - vbar)) / tau)
+ * with sbar = Pi_K(Ax - y/sigma) and ybar = y + sigma (sbar - Ax) from Steps 1-2 (A^*(2 ybar - y)
+ * = A^*(ybar + sigma (sbar - Ax))).  The multiplier of phi is zbar = tau (xbar - r) for the
+ * prox argument r, so that the stopping rule of Sec. 4.1 is evaluated at (xbar, ybar, zbar). */
+static int solve_primal(const orc_problem* P, const orc_params* prm, orc_result* res, double* xout, double* yout,
+                        double* zout, double* wout) {
+  int64_t n = P->n, m = P->m;
+  const int two = prm->method == 2;
+  double lamA = prm->lambda_A > 0.0 ? prm->lambda_A
+                                    : orc_power_A(P, prm->power_max_iter, prm->power_tol, prm->power_safety);
+  double lamQ = prm->lambda_Q > 0.0 ? prm->lambda_Q
+                                    : orc_power_Q(P, prm->power_max_iter, prm->power_tol, prm->power_safety);
+  if (m > 0 && !(lamA > 0.0)) lamA = 1.0;
+  double sigma = prm->sigma0;
+  if (!(sigma > 0.0)) {
+    double bb = 0.0;
+    for (int64_t i = 0; i < m; i++) {
+      double bl = isfinite(P->l[i]) ? fabs(P->l[i]) : 0.0;
+      double bu = isfinite(P->u[i]) ? fabs(P->u[i]) : 0.0;
+      double b = fmax(bl, bu);
+      bb += b * b;
+    }
+    double nb = sqrt(bb), nc = nrm2(P->c, n);
+    sigma = (nb >= 1e-16 && nb <= 1e16 && nc >= 1e-16 && nc <= 1e16) ? nb / nc : 1.0;
+  }
+  res->lambda_A = lamA;
+  res->lambda_Q = lamQ;
+  const double tau = two ? sigma * (1.0 + lamA) : lamQ + sigma * lamA;
+  double *x = vnew(n), *s = vnew(m), *y = vnew(m), *v = vnew(n), *t = vnew(n);
+  double *x0 = vnew(n), *s0 = vnew(m), *y0 = vnew(m), *v0 = vnew(n), *t0 = vnew(n);
+  double *xb = vnew(n), *sb = vnew(m), *yb = vnew(m), *vb = vnew(n), *tb = vnew(n), *zb = vnew(n);
+  double *Ax = vnew(m), *Qv = vnew(n), *w = vnew(m), *ATw = vnew(n);
+  if (prm->x0) {
+    memcpy(x, prm->x0, sizeof(double) * n);
+    memcpy(v, prm->x0, sizeof(double) * n);
+  }
+  if (prm->y0 && m > 0) memcpy(y, prm->y0, sizeof(double) * m);
+  memcpy(x0, x, sizeof(double) * n);
+  memcpy(v0, v, sizeof(double) * n);
+  if (m > 0) memcpy(y0, y, sizeof(double) * m);
+  int64_t k = 0;
+  int status = ORC_MAX_ITER;
+  double eta3[3] = {INFINITY, INFINITY, INFINITY}, pobj = NAN, dobj = NAN;
+  for (;;) {
+    orc_amul(P, x, Ax);
+    orc_qmul(P, two ? v : x, Qv);
+    for (int64_t i = 0; i < m; i++) {
+      /* Steps 1-2: with q = Ax - y/sigma, sbar = Pi_K(q) and ybar = y + sigma (sbar - Ax)
+       * = sigma (Pi_K(q) - q), evaluated in the second form so that ybar is exactly 0 on rows
+       * where the projection is inactive (its sign then matches K exactly) */
+      const double q = Ax[i] - y[i] / sigma;
+      sb[i] = clampd(q, P->l[i], P->u[i]);
+      yb[i] = sigma * (sb[i] - q);
+      w[i] = 2.0 * yb[i] - y[i];
+    }
+    if (two)
+      for (int64_t j = 0; j < n; j++) {
+        vb[j] = (lamQ * v[j] - Qv[j] + sigma * x[j] - t[j]) / (lamQ + sigma);   /* Step 1 (v) */
+        tb[j] = t[j] + sigma * (vb[j] - x[j]);                                  /* Step 2.2 */
+      }
+    orc_atmul(P, w, ATw);
+    for (int64_t j = 0; j < n; j++) {                            /* Step 3 */
+      double g = two ? P->c[j] - ATw[j] - tb[j] + sigma * (x[j] - vb[j]) : Qv[j] + P->c[j] - ATw[j];
+      double r = x[j] - g / tau;
+      xb[j] = prox_phi(P, j, r, 1.0 / tau);
+      zb[j] = tau * (xb[j] - r);
+    }
+    int64_t kd = k + 1;
+    if (k < prm->trace_len) {
+      if (prm->trace_x) memcpy(prm->trace_x + k * n, xb, sizeof(double) * n);
+      if (prm->trace_y && m > 0) memcpy(prm->trace_y + k * m, yb, sizeof(double) * m);
+      if (prm->trace_sigma) prm->trace_sigma[k] = sigma;
+    }
+    if ((kd % prm->check_every == 0) || kd >= prm->max_iter) {
+      orc_eta(P, xb, yb, zb, eta3, &pobj, &dobj);
+      if (isnan(eta3[0]) || isnan(eta3[1]) || isnan(eta3[2]) || isinf(pobj) || isinf(dobj)) {
+        status = ORC_NUMERICAL;
+        k = kd;
+        break;
+      }
+      if (res->iters_1e4 == 0 && fmax(eta3[0], fmax(eta3[1], eta3[2])) <= 1e-4) res->iters_1e4 = kd;
+      if (res->iters_1e6 == 0 && fmax(eta3[0], fmax(eta3[1], eta3[2])) <= 1e-6) res->iters_1e6 = kd;
+      if (fmax(eta3[0], fmax(eta3[1], eta3[2])) <= prm->tol) {
+        status = ORC_CONVERGED;
+        k = kd;
+        break;
+      }
+      if (kd >= prm->max_iter) {
+        k = kd;
+        break;
+      }
+    }
+    /* Steps 4-5: u = 1/(k+2) u^0 + (k+1)/(k+2) (2 ubar - u) */
+    const double a = 1.0 / (k + 2.0), b = (k + 1.0) / (k + 2.0);
+    for (int64_t j = 0; j < n; j++) {
+      x[j] = a * x0[j] + b * (2.0 * xb[j] - x[j]);
+      if (two) {
+        v[j] = a * v0[j] + b * (2.0 * vb[j] - v[j]);
+        t[j] = a * t0[j] + b * (2.0 * tb[j] - t[j]);
+      }
+    }
+    for (int64_t i = 0; i < m; i++) {
+      s[i] = a * s0[i] + b * (2.0 * sb[i] - s[i]);
+      y[i] = a * y0[i] + b * (2.0 * yb[i] - y[i]);
+    }
+    k = kd;
+  }
+  res->eta_p = eta3[0];
+  res->eta_d = eta3[1];
+  res->eta_gap = eta3[2];
+  res->pobj = pobj;
+  res->dobj = dobj;
+  res->iters = k;
+  res->sigma = sigma;
+  res->status = status;
+  if (xout) memcpy(xout, xb, sizeof(double) * n);
+  if (yout && m > 0) memcpy(yout, yb, sizeof(double) * m);
+  if (zout) memcpy(zout, zb, sizeof(double) * n);
+  if (wout) memcpy(wout, two ? vb : xb, sizeof(double) * n);
+  free(x); free(s); free(y); free(v); free(t); free(x0); free(s0); free(y0); free(v0); free(t0);
+  free(xb); free(sb); free(yb); free(vb); free(tb); free(zb); free(Ax); free(Qv); free(w); free(ATw);
+  return status;
+}
+
 /* Algorithm 4, on the preconditioned problem when prm->scaling applies (Sec. 4.1): with
  * x = D xs and y = E ys the scaled data are A_s = E A D, Q_s = D Q D, c_s = D c,
  * [l_s, u_s] = E [l, u], [L_s, U_s] = D^{-1} [L, U]. */
@@ -669,6 +804,11 @@ int orc_solve(const orc_problem* P, const orc_params* prm, orc_result* res, doub
               double* yout, double* zout, double* wout) {
   memset(res, 0, sizeof(*res));
   if (!validate(P, prm)) {
+    res->status = ORC_INVALID;
+    return ORC_INVALID;
+  }
+  if (prm->method == 1 || prm->method == 2) return solve_primal(P, prm, res, xout, yout, zout, wout);
+  if (prm->method != 0) {
     res->status = ORC_INVALID;
     return ORC_INVALID;
   }

@@ -61,6 +61,10 @@ typedef struct {
   int32_t sigma_fixed;       /* 1: keep sigma0 at restarts */
   int32_t scaling;           /* 1: Ruiz + Pock-Chambolle preconditioning of Sec. 4.1 when Q is
                                 explicit (DIAG/CSR/DIA terms only) and phi is the box indicator */
+  int32_t method;            /* 0: dual HPR-QP (Algorithm 4); 1: primal HPR on (1.3)
+                                (Algorithm 6); 2: primal HPR on (1.4) (Algorithm 7).  The primal
+                                methods run as printed: fixed sigma (sigma0), no restarts, and
+                                without preconditioning */
   const double* x0;          /* optional warm start (n); w0 = x0 */
   const double* y0;          /* optional warm start (m) */
   /* optional per-iteration trace (first trace_len iterations), any may be NULL */

@@ -46,7 +46,7 @@ class hprqp_params(C.Structure):
                 ("sigma_golden", C.c_int32), ("restart_off", C.c_int32), ("sigma_fixed", C.c_int32),
                 ("time_limit", C.c_double), ("iters_per_launch", C.c_int32), ("autotune", C.c_int32),
                 ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("launch_mode", C.c_int32), ("scaling", C.c_int32)]
+                ("launch_mode", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32)]
 
 
 class hprqp_kkt(C.Structure):

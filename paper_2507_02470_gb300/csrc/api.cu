@@ -54,6 +54,13 @@ struct hprqp_handle {
   bool scaled = false;
   std::vector<double> hd, he;
   double *ux = nullptr, *uy = nullptr, *uz = nullptr, *uw = nullptr;
+  // primal HPR methods (Appendix A): state allocated at their first solve
+  bool primal_ready = false;
+  double *px = nullptr, *ps = nullptr, *py = nullptr, *pv = nullptr, *pt = nullptr;
+  double *px0 = nullptr, *ps0 = nullptr, *py0 = nullptr, *pv0 = nullptr, *pt0 = nullptr;
+  double *pxb = nullptr, *psb = nullptr, *pyb = nullptr, *pvb = nullptr, *ptb = nullptr, *pzb = nullptr;
+  double *pAx = nullptr, *pQv = nullptr, *pw = nullptr, *pATw = nullptr, *pAxb = nullptr, *pQxb = nullptr,
+         *pATyb = nullptr, *ppn = nullptr, *ppm = nullptr, *pout = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -222,6 +229,7 @@ extern "C" void hprqp_default_params(hprqp_params* p) {
   p->iters_per_launch = 64;
   p->autotune = 1;
   p->scaling = 1;
+  p->method = 0;
 }
 
 extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
@@ -736,8 +744,10 @@ extern "C" hprqp_status hprqp_create(hprqp_handle** out, int64_t n, int64_t m, c
   if (params) h->prm = *params;
   else hprqp_default_params(&h->prm);
   if (h->prm.check_every < 1 || h->prm.restart_every < 1 || h->prm.iters_per_launch < 1 ||
-      h->prm.iters_per_launch > 4096 || h->prm.launch_mode < 0 || h->prm.launch_mode > 3) {
-    fail(nullptr, HPRQP_INVALID_ARG, "check_every, restart_every >= 1, 1 <= iters_per_launch <= 4096, launch_mode 0..3");
+      h->prm.iters_per_launch > 4096 || h->prm.launch_mode < 0 || h->prm.launch_mode > 3 || h->prm.method < 0 ||
+      h->prm.method > 2) {
+    fail(nullptr, HPRQP_INVALID_ARG,
+         "check_every, restart_every >= 1, 1 <= iters_per_launch <= 4096, launch_mode 0..3, method 0..2");
     delete h;
     return HPRQP_INVALID_ARG;
   }
@@ -1050,6 +1060,191 @@ static hprqp_status solve_stream(hprqp_handle* h, std::chrono::steady_clock::tim
   return finish_solve(h, t0, t1, lamA, lamQ, sigma, time_up);
 }
 
+
+// ------------------------------------------------------------------------------------ primal HPR
+// Appendix A, Algorithms 6 (method 1) and 7 (method 2); see primal.cu for the steps.
+static hprqp_status primal_alloc(hprqp_handle* h) {
+  if (h->primal_ready) return HPRQP_OK;
+  const int64_t n = h->n, m = h->m;
+  hprqp_status st;
+  double** nv[] = {&h->px, &h->pv, &h->pt, &h->px0, &h->pv0, &h->pt0, &h->pxb, &h->pvb, &h->ptb, &h->pzb,
+                   &h->pQv, &h->pATw, &h->pQxb, &h->pATyb};
+  for (double** q : nv)
+    if ((st = zeros(h, q, n))) return st;
+  double** mv[] = {&h->ps, &h->py, &h->ps0, &h->py0, &h->psb, &h->pyb, &h->pAx, &h->pw, &h->pAxb};
+  for (double** q : mv)
+    if ((st = zeros(h, q, m))) return st;
+  if ((st = zeros(h, &h->ppn, (size_t)primal_eta_blocks(n) * 8))) return st;
+  if ((st = zeros(h, &h->ppm, (size_t)primal_eta_blocks(std::max<int64_t>(m, 1)) * 4))) return st;
+  if ((st = zeros(h, &h->pout, 8))) return st;
+  h->primal_ready = true;
+  return HPRQP_OK;
+}
+
+// out = op(in) through the solver's operator kernels (op 0: A, 1: A^T, 2: Q)
+static hprqp_status primal_apply(hprqp_handle* h, int op, const double* in, double* out, int64_t& launches) {
+  Vec& V = h->args.V;
+  const int64_t nin = op == 1 ? h->m : h->n, nout = op == 0 ? h->m : h->n;
+  CU(h, cudaMemcpyAsync((void*)V.ain, in, nin * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CU(h, launch_apply(h->args, h->plan, op, h->stream));
+  CU(h, cudaMemcpyAsync(out, V.aout, nout * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  launches += 1 + (op == 2 && h->args.Q.has_pre() ? 1 : 0);
+  return HPRQP_OK;
+}
+
+static hprqp_status solve_primal(hprqp_handle* h, double tol, int64_t max_iter, std::chrono::steady_clock::time_point t0,
+                                 std::chrono::steady_clock::time_point t1, double lamA, double lamQ) {
+  hprqp_status st;
+  if ((st = primal_alloc(h))) return st;
+  Args& a = h->args;
+  Vec& V = a.V;
+  const int64_t n = h->n, m = h->m;
+  const bool HQ = a.Q.present(), HA = m > 0, two = h->prm.method == 2;
+  const double sigma = initial_sigma(h);
+  const double tau = two ? sigma * (1.0 + lamA) : lamQ + sigma * lamA;
+  const size_t nb8 = n * sizeof(double), mb8 = m * sizeof(double);
+  cudaStream_t s = h->stream;
+  int64_t L = 0;
+  // starting point: x = v = x0 (warm start or origin), y = y0, s = t = 0
+  if (!h->ws_x.empty()) CU(h, cudaMemcpyAsync(h->px, h->ws_x.data(), nb8, cudaMemcpyHostToDevice, s));
+  else CU(h, cudaMemsetAsync(h->px, 0, nb8, s));
+  CU(h, cudaMemcpyAsync(h->pv, h->px, nb8, cudaMemcpyDeviceToDevice, s));
+  CU(h, cudaMemsetAsync(h->pt, 0, nb8, s));
+  if (HA) {
+    if (!h->ws_y.empty()) CU(h, cudaMemcpyAsync(h->py, h->ws_y.data(), mb8, cudaMemcpyHostToDevice, s));
+    else CU(h, cudaMemsetAsync(h->py, 0, mb8, s));
+    CU(h, cudaMemsetAsync(h->ps, 0, mb8, s));
+    CU(h, cudaMemcpyAsync(h->py0, h->py, mb8, cudaMemcpyDeviceToDevice, s));
+    CU(h, cudaMemsetAsync(h->ps0, 0, mb8, s));
+    CU(h, cudaMemsetAsync(h->pATw, 0, nb8, s));
+  } else {
+    CU(h, cudaMemsetAsync(h->pATw, 0, nb8, s));
+    CU(h, cudaMemsetAsync(h->pATyb, 0, nb8, s));
+  }
+  CU(h, cudaMemcpyAsync(h->px0, h->px, nb8, cudaMemcpyDeviceToDevice, s));
+  CU(h, cudaMemcpyAsync(h->pv0, h->pv, nb8, cudaMemcpyDeviceToDevice, s));
+  CU(h, cudaMemsetAsync(h->pt0, 0, nb8, s));
+  if (!HQ) {
+    CU(h, cudaMemsetAsync(h->pQv, 0, nb8, s));
+    CU(h, cudaMemsetAsync(h->pQxb, 0, nb8, s));
+  }
+  double out[5] = {INFINITY, INFINITY, INFINITY, NAN, NAN};
+  int status = HPRQP_MAX_ITER;
+  int64_t k = 0, k14 = 0, k16 = 0;
+  double s14 = 0.0, s16 = 0.0;
+  bool time_up = false;
+  for (;;) {
+    if (HA && (st = primal_apply(h, 0, h->px, h->pAx, L))) return st;
+    if (HQ && (st = primal_apply(h, 2, two ? h->pv : h->px, h->pQv, L))) return st;
+    if (HA) {
+      CU(h, primal_rows(h->pAx, h->py, V.l, V.u, sigma, m, h->psb, h->pyb, h->pw, s));
+      L++;
+      if ((st = primal_apply(h, 1, h->pw, h->pATw, L))) return st;
+    }
+    if (two) {
+      CU(h, primal_vt(h->pv, h->pQv, h->px, h->pt, lamQ, sigma, n, h->pvb, h->ptb, s));
+      L++;
+    }
+    CU(h, primal_x(h->px, h->pQv, V.c, h->pATw, h->pvb, h->ptb, V.L, V.U, h->phi, h->lambda, sigma, tau, two ? 1 : 0,
+                   n, h->pxb, h->pzb, s));
+    L++;
+    const int64_t kd = k + 1;
+    if (kd % h->prm.check_every == 0 || kd >= max_iter) {
+      if (HA && (st = primal_apply(h, 0, h->pxb, h->pAxb, L))) return st;
+      if (HQ && (st = primal_apply(h, 2, h->pxb, h->pQxb, L))) return st;
+      if (HA && (st = primal_apply(h, 1, h->pyb, h->pATyb, L))) return st;
+      CU(h, primal_eta(h->pxb, h->pQxb, h->pATyb, h->pzb, h->pAxb, h->pyb, a, h->b_inf, h->c_inf, h->lambda, h->ppn,
+                       h->ppm, h->pout, s));
+      L += HA ? 3 : 2;
+      CU(h, cudaMemcpyAsync(out, h->pout, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(h, cudaStreamSynchronize(s));
+      const double rk = std::max(out[0], std::max(out[1], out[2]));
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (std::isnan(out[0]) || std::isnan(out[1]) || std::isnan(out[2]) || std::isinf(out[3]) || std::isinf(out[4])) {
+        status = HPRQP_NUMERICAL_ERROR;
+        k = kd;
+        break;
+      }
+      if (!k14 && rk <= 1e-4) {
+        k14 = kd;
+        s14 = el;
+      }
+      if (!k16 && rk <= 1e-6) {
+        k16 = kd;
+        s16 = el;
+      }
+      if (rk <= tol) {
+        status = HPRQP_OK;
+        k = kd;
+        break;
+      }
+      if (kd >= max_iter) {
+        k = kd;
+        break;
+      }
+      if (h->prm.time_limit > 0 && el > h->prm.time_limit) {
+        status = HPRQP_TIME_LIMIT;
+        time_up = true;
+        k = kd;
+        break;
+      }
+    }
+    // Steps 4-5
+    const double ha = 1.0 / (k + 2.0), hb = (k + 1.0) / (k + 2.0);
+    {
+      double* u[3] = {h->px, h->pv, h->pt};
+      const double* u0[3] = {h->px0, h->pv0, h->pt0};
+      const double* ub[3] = {h->pxb, h->pvb, h->ptb};
+      CU(h, primal_halpern(u, u0, ub, two ? 3 : 1, ha, hb, n, s));
+      L++;
+    }
+    if (HA) {
+      double* u[3] = {h->ps, h->py, nullptr};
+      const double* u0[3] = {h->ps0, h->py0, nullptr};
+      const double* ub[3] = {h->psb, h->pyb, nullptr};
+      CU(h, primal_halpern(u, u0, ub, 2, ha, hb, m, s));
+      L++;
+    }
+    k = kd;
+  }
+  (void)time_up;
+  // the output of the last iteration goes where hprqp_get reads it
+  CU(h, cudaMemcpyAsync(V.xb, h->pxb, nb8, cudaMemcpyDeviceToDevice, s));
+  CU(h, cudaMemcpyAsync(V.zb, h->pzb, nb8, cudaMemcpyDeviceToDevice, s));
+  CU(h, cudaMemcpyAsync(V.wb, two ? h->pvb : h->pxb, nb8, cudaMemcpyDeviceToDevice, s));
+  if (HA) CU(h, cudaMemcpyAsync(V.yb, h->pyb, mb8, cudaMemcpyDeviceToDevice, s));
+  CU(h, cudaStreamSynchronize(s));
+  auto t2 = std::chrono::steady_clock::now();
+  hprqp_kkt& K = h->kkt;
+  std::memset(&K, 0, sizeof(K));
+  K.eta_p = out[0];
+  K.eta_d = out[1];
+  K.eta_gap = out[2];
+  K.rel_kkt = std::max(out[0], std::max(out[1], out[2]));
+  K.pobj = out[3];
+  K.dobj = out[4];
+  K.iters = k;
+  K.restarts = 0;
+  K.sigma = sigma;
+  K.lambda_A = lamA;
+  K.lambda_Q = lamQ;
+  K.solve_seconds = std::chrono::duration<double>(t2 - t0).count();
+  K.power_seconds = std::chrono::duration<double>(t1 - t0).count();
+  h->launches += L;
+  K.kernel_launches = h->launches;
+  K.status = status;
+  K.iters_1e4 = k14;
+  K.iters_1e6 = k16;
+  K.seconds_1e4 = s14;
+  K.seconds_1e6 = s16;
+  h->last_status = status;
+  h->solved = true;
+  h->last_lamA = lamA;
+  h->last_lamQ = lamQ;
+  h->last_sigma0 = sigma;
+  return (hprqp_status)status;
+}
+
 // launch_mode 3: every pass of many inner steps in one cooperative launch (persist.cu);
 // the host checks the done flag (and the time limit) between launches.
 static hprqp_status solve_persist(hprqp_handle* h, std::chrono::steady_clock::time_point t0,
@@ -1098,6 +1293,10 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
     else if ((st = power_method(h, 1, &lamQ))) return st;
   }
   auto t1 = std::chrono::steady_clock::now();
+  if (h->prm.method != 0) {
+    if (h->scaled) return fail(h, HPRQP_INVALID_ARG, "the primal methods run without preconditioning: create with scaling = 0");
+    return solve_primal(h, tol, max_iter, t0, t1, lamA, lamQ);
+  }
   const double sigma = initial_sigma(h);
   if ((st = init_state(h, lamA, lamQ, sigma, tol, max_iter))) return st;
   CU(h, launch_stamp(a, h->stream));

@@ -93,6 +93,20 @@ cudaError_t launch_vmul_to(double* out, const double* v, const double* s, int64_
 int persist_max_blocks(int sms);
 cudaError_t launch_persist(const Args& a, const Plan& p, int grid, long long steps, unsigned* bar, int* err,
                            cudaStream_t s);
+// Primal HPR methods of Appendix A (primal.cu): the elementwise steps and the stopping rule
+cudaError_t primal_rows(const double* Ax, const double* y, const double* l, const double* u, double sigma, int64_t m,
+                        double* sb, double* yb, double* w, cudaStream_t s);
+cudaError_t primal_vt(const double* v, const double* Qv, const double* x, const double* t, double lamQ, double sigma,
+                      int64_t n, double* vb, double* tb, cudaStream_t s);
+cudaError_t primal_x(const double* x, const double* Qv, const double* c, const double* ATw, const double* vb,
+                     const double* tb, const double* L, const double* U, int phi, double lambda, double sigma,
+                     double tau, int two, int64_t n, double* xb, double* zb, cudaStream_t s);
+cudaError_t primal_halpern(double* const* u, const double* const* u0, const double* const* ub, int count, double a,
+                           double b, int64_t len, cudaStream_t s);
+int primal_eta_blocks(int64_t len);
+cudaError_t primal_eta(const double* xb, const double* Qxb, const double* ATyb, const double* zb, const double* Axb,
+                       const double* yb, const Args& a, double b_inf, double c_inf, double lambda, double* part_n,
+                       double* part_m, double* out, cudaStream_t s);
 // Records the device time stamp of the start of the iteration (tolerance ladder).
 cudaError_t launch_stamp(const Args& a, cudaStream_t s);
 // Fills the plain-variant grids of p from the occupancy of those kernels (after gQ, gA, gAT).

@@ -520,3 +520,50 @@ def test_scaled_solve_returns_the_unscaled_solution(seed):
     assert np.max(e3) <= 1.01e-10
     assert np.all(a.x >= qp.L - 1e-12) and np.all(a.x <= qp.U + 1e-12)
     assert a.iters < b.iters          # on these stretched columns the preconditioning pays
+
+
+# ------------------------------------------------------------------ primal HPR (Appendix A)
+def _primal_1d():
+    g = _golden("hand_1d_primal_iterates.txt")
+    qp = qpgen.from_dense(np.array([[g["q"]]]), np.array([g["c"]]), A=np.array([[1.0]]),
+                          l=np.array([-np.inf]), u=np.array([g["U_row"]]), L=np.array([g["L"]]),
+                          U=np.array([g["U"]]))
+    return g, qp
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_primal_hpr_hand_computed_iterates(method):
+    """Algorithms 6 and 7 as printed (fixed sigma, Halpern step, no restart): three iterations
+    computed by hand (golden file)."""
+    g, qp = _primal_1d()
+    for k in range(3):
+        s = oracle.solve(qp, tol=1e-30, max_iter=k + 1, method=method, sigma0=g["sigma"],
+                         lambda_A=g["lambda_A"], lambda_Q=g["lambda_Q"], scaling=0)
+        assert s.x[0] == pytest.approx(g[f"p{method}_xbar{k}"], abs=1e-15)
+        assert s.y[0] == pytest.approx(g[f"p{method}_ybar{k}"], abs=1e-15)
+
+
+@pytest.mark.parametrize("method", [1])
+def test_primal_hpr_fixed_point_is_the_kkt_point(method):
+    """Started at a KKT point (from a tight HPR-QP solve), Algorithm 6 stays there: the first
+    iterate meets the stopping rule (its slack s is not read by Steps 1-3, so (x*, y*) fixes
+    the state; Algorithm 7 would also need t = -Q x*, which a warm start does not set)."""
+    qp = qpgen.random_small(n=8, m=5, seed=81, q_kind="csr")
+    d = oracle.solve(qp, tol=1e-13, max_iter=400000, scaling=0)
+    assert d.status == "converged"
+    s = oracle.solve(qp, tol=1e-30, max_iter=1, method=method, x0=d.x, y0=d.y, check_every=1, scaling=0)
+    assert max(s.eta_p, s.eta_d, s.eta_gap) <= 1e-9
+    assert np.allclose(s.x, d.x, atol=1e-9)
+
+
+def test_primal_hpr_converges_slower_than_hpr_qp():
+    """Ablation of Sec. 1's design choices: without restarts and sigma updates the primal
+    methods need far more iterations than Algorithm 4 for the same accuracy."""
+    qp = qpgen.random_small(n=10, m=6, seed=82, q_kind="csr")
+    d = oracle.solve(qp, tol=1e-6, max_iter=400000, scaling=0)
+    for method in (1, 2):
+        s = oracle.solve(qp, tol=1e-6, max_iter=400000, method=method, scaling=0)
+        assert s.status in ("converged", "max_iter")
+        assert s.iters > d.iters
+        if s.status == "converged":
+            assert s.pobj == pytest.approx(d.pobj, rel=1e-4, abs=1e-6)
