@@ -117,11 +117,30 @@ __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const doub
           s1 = fma(v3, b3, s1);
         }
       }
-      for (; k < e; k += G) {
-        const int c = M.ci[k];
-        const double vv = M.v[k];
-        s0 = fma(vv, HPRQP_LDG(x0 + c), s0);
-        if (NR == 2) s1 = fma(vv, HPRQP_LDG(x1 + c), s1);
+      // the remaining 0-3 entries of this lane: all loads issued before the accumulation,
+      // which keeps the entry order (and so the sums) of the one-at-a-time loop
+      if (k < e) {
+        const bool h1 = k + G < e, h2 = k + 2 * G < e;
+        const int c0 = M.ci[k];
+        const int c1 = h1 ? M.ci[k + G] : c0;
+        const int c2 = h2 ? M.ci[k + 2 * G] : c0;
+        const double v0 = M.v[k];
+        const double v1 = h1 ? M.v[k + G] : 0.0;
+        const double v2 = h2 ? M.v[k + 2 * G] : 0.0;
+        const double a0 = HPRQP_LDG(x0 + c0);
+        const double a1 = h1 ? HPRQP_LDG(x0 + c1) : 0.0;
+        const double a2 = h2 ? HPRQP_LDG(x0 + c2) : 0.0;
+        s0 = fma(v0, a0, s0);
+        if (h1) s0 = fma(v1, a1, s0);
+        if (h2) s0 = fma(v2, a2, s0);
+        if (NR == 2) {
+          const double b0 = HPRQP_LDG(x1 + c0);
+          const double b1 = h1 ? HPRQP_LDG(x1 + c1) : 0.0;
+          const double b2 = h2 ? HPRQP_LDG(x1 + c2) : 0.0;
+          s1 = fma(v0, b0, s1);
+          if (h1) s1 = fma(v1, b1, s1);
+          if (h2) s1 = fma(v2, b2, s1);
+        }
       }
     }
     if (G > 1) {
@@ -296,12 +315,51 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
         const Csr& B = Q.fac[term];
         const int64_t rl = r - Q.toff[term];
         const int b = B.rp[rl], e = B.rp[rl + 1];
-        for (int k = b + lane; k < e; k += G) {
-          const int c = B.ci[k];
-          const double bv = B.v[k];
-          const double xc = which == 2 ? HPRQP_LDG(V.ATyb + c) - HPRQP_LDG(V.ATy0 + c) : HPRQP_LDG(x0 + c);
-          s0 = fma(bv, xc, s0);
-          if (two) s1 = fma(bv, HPRQP_LDG(x1 + c), s1);
+        // four entries' loads in flight before their (in-order) accumulation: the same sums
+        // as one entry at a time, with four times the memory-level parallelism on long rows
+        auto xval = [&](int c) {
+          return which == 2 ? HPRQP_LDG(V.ATyb + c) - HPRQP_LDG(V.ATy0 + c) : HPRQP_LDG(x0 + c);
+        };
+        int k = b + lane;
+        for (; k + 3 * G < e; k += 4 * G) {
+          const int c0 = B.ci[k], c1 = B.ci[k + G], c2 = B.ci[k + 2 * G], c3 = B.ci[k + 3 * G];
+          const double v0 = B.v[k], v1 = B.v[k + G], v2 = B.v[k + 2 * G], v3 = B.v[k + 3 * G];
+          const double a0 = xval(c0), a1 = xval(c1), a2 = xval(c2), a3 = xval(c3);
+          s0 = fma(v0, a0, s0);
+          s0 = fma(v1, a1, s0);
+          s0 = fma(v2, a2, s0);
+          s0 = fma(v3, a3, s0);
+          if (two) {
+            const double b0 = HPRQP_LDG(x1 + c0), b1 = HPRQP_LDG(x1 + c1), b2 = HPRQP_LDG(x1 + c2),
+                         b3 = HPRQP_LDG(x1 + c3);
+            s1 = fma(v0, b0, s1);
+            s1 = fma(v1, b1, s1);
+            s1 = fma(v2, b2, s1);
+            s1 = fma(v3, b3, s1);
+          }
+        }
+        if (k < e) {   // the remaining 0-3 entries, loads first, same order
+          const bool h1 = k + G < e, h2 = k + 2 * G < e;
+          const int c0 = B.ci[k];
+          const int c1 = h1 ? B.ci[k + G] : c0;
+          const int c2 = h2 ? B.ci[k + 2 * G] : c0;
+          const double v0 = B.v[k];
+          const double v1 = h1 ? B.v[k + G] : 0.0;
+          const double v2 = h2 ? B.v[k + 2 * G] : 0.0;
+          const double a0 = xval(c0);
+          const double a1 = h1 ? xval(c1) : 0.0;
+          const double a2 = h2 ? xval(c2) : 0.0;
+          s0 = fma(v0, a0, s0);
+          if (h1) s0 = fma(v1, a1, s0);
+          if (h2) s0 = fma(v2, a2, s0);
+          if (two) {
+            const double b0 = HPRQP_LDG(x1 + c0);
+            const double b1 = h1 ? HPRQP_LDG(x1 + c1) : 0.0;
+            const double b2 = h2 ? HPRQP_LDG(x1 + c2) : 0.0;
+            s1 = fma(v0, b0, s1);
+            if (h1) s1 = fma(v1, b1, s1);
+            if (h2) s1 = fma(v2, b2, s1);
+          }
         }
       }
       if (G > 1) {
@@ -688,7 +746,11 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
 }
 
 template <int G, int KIND, int VAR>
-__global__ void __launch_bounds__(kThreads) k_rows(Args a, Handles hd) { rows_body<G, KIND, VAR>(a, hd); }
+// plain steps keep six blocks per SM resident (at most 40 registers): their passes are
+// latency-bound gathers, so occupancy matters more than a few extra registers
+__global__ void __launch_bounds__(kThreads, VAR == VAR_PLAIN ? 6 : 1) k_rows(Args a, Handles hd) {
+  rows_body<G, KIND, VAR>(a, hd);
+}
 
 // ------------------------------------------------------------------------------------ restart (Alg. 5)
 __device__ __forceinline__ void sigma_argmin_dev(double t1, double t2, double t3, double lq, int golden,
