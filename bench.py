@@ -171,6 +171,12 @@ def run_learned(args, rank, world):
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
         cold = L.solve_members(base, te_data, Nte, lam=lam)
         warm = L.solve_members(base, te_data, Nte, lam=lam, starts=(Z0h, sig0h))
+    # ablation on the first members: the predicted start alone (sigma0 rule) and the predicted
+    # sigma0 alone (origin start)
+    na = min(Nte, 200)
+    te_a = lambda a, b: (Cte[a:b], Ute[a:b])
+    mu_only = L.solve_members(base, te_a, na, lam=lam, starts=(Z0h[:na], np.zeros(na)))
+    sig_only = L.solve_members(base, te_a, na, lam=lam, starts=(np.zeros((na, D)), sig0h[:na]))
     conv = sum(s == "converged" for s in cold["status"]) + sum(s == "converged" for s in warm["status"])
     objdiff = float(np.max(np.abs(warm["pobj"] - cold["pobj"]) / np.maximum(1.0, np.abs(cold["pobj"]))))
     t_cold = float(np.mean(cold["seconds"]))
@@ -215,6 +221,10 @@ def run_learned(args, rank, world):
             "warm": {"iters_mean": float(warm["iters"].mean()), "s_mean": t_warm,
                      "s_median": float(np.median(warm["seconds"])) + t_pred / Nte,
                      "inference_s_per_instance": t_pred / Nte},
+            "ablation": {"members": na, "cold_iters": float(cold["iters"][:na].mean()),
+                         "start_only_iters": float(mu_only["iters"].mean()),
+                         "sigma0_only_iters": float(sig_only["iters"].mean()),
+                         "both_iters": float(warm["iters"][:na].mean())},
             "speedup_vs_plain": round(t_cold / t_warm, 3), "converged": conv, "of": 2 * Nte,
             "max_rel_obj_diff": objdiff,
             "train": {"solves_s": round(t_train_solves, 2), "workers": args.c4_workers,
@@ -406,7 +416,16 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    qp, desc = workload(args.workload)
+    import qpgen
+    if args.workload == "c3":
+        # one portfolio instance of the batch (seed 0), the sample of each step
+        qp, desc = qpgen.portfolio(0), "batched portfolio CQPs: one instance (seed 0) per step"
+    elif args.workload == "c4":
+        base = qpgen.param_family_base(n=100_000, m=50_000, seed=0)
+        qp = qpgen.param_family_instance(base, 10_000_000)
+        desc = "learned-warm-start family member (cqp n=1e5, m=5e4), cold start"
+    else:
+        qp, desc = workload(args.workload)
     lam_A = oracle.power_A(qp, 200, 1e-6, 1.01) if qp.m else 0.0
     lam_Q = oracle.power_Q(qp, 200, 1e-6, 1.01)
     per = args.ref_iters
