@@ -60,7 +60,7 @@ def _oracle_one(args):
     return s.iters, _t.perf_counter() - t
 
 
-def run_batched(args, rank, world):
+def run_batched(args, rank, world, dist=None):
     """Config 3: the portfolio batch in one persistent launch, against the plain solver."""
     import torch
     import paper_2507_02470_gb300 as pkg
@@ -92,6 +92,8 @@ def run_batched(args, rank, world):
     its = 0
     conv = 0
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
         t0 = time.perf_counter()
@@ -105,7 +107,10 @@ def run_batched(args, rank, world):
         its += k["iters"]
         conv += k["status"] == "converged"
     dev_s = ev0.elapsed_time(ev1) / 1e3
-    t_step = max(dev_s, wall) / args.steps
+    # replicas: each rank solved its own 4096 instances; slowest rank's time, all ranks' iterations
+    t_all, its_all = aggregate(dist, max(dev_s, wall), float(its) * args.steps, "cuda")
+    t_step = t_all / args.steps
+    its = its_all / args.steps
     # the plain single-instance solver on a sample of the same instances (create + solve each)
     sample = list(range(0, count, max(1, count // args.plain_sample)))[:args.plain_sample]
     plain_t, plain_its = 0.0, 0
@@ -411,6 +416,19 @@ def cpu_baseline(qp, lam_A, lam_Q, iters):
             "sample": f"first {s.iters} HPR iterations of the same solve (lambda_A, lambda_Q given), {dt:.1f} s"}
 
 
+def aggregate(dist, t_rank, units_rank, device):
+    """Whole-job figures of independent replicas: the slowest rank's time (max) and the units
+    all ranks processed (sum); dist is torch.distributed or None (one process)."""
+    if dist is None:
+        return t_rank, units_rank
+    import torch
+    tt = torch.tensor([t_rank], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([units_rank], device=device, dtype=torch.float64)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle, timed on the host cores, bounded samples per step."""
     if rank != 0:
@@ -490,7 +508,7 @@ def main():
             dist.destroy_process_group()
         return
     if args.workload == "c3":
-        run_batched(args, rank, world)
+        run_batched(args, rank, world, dist)
         if dist:
             dist.destroy_process_group()
         return
@@ -533,14 +551,7 @@ def main():
     dev_s = ev0.elapsed_time(ev1) / 1e3
     t_rank = max(dev_s, wall)
     its_rank = float(sum(iters_per_step))
-    if dist:
-        tt = torch.tensor([t_rank], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ii = torch.tensor([its_rank], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ii, op=dist.ReduceOp.SUM)
-        t_all, its_all = float(tt.item()), float(ii.item())
-    else:
-        t_all, its_all = t_rank, its_rank
+    t_all, its_all = aggregate(dist, t_rank, its_rank, "cuda")
     kk = solver.kkt()
     value = its_all / t_all
 
