@@ -23,18 +23,53 @@
 #include "solver.cuh"
 
 // Loads of vectors that other blocks wrote.  Separate launches may read them through the
-// read-only cache (__ldg) and with restrict-qualified pointers; the persistent solver, which
-// runs every pass inside one launch separated by grid barriers, compiles these bodies with
-// HPRQP_COHERENT so that such loads go to L2 (__ldcg) and no pointer claims read-only data.
+// read-only cache and with restrict-qualified pointers; the persistent solver, which runs
+// every pass inside one launch separated by grid barriers, compiles these bodies with
+// HPRQP_COHERENT so that such loads go to L2 (__ldcg, see gather_f64) and no pointer claims
+// read-only data.
 #ifdef HPRQP_COHERENT
-#define HPRQP_LDG(p) __ldcg(p)
 #define HPRQP_RESTRICT
 #else
-#define HPRQP_LDG(p) __ldg(p)
 #define HPRQP_RESTRICT __restrict__
 #endif
 
 namespace hprqp {
+
+// L2 eviction priorities for the CSR passes: the stored matrix is read once per pass
+// (evict first, no L1 allocation) while the gathered vector is reused by every row that names
+// its entries (evict last), so the 4-8 MB vectors stay in L2 while 36 MB of A streams by.
+// The persistent solver keeps plain coherent loads.
+#ifdef HPRQP_COHERENT
+struct L2Pol {
+  __device__ __forceinline__ L2Pol() {}
+};
+__device__ __forceinline__ double gather_f64(const double* p, const L2Pol&) { return __ldcg(p); }
+__device__ __forceinline__ double stream_f64(const double* p, const L2Pol&) { return *p; }
+__device__ __forceinline__ int stream_i32(const int* p, const L2Pol&) { return *p; }
+#else
+struct L2Pol {
+  unsigned long long keep, drop;
+  __device__ __forceinline__ L2Pol() {
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(drop));
+  }
+};
+__device__ __forceinline__ double gather_f64(const double* p, const L2Pol& q) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(q.keep));
+  return v;
+}
+__device__ __forceinline__ double stream_f64(const double* p, const L2Pol& q) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(q.drop));
+  return v;
+}
+__device__ __forceinline__ int stream_i32(const int* p, const L2Pol& q) {
+  int v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(q.drop));
+  return v;
+}
+#endif
 
 // Conditional-node handles set by the controller (graph mode); zero flags when unused.
 struct Handles {
@@ -94,23 +129,28 @@ __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const doub
   const int lane = threadIdx.x % G;
   const int grp = threadIdx.x / G;
   constexpr int NG = kThreads / G;
+  const L2Pol pol;
 #pragma unroll 1
   for (int rr = grp; rr < kChunk; rr += NG) {
     const int64_t row = row0 + rr;
     double s0 = 0.0, s1 = 0.0;
     if (row < M.rows) {
-      const int b = M.rp[row], e = M.rp[row + 1];
+      const int b = stream_i32(M.rp + row, pol), e = stream_i32(M.rp + row + 1, pol);
       int k = b + lane;
       for (; k + 3 * G < e; k += 4 * G) {
-        const int c0 = M.ci[k], c1 = M.ci[k + G], c2 = M.ci[k + 2 * G], c3 = M.ci[k + 3 * G];
-        const double v0 = M.v[k], v1 = M.v[k + G], v2 = M.v[k + 2 * G], v3 = M.v[k + 3 * G];
-        const double a0 = HPRQP_LDG(x0 + c0), a1 = HPRQP_LDG(x0 + c1), a2 = HPRQP_LDG(x0 + c2), a3 = HPRQP_LDG(x0 + c3);
+        const int c0 = stream_i32(M.ci + k, pol), c1 = stream_i32(M.ci + k + G, pol),
+                  c2 = stream_i32(M.ci + k + 2 * G, pol), c3 = stream_i32(M.ci + k + 3 * G, pol);
+        const double v0 = stream_f64(M.v + k, pol), v1 = stream_f64(M.v + k + G, pol),
+                     v2 = stream_f64(M.v + k + 2 * G, pol), v3 = stream_f64(M.v + k + 3 * G, pol);
+        const double a0 = gather_f64(x0 + c0, pol), a1 = gather_f64(x0 + c1, pol), a2 = gather_f64(x0 + c2, pol),
+                     a3 = gather_f64(x0 + c3, pol);
         s0 = fma(v0, a0, s0);
         s0 = fma(v1, a1, s0);
         s0 = fma(v2, a2, s0);
         s0 = fma(v3, a3, s0);
         if (NR == 2) {
-          const double b0 = HPRQP_LDG(x1 + c0), b1 = HPRQP_LDG(x1 + c1), b2 = HPRQP_LDG(x1 + c2), b3 = HPRQP_LDG(x1 + c3);
+          const double b0 = gather_f64(x1 + c0, pol), b1 = gather_f64(x1 + c1, pol), b2 = gather_f64(x1 + c2, pol),
+                       b3 = gather_f64(x1 + c3, pol);
           s1 = fma(v0, b0, s1);
           s1 = fma(v1, b1, s1);
           s1 = fma(v2, b2, s1);
@@ -121,22 +161,22 @@ __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const doub
       // which keeps the entry order (and so the sums) of the one-at-a-time loop
       if (k < e) {
         const bool h1 = k + G < e, h2 = k + 2 * G < e;
-        const int c0 = M.ci[k];
-        const int c1 = h1 ? M.ci[k + G] : c0;
-        const int c2 = h2 ? M.ci[k + 2 * G] : c0;
-        const double v0 = M.v[k];
-        const double v1 = h1 ? M.v[k + G] : 0.0;
-        const double v2 = h2 ? M.v[k + 2 * G] : 0.0;
-        const double a0 = HPRQP_LDG(x0 + c0);
-        const double a1 = h1 ? HPRQP_LDG(x0 + c1) : 0.0;
-        const double a2 = h2 ? HPRQP_LDG(x0 + c2) : 0.0;
+        const int c0 = stream_i32(M.ci + k, pol);
+        const int c1 = h1 ? stream_i32(M.ci + k + G, pol) : c0;
+        const int c2 = h2 ? stream_i32(M.ci + k + 2 * G, pol) : c0;
+        const double v0 = stream_f64(M.v + k, pol);
+        const double v1 = h1 ? stream_f64(M.v + k + G, pol) : 0.0;
+        const double v2 = h2 ? stream_f64(M.v + k + 2 * G, pol) : 0.0;
+        const double a0 = gather_f64(x0 + c0, pol);
+        const double a1 = h1 ? gather_f64(x0 + c1, pol) : 0.0;
+        const double a2 = h2 ? gather_f64(x0 + c2, pol) : 0.0;
         s0 = fma(v0, a0, s0);
         if (h1) s0 = fma(v1, a1, s0);
         if (h2) s0 = fma(v2, a2, s0);
         if (NR == 2) {
-          const double b0 = HPRQP_LDG(x1 + c0);
-          const double b1 = h1 ? HPRQP_LDG(x1 + c1) : 0.0;
-          const double b2 = h2 ? HPRQP_LDG(x1 + c2) : 0.0;
+          const double b0 = gather_f64(x1 + c0, pol);
+          const double b1 = h1 ? gather_f64(x1 + c1, pol) : 0.0;
+          const double b2 = h2 ? gather_f64(x1 + c2, pol) : 0.0;
           s1 = fma(v0, b0, s1);
           if (h1) s1 = fma(v1, b1, s1);
           if (h2) s1 = fma(v2, b2, s1);
@@ -307,6 +347,7 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
     const int lane = threadIdx.x % G;
     const int64_t grp = gt / G, ngrp = gs / G;
     const int64_t ffac_pad = (ffac + ngrp - 1) / ngrp * ngrp;  // uniform trip count for the shuffles
+    const L2Pol pol;
     for (int64_t r = grp; r < ffac_pad; r += ngrp) {
       double s0 = 0.0, s1 = 0.0;
       if (r < ffac) {
@@ -314,24 +355,26 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
         while (term + 1 < Q.nfac && r >= Q.toff[term + 1]) term++;
         const Csr& B = Q.fac[term];
         const int64_t rl = r - Q.toff[term];
-        const int b = B.rp[rl], e = B.rp[rl + 1];
+        const int b = stream_i32(B.rp + rl, pol), e = stream_i32(B.rp + rl + 1, pol);
         // four entries' loads in flight before their (in-order) accumulation: the same sums
         // as one entry at a time, with four times the memory-level parallelism on long rows
         auto xval = [&](int c) {
-          return which == 2 ? HPRQP_LDG(V.ATyb + c) - HPRQP_LDG(V.ATy0 + c) : HPRQP_LDG(x0 + c);
+          return which == 2 ? gather_f64(V.ATyb + c, pol) - gather_f64(V.ATy0 + c, pol) : gather_f64(x0 + c, pol);
         };
         int k = b + lane;
         for (; k + 3 * G < e; k += 4 * G) {
-          const int c0 = B.ci[k], c1 = B.ci[k + G], c2 = B.ci[k + 2 * G], c3 = B.ci[k + 3 * G];
-          const double v0 = B.v[k], v1 = B.v[k + G], v2 = B.v[k + 2 * G], v3 = B.v[k + 3 * G];
+          const int c0 = stream_i32(B.ci + k, pol), c1 = stream_i32(B.ci + k + G, pol),
+                    c2 = stream_i32(B.ci + k + 2 * G, pol), c3 = stream_i32(B.ci + k + 3 * G, pol);
+          const double v0 = stream_f64(B.v + k, pol), v1 = stream_f64(B.v + k + G, pol),
+                       v2 = stream_f64(B.v + k + 2 * G, pol), v3 = stream_f64(B.v + k + 3 * G, pol);
           const double a0 = xval(c0), a1 = xval(c1), a2 = xval(c2), a3 = xval(c3);
           s0 = fma(v0, a0, s0);
           s0 = fma(v1, a1, s0);
           s0 = fma(v2, a2, s0);
           s0 = fma(v3, a3, s0);
           if (two) {
-            const double b0 = HPRQP_LDG(x1 + c0), b1 = HPRQP_LDG(x1 + c1), b2 = HPRQP_LDG(x1 + c2),
-                         b3 = HPRQP_LDG(x1 + c3);
+            const double b0 = gather_f64(x1 + c0, pol), b1 = gather_f64(x1 + c1, pol),
+                         b2 = gather_f64(x1 + c2, pol), b3 = gather_f64(x1 + c3, pol);
             s1 = fma(v0, b0, s1);
             s1 = fma(v1, b1, s1);
             s1 = fma(v2, b2, s1);
@@ -340,12 +383,12 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
         }
         if (k < e) {   // the remaining 0-3 entries, loads first, same order
           const bool h1 = k + G < e, h2 = k + 2 * G < e;
-          const int c0 = B.ci[k];
-          const int c1 = h1 ? B.ci[k + G] : c0;
-          const int c2 = h2 ? B.ci[k + 2 * G] : c0;
-          const double v0 = B.v[k];
-          const double v1 = h1 ? B.v[k + G] : 0.0;
-          const double v2 = h2 ? B.v[k + 2 * G] : 0.0;
+          const int c0 = stream_i32(B.ci + k, pol);
+          const int c1 = h1 ? stream_i32(B.ci + k + G, pol) : c0;
+          const int c2 = h2 ? stream_i32(B.ci + k + 2 * G, pol) : c0;
+          const double v0 = stream_f64(B.v + k, pol);
+          const double v1 = h1 ? stream_f64(B.v + k + G, pol) : 0.0;
+          const double v2 = h2 ? stream_f64(B.v + k + 2 * G, pol) : 0.0;
           const double a0 = xval(c0);
           const double a1 = h1 ? xval(c1) : 0.0;
           const double a2 = h2 ? xval(c2) : 0.0;
@@ -353,9 +396,9 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
           if (h1) s0 = fma(v1, a1, s0);
           if (h2) s0 = fma(v2, a2, s0);
           if (two) {
-            const double b0 = HPRQP_LDG(x1 + c0);
-            const double b1 = h1 ? HPRQP_LDG(x1 + c1) : 0.0;
-            const double b2 = h2 ? HPRQP_LDG(x1 + c2) : 0.0;
+            const double b0 = gather_f64(x1 + c0, pol);
+            const double b1 = h1 ? gather_f64(x1 + c1, pol) : 0.0;
+            const double b2 = h2 ? gather_f64(x1 + c2, pol) : 0.0;
             s1 = fma(v0, b0, s1);
             if (h1) s1 = fma(v1, b1, s1);
             if (h2) s1 = fma(v2, b2, s1);
