@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libhprqp_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-QKIND = {"diag": 1, "csr": 2, "dia": 3, "factor": 4, "dense_factor": 5}
+QKIND = {"diag": 1, "csr": 2, "dia": 3, "factor": 4, "dense_factor": 5, "qap": 6}
 STATUS = {0: "converged", 1: "max_iter", 3: "numerical_error", 4: "invalid_arg"}
 
 

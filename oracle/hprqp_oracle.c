@@ -68,6 +68,26 @@ void orc_qmul(const orc_problem* P, const double* v, double* out) {
       for (int64_t r = 0; r < q->p; r++)
         for (int32_t k = q->rowptr[r]; k < q->rowptr[r + 1]; k++) out[q->colidx[k]] += q->vals[k] * t1[r];
       free(t1);
+    } else if (q->kind == ORC_Q_QAP) {
+      /* Sec. 4.5: Q vec(X) = vec(Ahat X Bhat - S X - X T), all four d x d and symmetric */
+      const int64_t d = q->p;
+      const double *Ah = q->dense, *Bh = q->dense + d * d, *S = q->dense + 2 * d * d, *T = q->dense + 3 * d * d;
+      double* AX = vnew(d * d);
+      for (int64_t i = 0; i < d; i++)
+        for (int64_t j = 0; j < d; j++) {
+          double s = 0.0;
+          for (int64_t k = 0; k < d; k++) s += Ah[i * d + k] * v[k + j * d];
+          AX[i + j * d] = s;
+        }
+      for (int64_t i = 0; i < d; i++)
+        for (int64_t j = 0; j < d; j++) {
+          double s = 0.0;
+          for (int64_t k = 0; k < d; k++) s += AX[i + k * d] * Bh[k * d + j];
+          for (int64_t k = 0; k < d; k++) s -= S[i * d + k] * v[k + j * d];
+          for (int64_t k = 0; k < d; k++) s -= v[i + k * d] * T[k * d + j];
+          out[i + j * d] += s;
+        }
+      free(AX);
     } else if (q->kind == ORC_Q_DENSE) {
       /* F^T (F v), F row-major p x n */
       double* t1 = vnew(q->p);

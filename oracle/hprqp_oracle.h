@@ -16,7 +16,7 @@
 extern "C" {
 #endif
 
-enum { ORC_Q_DIAG = 1, ORC_Q_CSR = 2, ORC_Q_DIA = 3, ORC_Q_FACTOR = 4, ORC_Q_DENSE = 5 };
+enum { ORC_Q_DIAG = 1, ORC_Q_CSR = 2, ORC_Q_DIA = 3, ORC_Q_FACTOR = 4, ORC_Q_DENSE = 5, ORC_Q_QAP = 6 };
 enum { ORC_PHI_BOX = 0, ORC_PHI_L1 = 1, ORC_PHI_L1_BOX = 2 };
 enum { ORC_CONVERGED = 0, ORC_MAX_ITER = 1, ORC_NUMERICAL = 3, ORC_INVALID = 4 };
 
@@ -30,7 +30,10 @@ typedef struct {
   int32_t ndiag;             /* DIA: symmetric band, offsets >= 0 */
   const int32_t* offsets;
   const double* diags;       /* DIA: ndiag x n, diags[k*n+i] = Q[i][i+off_k] */
-  const double* dense;       /* DIAG: n entries; DENSE: F row-major p x n */
+  const double* dense;       /* DIAG: n entries; DENSE: F row-major p x n; QAP: the symmetric
+                                d x d matrices Ahat, Bhat, S, T one after another (p = d,
+                                n = d^2), Q vec(X) = vec(Ahat X Bhat - S X - X T) with
+                                vec(X)[i + j d] = X[i][j] (Sec. 4.5) */
 } orc_qterm;
 
 typedef struct {

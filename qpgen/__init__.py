@@ -31,14 +31,15 @@ _PHI_NAMES = {"box": PHI_BOX, "l1": PHI_L1, "l1_box": PHI_L1_BOX}
 
 @dataclass
 class QTerm:
-    kind: str                                   # diag | csr | dia | factor | dense_factor
+    kind: str                                   # diag | csr | dia | factor | dense_factor | qap
     p: int = 0                                  # rows of B or F
     rowptr: Optional[np.ndarray] = None         # int32
     colidx: Optional[np.ndarray] = None         # int32
     vals: Optional[np.ndarray] = None           # float64
     offsets: Optional[np.ndarray] = None        # int32, dia only
     diags: Optional[np.ndarray] = None          # float64 [ndiag, n], dia only
-    dense: Optional[np.ndarray] = None          # float64: diag (n,) or F (p, n) row-major
+    dense: Optional[np.ndarray] = None          # float64: diag (n,), F (p, n) row-major, or the four
+                                                # symmetric d x d matrices of a qap term (p = d)
 
 
 @dataclass
@@ -94,6 +95,12 @@ def qterm_scipy(t: QTerm, n: int) -> sp.csr_matrix:
     if t.kind == "dense_factor":
         F = np.asarray(t.dense).reshape(t.p, n)
         return sp.csr_matrix(F.T @ F)
+    if t.kind == "qap":
+        d = t.p
+        M = np.asarray(t.dense).reshape(4, d, d)
+        I = np.eye(d)
+        # column-major vec: vec(A X B) = (B^T kron A) vec(X), vec(S X) = (I kron S), vec(X T) = (T^T kron I)
+        return sp.csr_matrix(np.kron(M[1], M[0]) - np.kron(I, M[2]) - np.kron(M[3], I))
     raise ValueError(t.kind)
 
 
@@ -342,6 +349,67 @@ def ws_family_data(base: QP, seeds) -> tuple:
         C[k] = q.c
         U[k] = q.u
     return C, U
+
+
+def qap_matrices(d: int, seed: int = 0):
+    """A QAPLIB-like pair: a symmetric flow matrix (integers 0..9 on 60 % of the pairs, zero
+    diagonal) and the Manhattan distances of d random points on a sqrt(d)-sized grid."""
+    rng = np.random.default_rng(seed)
+    F = rng.integers(0, 10, (d, d)) * (rng.random((d, d)) < 0.6)
+    F = np.triu(F, 1)
+    F = (F + F.T).astype(np.float64)
+    side = max(2, int(np.ceil(np.sqrt(d))) + 1)
+    pts = rng.integers(0, side, (d, 2))
+    D = np.abs(pts[:, None, :] - pts[None, :, :]).sum(axis=2).astype(np.float64)
+    return F, D
+
+
+def qap_relaxation(d: int = 16, seed: int = 0, Ahat=None, Bhat=None) -> QP:
+    """The convex QAP relaxation of Sec. 4.5: min <vec X, Qhat vec X> over doubly stochastic
+    X >= 0, Qhat = Bhat (x) Ahat - I (x) S - T (x) I, passed as one matrix-free "qap" term
+    (Q = 2 Qhat, c = 0).  S = V_A diag(s) V_A^T, T = V_B diag(t) V_B^T from the eigen-
+    decompositions of Ahat (alpha descending) and Bhat (beta ascending) and an optimal (s, t)
+    of max <e, s + t> s.t. s_i + t_j <= alpha_i beta_j, solved numerically (HiGHS)."""
+    import scipy.optimize as so
+    if Ahat is None or Bhat is None:
+        Ahat, Bhat = qap_matrices(d, seed)
+    d = Ahat.shape[0]
+    aw, av = np.linalg.eigh(Ahat)
+    oa = np.argsort(-aw)
+    alpha, VA = aw[oa], av[:, oa]
+    bw, bv = np.linalg.eigh(Bhat)
+    ob = np.argsort(bw)
+    beta, VB = bw[ob], bv[:, ob]
+    # LP in (s, t): rows s_i + t_j <= alpha_i beta_j
+    ii, jj = np.meshgrid(np.arange(d), np.arange(d), indexing="ij")
+    rows = np.arange(d * d)
+    Aub = sp.csr_matrix((np.ones(2 * d * d), (np.concatenate([rows, rows]),
+                                              np.concatenate([ii.ravel(), d + jj.ravel()]))), shape=(d * d, 2 * d))
+    res = so.linprog(-np.ones(2 * d), A_ub=Aub, b_ub=np.outer(alpha, beta).ravel(), bounds=(None, None),
+                     method="highs")
+    if res.status != 0:
+        raise RuntimeError(f"QAP bound LP failed: {res.message}")
+    sv, tv = res.x[:d], res.x[d:]
+    S = VA @ np.diag(sv) @ VA.T
+    T = VB @ np.diag(tv) @ VB.T
+    S = 0.5 * (S + S.T)
+    T = 0.5 * (T + T.T)
+    n = d * d
+    dense = np.concatenate([2.0 * Ahat, Bhat, 2.0 * S, 2.0 * T]).reshape(-1)
+    term = QTerm("qap", p=d, dense=dense)
+    # X e = e (row sums) and X^T e = e (column sums), vec(X)[i + j d] = X[i][j]
+    r_rows = np.repeat(np.arange(d), d)                 # row-sum constraint i: entries (i, j) for all j
+    r_cols = (np.arange(d)[:, None] + d * np.arange(d)[None, :]).ravel()
+    c_rows = d + np.repeat(np.arange(d), d)             # column-sum constraint j: entries (i, j) for all i
+    c_cols = (np.arange(d)[None, :] + d * np.arange(d)[:, None]).ravel()
+    Amat = sp.csr_matrix((np.ones(2 * n), (np.concatenate([r_rows, c_rows]), np.concatenate([r_cols, c_cols]))),
+                         shape=(2 * d, n))
+    rp, ci, va = csr_from_scipy(Amat)
+    qp = QP(n, 2 * d, rp, ci, va, np.zeros(n), np.ones(2 * d), np.ones(2 * d), np.zeros(n), np.full(n, np.inf),
+            PHI_BOX, 0.0, [term], name=f"qap_d{d}_s{seed}")
+    qp.qap_bound_const = float(sv.sum() + tv.sum())
+    qp.qap_Ahat, qp.qap_Bhat = Ahat, Bhat
+    return qp
 
 
 # --------------------------------------------------------------------------------------

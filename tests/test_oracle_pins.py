@@ -567,3 +567,54 @@ def test_primal_hpr_converges_slower_than_hpr_qp():
         assert s.iters > d.iters
         if s.status == "converged":
             assert s.pobj == pytest.approx(d.pobj, rel=1e-4, abs=1e-6)
+
+
+# ------------------------------------------------------------------ QAP relaxation (Sec. 4.5)
+def test_qap_operator_is_the_kronecker_form_and_psd():
+    """Q vec(X) = vec(Ahat X Bhat - S X - X T) equals (Bhat (x) Ahat - I (x) S - T (x) I) vec(X)
+    (column-major vec), and the LP-derived S, T leave it positive semidefinite."""
+    qp = qpgen.qap_relaxation(d=7, seed=3)
+    A, Q = D.dense_of(qp)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        v = rng.standard_normal(qp.n)
+        assert np.allclose(oracle.qmul(qp, v), Q @ v, rtol=1e-12, atol=1e-10)
+    assert np.linalg.eigvalsh(Q).min() >= -1e-9 * np.abs(Q).max()
+
+
+def test_qap_bound_lp_value_and_permutation_identity():
+    """The (s, t) LP's value is sum_i alpha_i beta_i (alpha descending, beta ascending: the
+    rearrangement inequality makes the identity assignment optimal in its dual), and for every
+    permutation matrix P the relaxation's objective plus sum(s) + sum(t) is the QAP objective
+    tr(Ahat P Bhat P^T)."""
+    d = 6
+    qp = qpgen.qap_relaxation(d=d, seed=4)
+    Ah, Bh = qp.qap_Ahat, qp.qap_Bhat
+    alpha = np.sort(np.linalg.eigvalsh(Ah))[::-1]
+    beta = np.sort(np.linalg.eigvalsh(Bh))
+    assert qp.qap_bound_const == pytest.approx(float(alpha @ beta), rel=1e-9, abs=1e-9)
+    _, Q = D.dense_of(qp)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        perm = rng.permutation(d)
+        P = np.eye(d)[perm]
+        x = P.reshape(-1, order="F")
+        rel_obj = 0.5 * x @ (Q @ x)               # the solver's objective is 1/2 <x, Qx>, Q = 2 Qhat
+        assert rel_obj + qp.qap_bound_const == pytest.approx(np.trace(Ah @ P @ Bh @ P.T), rel=1e-9, abs=1e-9)
+
+
+def test_qap_relaxation_bound_below_brute_force_optimum():
+    """The oracle's optimum of the relaxation plus the LP constant is a lower bound of the QAP
+    optimum found by enumerating all permutations (d = 6)."""
+    import itertools
+    d = 6
+    qp = qpgen.qap_relaxation(d=d, seed=5)
+    s = oracle.solve(qp, tol=1e-9, max_iter=400000)
+    assert s.status == "converged"
+    Ah, Bh = qp.qap_Ahat, qp.qap_Bhat
+    best = min(np.trace(Ah @ np.eye(d)[list(p)] @ Bh @ np.eye(d)[list(p)].T) for p in itertools.permutations(range(d)))
+    qpb = s.pobj + qp.qap_bound_const
+    assert qpb <= best + 1e-6
+    assert qpb >= qp.qap_bound_const - 1e-6        # Qhat is PSD
+    X = s.x.reshape(d, d, order="F")
+    assert np.allclose(X.sum(axis=0), 1, atol=1e-6) and np.allclose(X.sum(axis=1), 1, atol=1e-6)
