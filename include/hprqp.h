@@ -50,7 +50,12 @@ typedef enum hprqp_qkind {
                                 diags[k*n + i] = Q[i][i + offsets[k]] (entries with
                                 i + offsets[k] >= n are ignored)                          */
   HPRQP_Q_FACTOR = 4,        /* Q += B^T B, B a p x n CSR matrix (matrix-free)            */
-  HPRQP_Q_DENSE_FACTOR = 5   /* Q += F^T F, F a dense row-major p x n matrix              */
+  HPRQP_Q_DENSE_FACTOR = 5,  /* Q += F^T F, F a dense row-major p x n matrix              */
+  HPRQP_Q_QAP = 6            /* Q vec(X) += vec(Ahat X Bhat - S X - X T) for d x d X with
+                                n = d^2, vec(X)[i + j d] = X[i][j] (the QAP relaxation of
+                                Sec. 4.5): p = d, dense = Ahat, Bhat, S, T (symmetric d x d,
+                                4 d^2 values one after another); applied with cuBLAS DGEMMs;
+                                at most one such term; not with launch_mode 3 */
 } hprqp_qkind;
 
 typedef enum hprqp_phi {

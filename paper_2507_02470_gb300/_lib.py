@@ -21,7 +21,7 @@ HPRQP_OK, HPRQP_MAX_ITER, HPRQP_TIME_LIMIT, HPRQP_NUMERICAL_ERROR = 0, 1, 2, 3
 HPRQP_INVALID_ARG, HPRQP_CUDA_ERROR, HPRQP_TIMEOUT, HPRQP_OOM = 4, 5, 6, 7
 STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "time_limit", 3: "numerical_error", 4: "invalid_arg",
                 5: "cuda_error", 6: "timeout", 7: "oom"}
-QKIND = {"diag": 1, "csr": 2, "dia": 3, "factor": 4, "dense_factor": 5}
+QKIND = {"diag": 1, "csr": 2, "dia": 3, "factor": 4, "dense_factor": 5, "qap": 6}
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

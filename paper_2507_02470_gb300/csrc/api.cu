@@ -5,6 +5,8 @@
 // transposed row is fixed), pick the SpMV schedule, run the power method of Sec. 4.1, and
 // drive Algorithm 4 as a CUDA graph of `iters_per_launch` inner steps whose kernels stop
 // themselves once the device-side controller has set the done flag.
+#include <cublas_v2.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -54,6 +56,8 @@ struct hprqp_handle {
   bool scaled = false;
   std::vector<double> hd, he;
   double *ux = nullptr, *uy = nullptr, *uz = nullptr, *uw = nullptr;
+  void* blas = nullptr;            // cuBLAS handle (QAP term only)
+  void* blas_ws = nullptr;
   // primal HPR methods (Appendix A): state allocated at their first solve
   bool primal_ready = false;
   double *px = nullptr, *ps = nullptr, *py = nullptr, *pv = nullptr, *pt = nullptr;
@@ -239,6 +243,7 @@ extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
 static void release(hprqp_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
   if (h->g_iter) cudaGraphExecDestroy(h->g_iter);
   for (auto& g : h->g_pw)
     if (g) cudaGraphExecDestroy(g);
@@ -316,6 +321,22 @@ static hprqp_status data_norms(hprqp_handle* h, const std::vector<double>& hc, c
   h->nc2 = nc2;
   h->b_inf = bi;
   h->c_inf = ci;
+  return HPRQP_OK;
+}
+
+// cuBLAS handle with a fixed workspace (the products are captured into CUDA graphs)
+static hprqp_status blas_init(hprqp_handle* h) {
+  if (h->blas) return HPRQP_OK;
+  cublasHandle_t b;
+  if (cublasCreate(&b) != CUBLAS_STATUS_SUCCESS) return fail(h, HPRQP_CUDA_ERROR, "cublasCreate failed");
+  h->blas = b;
+  const size_t ws = (size_t)32 << 20;
+  void* p = nullptr;
+  hprqp_status st = dalloc(h, &p, ws);
+  if (st) return st;
+  h->blas_ws = p;
+  if (cublasSetWorkspace(b, p, ws) != CUBLAS_STATUS_SUCCESS) return fail(h, HPRQP_CUDA_ERROR, "cublasSetWorkspace failed");
+  h->plan.blas = b;
   return HPRQP_OK;
 }
 
@@ -438,6 +459,8 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   std::vector<std::vector<double>> dia_vals;
   std::vector<HostCsr> facs;
   std::vector<std::pair<int64_t, std::vector<double>>> dens;
+  int64_t qap_d = 0;
+  std::vector<double> qap_vals;
   std::vector<HostCsr> csr_terms;
   int nterms = Q ? Q->nterms : 0;
   if (nterms < 0 || (nterms > 0 && !Q->terms)) return fail(h, HPRQP_INVALID_ARG, "bad Q operator");
@@ -504,6 +527,14 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
       for (double x : F)
         if (!std::isfinite(x)) return fail(h, HPRQP_INVALID_ARG, "Q dense factor: non-finite value");
       dens.push_back({q.p, std::move(F)});
+    } else if (q.kind == HPRQP_Q_QAP) {
+      if (qap_d) return fail(h, HPRQP_INVALID_ARG, "at most one QAP term");
+      if (q.p <= 0 || q.p * q.p != n) return fail(h, HPRQP_INVALID_ARG, "QAP term: need p = d with n = d^2");
+      if (h->prm.launch_mode == 3) return fail(h, HPRQP_INVALID_ARG, "QAP term: not with launch_mode 3");
+      if ((st = fetch(h, qap_vals, q.dense, (size_t)4 * q.p * q.p))) return st;
+      for (double x : qap_vals)
+        if (!std::isfinite(x)) return fail(h, HPRQP_INVALID_ARG, "QAP term: non-finite value");
+      qap_d = q.p;
     } else {
       return fail(h, HPRQP_INVALID_ARG, "unknown Q term kind %d", q.kind);
     }
@@ -633,6 +664,21 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     QD.dense_p[g] = dens[g].first;
     QD.toff[QD.nfac + g] = toff;
     toff += dens[g].first;
+  }
+  QD.tfd = toff;
+  if (qap_d) {
+    // the QAP product x -> vec(Ahat X Bhat - S X - X T) goes to the intermediate buffers
+    // after the factor rows; cuBLAS runs its four DGEMMs on the handle's stream
+    double *dq, *tmp, *qin;
+    if ((st = upload(h, &dq, qap_vals)) || (st = zeros(h, &tmp, (size_t)qap_d * qap_d)) || (st = zeros(h, &qin, n)))
+      return st;
+    QD.qap_d = qap_d;
+    QD.qap = dq;
+    QD.qap_tmp = tmp;
+    QD.qap_in = qin;
+    QD.qap_off = toff;
+    toff += n;
+    if ((st = blas_init(h))) return st;
   }
   QD.tlen = toff;
 

@@ -41,9 +41,18 @@ struct QDev {
   int64_t dense_p[kMaxDense] = {0};
   const double* dense[kMaxDense] = {nullptr};   // F_g row-major p x n
   int64_t toff[kMaxFac + kMaxDense] = {0};
-  int64_t tlen = 0;
-  __host__ __device__ bool present() const { return diag || csr.rows || ndia || nfac || ndense; }
-  __host__ __device__ bool has_pre() const { return nfac || ndense; }
+  // QAP term (Sec. 4.5): Ahat, Bhat, S, T (d x d each, contiguous); its product Q_qap x is
+  // formed before a pass (cuBLAS) into the intermediate buffer at qap_off, like B_f x
+  int64_t qap_d = 0;
+  const double* qap = nullptr;
+  double* qap_tmp = nullptr;    // d x d scratch
+  double* qap_in = nullptr;     // n scratch (restart difference)
+  int64_t qap_off = 0;
+  int64_t tfd = 0;              // intermediate rows of the factor and dense terms
+  int64_t tlen = 0;             // tfd, plus n for the QAP product
+  __host__ __device__ bool present() const { return diag || csr.rows || ndia || nfac || ndense || qap_d; }
+  __host__ __device__ bool has_pre() const { return nfac || ndense || qap_d; }   // products before a pass
+  __host__ __device__ bool has_fd() const { return nfac || ndense; }             // ... by k_pre
 };
 
 // Scalars of the running iteration.  Written by the controller (the last block of the

@@ -233,6 +233,7 @@ __device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double
       if (j - o >= 0) acc = fma(d[j - o], x[j - o], acc);
     }
   }
+  if (Q.qap_d) acc += t[Q.qap_off + j];   // (Q_qap x)_j, formed before the pass
   if (with_dense) {
     for (int g = 0; g < Q.ndense; g++) {
       const double* F = Q.dense[g];
@@ -422,7 +423,7 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
   if (Q.ndense) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = gt >> 5, nwarps = gs >> 5;
-    for (int64_t r = ffac + warp; r < Q.tlen; r += nwarps) {
+    for (int64_t r = ffac + warp; r < Q.tfd; r += nwarps) {
       int term = Q.nfac;
       while (term + 1 < nt && r >= Q.toff[term + 1]) term++;
       const int64_t rl = r - Q.toff[term];
@@ -893,6 +894,7 @@ __device__ __forceinline__ void restart_body(const Args& a) {
               if (j - o >= 0) qd = fma(dg[j - o], V.ATyb[j - o] - V.ATy0[j - o], qd);
             }
           }
+          if (Q.qap_d) qd += V.t2[Q.qap_off + j];   // (Q_qap d)_j from the pre-pass
           S[4] = fma(d, qd, S[4]);
         }
       }
@@ -903,7 +905,7 @@ __device__ __forceinline__ void restart_body(const Args& a) {
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   if (HQ && HA) {
-    for (int64_t r = gt; r < Q.tlen; r += gs) S[4] = fma(V.t2[r], V.t2[r], S[4]);
+    for (int64_t r = gt; r < Q.tfd; r += gs) S[4] = fma(V.t2[r], V.t2[r], S[4]);
   }
   for (int64_t i = gt; i < a.m; i += gs) {
     const double dy = V.yb[i] - V.y0[i];

@@ -75,7 +75,7 @@ struct PersistParams {
 __global__ void __launch_bounds__(kThreads) k_persist(Args a, PersistParams p) {
   const Handles none;
   Ctrl* C = a.C;
-  const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
+  const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_fd();   // (no QAP term here)
   for (long long it = 0; it < p.steps; ++it) {
     if (*(volatile int*)&C->done) return;
     // one inner step, in the order of the separate launches

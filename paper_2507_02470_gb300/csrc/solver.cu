@@ -7,6 +7,8 @@
 // the solve is done.  The controller in the last block of every step sets the value of its own
 // restart IF node and of the next SWITCH node with cudaGraphSetConditional, so the host only
 // polls a done flag between launches.
+#include <cublas_v2.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -55,6 +57,48 @@ static ZxKernel zxk(int var) {
     if (ev) cudaEventRecord(ev[kind][1], s); \
   } while (0)
 
+
+// ------------------------------------------------------------------------------------ QAP term
+// out = vec(Ahat X Bhat - S X - X T) for X = reshape(x, d, d) column-major (Sec. 4.5); all
+// four matrices symmetric, so row- and column-major storage coincide.
+static cudaError_t qap_product(const QDev& Q, cublasHandle_t b, const double* x, double* out) {
+  const int d = (int)Q.qap_d;
+  const double *Ah = Q.qap, *Bh = Q.qap + (size_t)d * d, *S = Q.qap + 2 * (size_t)d * d, *T = Q.qap + 3 * (size_t)d * d;
+  const double one = 1.0, zero = 0.0, mone = -1.0;
+  cublasStatus_t st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &one, Ah, d, x, d, &zero, Q.qap_tmp, d);
+  if (st == CUBLAS_STATUS_SUCCESS)
+    st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &one, Q.qap_tmp, d, Bh, d, &zero, out, d);
+  if (st == CUBLAS_STATUS_SUCCESS) st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &mone, S, d, x, d, &one, out, d);
+  if (st == CUBLAS_STATUS_SUCCESS) st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &mone, x, d, T, d, &one, out, d);
+  return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
+
+__global__ void k_qap_diff(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
+                           int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) out[i] = a[i] - b[i];
+}
+
+cudaError_t launch_qap(const Args& a, const Plan& p, int which, int tt, cudaStream_t s) {
+  const QDev& Q = a.Q;
+  if (!Q.qap_d) return cudaSuccess;
+  cublasHandle_t b = (cublasHandle_t)p.blas;
+  if (!b || cublasSetStream(b, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorNotReady;
+  const Vec& V = a.V;
+  double* t = (which == 0 || which >= 3) ? V.t1 : V.t2;
+  const double* x = which == 0 ? (a.m > 0 ? V.wh : V.wb) : which == 1 ? V.wb : which == 3 ? V.ain : which == 4 ? V.pv
+                                                                                                     : Q.qap_in;
+  if (which == 2) {
+    const int blocks = (int)std::min<int64_t>((a.n + kThreads - 1) / kThreads, 152 * 8);
+    k_qap_diff<<<blocks, kThreads, 0, s>>>(V.ATyb, V.ATy0, Q.qap_in, a.n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = qap_product(Q, b, x, t + Q.qap_off);
+  if (e == cudaSuccess && which == 0 && tt != 0) e = qap_product(Q, b, V.xb, t + Q.tlen + Q.qap_off);
+  return e;
+}
+
 // One inner step in variant `var`; the last kernel of the step receives the handles.
 cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, const Handles& hd,
                         cudaEvent_t (*ev)[2]) {
@@ -65,14 +109,26 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   const bool pl = var == VAR_PLAIN && p.wZX > 0;
   TIMED(0, (zxk(var)<<<pl ? p.wZX : p.gridE, kThreads, 0, s>>>(a)));
   if (HQ) {
-    if (pre) TIMED(1, (prek(p.gPre, tt)<<<p.gridPre, kThreads, 0, s>>>(a, 0)));
+    if (pre) {
+      if (ev) cudaEventRecord(ev[1][0], s);
+      if (a.Q.has_fd()) prek(p.gPre, tt)<<<p.gridPre, kThreads, 0, s>>>(a, 0);
+      const cudaError_t qe = launch_qap(a, p, 0, tt, s);
+      if (qe != cudaSuccess) return qe;
+      if (ev) cudaEventRecord(ev[1][1], s);
+    }
     TIMED(2, (rowk(K_Q1, var, p.gQ)<<<pl ? p.wQ1 : p.gridN, kThreads, 0, s>>>(a, HA ? none : hd)));
   }
   if (HA) {
     TIMED(3, (rowk(K_A1, var, p.gA)<<<pl ? p.wA1 : p.gridM, kThreads, 0, s>>>(a, none)));
     TIMED(4, (rowk(K_AT, var, p.gAT)<<<pl ? p.wAT : p.gridN, kThreads, 0, s>>>(a, HQ ? none : hd)));
     if (HQ) {
-      if (pre) TIMED(5, (prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 1)));
+      if (pre) {
+        if (ev) cudaEventRecord(ev[5][0], s);
+        if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 1);
+        const cudaError_t qe = launch_qap(a, p, 1, 0, s);
+        if (qe != cudaSuccess) return qe;
+        if (ev) cudaEventRecord(ev[5][1], s);
+      }
       TIMED(6, (rowk(K_Q2, var, p.gQ)<<<pl ? p.wQ2 : p.gridN, kThreads, 0, s>>>(a, hd)));
     }
   }
@@ -126,7 +182,13 @@ cudaError_t plan_plain_grids(const Args& a, Plan& p, int sms) {
 }
 
 cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2]) {
-  if (a.Q.present() && a.m > 0 && a.Q.has_pre()) TIMED(7, (prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 2)));
+  if (a.Q.present() && a.m > 0 && a.Q.has_pre()) {
+    if (ev) cudaEventRecord(ev[7][0], s);
+    if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 2);
+    const cudaError_t qe = launch_qap(a, p, 2, 0, s);
+    if (qe != cudaSuccess) return qe;
+    if (ev) cudaEventRecord(ev[7][1], s);
+  }
   const int G = p.gQ;
   void (*kr)(Args) = G == 1 ? k_restart<1> : G == 2 ? k_restart<2> : G == 4 ? k_restart<4>
                      : G == 8 ? k_restart<8> : G == 16 ? k_restart<16> : k_restart<32>;
@@ -142,15 +204,20 @@ cudaError_t launch_step_var(const Args& a, const Plan& p, cudaStream_t s, int va
   return launch_step(a, p, s, var, Handles(), ev);
 }
 
+// kernels before a Q pass: the factor pre-pass and the four DGEMMs of a QAP product
+static int pre_kernels(const Args& a) { return (a.Q.has_fd() ? 1 : 0) + (a.Q.qap_d ? 4 : 0); }
+
 int kernels_per_step(const Args& a) {
-  const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
+  const bool HQ = a.Q.present(), HA = a.m > 0;
   int k = 1;
-  if (HQ) k += 1 + (pre ? 1 : 0);
-  if (HA) k += 2 + (HQ ? 1 + (pre ? 1 : 0) : 0);
+  if (HQ) k += 1 + pre_kernels(a);
+  if (HA) k += 2 + (HQ ? 1 + pre_kernels(a) : 0);
   if (!HQ && !HA) k += 1;
   return k;
 }
-int kernels_per_restart(const Args& a) { return 1 + ((a.Q.present() && a.m > 0 && a.Q.has_pre()) ? 1 : 0); }
+int kernels_per_restart(const Args& a) {
+  return 1 + ((a.Q.present() && a.m > 0 && a.Q.has_pre()) ? pre_kernels(a) + (a.Q.qap_d ? 1 : 0) : 0);
+}
 int kernels_per_iteration(const Args& a) { return kernels_per_step(a) + kernels_per_restart(a); }
 
 // ------------------------------------------------------------------------------------ dispatch
@@ -250,7 +317,11 @@ cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s) {
   } else if (op == 1) {
     rowk(K_APPLY_AT, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
   } else {
-    if (a.Q.has_pre()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 3);
+    if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 3);
+    {
+      const cudaError_t qe = launch_qap(a, p, 3, 0, s);
+      if (qe != cudaSuccess) return qe;
+    }
     rowk(K_APPLY_Q, 0, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, none);
   }
   return cudaGetLastError();
@@ -293,7 +364,11 @@ cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStrea
     rowk(K_APPLY_AT_P, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
     rowk(K_POWER_A, 0, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none);
   } else {
-    if (a.Q.has_pre()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 4);
+    if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 4);
+    {
+      const cudaError_t qe = launch_qap(a, p, 4, 0, s);
+      if (qe != cudaSuccess) return qe;
+    }
     rowk(K_POWER_Q, 0, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, none);
   }
   return cudaGetLastError();

@@ -53,6 +53,7 @@ struct Plan {
   // kernel; the reducing variants keep gridN/gridM/gridE, which size the partial-sum regions
   int wZX = 0, wQ1 = 0, wA1 = 0, wAT = 0, wQ2 = 0;
   int gridP = 0;   // blocks of the persistent (cooperative) solver
+  void* blas = nullptr;   // cuBLAS handle for a QAP term's products
 };
 
 // sigma and the scalars derived from it (host and device use the same arithmetic)
@@ -107,6 +108,9 @@ int primal_eta_blocks(int64_t len);
 cudaError_t primal_eta(const double* xb, const double* Qxb, const double* ATyb, const double* zb, const double* Axb,
                        const double* yb, const Args& a, double b_inf, double c_inf, double lambda, double* part_n,
                        double* part_m, double* out, cudaStream_t s);
+// The QAP term's product(s) before a pass that needs them (which as for k_pre; tt: 0 one
+// vector, 1 or 2 also x-bar for the stopping test); no-op without a QAP term.
+cudaError_t launch_qap(const Args& a, const Plan& p, int which, int tt, cudaStream_t s);
 // Records the device time stamp of the start of the iteration (tolerance ladder).
 cudaError_t launch_stamp(const Args& a, cudaStream_t s);
 // Fills the plain-variant grids of p from the occupancy of those kernels (after gQ, gA, gAT).
