@@ -41,6 +41,9 @@ def workload(name: str):
         return qpgen.plain_cqp(), "cqp n=1000 m=500 A 1% dense, Q=M^T M (M 100 x 1000, 2%), C=[0,10]^n"
     if name == "c2":
         return qpgen.lasso(), "lasso p=5e4 q=5e5 nnz(B)=1.25e7, Q=B^T B matrix-free, lam=0.1||B^T b||_inf"
+    if name == "qap":
+        return qpgen.qap_relaxation(d=256, seed=0), \
+            "QAP relaxation (Sec. 4.5) d=256: n=65536, m=512, Q = Bhat(x)Ahat - I(x)S - T(x)I matrix-free (cuBLAS DGEMMs)"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -333,6 +336,8 @@ def algorithmic(qp):
         elif t.kind == "dense_factor":
             q_bytes += 8 * t.p * n
             q_flops += t.p * n
+        elif t.kind == "qap":
+            q_bytes += 8 * n            # the product formed by cuBLAS before the pass, added in it
     pre_bytes = 12 * fac_nnz + 4 * sum(t.p + 1 for t in qp.qterms if t.kind == "factor")
     pre_flops = fac_nnz
     HA = m > 0
@@ -473,7 +478,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4", "qap"])
     ap.add_argument("--c4-train", type=int, default=2000)
     ap.add_argument("--c4-test", type=int, default=100)
     ap.add_argument("--c4-epochs", type=int, default=30)
