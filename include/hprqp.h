@@ -152,6 +152,15 @@ typedef struct hprqp_kkt {
   double seconds_1e4, seconds_1e6;
 } hprqp_kkt;
 
+/* One stopping test of a solve (every check_every iterations, Sec. 4.1). */
+typedef struct hprqp_check {
+  int64_t iter, restarts;    /* iterations and restarts completed at the test */
+  double sigma;              /* penalty parameter in use */
+  double eta_p, eta_d, eta_gap, pobj, dobj;
+  double R;                  /* the last R~ of eq. (2.12) evaluated */
+  double seconds;            /* device time since the first inner step */
+} hprqp_check;
+
 /* Kernel kinds reported by hprqp_profile. */
 enum {
   HPRQP_PROF_ZX = 0,         /* pending Halpern/restart update + eqs. (3.1)-(3.3), elementwise */
@@ -213,6 +222,10 @@ hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* in, double* 
  * averaged over the steps that restarted).  The iterate is left in an unspecified state:
  * call hprqp_solve again before hprqp_get.  Requires a previous hprqp_solve. */
 hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms);
+
+/* Copies the records of the stopping tests of the last hprqp_solve (Algorithm 4 only; the
+ * last 512 are kept), oldest first, into out (host memory, cap entries) and sets *count. */
+hprqp_status hprqp_history(hprqp_handle* h, hprqp_check* out, int32_t cap, int32_t* count);
 
 /* Allocation-free power method.  The paper has no counterpart to this entry point; it exists
  * for callers that cannot allocate device memory at the moment they need lambda_A: code that

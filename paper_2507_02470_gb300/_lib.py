@@ -63,6 +63,12 @@ class hprqp_kkt(C.Structure):
         return d
 
 
+class hprqp_check(C.Structure):
+    _fields_ = [("iter", C.c_int64), ("restarts", C.c_int64), ("sigma", C.c_double), ("eta_p", C.c_double),
+                ("eta_d", C.c_double), ("eta_gap", C.c_double), ("pobj", C.c_double), ("dobj", C.c_double),
+                ("R", C.c_double), ("seconds", C.c_double)]
+
+
 class hprqp_problem(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("Q", C.POINTER(hprqp_qop)), ("A_rowptr", C.c_void_p),
                 ("A_colidx", C.c_void_p), ("A_vals", C.c_void_p), ("c", C.c_void_p), ("l", C.c_void_p),
@@ -93,6 +99,7 @@ SIGNATURES = [
     ("hprqp_batch_last_error", C.c_char_p, [_vp]),
     ("hprqp_last_error", C.c_char_p, [_vp]),
     ("hprqp_set_data", C.c_int, [_vp, _vp, _vp, _vp]),
+    ("hprqp_history", C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     ("hprqp_set_lambda", C.c_int, [_vp, _dbl, _dbl]),
     # learned warm start (include/hprqp_learn.h)
     ("hprqp_gemm_bf16", C.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
@@ -289,6 +296,13 @@ class Solver:
         k = hprqp_kkt()
         self._check(lib().hprqp_get(self.h, None, None, None, None, C.byref(k)))
         return k.as_dict()
+
+    def history(self, cap=512):
+        """The stopping tests of the last solve (oldest first) as a list of dicts."""
+        buf = (hprqp_check * cap)()
+        cnt = _i32(0)
+        self._check(lib().hprqp_history(self.h, C.cast(buf, _vp), cap, C.byref(cnt)))
+        return [{k: getattr(buf[i], k) for k, _ in hprqp_check._fields_} for i in range(cnt.value)]
 
     def apply(self, op, v):
         """op 'A' (n -> m), 'AT' (m -> n) or 'Q' (n -> n) applied on the GPU."""

@@ -6,6 +6,7 @@
 // drive Algorithm 4 as a CUDA graph of `iters_per_launch` inner steps whose kernels stop
 // themselves once the device-side controller has set the done flag.
 #include <cublas_v2.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -68,6 +69,12 @@ struct hprqp_handle {
 };
 
 static thread_local std::string g_create_err;
+
+// NVTX range for profilers (setup, power method, iteration, output); free when none attaches
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // ------------------------------------------------------------------------------------ helpers
 static hprqp_status fail(hprqp_handle* h, hprqp_status st, const char* fmt, ...) {
@@ -750,6 +757,8 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     if ((st = dalloc(h, &p, 16 * sizeof(unsigned)))) return st;
     CU(h, cudaMemsetAsync(p, 0, 16 * sizeof(unsigned), h->stream));
     a.counters = (unsigned*)p;
+    if ((st = dalloc(h, &p, sizeof(CheckRec) * kHistCap))) return st;
+    a.hist = (CheckRec*)p;
     if ((st = dalloc(h, &p, sizeof(Ctrl)))) return st;
     CU(h, cudaMemsetAsync(p, 0, sizeof(Ctrl), h->stream));
     h->dctrl = (Ctrl*)p;
@@ -808,7 +817,11 @@ extern "C" hprqp_status hprqp_create(hprqp_handle** out, int64_t n, int64_t m, c
     }
     h->own_stream = true;
   }
-  hprqp_status st = create_impl(h, n, m, Q, A_rowptr, A_colidx, A_vals, c, l, u, L, U, phi, lambda);
+  hprqp_status st;
+  {
+    Range r("hprqp_create");
+    st = create_impl(h, n, m, Q, A_rowptr, A_colidx, A_vals, c, l, u, L, U, phi, lambda);
+  }
   if (st != HPRQP_OK) {
     if (g_create_err.empty()) g_create_err = h->err;
     release(h);
@@ -949,6 +962,7 @@ static hprqp_status build_pw_graph(hprqp_handle* h, int which) {
 // Power method of Sec. 4.1 on A A^* (which = 0, R^m) or Q (which = 1, R^n); returns the
 // Rayleigh quotient at convergence times the safety factor.
 static hprqp_status power_method(hprqp_handle* h, int which, double* lam) {
+  Range rg(which == 0 ? "hprqp_power_A" : "hprqp_power_Q");
   const int64_t dim = which == 0 ? h->m : h->n;
   hprqp_status st;
   if ((st = build_pw_graph(h, which))) return st;
@@ -1347,6 +1361,7 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   if ((st = init_state(h, lamA, lamQ, sigma, tol, max_iter))) return st;
   CU(h, launch_stamp(a, h->stream));
   h->launches += 1;
+  Range rg("hprqp_iterate");
   if (h->prm.launch_mode == 2) return solve_stream(h, t0, t1, lamA, lamQ, sigma);
   if (h->prm.launch_mode == 3) return solve_persist(h, t0, t1, lamA, lamQ, sigma);
   if ((st = build_iter_graph(h))) return st;
@@ -1425,6 +1440,24 @@ static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::tim
   return (hprqp_status)status;
 }
 
+extern "C" hprqp_status hprqp_history(hprqp_handle* h, hprqp_check* out, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return HPRQP_INVALID_ARG;
+  if (!h->solved) return fail(h, HPRQP_INVALID_ARG, "hprqp_history before hprqp_solve");
+  static_assert(sizeof(hprqp_check) == sizeof(CheckRec), "record layouts differ");
+  const long long total = h->prm.method != 0 ? 0 : h->hctrl->hist_n;
+  const int64_t kept = std::min<long long>(total, kHistCap);
+  const int64_t nout = std::min<int64_t>(kept, cap);
+  std::vector<CheckRec> ring(kHistCap);
+  CU(h, cudaMemcpy(ring.data(), h->args.hist, sizeof(CheckRec) * kHistCap, cudaMemcpyDeviceToHost));
+  // the last nout records, oldest first
+  for (int64_t i = 0; i < nout; i++) {
+    const long long idx = (total - nout + i) % kHistCap;
+    std::memcpy(&out[i], &ring[idx], sizeof(CheckRec));
+  }
+  *count = (int32_t)nout;
+  return HPRQP_OK;
+}
+
 extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms) {
   if (!h) return HPRQP_INVALID_ARG;
   if (!h->solved) return fail(h, HPRQP_INVALID_ARG, "hprqp_profile before hprqp_solve");
@@ -1488,6 +1521,7 @@ static hprqp_status copy_out(hprqp_handle* h, double* dst, const double* src, si
 extern "C" hprqp_status hprqp_get(hprqp_handle* h, double* x, double* y, double* z, double* w, hprqp_kkt* kkt) {
   if (!h) return HPRQP_INVALID_ARG;
   if (!h->solved) return fail(h, HPRQP_INVALID_ARG, "hprqp_get before hprqp_solve");
+  Range rg("hprqp_get");
   hprqp_status st;
   Vec& V = h->args.V;
   if (z && h->last_status == HPRQP_TIME_LIMIT) CU(h, launch_zbar(h->args, h->plan, h->stream));

@@ -55,6 +55,13 @@ struct QDev {
   __host__ __device__ bool has_fd() const { return nfac || ndense; }             // ... by k_pre
 };
 
+// One stopping test of a solve (the controller appends it to a ring of kHistCap records).
+constexpr int kHistCap = 512;
+struct CheckRec {
+  long long iter, restarts;
+  double sigma, eta_p, eta_d, eta_gap, pobj, dobj, R, seconds;
+};
+
 // Scalars of the running iteration.  Written by the controller (the last block of the
 // last kernel of an iteration) and by the restart kernel; read by every kernel.
 struct Ctrl {
@@ -85,6 +92,7 @@ struct Ctrl {
   // with the device time stamp (%globaltimer, ns) of that test and of the first step
   long long ladder_k[2];
   unsigned long long ladder_ns[2], t0_ns;
+  long long hist_n;            // stopping tests recorded so far (ring of kHistCap)
   // power method state
   double pw_lam, pw_scale;
   long long pw_it, pw_max;

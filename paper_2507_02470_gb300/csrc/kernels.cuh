@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) { pre_body<
 // ------------------------------------------------------------------------------------ controller
 // One pass of the Sec. 3.2 / Sec. 4.1 logic after an inner step; Ls: end-of-step sums,
 // P3: y-step sums.  Runs on one thread.
-__device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const double* P3) {
+__device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const double* P3, CheckRec* hist = nullptr) {
   const long long kd = C.k + 1;
   bool bad = false;
   double R = 0.0;
@@ -478,6 +478,20 @@ __device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const doub
     C.dobj = dobj;
     if (isnan(eta_p) || isnan(eta_d) || isnan(eta_g) || isinf(pobj) || isinf(dobj)) bad = true;
     const double rk = fmax(eta_p, fmax(eta_d, eta_g));
+    if (hist) {
+      CheckRec& h = hist[C.hist_n % kHistCap];
+      h.iter = kd;
+      h.restarts = C.r;
+      h.sigma = C.sigma;
+      h.eta_p = eta_p;
+      h.eta_d = eta_d;
+      h.eta_gap = eta_g;
+      h.pobj = pobj;
+      h.dobj = dobj;
+      h.R = C.R;
+      h.seconds = 1e-9 * (double)(global_ns() - C.t0_ns);
+      C.hist_n++;
+    }
     if (!bad && C.ladder_k[0] == 0 && rk <= 1e-4) {
       C.ladder_k[0] = kd;
       C.ladder_ns[0] = global_ns();
@@ -614,7 +628,7 @@ __device__ __forceinline__ void end_iteration(EndTerms& T, const Args& a, const 
     if (a.m > 0) reduce_partials<kW3>(a.part3, a.nbM, kW3, 0x6u, P3, red);
   }
   if (threadIdx.x == 0) {
-    controller(*a.C, Ls, P3);
+    controller(*a.C, Ls, P3, a.hist);
     set_handles(*a.C, hd);
   }
 }

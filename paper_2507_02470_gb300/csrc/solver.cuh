@@ -39,6 +39,7 @@ struct Args {
   double* partP;
   unsigned* counters;       // [0] end-of-iteration, [1] restart, [2] power
   int nbM;                  // blocks of the m-row kernel (rows of part3)
+  CheckRec* hist;           // stopping-test records (kHistCap), or null
 };
 
 // Row-kernel kinds

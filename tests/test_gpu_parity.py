@@ -226,3 +226,22 @@ def test_persistent_solver_matches_oracle(pkg, name):
     assert abs(kkt["pobj"] - full.pobj) <= OBJ_TOL * (1 + abs(full.pobj))
     e, _, _ = oracle.eta(qp, x, y, z)
     assert np.max(e) <= 1.05e-8, e
+
+
+def test_stopping_test_history(pkg):
+    """Every stopping test of a solve is recorded on the device (iteration, restarts, sigma,
+    eta's, objectives, R~, device time); the last one is the solve's result."""
+    qp = PROBLEMS["plain"]
+    with pkg.Solver(qp) as s:
+        assert s.solve(tol=1e-8, max_iter=500000) == "converged"
+        k = s.kkt()
+        hist = s.history()
+    assert len(hist) == min(512, k["iters"] // 100)
+    assert [h["iter"] for h in hist] == list(range(k["iters"] - 100 * (len(hist) - 1), k["iters"] + 1, 100))
+    last = hist[-1]
+    for key in ("eta_p", "eta_d", "eta_gap", "pobj", "dobj", "sigma"):
+        assert last[key] == k[key], key
+    assert last["restarts"] == k["restarts"]
+    secs = [h["seconds"] for h in hist]
+    assert all(b >= a for a, b in zip(secs, secs[1:])) and secs[0] > 0
+    assert max(last["eta_p"], last["eta_d"], last["eta_gap"]) <= 1e-8
