@@ -351,20 +351,23 @@ class LearnedWarmStart:
         self.mlp.close()
 
 
-def solve_members(base, data, N, stream=None, Z=None, starts=None, lam=None, tol=1e-8, workers=1):
+def solve_members(base, data, N, stream=None, Z=None, starts=None, lam=None, tol=1e-8, workers=1,
+                  fallback=True):
     """Solves members 0..N-1 of a family with the plain solver (one handle per worker thread,
     each on its own CUDA stream).  data(b0, b1) -> (Cs, Us) as in ``LearnedWarmStart.fit``;
     starts: optional (Z0 (N x D) host/CUDA, sigma0 (N,)) warm starts; lam: (lambda_A,
-    lambda_Q) to skip the power method.  Writes solutions into Z (N x D, CUDA) if given and
-    returns a dict of per-member iterations, seconds, objectives, final sigmas and the
-    lambdas used."""
+    lambda_Q) to skip the power method.  With ``fallback`` a member whose warm start is
+    rejected (non-finite) or whose warm-started solve does not converge is solved again from
+    the origin (counted in "fallbacks").  Writes solutions into Z (N x D, CUDA) if given and
+    returns a dict of per-member iterations, seconds, objectives, final sigmas, the lambdas
+    used and the fallback count."""
     import threading
     import time
     import torch
     from ._lib import Solver
     n, m = base.n, base.m
     out = {"iters": np.zeros(N, dtype=np.int64), "seconds": np.zeros(N), "pobj": np.zeros(N),
-           "sigma": np.zeros(N), "status": [""] * N}
+           "sigma": np.zeros(N), "status": [""] * N, "fallbacks": 0}
     lam_box = [lam]
     lock = threading.Lock()
     errors = []
@@ -380,12 +383,24 @@ def solve_members(base, data, N, stream=None, Z=None, starts=None, lam=None, tol
                     Cs, Us = data(b0, b0 + 1)
                     s.set_data(c=Cs[0], u=Us[0])
                     t0 = time.perf_counter()
-                    if starts is not None:
+                    warm_ok = starts is not None
+                    if warm_ok:
                         z0, sg = starts
-                        s.set_warm_start(z0[b0, :n], z0[b0, n:], float(sg[b0]))
-                    else:
+                        try:
+                            s.set_warm_start(z0[b0, :n], z0[b0, n:], float(sg[b0]))
+                        except HPRQPError:
+                            if not fallback:
+                                raise
+                            warm_ok = False
+                    if not warm_ok:
                         s.set_warm_start(None, None, 0.0)
                     status = s.solve(tol=tol)
+                    if starts is not None and fallback and (not warm_ok or status != "converged"):
+                        if warm_ok:                     # the warm-started solve failed: cold
+                            s.set_warm_start(None, None, 0.0)
+                            status = s.solve(tol=tol)
+                        with lock:
+                            out["fallbacks"] += 1
                     dt = time.perf_counter() - t0
                     if Z is not None:
                         _, _, _, _, k = s.get(Z[b0, :n], Z[b0, n:], None, None)

@@ -224,3 +224,19 @@ def test_learned_warm_start_reduces_iterations(env):
     assert np.all(np.abs(warm["pobj"] - cold["pobj"]) <= 1e-6 * np.maximum(1.0, np.abs(cold["pobj"])))
     assert warm["iters"].mean() < 0.9 * cold["iters"].mean(), (warm["iters"].mean(), cold["iters"].mean())
     ws.close()
+
+
+def test_warm_start_falls_back_to_cold(env):
+    """A rejected prediction (non-finite) is replaced by the cold start, and the member still
+    converges to the cold start's objective."""
+    torch, p, L = env
+    base = qpgen.param_family_base(n=2000, m=1000, seed=7)
+    C, U = qpgen.ws_family_data(base, range(3))
+    data = lambda a, b: (C[a:b], U[a:b])
+    cold = L.solve_members(base, data, 3)
+    Z0 = np.zeros((3, base.n + base.m))
+    Z0[1, 5] = np.nan
+    warm = L.solve_members(base, data, 3, starts=(Z0, np.ones(3)), lam=cold["lambda"])
+    assert warm["fallbacks"] == 1
+    assert all(s == "converged" for s in warm["status"])
+    assert np.allclose(warm["pobj"], cold["pobj"], rtol=1e-6)
