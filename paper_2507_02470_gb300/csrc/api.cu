@@ -835,18 +835,20 @@ extern "C" hprqp_status hprqp_create(hprqp_handle** out, int64_t n, int64_t m, c
 extern "C" hprqp_status hprqp_set_warm_start(hprqp_handle* h, const double* x0, const double* y0, double sigma0) {
   if (!h) return HPRQP_INVALID_ARG;
   hprqp_status st;
-  h->ws_x.clear();
-  h->ws_y.clear();
+  // validate into temporaries: a rejected warm start leaves the previous one in place
+  std::vector<double> wx, wy;
   if (x0) {
-    if ((st = fetch(h, h->ws_x, x0, h->n))) return st;
-    for (double v : h->ws_x)
+    if ((st = fetch(h, wx, x0, h->n))) return st;
+    for (double v : wx)
       if (!std::isfinite(v)) return fail(h, HPRQP_INVALID_ARG, "warm start x0 is not finite");
   }
   if (y0 && h->m > 0) {
-    if ((st = fetch(h, h->ws_y, y0, h->m))) return st;
-    for (double v : h->ws_y)
+    if ((st = fetch(h, wy, y0, h->m))) return st;
+    for (double v : wy)
       if (!std::isfinite(v)) return fail(h, HPRQP_INVALID_ARG, "warm start y0 is not finite");
   }
+  h->ws_x.swap(wx);
+  h->ws_y.swap(wy);
   h->ws_sigma = sigma0 > 0 && std::isfinite(sigma0) ? sigma0 : 0.0;
   return HPRQP_OK;
 }
