@@ -569,7 +569,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   // ---- preconditioning (Sec. 4.1: only when Q is explicit; the box-only phi keeps the
   // prox a plain clip in the scaled variables).  b_inf, c_inf of the stopping test stay those
   // of the original data; the sigma0 norms become those of the scaled data.
-  h->scaled = h->prm.scaling && phi == PHI_BOX && facs.empty() && dens.empty();
+  h->scaled = h->prm.scaling && phi == PHI_BOX && facs.empty() && dens.empty() && qap_d == 0;
   if (h->scaled) {
     precondition(n, m, qdiag, qcsr, dia_off, dia_vals, A, h->hd, h->he);
     const std::vector<double>& d = h->hd;

@@ -499,6 +499,7 @@ def test_pock_chambolle_pass_bounds_the_scaled_norm(seed, kind):
 
 def test_scaling_skipped_when_q_is_matrix_free_or_l1():
     assert not oracle.scaling(qpgen.random_small(n=6, m=3, seed=64, q_kind="factor", q_rank=3))[2]
+    assert not oracle.scaling(qpgen.qap_relaxation(d=4, seed=1))[2]
     assert not oracle.scaling(qpgen.random_small(n=6, m=3, seed=65, q_kind="csr", phi="l1", lam=0.3))[2]
 
 
