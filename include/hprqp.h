@@ -108,7 +108,11 @@ typedef struct hprqp_params {
   int32_t sigma_fixed;       /* 1: keep sigma0 at restarts */
   double time_limit;         /* seconds, <= 0: none (Sec. 4.1 uses 3600) */
   int32_t iters_per_launch;  /* iterations captured per CUDA-graph launch, default 64 */
-  int32_t autotune;          /* 1 (default): time SpMV schedules at create and pick the best */
+  int32_t autotune;          /* 1 (default): time the SpMV schedules (lanes per row 1-32,
+                                or the staged form that streams a chunk's entries as one
+                                range) at create and pick the fastest for each operator;
+                                0: lanes per row from the mean row length; 2: the staged
+                                form for every CSR pass */
   int32_t verbose;           /* 0: silent */
   hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
   hprqp_free_fn free;
@@ -133,6 +137,9 @@ typedef struct hprqp_params {
                                 (1.4)), for ablations: fixed sigma (sigma0 or the Sec. 4.1 rule),
                                 no restarts, stopping rule of Sec. 4.1 every check_every steps;
                                 they need scaling = 0 and run as stream launches */
+  int32_t pdl;               /* 1 (default): consecutive kernels of a step are programmatic
+                                dependent launches (a kernel's launch overlaps the end of the
+                                one before it; results unchanged); 0: ordinary launches */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
@@ -150,6 +157,9 @@ typedef struct hprqp_kkt {
    * device time from the first step to that test); 0 when not reached */
   int64_t iters_1e4, iters_1e6;
   double seconds_1e4, seconds_1e6;
+  /* SpMV schedule picked at create: lanes per row of the Q, A and A^T passes and of the
+   * factor pre-pass (0: the staged chunk form); 0 throughout from the batched solver */
+  int32_t lanes_q, lanes_a, lanes_at, lanes_pre;
 } hprqp_kkt;
 
 /* One stopping test of a solve (every check_every iterations, Sec. 4.1). */

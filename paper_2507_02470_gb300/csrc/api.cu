@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <functional>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -241,6 +242,7 @@ extern "C" void hprqp_default_params(hprqp_params* p) {
   p->autotune = 1;
   p->scaling = 1;
   p->method = 0;
+  p->pdl = 1;
 }
 
 extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
@@ -273,11 +275,13 @@ extern "C" void hprqp_destroy(hprqp_handle* h) { release(h); }
 // ------------------------------------------------------------------------------------ autotune
 static int tune_G(hprqp_handle* h, const Csr& M, int grid, double* x, double* y, int fallback) {
   if (M.rows == 0 || M.nnz == 0) return fallback;
+  if (h->prm.autotune == 2) return 0;
   if (!h->prm.autotune) {
     double avg = (double)M.nnz / (double)M.rows;
     return avg < 6 ? 1 : avg < 12 ? 2 : avg < 24 ? 4 : avg < 64 ? 8 : 32;
   }
-  const int cand[6] = {1, 2, 4, 8, 16, 32};
+  // lanes per row (1-32) or 0: the staged form that streams each chunk's entries as a block
+  const int cand[7] = {0, 1, 2, 4, 8, 16, 32};
   float best = 1e30f;
   int bestG = fallback;
   for (int G : cand) {
@@ -722,6 +726,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   P.gridM = std::min(chunks(m), sms * per_sm);
   P.gridE = std::min(chunks(n), sms * 8);
   P.gridPre = (int)std::min<int64_t>(std::max<int64_t>(1, (toff + 7) / 8), sms * 8);
+  std::function<int(int)> pre_grid;
   {
     // lanes per factor row of the pre-pass: full warps only for long rows (the shuffle
     // reduction costs FP64 instructions that short rows cannot amortise)
@@ -736,8 +741,11 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     // need (a short factor such as S with 1e4 rows needs 40 blocks, not a full wave)
     int64_t drows = 0;   // dense factor rows take one warp each
     for (auto& F : dens) drows += F.first;
-    P.gridPre = (int)std::min<int64_t>(
-        std::max<int64_t>(1, (frows * P.gPre + drows * 32 + kThreads - 1) / kThreads), (int64_t)sms * 8);
+    pre_grid = [frows, drows, sms](int G) {
+      return (int)std::min<int64_t>(std::max<int64_t>(1, (frows * G + drows * 32 + kThreads - 1) / kThreads),
+                                    (int64_t)sms * 8);
+    };
+    P.gridPre = pre_grid(P.gPre);
   }
   a.nbM = P.gridM;
   if (h->prm.launch_mode == 3) {
@@ -781,6 +789,25 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     for (int f = 0; f < QD.nfac; f++)
       if (!big || QD.fact[f].nnz > big->nnz) big = &QD.fact[f];
     P.gQ = big ? tune_G(h, *big, P.gridN, ain, aout, 1) : 1;
+    if (QD.nfac > 0 && h->prm.autotune == 1) {
+      // lanes per factor row of the pre-pass, timed on the pre-pass itself
+      float best = 1e30f;
+      for (int G : {1, 4, 8, 32}) {
+        const int grid = pre_grid(G);
+        CU(h, launch_pre_probe(a, G, grid, h->stream));
+        CU(h, cudaEventRecord(h->ev[0], h->stream));
+        for (int r = 0; r < 3; r++) CU(h, launch_pre_probe(a, G, grid, h->stream));
+        CU(h, cudaEventRecord(h->ev[1], h->stream));
+        CU(h, cudaEventSynchronize(h->ev[1]));
+        float ms = 0;
+        CU(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+        if (ms < best) {
+          best = ms;
+          P.gPre = G;
+          P.gridPre = grid;
+        }
+      }
+    }
     CU(h, cudaStreamSynchronize(h->stream));
     CU(h, cudaGetLastError());
     CU(h, plan_plain_grids(a, P, sms));
@@ -902,18 +929,23 @@ static hprqp_status build_iter_graph(hprqp_handle* h) {
   cudaGraph_t g;
   // preferred: device-selected step variants through conditional nodes
   if (!h->side) CU(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-  cudaError_t be = h->prm.launch_mode == 0
-                       ? build_conditional_graph(h->args, h->plan, h->stream, h->side, h->prm.iters_per_launch, &g)
-                       : cudaErrorNotSupported;
-  if (be == cudaSuccess) {
-    cudaError_t ie = cudaGraphInstantiate(&h->g_iter, g, 0);
-    cudaGraphDestroy(g);
-    if (ie == cudaSuccess) {
-      h->conditional = true;
-      return HPRQP_OK;
+  // with programmatic launches first; without them if the driver rejects that graph
+  for (int attempt = 0; attempt < 2 && h->prm.launch_mode == 0; attempt++) {
+    h->plan.pdl = attempt == 0 && h->prm.pdl ? 1 : 0;
+    if (attempt == 1 && !h->prm.pdl) break;
+    cudaError_t be = build_conditional_graph(h->args, h->plan, h->stream, h->side, h->prm.iters_per_launch, &g);
+    if (be == cudaSuccess) {
+      cudaError_t ie = cudaGraphInstantiate(&h->g_iter, g, 0);
+      cudaGraphDestroy(g);
+      if (ie == cudaSuccess) {
+        h->conditional = true;
+        return HPRQP_OK;
+      }
+      h->g_iter = nullptr;
     }
-    h->g_iter = nullptr;
+    cudaGetLastError();
   }
+  h->plan.pdl = 0;
   cudaGetLastError();
   // fallback: every kernel launched each step, variants decided inside the kernels
   h->conditional = false;
@@ -1279,6 +1311,10 @@ static hprqp_status solve_primal(hprqp_handle* h, double tol, int64_t max_iter, 
   auto t2 = std::chrono::steady_clock::now();
   hprqp_kkt& K = h->kkt;
   std::memset(&K, 0, sizeof(K));
+  K.lanes_q = h->plan.gQ;
+  K.lanes_a = h->plan.gA;
+  K.lanes_at = h->plan.gAT;
+  K.lanes_pre = h->plan.gPre;
   K.eta_p = out[0];
   K.eta_d = out[1];
   K.eta_gap = out[2];
@@ -1404,6 +1440,10 @@ static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::tim
   if (!C.done) status = time_up ? HPRQP_TIME_LIMIT : HPRQP_MAX_ITER;
   hprqp_kkt& K = h->kkt;
   std::memset(&K, 0, sizeof(K));
+  K.lanes_q = h->plan.gQ;
+  K.lanes_a = h->plan.gA;
+  K.lanes_at = h->plan.gAT;
+  K.lanes_pre = h->plan.gPre;
   K.eta_p = C.eta_p;
   K.eta_d = C.eta_d;
   K.eta_gap = C.eta_gap;
@@ -1464,6 +1504,7 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
   if (!h) return HPRQP_INVALID_ARG;
   if (!h->solved) return fail(h, HPRQP_INVALID_ARG, "hprqp_profile before hprqp_solve");
   if (iters < 1 || !ms) return fail(h, HPRQP_INVALID_ARG, "need iters >= 1 and an output array");
+  Range rg("hprqp_profile");
   hprqp_status st;
   if ((st = init_state(h, h->last_lamA, h->last_lamQ, h->last_sigma0, 1e-300, (int64_t)iters + 1))) return st;
   cudaEvent_t ev[HPRQP_PROF_KINDS][2];

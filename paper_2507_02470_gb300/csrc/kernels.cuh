@@ -78,6 +78,14 @@ struct Handles {
   int has_next = 0, has_rs = 0;
 };
 
+// Entry of every kernel that the step launchers may start as a programmatic dependent launch:
+// wait until the preceding kernel of the stream has finished and its writes are visible (a
+// no-op after an ordinary launch), then allow the next kernel to begin launching.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 enum { VAR_PLAIN = 0, VAR_R = 1, VAR_T = 2, VAR_RUNTIME = 3 };
 
 template <int VAR>
@@ -124,8 +132,9 @@ __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, dou
 // ------------------------------------------------------------------------------------ CSR pass
 // Row sums of a chunk of kChunk rows, G lanes per row, into shared rs0/rs1 (add: accumulate).
 template <int G, int NR>
-__device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
-                                          const double* HPRQP_RESTRICT x1, double* rs0, double* rs1, bool add) {
+__device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
+                                                const double* HPRQP_RESTRICT x1, double* rs0, double* rs1,
+                                                bool add) {
   const int lane = threadIdx.x % G;
   const int grp = threadIdx.x / G;
   constexpr int NG = kThreads / G;
@@ -195,6 +204,78 @@ __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const doub
       if (NR == 2) rs1[rr] = add ? rs1[rr] + s1 : s1;
     }
   }
+}
+
+// Staged form of the same row sums (G = 0).  A chunk's entries [rp[row0], rp[row0 + R]) form
+// one contiguous range, which the whole block streams in windows of kWin entries (coalesced
+// index and value loads, every gather of a window in flight at once) into shared memory; each
+// thread then sums its own row's entries of the window in entry order.  Rows of a few tens of
+// entries are latency-bound in the lane form, which walks index -> gather row after row; here
+// one such round trip serves up to kWin entries of many rows.
+constexpr int kWin = 1024;
+template <int NR>
+__device__ __forceinline__ void csr_chunk_staged(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
+                                                 const double* HPRQP_RESTRICT x1, double* rs0, double* rs1,
+                                                 bool add) {
+  __shared__ int srp[kChunk + 1];
+  __shared__ double sv[kWin];
+  __shared__ double sx[NR][kWin];
+  constexpr int kPer = kWin / kThreads;
+  const int t = threadIdx.x;
+  const L2Pol pol;
+  const int nr = (int)(M.rows - row0 < (int64_t)kChunk ? M.rows - row0 : (int64_t)kChunk);
+  if (nr <= 0) return;   // block-uniform: no row of this matrix in the chunk
+  __syncthreads();   // an earlier pass over this chunk may still read srp, sv, sx
+  for (int i = t; i <= nr; i += kThreads) srp[i] = stream_i32(M.rp + row0 + i, pol);
+  __syncthreads();
+  const int b = srp[0], e = srp[nr];
+  const int rb = t < nr ? srp[t] : 0, re = t < nr ? srp[t + 1] : 0;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll 1
+  for (int w0 = b; w0 < e; w0 += kWin) {
+    const int wn = e - w0 < kWin ? e - w0 : kWin;
+    int c[kPer];
+    double v[kPer], g0[kPer], g1[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+      const int i = t + q * kThreads;
+      c[q] = i < wn ? stream_i32(M.ci + w0 + i, pol) : 0;
+      v[q] = i < wn ? stream_f64(M.v + w0 + i, pol) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+      const int i = t + q * kThreads;
+      g0[q] = i < wn ? gather_f64(x0 + c[q], pol) : 0.0;
+      if (NR == 2) g1[q] = i < wn ? gather_f64(x1 + c[q], pol) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+      const int i = t + q * kThreads;
+      if (i < wn) {
+        sv[i] = v[q];
+        sx[0][i] = g0[q];
+        if (NR == 2) sx[NR - 1][i] = g1[q];
+      }
+    }
+    __syncthreads();
+    const int lo = (rb > w0 ? rb : w0) - w0, hi = (re < w0 + wn ? re : w0 + wn) - w0;
+    for (int k = lo; k < hi; k++) {
+      s0 = fma(sv[k], sx[0][k], s0);
+      if (NR == 2) s1 = fma(sv[k], sx[NR - 1][k], s1);
+    }
+    __syncthreads();
+  }
+  if (t < nr) {
+    rs0[t] = add ? rs0[t] + s0 : s0;
+    if (NR == 2) rs1[t] = add ? rs1[t] + s1 : s1;
+  }
+}
+
+template <int G, int NR>
+__device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
+                                          const double* HPRQP_RESTRICT x1, double* rs0, double* rs1, bool add) {
+  if constexpr (G == 0) csr_chunk_staged<NR>(M, row0, x0, x1, rs0, rs1, add);
+  else csr_chunk_lanes<G, NR>(M, row0, x0, x1, rs0, rs1, add);
 }
 
 // All CSR-like parts of Q (explicit CSR and every B_f^T with its intermediate t_f) for a chunk.
@@ -319,7 +400,10 @@ __device__ __forceinline__ void zx_body(const Args& a) {
 }
 
 template <int VAR>
-__global__ void __launch_bounds__(kThreads) k_zx(Args a) { zx_body<VAR>(a); }
+__global__ void __launch_bounds__(kThreads) k_zx(Args a) {
+  pdl_enter();
+  zx_body<VAR>(a);
+}
 
 // ------------------------------------------------------------------------------------ factor pre-pass
 // t = B_f x for every factor term (G lanes per row), t = F_g x for every dense term (one warp
@@ -448,7 +532,10 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
 }
 
 template <int G, int TT>
-__global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) { pre_body<G, TT>(a, which); }
+__global__ void __launch_bounds__(kThreads) k_pre(Args a, int which) {
+  pdl_enter();
+  pre_body<G, TT>(a, which);
+}
 
 // ------------------------------------------------------------------------------------ controller
 // One pass of the Sec. 3.2 / Sec. 4.1 logic after an inner step; Ls: end-of-step sums,
@@ -807,6 +894,7 @@ template <int G, int KIND, int VAR>
 // plain steps keep six blocks per SM resident (at most 40 registers): their passes are
 // latency-bound gathers, so occupancy matters more than a few extra registers
 __global__ void __launch_bounds__(kThreads, VAR == VAR_PLAIN ? 6 : 1) k_rows(Args a, Handles hd) {
+  pdl_enter();
   rows_body<G, KIND, VAR>(a, hd);
 }
 
@@ -955,7 +1043,10 @@ __device__ __forceinline__ void restart_body(const Args& a) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_restart(Args a) { restart_body<G>(a); }
+__global__ void __launch_bounds__(kThreads) k_restart(Args a) {
+  pdl_enter();
+  restart_body<G>(a);
+}
 
 using RowKernel = void (*)(Args, Handles);
 
@@ -968,6 +1059,7 @@ template <int KIND>
 RowKernel pick_row(int var, int G) {
 #define HPRQP_ROW_G(VAR)                                        \
   switch (G) {                                                  \
+    case 0: return k_rows<0, KIND, VAR>;                        \
     case 1: return k_rows<1, KIND, VAR>;                        \
     case 2: return k_rows<2, KIND, VAR>;                        \
     case 4: return k_rows<4, KIND, VAR>;                        \

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <utility>
 #include <vector>
 
 #include "kernels.cuh"
@@ -99,6 +100,38 @@ cudaError_t launch_qap(const Args& a, const Plan& p, int which, int tt, cudaStre
   return e;
 }
 
+// Launches kernel k; with pdl set it is a programmatic dependent launch (it may start while
+// the previous kernel of the stream drains; the kernel itself waits for that kernel's results).
+template <typename... P, typename... A>
+static cudaError_t launch_k(bool pdl, void (*k)(P...), int grid, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
+// Kernel sequence on one stream: programmatic launches only directly after another kernel of
+// this library (not first in a graph body, not after cuBLAS, not between profiling events).
+struct Seq {
+  cudaStream_t s;
+  bool pdl;
+  bool prev = false;
+  cudaError_t e = cudaSuccess;
+  template <typename... P, typename... A>
+  void operator()(void (*k)(P...), int grid, A&&... args) {
+    if (e == cudaSuccess) e = launch_k(pdl && prev, k, grid, s, std::forward<A>(args)...);
+    prev = true;
+  }
+  void other() { prev = false; }
+};
+
 // One inner step in variant `var`; the last kernel of the step receives the handles.
 cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, const Handles& hd,
                         cudaEvent_t (*ev)[2]) {
@@ -107,35 +140,43 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   const int tt = var == VAR_T ? 1 : var == VAR_RUNTIME ? 2 : 0;
   // plain steps write no partial sums, so they may run at their own (larger) grids
   const bool pl = var == VAR_PLAIN && p.wZX > 0;
-  TIMED(0, (zxk(var)<<<pl ? p.wZX : p.gridE, kThreads, 0, s>>>(a)));
+  Seq L{s, p.pdl != 0 && !ev};
+  TIMED(0, L(zxk(var), pl ? p.wZX : p.gridE, a));
   if (HQ) {
     if (pre) {
       if (ev) cudaEventRecord(ev[1][0], s);
-      if (a.Q.has_fd()) prek(p.gPre, tt)<<<p.gridPre, kThreads, 0, s>>>(a, 0);
-      const cudaError_t qe = launch_qap(a, p, 0, tt, s);
-      if (qe != cudaSuccess) return qe;
+      if (a.Q.has_fd()) L(prek(p.gPre, tt), p.gridPre, a, 0);
+      if (a.Q.qap_d) {
+        L.other();
+        const cudaError_t qe = launch_qap(a, p, 0, tt, s);
+        if (qe != cudaSuccess) return qe;
+      }
       if (ev) cudaEventRecord(ev[1][1], s);
     }
-    TIMED(2, (rowk(K_Q1, var, p.gQ)<<<pl ? p.wQ1 : p.gridN, kThreads, 0, s>>>(a, HA ? none : hd)));
+    TIMED(2, L(rowk(K_Q1, var, p.gQ), pl ? p.wQ1 : p.gridN, a, HA ? none : hd));
   }
   if (HA) {
-    TIMED(3, (rowk(K_A1, var, p.gA)<<<pl ? p.wA1 : p.gridM, kThreads, 0, s>>>(a, none)));
-    TIMED(4, (rowk(K_AT, var, p.gAT)<<<pl ? p.wAT : p.gridN, kThreads, 0, s>>>(a, HQ ? none : hd)));
+    TIMED(3, L(rowk(K_A1, var, p.gA), pl ? p.wA1 : p.gridM, a, none));
+    TIMED(4, L(rowk(K_AT, var, p.gAT), pl ? p.wAT : p.gridN, a, HQ ? none : hd));
     if (HQ) {
       if (pre) {
         if (ev) cudaEventRecord(ev[5][0], s);
-        if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 1);
-        const cudaError_t qe = launch_qap(a, p, 1, 0, s);
-        if (qe != cudaSuccess) return qe;
+        if (a.Q.has_fd()) L(prek(p.gPre, 0), p.gridPre, a, 1);
+        if (a.Q.qap_d) {
+          L.other();
+          const cudaError_t qe = launch_qap(a, p, 1, 0, s);
+          if (qe != cudaSuccess) return qe;
+        }
         if (ev) cudaEventRecord(ev[5][1], s);
       }
-      TIMED(6, (rowk(K_Q2, var, p.gQ)<<<pl ? p.wQ2 : p.gridN, kThreads, 0, s>>>(a, hd)));
+      TIMED(6, L(rowk(K_Q2, var, p.gQ), pl ? p.wQ2 : p.gridN, a, hd));
     }
   }
   if (!HQ && !HA) {
     // neither operator: the controller still needs its (empty-operator) pass
-    TIMED(4, (rowk(K_AT, var, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, hd)));
+    TIMED(4, L(rowk(K_AT, var, p.gAT), p.gridN, a, hd));
   }
+  if (L.e != cudaSuccess) return L.e;
   return cudaGetLastError();
 }
 
@@ -182,17 +223,22 @@ cudaError_t plan_plain_grids(const Args& a, Plan& p, int sms) {
 }
 
 cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2]) {
+  Seq L{s, p.pdl != 0 && !ev};
   if (a.Q.present() && a.m > 0 && a.Q.has_pre()) {
     if (ev) cudaEventRecord(ev[7][0], s);
-    if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 2);
-    const cudaError_t qe = launch_qap(a, p, 2, 0, s);
-    if (qe != cudaSuccess) return qe;
+    if (a.Q.has_fd()) L(prek(p.gPre, 0), p.gridPre, a, 2);
+    if (a.Q.qap_d) {
+      L.other();
+      const cudaError_t qe = launch_qap(a, p, 2, 0, s);
+      if (qe != cudaSuccess) return qe;
+    }
     if (ev) cudaEventRecord(ev[7][1], s);
   }
   const int G = p.gQ;
-  void (*kr)(Args) = G == 1 ? k_restart<1> : G == 2 ? k_restart<2> : G == 4 ? k_restart<4>
+  void (*kr)(Args) = G <= 1 ? k_restart<1> : G == 2 ? k_restart<2> : G == 4 ? k_restart<4>
                      : G == 8 ? k_restart<8> : G == 16 ? k_restart<16> : k_restart<32>;
-  TIMED(8, (kr<<<p.gridN, kThreads, 0, s>>>(a)));
+  TIMED(8, L(kr, p.gridN, a));
+  if (L.e != cudaSuccess) return L.e;
   return cudaGetLastError();
 }
 
@@ -409,8 +455,15 @@ __global__ void __launch_bounds__(kThreads) k_spmv_probe(Csr M, const double* x,
   }
 }
 
+// the factor pre-pass t = B_f ain (which = 3) at G lanes per row, for the schedule autotuner
+cudaError_t launch_pre_probe(const Args& a, int G, int grid, cudaStream_t s) {
+  prek(G, 0)<<<grid, kThreads, 0, s>>>(a, 3);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s) {
   switch (G) {
+    case 0: k_spmv_probe<0><<<grid, kThreads, 0, s>>>(M, x, y); break;
     case 1: k_spmv_probe<1><<<grid, kThreads, 0, s>>>(M, x, y); break;
     case 2: k_spmv_probe<2><<<grid, kThreads, 0, s>>>(M, x, y); break;
     case 4: k_spmv_probe<4><<<grid, kThreads, 0, s>>>(M, x, y); break;

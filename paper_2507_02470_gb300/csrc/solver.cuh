@@ -48,13 +48,16 @@ enum Kind { K_Q1 = 0, K_A1 = 1, K_AT = 2, K_Q2 = 3, K_APPLY_Q = 4, K_APPLY_A = 5
 
 // Launch plan chosen at create time (lanes per row of each CSR pass, grid sizes).
 struct Plan {
-  int gQ = 1, gA = 1, gAT = 1, gPre = 32;   // lanes per row
+  int gQ = 1, gA = 1, gAT = 1, gPre = 32;   // lanes per row (0: staged chunk form)
   int gridN = 0, gridM = 0, gridE = 0, gridPre = 0;   // blocks of the n-row, m-row, elementwise, pre kernels
   // blocks of the plain (non-reducing) step variants: one full wave at the occupancy of each
   // kernel; the reducing variants keep gridN/gridM/gridE, which size the partial-sum regions
   int wZX = 0, wQ1 = 0, wA1 = 0, wAT = 0, wQ2 = 0;
   int gridP = 0;   // blocks of the persistent (cooperative) solver
   void* blas = nullptr;   // cuBLAS handle for a QAP term's products
+  // programmatic dependent launch between consecutive kernels of a step (each kernel waits for
+  // its predecessor with griddepcontrol.wait, so only its launch overlaps the predecessor's end)
+  int pdl = 0;
 };
 
 // sigma and the scalars derived from it (host and device use the same arithmetic)
@@ -86,6 +89,7 @@ cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStrea
 cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s);
 cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s);
 cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_pre_probe(const Args& a, int G, int grid, cudaStream_t s);
 // v[i] *= s[i] for i < n
 cudaError_t launch_vmul(double* v, const double* s, int64_t n, cudaStream_t st);
 // out[i] = v[i] * s[i] for i < n

@@ -20,6 +20,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c4"])
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--warm-iters", type=int, default=20, help="iterations of the solve before profiling")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="SpMV schedule: 1 timed choice, 0 lanes from row length, 2 staged chunks")
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -31,12 +33,14 @@ def main(argv=None):
           "c1": lambda: qpgen.large_cqp(n=1_000_000, m=500_000, seed=0),
           "c2": lambda: qpgen.lasso(),
           "c4": lambda: qpgen.param_family_base(n=100_000, m=50_000, seed=0)}[args.workload]()
-    with pkg.Solver(qp, launch_mode=2) as s:
+    with pkg.Solver(qp, launch_mode=2, autotune=args.autotune) as s:
         s.solve(tol=1e-30, max_iter=args.warm_iters)
         k = s.kkt()
         ms = s.profile(iters=args.iters)
-    print(json.dumps({"workload": args.workload, "n": qp.n, "m": qp.m, "iters": args.iters,
+    print(json.dumps({"workload": args.workload, "autotune": args.autotune, "n": qp.n, "m": qp.m,
+                      "iters": args.iters,
                       "lambda_A": k["lambda_A"], "lambda_Q": k["lambda_Q"],
+                      "lanes": {q: k["lanes_" + q] for q in ("q", "a", "at", "pre")},
                       "ms": {a: round(b, 5) for a, b in ms.items()}}), flush=True)
 
 

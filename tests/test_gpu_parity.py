@@ -245,3 +245,61 @@ def test_stopping_test_history(pkg):
     secs = [h["seconds"] for h in hist]
     assert all(b >= a for a, b in zip(secs, secs[1:])) and secs[0] > 0
     assert max(last["eta_p"], last["eta_d"], last["eta_gap"]) <= 1e-8
+
+
+def _long_and_empty_rows():
+    """n = 1500: Q = diag(d) + u u^T stored as CSR (every row 1500 entries, so each row spans
+    two staging windows of 1024 entries), A with one dense row, five empty rows and a ragged
+    tail past the last full chunk of 256 rows."""
+    rng = np.random.default_rng(11)
+    n, m = 1500, 300
+    uu = rng.standard_normal(n) / np.sqrt(n)
+    Q = np.diag(rng.uniform(0.5, 1.5, n)) + np.outer(uu, uu)
+    A = np.where(rng.random((m, n)) < 0.01, rng.standard_normal((m, n)), 0.0)
+    A[0] = 1.0
+    A[5:10] = 0.0
+    return qpgen.from_dense(Q, rng.standard_normal(n), A=A, l=np.full(m, -1.0), u=np.full(m, 1.0),
+                            L=np.full(n, -2.0), U=np.full(n, 2.0))
+
+
+STAGED = dict(PROBLEMS, long_rows=_long_and_empty_rows())
+
+
+@pytest.mark.parametrize("name", list(STAGED))
+def test_staged_schedule_matches_oracle(pkg, name):
+    """autotune = 2 runs every CSR pass in the staged chunk form (the block streams a chunk's
+    entries in windows, then each thread sums its own row): same products and iterates."""
+    qp = STAGED[name]
+    rng = np.random.default_rng(1)
+    K = 50
+    ref = oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K)
+    with pkg.Solver(qp, autotune=2, lambda_A=ref.lambda_A if qp.m else 0.0, lambda_Q=ref.lambda_Q) as s:
+        v = rng.standard_normal(qp.n)
+        assert rel(s.apply("Q", v), oracle.qmul(qp, v)) <= 1e-13
+        if qp.m:
+            yv = rng.standard_normal(qp.m)
+            assert rel(s.apply("A", v), oracle.amul(qp, v)) <= 1e-13
+            assert rel(s.apply("AT", yv), oracle.atmul(qp, yv)) <= 1e-13
+        for k in (1, 11, 21, 50):
+            s.solve(tol=1e-30, max_iter=k)
+            x, y, *_ = s.get()
+            assert rel(x, ref.trace["x"][k - 1]) <= ITER_TOL, (name, k)
+            if qp.m:
+                assert rel(y, ref.trace["y"][k - 1]) <= ITER_TOL, (name, k)
+
+
+@pytest.mark.parametrize("name", ["plain", "large_sum", "lasso"])
+def test_programmatic_launches_change_nothing(pkg, name):
+    """The step kernels as programmatic dependent launches (the default) reach bit-identical
+    iterates to ordinary launches: each kernel still waits for its predecessor's results.
+    (Both handles take the schedule from the row lengths: the timed autotuner may pick
+    different lanes per row for two handles, which changes the rounding.)"""
+    qp = PROBLEMS[name]
+    out = []
+    for pdl in (1, 0):
+        with pkg.Solver(qp, pdl=pdl, autotune=0) as s:
+            s.solve(tol=1e-30, max_iter=333)
+            x, y, z, w, k = s.get()
+            out.append((x, y, k["iters"], k["restarts"]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2:] == out[1][2:]
