@@ -493,6 +493,8 @@ def main():
                     help="0 conditional CUDA graph (default), 1 flat graph, 2 stream launches (for profilers)")
     ap.add_argument("--pdl", type=int, default=1,
                     help="1 (default): programmatic dependent launches between the kernels of a step")
+    ap.add_argument("--fixed-schedule", type=int, default=1,
+                    help="1 (default): whole check periods through the fixed-schedule graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -529,7 +531,8 @@ def main():
     pkg.build()
     qp, desc = workload(args.workload)
     stream = torch.cuda.Stream()
-    solver = pkg.Solver(qp, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl)
+    solver = pkg.Solver(qp, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl,
+                        fixed_schedule=args.fixed_schedule)
     iters_per_step, solve_s = [], []
     for _ in range(args.warmup):
         solver.solve(tol=TOL, max_iter=1_000_000)
@@ -586,7 +589,8 @@ def main():
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        with pkg.Solver(pinned, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl) as s2:
+        with pkg.Solver(pinned, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl,
+                        fixed_schedule=args.fixed_schedule) as s2:
             s2.solve(tol=TOL, max_iter=1_000_000)
             _, _, _, _, k2 = s2.get(outx, outy if qp.m else None, outz, outw)
         torch.cuda.synchronize()
@@ -607,7 +611,7 @@ def main():
             "config": {"workload": desc, "tol": TOL, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (working set > 129 MB), no flush needed",
                        "check_every": int(solver.params.check_every), "restart_every": int(solver.params.restart_every),
-                       "launch_mode": args.launch_mode, "pdl": args.pdl},
+                       "launch_mode": args.launch_mode, "pdl": args.pdl, "fixed_schedule": args.fixed_schedule},
             "time_to_tol_s": round(statistics.median(solve_s), 4),
             "tolerance_ladder": {
                 "1e-4": {"iters": kkts[-1]["iters_1e4"], "s": round(statistics.median(k["seconds_1e4"] for k in kkts), 4)},

@@ -140,6 +140,11 @@ typedef struct hprqp_params {
   int32_t pdl;               /* 1 (default): consecutive kernels of a step are programmatic
                                 dependent launches (a kernel's launch overlaps the end of the
                                 one before it; results unchanged); 0: ordinary launches */
+  int32_t fixed_schedule;    /* 1 (default, launch_mode 0): while a whole period remains, run
+                                graphs whose step variants are fixed by position (R~ test every
+                                restart_every, stopping test every check_every steps) with one
+                                conditional node per R~ test instead of two per step; results
+                                unchanged.  0: every step through the dynamic graph */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */

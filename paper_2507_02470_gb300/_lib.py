@@ -47,7 +47,7 @@ class hprqp_params(C.Structure):
                 ("time_limit", C.c_double), ("iters_per_launch", C.c_int32), ("autotune", C.c_int32),
                 ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("launch_mode", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32),
-                ("pdl", C.c_int32)]
+                ("pdl", C.c_int32), ("fixed_schedule", C.c_int32)]
 
 
 class hprqp_kkt(C.Structure):

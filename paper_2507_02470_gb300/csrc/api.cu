@@ -42,6 +42,8 @@ struct hprqp_handle {
   std::vector<double> ws_x, ws_y;
   double ws_sigma = 0.0;
   cudaGraphExec_t g_iter = nullptr;
+  cudaGraphExec_t g_fixed = nullptr;   // fixed-schedule graph of fixed_L steps (conditional mode)
+  int fixed_L = 0;
   cudaGraphExec_t g_pw[2] = {nullptr, nullptr};
   int pw_chunk = 16;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -243,6 +245,7 @@ extern "C" void hprqp_default_params(hprqp_params* p) {
   p->scaling = 1;
   p->method = 0;
   p->pdl = 1;
+  p->fixed_schedule = 1;
 }
 
 extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
@@ -254,6 +257,7 @@ static void release(hprqp_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
   if (h->g_iter) cudaGraphExecDestroy(h->g_iter);
+  if (h->g_fixed) cudaGraphExecDestroy(h->g_fixed);
   for (auto& g : h->g_pw)
     if (g) cudaGraphExecDestroy(g);
   for (auto& e : h->ev)
@@ -924,6 +928,34 @@ extern "C" hprqp_status hprqp_set_lambda(hprqp_handle* h, double lambda_A, doubl
 }
 
 // ------------------------------------------------------------------------------------ graphs
+// The fixed-schedule graph (used while at least fixed_L iterations remain): L = lcm of the
+// R~-test and stopping-test periods, at most 1024 steps; left out when larger or when the
+// driver rejects it (the dynamic graph then runs every step).
+static void build_fixed(hprqp_handle* h) {
+  const int64_t ce = h->prm.check_every, re = h->prm.restart_off ? ce : h->prm.restart_every;
+  int64_t a = re, b = ce;
+  while (b) {
+    const int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  const int64_t L = re / a * ce;
+  if (L > 1024) return;
+  cudaGraph_t g;
+  if (build_fixed_graph(h->args, h->plan, h->stream, h->side, (int)L, (int)re, (int)ce, &g) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->g_fixed, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    h->g_fixed = nullptr;
+    return;
+  }
+  h->fixed_L = (int)L;
+}
+
 static hprqp_status build_iter_graph(hprqp_handle* h) {
   if (h->g_iter) return HPRQP_OK;
   cudaGraph_t g;
@@ -939,6 +971,7 @@ static hprqp_status build_iter_graph(hprqp_handle* h) {
       cudaGraphDestroy(g);
       if (ie == cudaSuccess) {
         h->conditional = true;
+        if (h->prm.fixed_schedule) build_fixed(h);
         return HPRQP_OK;
       }
       h->g_iter = nullptr;
@@ -1403,11 +1436,29 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   if (h->prm.launch_mode == 2) return solve_stream(h, t0, t1, lamA, lamQ, sigma);
   if (h->prm.launch_mode == 3) return solve_persist(h, t0, t1, lamA, lamQ, sigma);
   if ((st = build_iter_graph(h))) return st;
-  // ---- Algorithm 4 in graph launches of iters_per_launch steps; double-buffered done poll
-  const int64_t per = h->prm.iters_per_launch;
-  const int64_t max_launch = (max_iter + per - 1) / per + 2;
-  const int64_t nodes = h->conditional ? 1 : per * kernels_per_iteration(a);
   bool time_up = false;
+  // ---- Algorithm 4 in launches of the fixed-schedule graph while fixed_L steps remain
+  int64_t k0 = 0;
+  if (h->g_fixed && max_iter >= h->fixed_L) {
+    for (; max_iter - k0 >= h->fixed_L; k0 += h->fixed_L) {
+      CU(h, cudaGraphLaunch(h->g_fixed, h->stream));
+      h->launches += 1;
+      CU(h, cudaMemcpyAsync(&h->hflags[0], &h->dctrl->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CU(h, cudaStreamSynchronize(h->stream));
+      if (h->hflags[0]) return finish_solve(h, t0, t1, lamA, lamQ, sigma, false);
+      if (h->prm.time_limit > 0 &&
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > h->prm.time_limit)
+        return finish_solve(h, t0, t1, lamA, lamQ, sigma, true);
+    }
+    // a restart decided at the last fixed step runs before the dynamic graph's first step
+    CU(h, launch_restart(a, h->plan, h->stream));
+    h->launches += kernels_per_restart(a);
+  }
+  // ---- the rest in launches of the dynamic graph (iters_per_launch steps); double-buffered
+  // done poll
+  const int64_t per = h->prm.iters_per_launch;
+  const int64_t max_launch = (max_iter - k0 + per - 1) / per + 2;
+  const int64_t nodes = h->conditional ? 1 : per * kernels_per_iteration(a);
   for (int64_t i = 0; i < max_launch; i++) {
     CU(h, cudaGraphLaunch(h->g_iter, h->stream));
     h->launches += nodes;

@@ -76,6 +76,7 @@ struct Handles {
   unsigned long long sw_next = 0;   // SWITCH node of the next inner step
   unsigned long long rs_cur = 0;    // IF node of this step's restart pass
   int has_next = 0, has_rs = 0;
+  int fixed = 0;                    // 1: graph with a fixed variant schedule (values of fixed_value)
 };
 
 // Entry of every kernel that the step launchers may start as a programmatic dependent launch:
@@ -100,6 +101,15 @@ __device__ __forceinline__ bool var_ttest(const Ctrl* C) {
 // switch value of the next step: 0 plain, 1 R~ test, 2 stopping test, 3 nothing (done)
 __device__ __forceinline__ unsigned next_variant(const Ctrl& C) {
   return C.done ? 3u : C.ttest ? 2u : C.rtest ? 1u : 0u;
+}
+// switch value in the fixed-schedule graph, at a step that follows a possible restart:
+// 0 the step's scheduled variant, 1 with the R~ test (first step after a restart), 2 the
+// restart pass of Algorithm 5 and then that step, 3 nothing (done)
+__device__ __forceinline__ unsigned fixed_value(const Ctrl& C) {
+  return C.done ? 3u : C.restart_pending ? 2u : C.rtest ? 1u : 0u;
+}
+__device__ __forceinline__ unsigned switch_value(const Ctrl& C, const Handles& hd) {
+  return hd.fixed ? fixed_value(C) : next_variant(C);
 }
 
 // ------------------------------------------------------------------------------------ prox
@@ -640,7 +650,7 @@ __device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const doub
 
 __device__ __forceinline__ void set_handles(const Ctrl& C, const Handles& hd) {
   if (hd.has_rs) cudaGraphSetConditional(hd.rs_cur, (!C.done && C.restart_pending) ? 1u : 0u);
-  if (hd.has_next) cudaGraphSetConditional(hd.sw_next, next_variant(C));
+  if (hd.has_next) cudaGraphSetConditional(hd.sw_next, switch_value(C, hd));
 }
 
 // Per-row contributions to the R~ and stopping-rule sums (end of an inner step).

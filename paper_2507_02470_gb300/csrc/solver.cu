@@ -268,7 +268,7 @@ int kernels_per_iteration(const Args& a) { return kernels_per_step(a) + kernels_
 
 // ------------------------------------------------------------------------------------ dispatch
 __global__ void k_dispatch(Args a, Handles hd) {
-  if (threadIdx.x == 0 && hd.has_next) cudaGraphSetConditional(hd.sw_next, next_variant(*a.C));
+  if (threadIdx.x == 0 && hd.has_next) cudaGraphSetConditional(hd.sw_next, switch_value(*a.C, hd));
 }
 
 static cudaError_t add_cond(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
@@ -342,6 +342,71 @@ cudaError_t build_conditional_graph(const Args& a, const Plan& p, cudaStream_t s
     cudaGraph_t tmp;
     e = cudaStreamEndCapture(s2, &tmp);
     if (le != cudaSuccess) e = le;
+  }
+  cudaGraph_t gout = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(s, &gout);
+  if (e == cudaSuccess) e = ee;
+  if (e != cudaSuccess) {
+    if (gout) cudaGraphDestroy(gout);
+    cudaGetLastError();
+    return e;
+  }
+  *out = gout;
+  return cudaSuccess;
+}
+
+// Graph of L inner steps with the step variants fixed by position (L a common multiple of
+// restart_every and check_every, launched only at iteration counts that are multiples of L):
+// the R~ test at multiples of restart_every, the stopping test at multiples of check_every.
+// The only data-dependent choice, whether a restart happened at the step before (then the
+// restart pass of Algorithm 5 runs and the next step records R~_{r,0}), is one SWITCH node
+// after every R~ test; the dynamic graph above spends a SWITCH and an IF node on every step.
+cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int L, int re, int ce,
+                              cudaGraph_t* out) {
+  auto sR = [&](int q) { return q % re == 0; };
+  auto sT = [&](int q) { return q % ce == 0; };
+  auto is_sw = [&](int q) { return sR(q == 1 ? L : q - 1); };
+  auto var0 = [&](int q) { return sT(q) ? (int)VAR_T : sR(q) ? (int)VAR_R : (int)VAR_PLAIN; };
+  auto varR = [&](int q) { return sT(q) ? (int)VAR_T : (int)VAR_R; };
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+  std::vector<cudaGraphConditionalHandle> sw(L + 1);
+  for (int q = 1; q <= L && e == cudaSuccess; q++)
+    if (is_sw(q)) e = cudaGraphConditionalHandleCreate(&sw[q], g, 3u, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    Handles h0;
+    h0.fixed = 1;
+    h0.sw_next = sw[1];
+    h0.has_next = is_sw(1) ? 1 : 0;
+    k_dispatch<<<1, 32, 0, s>>>(a, h0);
+    e = cudaGetLastError();
+  }
+  for (int q = 1; q <= L && e == cudaSuccess; q++) {
+    Handles hd;
+    hd.fixed = 1;
+    if (q < L && is_sw(q + 1)) {
+      hd.sw_next = sw[q + 1];
+      hd.has_next = 1;
+    }
+    if (!is_sw(q)) {
+      e = launch_step(a, p, s, var0(q), hd, nullptr);
+      continue;
+    }
+    cudaGraph_t bodies[4];
+    e = add_cond(s, sw[q], cudaGraphCondTypeSwitch, 4, bodies);
+    for (int v = 0; v < 3 && e == cudaSuccess; v++) {
+      e = cudaStreamBeginCaptureToGraph(s2, bodies[v], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) break;
+      cudaError_t le = v == 2 ? launch_restart(a, p, s2, nullptr) : cudaSuccess;
+      if (le == cudaSuccess) le = launch_step(a, p, s2, v == 0 ? var0(q) : varR(q), hd, nullptr);
+      cudaGraph_t tmp;
+      e = cudaStreamEndCapture(s2, &tmp);
+      if (le != cudaSuccess) e = le;
+    }
+    // body 3 stays empty: the solve is finished
   }
   cudaGraph_t gout = nullptr;
   cudaError_t ee = cudaStreamEndCapture(s, &gout);

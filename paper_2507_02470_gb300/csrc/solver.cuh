@@ -81,6 +81,10 @@ cudaError_t launch_iteration(const Args& a, const Plan& p, cudaStream_t s, cudaE
 cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
 cudaError_t build_conditional_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int steps,
                                     cudaGraph_t* out);
+// Graph of L steps whose variants are fixed by position (R~ test every re, stopping test
+// every ce steps; L a multiple of both), one SWITCH node after each R~ test for the restart.
+cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int L, int re, int ce,
+                              cudaGraph_t* out);
 int kernels_per_step(const Args& a);
 int kernels_per_restart(const Args& a);
 int kernels_per_iteration(const Args& a);

@@ -303,3 +303,23 @@ def test_programmatic_launches_change_nothing(pkg, name):
             out.append((x, y, k["iters"], k["restarts"]))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2:] == out[1][2:]
+
+
+@pytest.mark.parametrize("name,extra", [("plain", {}), ("large_sum", {}), ("lasso", {}), ("csrQ", {}),
+                                        ("plain", {"sigma_fixed": 1}), ("plain", {"restart_off": 1}),
+                                        ("plain", {"check_every": 30, "restart_every": 7})])
+def test_fixed_schedule_graph_matches_dynamic_graph(pkg, name, extra):
+    """Whole periods through the fixed-schedule graph (one conditional node per R~ test) and
+    the tail through the dynamic graph give bit-identical iterates, restarts and stopping
+    values to running every step through the dynamic graph."""
+    qp = PROBLEMS[name]
+    for tol, it in ((1e-30, 333), (1e-8, 200000)):
+        out = []
+        for fixed in (1, 0):
+            with pkg.Solver(qp, fixed_schedule=fixed, autotune=0, **extra) as s:
+                st = s.solve(tol=tol, max_iter=it)
+                x, y, z, w, k = s.get()
+                out.append((st, x, y, k["iters"], k["restarts"], k["sigma"], k["pobj"], k["rel_kkt"]))
+        assert out[0][0] == out[1][0]
+        assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+        assert out[0][3:] == out[1][3:], (out[0][3:], out[1][3:])
