@@ -132,15 +132,17 @@ struct Seq {
   void other() { prev = false; }
 };
 
-// One inner step in variant `var`; the last kernel of the step receives the handles.
+// One inner step in variant `var`; the last kernel of the step receives the handles.  chained:
+// the previous node on s is this library's kernel (its first kernel may then launch early too).
 cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, const Handles& hd,
-                        cudaEvent_t (*ev)[2]) {
+                        cudaEvent_t (*ev)[2], bool chained = false) {
   const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
   const Handles none;
   const int tt = var == VAR_T ? 1 : var == VAR_RUNTIME ? 2 : 0;
   // plain steps write no partial sums, so they may run at their own (larger) grids
   const bool pl = var == VAR_PLAIN && p.wZX > 0;
   Seq L{s, p.pdl != 0 && !ev};
+  L.prev = chained;
   TIMED(0, L(zxk(var), pl ? p.wZX : p.gridE, a));
   if (HQ) {
     if (pre) {
@@ -392,7 +394,8 @@ cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cuda
       hd.has_next = 1;
     }
     if (!is_sw(q)) {
-      e = launch_step(a, p, s, var0(q), hd, nullptr);
+      // directly after the previous step's last kernel unless that step sat in a SWITCH body
+      e = launch_step(a, p, s, var0(q), hd, nullptr, q > 1 && !is_sw(q - 1));
       continue;
     }
     cudaGraph_t bodies[4];
