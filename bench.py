@@ -495,6 +495,8 @@ def main():
                     help="1 (default): programmatic dependent launches between the kernels of a step")
     ap.add_argument("--fixed-schedule", type=int, default=1,
                     help="1 (default): whole check periods through the fixed-schedule graph")
+    ap.add_argument("--tiled-factor", type=int, default=1,
+                    help="1 (default): shared-memory-tiled products for large factor terms; 0 off")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -532,7 +534,7 @@ def main():
     qp, desc = workload(args.workload)
     stream = torch.cuda.Stream()
     solver = pkg.Solver(qp, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl,
-                        fixed_schedule=args.fixed_schedule)
+                        fixed_schedule=args.fixed_schedule, tiled_factor=args.tiled_factor)
     iters_per_step, solve_s = [], []
     for _ in range(args.warmup):
         solver.solve(tol=TOL, max_iter=1_000_000)
@@ -590,7 +592,7 @@ def main():
         torch.cuda.synchronize()
         t = time.perf_counter()
         with pkg.Solver(pinned, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl,
-                        fixed_schedule=args.fixed_schedule) as s2:
+                        fixed_schedule=args.fixed_schedule, tiled_factor=args.tiled_factor) as s2:
             s2.solve(tol=TOL, max_iter=1_000_000)
             _, _, _, _, k2 = s2.get(outx, outy if qp.m else None, outz, outw)
         torch.cuda.synchronize()
@@ -611,7 +613,8 @@ def main():
             "config": {"workload": desc, "tol": TOL, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (working set > 129 MB), no flush needed",
                        "check_every": int(solver.params.check_every), "restart_every": int(solver.params.restart_every),
-                       "launch_mode": args.launch_mode, "pdl": args.pdl, "fixed_schedule": args.fixed_schedule},
+                       "launch_mode": args.launch_mode, "pdl": args.pdl, "fixed_schedule": args.fixed_schedule,
+                       "tiled_factor": args.tiled_factor},
             "time_to_tol_s": round(statistics.median(solve_s), 4),
             "tolerance_ladder": {
                 "1e-4": {"iters": kkts[-1]["iters_1e4"], "s": round(statistics.median(k["seconds_1e4"] for k in kkts), 4)},

@@ -145,6 +145,11 @@ typedef struct hprqp_params {
                                 restart_every, stopping test every check_every steps) with one
                                 conditional node per R~ test instead of two per step; results
                                 unchanged.  0: every step through the dynamic graph */
+  int32_t tiled_factor;      /* factor terms B_f^T B_f: 1 (default) a large factor (>= 2e6
+                                entries, >= 8 per row and column) also gets a copy stored tile
+                                by tile, and the one-vector products B_f x, B_f^T t gather from
+                                shared-memory tiles; 2: every factor that fits; 0: never.  Not
+                                with launch_mode 3.  Sums in another order (rounding only) */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
@@ -165,6 +170,7 @@ typedef struct hprqp_kkt {
   /* SpMV schedule picked at create: lanes per row of the Q, A and A^T passes and of the
    * factor pre-pass (0: the staged chunk form); 0 throughout from the batched solver */
   int32_t lanes_q, lanes_a, lanes_at, lanes_pre;
+  int32_t tiled_terms;       /* factor terms whose one-vector products use shared-memory tiles */
 } hprqp_kkt;
 
 /* One stopping test of a solve (every check_every iterations, Sec. 4.1). */

@@ -47,7 +47,8 @@ class hprqp_params(C.Structure):
                 ("time_limit", C.c_double), ("iters_per_launch", C.c_int32), ("autotune", C.c_int32),
                 ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("launch_mode", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32),
-                ("pdl", C.c_int32), ("fixed_schedule", C.c_int32)]
+                ("pdl", C.c_int32), ("fixed_schedule", C.c_int32),
+                ("tiled_factor", C.c_int32)]
 
 
 class hprqp_kkt(C.Structure):
@@ -57,7 +58,8 @@ class hprqp_kkt(C.Structure):
                 ("solve_seconds", C.c_double), ("power_seconds", C.c_double), ("kernel_launches", C.c_int64),
                 ("status", C.c_int32), ("iters_1e4", C.c_int64), ("iters_1e6", C.c_int64),
                 ("seconds_1e4", C.c_double), ("seconds_1e6", C.c_double), ("lanes_q", C.c_int32),
-                ("lanes_a", C.c_int32), ("lanes_at", C.c_int32), ("lanes_pre", C.c_int32)]
+                ("lanes_a", C.c_int32), ("lanes_at", C.c_int32), ("lanes_pre", C.c_int32),
+                ("tiled_terms", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

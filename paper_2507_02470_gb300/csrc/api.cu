@@ -205,6 +205,92 @@ static HostCsr transpose(const HostCsr& M) {
   return T;
 }
 
+// SELL-32-1024 copy of M tile by tile over its columns (tile k: columns [k W, (k+1) W),
+// W = kTileW): per tile, rows in windows of 1024 sorted by their entry count in the tile
+// (ties by row), slices of 32 rows padded with zero values to the slice's longest row, a
+// row's entries in their order inside the row, column indices relative to the tile.
+static hprqp_status build_sell(hprqp_handle* h, SellTiles& S, const HostCsr& M) {
+  static_assert(kTileW <= 65536, "tile-local columns must fit 16 bits");
+  const int64_t rows = M.rows, W = kTileW;
+  const int nt = (int)std::max<int64_t>(1, (M.cols + W - 1) / W);
+  const int64_t nsl = (rows + kSellC - 1) / kSellC;
+  std::vector<int> len((size_t)nt * (size_t)rows, 0);
+  for (int64_t r = 0; r < rows; r++)
+    for (int q = M.rp[r]; q < M.rp[r + 1]; q++) len[(size_t)(M.ci[q] / W) * (size_t)rows + (size_t)r]++;
+  std::vector<int> off((size_t)nt * (size_t)(nsl + 1));
+  std::vector<int> perm((size_t)nt * (size_t)nsl * kSellC, -1);
+  std::vector<int> slot((size_t)nt * (size_t)rows);   // slice * 32 + lane of (tile, row)
+  int64_t tot = 0;
+  std::vector<int> order;
+  for (int k = 0; k < nt; k++) {
+    const int* lk = len.data() + (size_t)k * (size_t)rows;
+    for (int64_t r0 = 0; r0 < rows; r0 += kSellWin) {
+      const int64_t cnt = std::min<int64_t>(kSellWin, rows - r0);
+      order.resize((size_t)cnt);
+      for (int64_t i = 0; i < cnt; i++) order[(size_t)i] = (int)(r0 + i);
+      std::stable_sort(order.begin(), order.end(), [lk](int x, int y) { return lk[x] > lk[y]; });
+      for (int64_t i = 0; i < cnt; i += kSellC) {
+        const int64_t sl = (r0 + i) / kSellC;
+        int width = 0;
+        for (int l = 0; l < kSellC && i + l < cnt; l++) {
+          const int r = order[(size_t)(i + l)];
+          perm[((size_t)k * (size_t)nsl + (size_t)sl) * kSellC + l] = r;
+          slot[(size_t)k * (size_t)rows + (size_t)r] = (int)(sl * kSellC + l);
+          width = std::max(width, lk[r]);
+        }
+        off[(size_t)k * (size_t)(nsl + 1) + (size_t)sl] = (int)tot;
+        tot += (int64_t)width * kSellC;
+        if (tot >= ((int64_t)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "tiled factor copy: too many entries");
+      }
+    }
+    off[(size_t)k * (size_t)(nsl + 1) + (size_t)nsl] = (int)tot;
+  }
+  std::vector<unsigned short> col((size_t)tot, 0);
+  std::vector<double> val((size_t)tot, 0.0);
+  std::vector<int> m((size_t)nt);
+  for (int64_t r = 0; r < rows; r++) {
+    std::fill(m.begin(), m.end(), 0);
+    for (int q = M.rp[r]; q < M.rp[r + 1]; q++) {
+      const int k = (int)(M.ci[q] / W);
+      const int sp = slot[(size_t)k * (size_t)rows + (size_t)r];
+      const size_t pos = (size_t)off[(size_t)k * (size_t)(nsl + 1) + (size_t)(sp / kSellC)] +
+                         (size_t)m[(size_t)k] * kSellC + (size_t)(sp % kSellC);
+      col[pos] = (unsigned short)(M.ci[q] - k * W);
+      val[pos] = M.v[q];
+      m[(size_t)k]++;
+    }
+  }
+  hprqp_status st;
+  int *d_off, *d_perm;
+  unsigned short* d_col;
+  double* d_val;
+  if ((st = upload(h, &d_off, off)) || (st = upload(h, &d_perm, perm)) || (st = upload(h, &d_col, col)) ||
+      (st = upload(h, &d_val, val)))
+    return st;
+  // the host vectors are released on return: finish the copies first
+  CU(h, cudaStreamSynchronize(h->stream));
+  S.rows = rows;
+  S.ntile = nt;
+  S.nsl = nsl;
+  S.off = d_off;
+  S.perm = d_perm;
+  S.col = d_col;
+  S.val = d_val;
+  return HPRQP_OK;
+}
+
+// Tiled copies of a factor term B (p x n) for the shared-memory products of tiled.cu: B tiled
+// over its columns (the entries of x), B^T over its columns (the entries of t = B x).
+static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, int sms) {
+  hprqp_status st;
+  if ((st = build_sell(h, T.b, B)) || (st = build_sell(h, T.bt, transpose(B)))) return st;
+  T.p = B.rows;
+  const int64_t nwin = (T.b.nsl + kSellWin / kSellC - 1) / (kSellWin / kSellC);
+  // one wave of (tile, window range) blocks at one block per SM
+  T.nrange = (int)std::max<int64_t>(1, std::min<int64_t>(sms / T.b.ntile, nwin));
+  return zeros(h, &T.part, (size_t)T.b.ntile * (size_t)B.rows);
+}
+
 static hprqp_status upload_csr(hprqp_handle* h, Csr& d, const HostCsr& M) {
   d.rows = M.rows;
   d.cols = M.cols;
@@ -246,6 +332,7 @@ extern "C" void hprqp_default_params(hprqp_params* p) {
   p->method = 0;
   p->pdl = 1;
   p->fixed_schedule = 1;
+  p->tiled_factor = 1;
 }
 
 extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
@@ -695,6 +782,30 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     toff += n;
     if ((st = blas_init(h))) return st;
   }
+  // ---- tiled copies of large factor terms: their one-vector products gather through shared
+  // memory (tiled.cu); u = B_f^T B_f x goes to the intermediate buffers at uoff
+  {
+    int tdev = 0, tsms = 0, optin = 0;
+    CU(h, cudaGetDevice(&tdev));
+    CU(h, cudaDeviceGetAttribute(&tsms, cudaDevAttrMultiProcessorCount, tdev));
+    CU(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, tdev));
+    const bool room = optin >= (int)(kTileW * sizeof(double)) + 1024;
+    bool any = false;
+    for (int f = 0; f < QD.nfac; f++) {
+      const HostCsr& B = facs[f];
+      const int64_t nnz = B.rp[B.rows];
+      const int64_t kb = (n + kTileW - 1) / kTileW, kt = (B.rows + kTileW - 1) / kTileW;
+      const bool fits = room && h->prm.launch_mode != 3 && kt <= 8 && kb * B.rows <= ((int64_t)1 << 28);
+      const bool large = nnz >= 2000000 && nnz >= 8 * std::max<int64_t>(n, B.rows);
+      if (!fits || !(h->prm.tiled_factor == 2 || (h->prm.tiled_factor == 1 && large))) continue;
+      if ((st = build_tiled(h, QD.tf[f], B, tsms))) return st;
+      QD.tiled[f] = 1;
+      QD.uoff[f] = toff;
+      toff += n;
+      any = true;
+    }
+    if (any) CU(h, tiled_setup());
+  }
   QD.tlen = toff;
 
   // ---- work vectors (all n- and m-vectors exist; unused ones stay zero)
@@ -729,6 +840,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   P.gridN = std::min(chunks(n), sms * per_sm);
   P.gridM = std::min(chunks(m), sms * per_sm);
   P.gridE = std::min(chunks(n), sms * 8);
+  P.gridT = tiled_tbt_grid(n, sms);
   P.gridPre = (int)std::min<int64_t>(std::max<int64_t>(1, (toff + 7) / 8), sms * 8);
   std::function<int(int)> pre_grid;
   {
@@ -1053,7 +1165,7 @@ static hprqp_status power_method(hprqp_handle* h, int which, double* lam) {
   const int64_t max_launch = h->prm.power_max_iter / h->pw_chunk + 3;
   int* flag = h->hflags;
   h->launches += 1;
-  const int64_t pw_nodes = (int64_t)h->pw_chunk * (which == 0 ? 4 : 3 + (h->args.Q.has_pre() ? 1 : 0));
+  const int64_t pw_nodes = (int64_t)h->pw_chunk * kernels_per_power_iter(h->args, which);
   for (int64_t i = 0; i < max_launch; i++) {
     CU(h, cudaGraphLaunch(h->g_pw[which], h->stream));
     h->launches += pw_nodes;
@@ -1348,6 +1460,7 @@ static hprqp_status solve_primal(hprqp_handle* h, double tol, int64_t max_iter, 
   K.lanes_a = h->plan.gA;
   K.lanes_at = h->plan.gAT;
   K.lanes_pre = h->plan.gPre;
+  for (int f = 0; f < h->args.Q.nfac; f++) K.tiled_terms += h->args.Q.tiled[f];
   K.eta_p = out[0];
   K.eta_d = out[1];
   K.eta_gap = out[2];
@@ -1495,6 +1608,7 @@ static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::tim
   K.lanes_a = h->plan.gA;
   K.lanes_at = h->plan.gAT;
   K.lanes_pre = h->plan.gPre;
+  for (int f = 0; f < h->args.Q.nfac; f++) K.tiled_terms += h->args.Q.tiled[f];
   K.eta_p = C.eta_p;
   K.eta_d = C.eta_d;
   K.eta_gap = C.eta_gap;

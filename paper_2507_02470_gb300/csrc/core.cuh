@@ -25,6 +25,33 @@ struct Csr {
   const double* v = nullptr;
 };
 
+// Shared-memory-tiled copy of a factor term B_f (p x n) for products with one vector: t = B x
+// runs per column tile of x (kTileW entries held in shared memory) into per-tile partial sums,
+// u = B^T t per tile of t; both gather from shared memory instead of L2.  Each tile of a
+// matrix M (B or B^T) is stored as sliced ELLPACK with sorting (SELL-32-1024): rows taken in
+// windows of 1024, sorted inside the window by their entry count in the tile, cut into slices
+// of 32 rows (one per lane of a warp), entry m of a slice's lane l at off + 32 m + l, padded
+// with zero values to the longest row of the slice.  Column indices are tile-local (16 bits).
+constexpr int kTileW = 25600;   // doubles per shared-memory tile (200 KB)
+constexpr int kSellC = 32;      // rows per slice
+constexpr int kSellWin = 1024;  // rows per sorting window (= slices of one block's warps)
+struct SellTiles {
+  int64_t rows = 0;               // rows of M
+  int ntile = 0;                  // column tiles of M
+  int64_t nsl = 0;                // slices per tile: ceil(rows / 32)
+  const int* off = nullptr;       // ntile x (nsl + 1) entry offsets of the slices
+  const int* perm = nullptr;      // ntile x (nsl * 32): row of each slice lane, -1 for padding
+  const unsigned short* col = nullptr;   // tile-local columns
+  const double* val = nullptr;
+};
+struct TiledFac {
+  int64_t p = 0;
+  int nrange = 0;                 // blocks per column tile of B (windows split among them)
+  SellTiles b;                    // B (p x n): tiles over the columns of B (entries of x)
+  SellTiles bt;                   // B^T (n x p): tiles over the rows of B (entries of t)
+  double* part = nullptr;         // b.ntile x p partial sums of B x, one row per column tile
+};
+
 // Q = diag(d) + sym band + CSR + sum_f B_f^T B_f + sum_g F_g^T F_g   (Sec. 1: Q may be
 // matrix-free).  The factor intermediates t = B v, F v live in one buffer at toff[].
 struct QDev {
@@ -48,6 +75,12 @@ struct QDev {
   double* qap_tmp = nullptr;    // d x d scratch
   double* qap_in = nullptr;     // n scratch (restart difference)
   int64_t qap_off = 0;
+  // factor terms with a tiled copy: their one-vector products (t = B x, then u = B^T t into
+  // the intermediate buffer at uoff) run in the tiled kernels; the two-vector products of a
+  // stopping test keep the CSR pre-pass and row pass
+  int tiled[kMaxFac] = {0};
+  TiledFac tf[kMaxFac];
+  int64_t uoff[kMaxFac] = {0};
   int64_t tfd = 0;              // intermediate rows of the factor and dense terms
   int64_t tlen = 0;             // tfd, plus n for the QAP product
   __host__ __device__ bool present() const { return diag || csr.rows || ndia || nfac || ndense || qap_d; }

@@ -298,6 +298,7 @@ __device__ __forceinline__ void q_csr_chunk(const QDev& Q, int64_t row0, const d
     add = true;
   }
   for (int f = 0; f < Q.nfac; f++) {
+    if (NR == 1 && Q.tiled[f]) continue;   // B_f^T t_f formed by the tiled kernels (q_local)
     csr_chunk<G, NR>(Q.fact[f], row0, t0 + Q.toff[f], NR == 2 ? t1 + Q.toff[f] : nullptr, rs0, rs1, add);
     add = true;
   }
@@ -309,9 +310,10 @@ __device__ __forceinline__ void q_csr_chunk(const QDev& Q, int64_t row0, const d
   }
 }
 
-// Row-local parts of (Q x)_j: diagonal, symmetric band, and F_g^T t_g of the dense factors.
+// Row-local parts of (Q x)_j: diagonal, symmetric band, F_g^T t_g of the dense factors, and
+// (tiled_u: a one-vector pass) the tiled factors' B_f^T t_f formed before the pass.
 __device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double* HPRQP_RESTRICT x,
-                                          const double* HPRQP_RESTRICT t, bool with_dense) {
+                                          const double* HPRQP_RESTRICT t, bool with_dense, bool tiled_u) {
   double acc = 0.0;
   if (Q.diag) acc = Q.diag[j] * x[j];
   for (int k = 0; k < Q.ndia; k++) {
@@ -325,6 +327,9 @@ __device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double
     }
   }
   if (Q.qap_d) acc += t[Q.qap_off + j];   // (Q_qap x)_j, formed before the pass
+  if (tiled_u)
+    for (int f = 0; f < Q.nfac; f++)
+      if (Q.tiled[f]) acc += t[Q.uoff[f] + j];
   if (with_dense) {
     for (int g = 0; g < Q.ndense; g++) {
       const double* F = Q.dense[g];
@@ -445,9 +450,12 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
     const L2Pol pol;
     for (int64_t r = grp; r < ffac_pad; r += ngrp) {
       double s0 = 0.0, s1 = 0.0;
-      if (r < ffac) {
-        int term = 0;
+      int term = 0;
+      if (r < ffac)
         while (term + 1 < Q.nfac && r >= Q.toff[term + 1]) term++;
+      // one-vector products of a tiled factor are formed by the tiled kernels
+      const bool mine = r < ffac && !(Q.tiled[term] && !two);
+      if (mine) {
         const Csr& B = Q.fac[term];
         const int64_t rl = r - Q.toff[term];
         const int b = stream_i32(B.rp + rl, pol), e = stream_i32(B.rp + rl + 1, pol);
@@ -507,7 +515,7 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
           if (two) s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
         }
       }
-      if (lane == 0 && r < ffac) {
+      if (lane == 0 && mine) {
         t[r] = s0;
         if (two) t[Q.tlen + r] = s1;
       }
@@ -789,8 +797,8 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
       const double r0 = rs0[threadIdx.x];
       if (KIND == K_Q1) {
         const double* src = HA ? V.wh : V.wb;
-        const double qwh = r0 + q_local(Q, j, src, V.t1, true);
-        if (RED && ttest) V.Qxb[j] = rs1[threadIdx.x] + q_local(Q, j, V.xb, V.t1 + Q.tlen, true);
+        const double qwh = r0 + q_local(Q, j, src, V.t1, true, !(RED && ttest));
+        if (RED && ttest) V.Qxb[j] = rs1[threadIdx.x] + q_local(Q, j, V.xb, V.t1 + Q.tlen, true, false);
         if (HA) {
           // v = what + sigma (Q w - Q wbar_{1/2})   (eq. (3.5), second form)
           const double xh = fma(2.0, V.xb[j], -V.x[j]);
@@ -801,7 +809,7 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
           if (RED) end_row(T, a, j, rtest, ttest, HQ, HA, qwh);
         }
       } else if (KIND == K_Q2) {
-        const double qwb = r0 + q_local(Q, j, V.wb, V.t2, true);
+        const double qwb = r0 + q_local(Q, j, V.wb, V.t2, true, true);
         V.Qwb[j] = qwb;
         if (RED) end_row(T, a, j, rtest, ttest, HQ, HA, qwb);
       } else if (KIND == K_A1) {
@@ -844,13 +852,13 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
           end_row(T, a, j, rtest, ttest, HQ, HA, 0.0);
         }
       } else if (KIND == K_APPLY_Q) {
-        V.aout[j] = r0 + q_local(Q, j, V.ain, V.t1, true);
+        V.aout[j] = r0 + q_local(Q, j, V.ain, V.t1, true, true);
       } else if (KIND == K_APPLY_A || KIND == K_APPLY_AT) {
         V.aout[j] = r0;
       } else if (KIND == K_APPLY_AT_P) {
         V.ptmp[j] = r0;
       } else if (KIND == K_POWER_Q || KIND == K_POWER_A) {
-        const double wv = KIND == K_POWER_Q ? r0 + q_local(Q, j, V.pv, V.t1, true) : r0;
+        const double wv = KIND == K_POWER_Q ? r0 + q_local(Q, j, V.pv, V.t1, true, true) : r0;
         V.pw[j] = wv;
         pw[0] = fma(V.pv[j], wv, pw[0]);
         pw[1] = fma(wv, wv, pw[1]);

@@ -132,6 +132,21 @@ struct Seq {
   void other() { prev = false; }
 };
 
+// Whether the CSR pre-pass has work before a Q pass: dense factors, factors without a tiled
+// copy, or the two-vector pass of a stopping test (tiled factors take the CSR path there).
+static bool pre_has_work(const Args& a, int which, int tt) {
+  if (!a.Q.has_fd()) return false;
+  if (a.Q.ndense) return true;
+  for (int f = 0; f < a.Q.nfac; f++)
+    if (!a.Q.tiled[f]) return true;
+  return which == 0 && tt != 0;
+}
+static int tiled_terms(const Args& a) {
+  int c = 0;
+  for (int f = 0; f < a.Q.nfac; f++) c += a.Q.tiled[f];
+  return c;
+}
+
 // One inner step in variant `var`; the last kernel of the step receives the handles.  chained:
 // the previous node on s is this library's kernel (its first kernel may then launch early too).
 cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, const Handles& hd,
@@ -143,16 +158,29 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   const bool pl = var == VAR_PLAIN && p.wZX > 0;
   Seq L{s, p.pdl != 0 && !ev};
   L.prev = chained;
+  // the products that precede a Q pass: CSR pre-pass, tiled factor kernels, QAP DGEMMs
+  auto pre_pass = [&](int which, int ptt) -> cudaError_t {
+    if (pre_has_work(a, which, ptt)) L(prek(p.gPre, ptt), p.gridPre, a, which);
+    if (L.e != cudaSuccess) return L.e;
+    if (tiled_terms(a)) {
+      int nt = 0;
+      const cudaError_t te = launch_tiled(a, p, which, ptt, s, &nt);
+      if (te != cudaSuccess) return te;
+      if (nt) L.prev = true;
+    }
+    if (a.Q.qap_d) {
+      L.other();
+      const cudaError_t qe = launch_qap(a, p, which, ptt, s);
+      if (qe != cudaSuccess) return qe;
+    }
+    return cudaSuccess;
+  };
   TIMED(0, L(zxk(var), pl ? p.wZX : p.gridE, a));
   if (HQ) {
     if (pre) {
       if (ev) cudaEventRecord(ev[1][0], s);
-      if (a.Q.has_fd()) L(prek(p.gPre, tt), p.gridPre, a, 0);
-      if (a.Q.qap_d) {
-        L.other();
-        const cudaError_t qe = launch_qap(a, p, 0, tt, s);
-        if (qe != cudaSuccess) return qe;
-      }
+      const cudaError_t pe = pre_pass(0, tt);
+      if (pe != cudaSuccess) return pe;
       if (ev) cudaEventRecord(ev[1][1], s);
     }
     TIMED(2, L(rowk(K_Q1, var, p.gQ), pl ? p.wQ1 : p.gridN, a, HA ? none : hd));
@@ -163,12 +191,8 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
     if (HQ) {
       if (pre) {
         if (ev) cudaEventRecord(ev[5][0], s);
-        if (a.Q.has_fd()) L(prek(p.gPre, 0), p.gridPre, a, 1);
-        if (a.Q.qap_d) {
-          L.other();
-          const cudaError_t qe = launch_qap(a, p, 1, 0, s);
-          if (qe != cudaSuccess) return qe;
-        }
+        const cudaError_t pe = pre_pass(1, 0);
+        if (pe != cudaSuccess) return pe;
         if (ev) cudaEventRecord(ev[5][1], s);
       }
       TIMED(6, L(rowk(K_Q2, var, p.gQ), pl ? p.wQ2 : p.gridN, a, hd));
@@ -228,7 +252,13 @@ cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEve
   Seq L{s, p.pdl != 0 && !ev};
   if (a.Q.present() && a.m > 0 && a.Q.has_pre()) {
     if (ev) cudaEventRecord(ev[7][0], s);
-    if (a.Q.has_fd()) L(prek(p.gPre, 0), p.gridPre, a, 2);
+    if (pre_has_work(a, 2, 0)) L(prek(p.gPre, 0), p.gridPre, a, 2);
+    if (tiled_terms(a)) {
+      int nt = 0;
+      const cudaError_t te = launch_tiled(a, p, 2, 0, s, &nt);
+      if (te != cudaSuccess) return te;
+      if (nt) L.prev = true;
+    }
     if (a.Q.qap_d) {
       L.other();
       const cudaError_t qe = launch_qap(a, p, 2, 0, s);
@@ -252,8 +282,11 @@ cudaError_t launch_step_var(const Args& a, const Plan& p, cudaStream_t s, int va
   return launch_step(a, p, s, var, Handles(), ev);
 }
 
-// kernels before a Q pass: the factor pre-pass and the four DGEMMs of a QAP product
-static int pre_kernels(const Args& a) { return (a.Q.has_fd() ? 1 : 0) + (a.Q.qap_d ? 4 : 0); }
+// kernels before a Q pass of a plain step: the factor pre-pass, the tiled factor kernels and
+// the four DGEMMs of a QAP product
+static int pre_kernels(const Args& a) {
+  return (pre_has_work(a, 1, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 4 : 0);
+}
 
 int kernels_per_step(const Args& a) {
   const bool HQ = a.Q.present(), HA = a.m > 0;
@@ -264,7 +297,9 @@ int kernels_per_step(const Args& a) {
   return k;
 }
 int kernels_per_restart(const Args& a) {
-  return 1 + ((a.Q.present() && a.m > 0 && a.Q.has_pre()) ? pre_kernels(a) + (a.Q.qap_d ? 1 : 0) : 0);
+  return 1 + ((a.Q.present() && a.m > 0 && a.Q.has_pre())
+                  ? (pre_has_work(a, 2, 0) ? 1 : 0) + 2 * tiled_terms(a) + (a.Q.qap_d ? 5 : 0)
+                  : 0);
 }
 int kernels_per_iteration(const Args& a) { return kernels_per_step(a) + kernels_per_restart(a); }
 
@@ -431,9 +466,10 @@ cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s) {
   } else if (op == 1) {
     rowk(K_APPLY_AT, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
   } else {
-    if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 3);
+    if (pre_has_work(a, 3, 0)) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 3);
     {
-      const cudaError_t qe = launch_qap(a, p, 3, 0, s);
+      cudaError_t qe = tiled_terms(a) ? launch_tiled(a, p, 3, 0, s, nullptr) : cudaSuccess;
+      if (qe == cudaSuccess) qe = launch_qap(a, p, 3, 0, s);
       if (qe != cudaSuccess) return qe;
     }
     rowk(K_APPLY_Q, 0, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, none);
@@ -468,6 +504,11 @@ cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStrea
   return cudaGetLastError();
 }
 
+int kernels_per_power_iter(const Args& a, int which) {
+  if (which == 0) return 4;
+  return 3 + (pre_has_work(a, 4, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 4 : 0);
+}
+
 cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s) {
   const int64_t dim = which == 0 ? a.m : a.n;
   const Handles none;
@@ -478,9 +519,10 @@ cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStrea
     rowk(K_APPLY_AT_P, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
     rowk(K_POWER_A, 0, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none);
   } else {
-    if (a.Q.has_fd()) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 4);
+    if (pre_has_work(a, 4, 0)) prek(p.gPre, 0)<<<p.gridPre, kThreads, 0, s>>>(a, 4);
     {
-      const cudaError_t qe = launch_qap(a, p, 4, 0, s);
+      cudaError_t qe = tiled_terms(a) ? launch_tiled(a, p, 4, 0, s, nullptr) : cudaSuccess;
+      if (qe == cudaSuccess) qe = launch_qap(a, p, 4, 0, s);
       if (qe != cudaSuccess) return qe;
     }
     rowk(K_POWER_Q, 0, p.gQ)<<<p.gridN, kThreads, 0, s>>>(a, none);

@@ -54,6 +54,7 @@ struct Plan {
   // kernel; the reducing variants keep gridN/gridM/gridE, which size the partial-sum regions
   int wZX = 0, wQ1 = 0, wA1 = 0, wAT = 0, wQ2 = 0;
   int gridP = 0;   // blocks of the persistent (cooperative) solver
+  int gridT = 0;   // blocks of the tiled B^T t kernel
   void* blas = nullptr;   // cuBLAS handle for a QAP term's products
   // programmatic dependent launch between consecutive kernels of a step (each kernel waits for
   // its predecessor with griddepcontrol.wait, so only its launch overlaps the predecessor's end)
@@ -90,10 +91,16 @@ int kernels_per_restart(const Args& a);
 int kernels_per_iteration(const Args& a);
 cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s);
 cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s);
+int kernels_per_power_iter(const Args& a, int which);
 cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s);
 cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s);
 cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_pre_probe(const Args& a, int G, int grid, cudaStream_t s);
+// shared-memory-tiled factor products (tiled.cu): t = B_f x, then (which != 2) u = B_f^T t,
+// for every tiled factor term; *launched receives the number of kernels
+cudaError_t tiled_setup();
+int tiled_tbt_grid(int64_t n, int sms);
+cudaError_t launch_tiled(const Args& a, const Plan& p, int which, int tt, cudaStream_t s, int* launched);
 // v[i] *= s[i] for i < n
 cudaError_t launch_vmul(double* v, const double* s, int64_t n, cudaStream_t st);
 // out[i] = v[i] * s[i] for i < n

@@ -22,6 +22,8 @@ def main(argv=None):
     ap.add_argument("--warm-iters", type=int, default=20, help="iterations of the solve before profiling")
     ap.add_argument("--autotune", type=int, default=1,
                     help="SpMV schedule: 1 timed choice, 0 lanes from row length, 2 staged chunks")
+    ap.add_argument("--tiled-factor", type=int, default=1,
+                    help="shared-memory-tiled factor products: 1 auto, 0 off, 2 forced")
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -33,11 +35,12 @@ def main(argv=None):
           "c1": lambda: qpgen.large_cqp(n=1_000_000, m=500_000, seed=0),
           "c2": lambda: qpgen.lasso(),
           "c4": lambda: qpgen.param_family_base(n=100_000, m=50_000, seed=0)}[args.workload]()
-    with pkg.Solver(qp, launch_mode=2, autotune=args.autotune) as s:
+    with pkg.Solver(qp, launch_mode=2, autotune=args.autotune, tiled_factor=args.tiled_factor) as s:
         s.solve(tol=1e-30, max_iter=args.warm_iters)
         k = s.kkt()
         ms = s.profile(iters=args.iters)
-    print(json.dumps({"workload": args.workload, "autotune": args.autotune, "n": qp.n, "m": qp.m,
+    print(json.dumps({"workload": args.workload, "autotune": args.autotune, "tiled_factor": args.tiled_factor,
+                      "n": qp.n, "m": qp.m,
                       "iters": args.iters,
                       "lambda_A": k["lambda_A"], "lambda_Q": k["lambda_Q"],
                       "lanes": {q: k["lanes_" + q] for q in ("q", "a", "at", "pre")},
