@@ -86,32 +86,37 @@ __device__ __forceinline__ double sell_row(int b, int e, int lane, const unsigne
 
 // The slices [s0, s1) of one tile, shared among the warps of the block: round i gives warp w
 // slice s0 + 32 i + (w + i) mod 32 (inside a window the slices run from the longest rows to
-// the shortest, so the rotation gives every warp long and short slices); out(row, sum) for
-// each lane's row.  The next slice's bounds and row are loaded before the current entries.
-template <typename Out>
+// the shortest, so the rotation gives every warp long and short slices).  For each lane's row:
+// out(row, sum, pre(row)), where pre(row) (a load the output needs) is issued together with
+// the next slice's bounds and row, before the current slice's entries.
+template <typename Pre, typename Out>
 __device__ __forceinline__ void sell_slices(const int* off, const int* perm, const unsigned short* col,
                                             const double* val, int64_t s0, int64_t s1, const double* tab,
-                                            Out out) {
+                                            Pre pre, Out out) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   auto slice = [&](int64_t i) { return s0 + i * 32 + (warp + i) % 32; };
   const int64_t rounds = (s1 - s0 + 31) / 32;
   int nb = 0, ne = 0, nrow = -1;
+  double npre = 0.0;
   if (rounds > 0 && slice(0) < s1) {
     nb = off[slice(0)];
     ne = off[slice(0) + 1];
     nrow = perm[slice(0) * kSellC + lane];
+    if (nrow >= 0) npre = pre(nrow);
   }
   for (int64_t i = 0; i < rounds; i++) {
     if (slice(i) >= s1) continue;   // the same for the whole warp
     const int b = nb, e = ne, row = nrow;
+    const double rpre = npre;
     if (i + 1 < rounds && slice(i + 1) < s1) {
       const int64_t sl = slice(i + 1);
       nb = off[sl];
       ne = off[sl + 1];
       nrow = perm[sl * kSellC + lane];
+      if (nrow >= 0) npre = pre(nrow);
     }
     const double acc = sell_row(b, e, lane, col, val, tab);
-    if (row >= 0) out(row, acc);
+    if (row >= 0) out(row, acc, rpre);
   }
 }
 
@@ -139,7 +144,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tb(Args a, int which, int f) {
   const int* off = M.off + (size_t)k * (size_t)(M.nsl + 1);
   const int* perm = M.perm + (size_t)k * (size_t)M.nsl * kSellC;
   double* part = T.part + (size_t)k * (size_t)p;
-  sell_slices(off, perm, M.col, M.val, s0, s1, sx, [&](int row, double acc) { part[row] = acc; });
+  sell_slices(off, perm, M.col, M.val, s0, s1, sx, [](int) { return 0.0; },
+              [&](int row, double acc, double) { part[row] = acc; });
 }
 
 // t = sum of the tiles' partial sums, in tile order
@@ -180,9 +186,12 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tbt(Args a, int which, int f) 
   double* tb = which == 1 ? V.t2 : V.t1;
   const double* tv = tb + a.Q.toff[f];
   double* u = tb + a.Q.uoff[f];
-  // this block's share of the slices: the same in every tile, so u of the previous tile was
-  // written by this block
-  const int64_t s0 = (int64_t)blockIdx.x * M.nsl / gridDim.x, s1 = (int64_t)(blockIdx.x + 1) * M.nsl / gridDim.x;
+  // this block's share: whole windows (a window holds the same rows in every tile, sorted
+  // differently), so u of the previous tile was written by this block
+  constexpr int spw = kSellWin / kSellC;
+  const int64_t nwin = (M.nsl + spw - 1) / spw;
+  const int64_t w0 = (int64_t)blockIdx.x * nwin / gridDim.x, w1 = (int64_t)(blockIdx.x + 1) * nwin / gridDim.x;
+  const int64_t s0 = w0 * spw, s1 = w1 * spw < M.nsl ? w1 * spw : M.nsl;
   for (int k = 0; k < M.ntile; k++) {
     const int64_t c0 = (int64_t)k * kTileW;
     const int cw = (int)(p - c0 < (int64_t)kTileW ? p - c0 : (int64_t)kTileW);
@@ -192,7 +201,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tbt(Args a, int which, int f) 
     const int* off = M.off + (size_t)k * (size_t)(M.nsl + 1);
     const int* perm = M.perm + (size_t)k * (size_t)M.nsl * kSellC;
     const bool first = k == 0;
-    sell_slices(off, perm, M.col, M.val, s0, s1, st, [&](int j, double acc) { u[j] = first ? acc : u[j] + acc; });
+    sell_slices(off, perm, M.col, M.val, s0, s1, st, [&](int j) { return first ? 0.0 : u[j]; },
+                [&](int j, double acc, double prev) { u[j] = first ? acc : prev + acc; });
   }
 }
 
