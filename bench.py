@@ -310,10 +310,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def algorithmic(qp):
+TILE_W = 25600   # entries of x (or t) per shared-memory tile in the tiled factor products
+
+
+def algorithmic(qp, tiled=False):
     """Algorithmic HBM bytes and FP64 instructions per launch of each kernel kind (one
     non-checking inner step; vectors counted once per pass, CSR at 12 B/nnz + 4 B/row,
-    band at 8 B per stored diagonal entry)."""
+    band at 8 B per stored diagonal entry).  tiled: the factor terms run as shared-memory
+    tiled products (10 B per entry, per-tile partial sums of B x, u = B^T t tile by tile),
+    all inside the pre-pass group, and the row pass only adds u."""
     n, m = qp.n, qp.m
     nnzA = int(qp.A_rowptr[-1]) if m else 0
     q_bytes = 0
@@ -329,6 +334,9 @@ def algorithmic(qp):
         elif t.kind == "csr":
             q_bytes += 12 * int(t.rowptr[-1]) + 4 * n
             q_flops += int(t.rowptr[-1])
+        elif t.kind == "factor" and tiled:
+            fac_nnz += int(t.rowptr[-1])
+            q_bytes += 8 * n                             # u = B^T t, formed before the pass
         elif t.kind == "factor":
             fac_nnz += int(t.rowptr[-1])
             q_bytes += 12 * int(t.rowptr[-1]) + 4 * n   # B^T pass (rows n)
@@ -340,6 +348,16 @@ def algorithmic(qp):
             q_bytes += 8 * n            # the product formed by cuBLAS before the pass, added in it
     pre_bytes = 12 * fac_nnz + 4 * sum(t.p + 1 for t in qp.qterms if t.kind == "factor")
     pre_flops = fac_nnz
+    if tiled:
+        pre_bytes, pre_flops = 0, 0
+        for t in qp.qterms:
+            if t.kind != "factor":
+                continue
+            nnz, kb, kt = int(t.rowptr[-1]), -(-n // TILE_W), -(-t.p // TILE_W)
+            # B x and B^T t at 10 B per entry, x once, kb partial rows written and read, t,
+            # u written once per tile of t and read back for every tile after the first
+            pre_bytes += 20 * nnz + 8 * n + 16 * kb * t.p + 8 * t.p + 8 * n * (2 * kt - 1)
+            pre_flops += 2 * nnz + kb * t.p + (kt - 1) * n
     HA = m > 0
     zx_vec = (15 if HA else 11) if qp.qterms else 8
     zx_out = 6 if HA else 5
@@ -355,8 +373,8 @@ def algorithmic(qp):
     return out
 
 
-def roofline(prof, qp, pk, pk_src, traffic):
-    alg = algorithmic(qp)
+def roofline(prof, qp, pk, pk_src, traffic, tiled=False):
+    alg = algorithmic(qp, tiled)
     name = max((k for k in prof if k in alg and prof[k] > 0), key=lambda k: prof[k])
     ms = prof[name]
     b, f = alg[name]
@@ -570,7 +588,8 @@ def main():
     # per-kernel durations (CUDA events on the solver's stream), then the e2e leg
     prof = solver.profile(iters=40)
     pk, pk_src = peaks()
-    roof = roofline(prof, qp, pk, pk_src, traffic_table(args.workload))
+    nfac = sum(1 for t in qp.qterms if t.kind == "factor")
+    roof = roofline(prof, qp, pk, pk_src, traffic_table(args.workload), tiled=nfac > 0 and kk["tiled_terms"] == nfac)
 
     # end to end through the C ABI with host buffers: create (H2D), solve, get (D2H)
     host = {k: (torch.from_numpy(np.ascontiguousarray(v)).pin_memory() if isinstance(v, np.ndarray) else v)
