@@ -205,8 +205,8 @@ static HostCsr transpose(const HostCsr& M) {
   return T;
 }
 
-// SELL-32-1024 copy of M tile by tile over its columns (tile k: columns [k W, (k+1) W),
-// W = kTileW): per tile, rows in windows of 1024 sorted by their entry count in the tile
+// SELL-32-512 copy of M tile by tile over its columns (tile k: columns [k W, (k+1) W),
+// W = kTileW): per tile, rows in windows of 512 sorted by their entry count in the tile
 // (ties by row), slices of 32 rows padded with zero values to the slice's longest row, a
 // row's entries in their order inside the row, column indices relative to the tile.
 static hprqp_status build_sell(hprqp_handle* h, SellTiles& S, const HostCsr& M) {

@@ -28,13 +28,13 @@ struct Csr {
 // Shared-memory-tiled copy of a factor term B_f (p x n) for products with one vector: t = B x
 // runs per column tile of x (kTileW entries held in shared memory) into per-tile partial sums,
 // u = B^T t per tile of t; both gather from shared memory instead of L2.  Each tile of a
-// matrix M (B or B^T) is stored as sliced ELLPACK with sorting (SELL-32-1024): rows taken in
-// windows of 1024, sorted inside the window by their entry count in the tile, cut into slices
+// matrix M (B or B^T) is stored as sliced ELLPACK with sorting (SELL-32-512): rows taken in
+// windows of 512, sorted inside the window by their entry count in the tile, cut into slices
 // of 32 rows (one per lane of a warp), entry m of a slice's lane l at off + 32 m + l, padded
 // with zero values to the longest row of the slice.  Column indices are tile-local (16 bits).
 constexpr int kTileW = 25600;   // doubles per shared-memory tile (200 KB)
 constexpr int kSellC = 32;      // rows per slice
-constexpr int kSellWin = 1024;  // rows per sorting window (= slices of one block's warps)
+constexpr int kSellWin = 512;   // rows per sorting window (16 slices)
 struct SellTiles {
   int64_t rows = 0;               // rows of M
   int ntile = 0;                  // column tiles of M

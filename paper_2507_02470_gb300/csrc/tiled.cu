@@ -10,7 +10,7 @@
 // Why: on GB300 both the FP64 pipe (one warp instruction per 19 cycles per SM) and random
 // gathers from L2 (one L1 wavefront per distinct line, about one gather per SM cycle) bound
 // these products.  Here each lane owns a row of a 32-row slice (SELL-32 with rows sorted by
-// length inside windows of 1024): the loads are coalesced, every FMA instruction works on 32
+// length inside windows of 512): the loads are coalesced, every FMA instruction works on 32
 // rows with little padding and no shuffle reduction, and the gathers hit shared memory.
 // u goes to the intermediate buffer at uoff, where the row pass adds it.
 #include "kernels.cuh"
@@ -19,7 +19,6 @@ namespace hprqp {
 
 constexpr int kTThreads = 1024;   // threads per tiled block (one block per SM: 200 KB tile)
 constexpr size_t kTSmem = (size_t)kTileW * sizeof(double);
-static_assert(kTThreads / 32 * kSellC == kSellWin, "one slice per warp of a window");
 
 namespace {
 
