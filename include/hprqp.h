@@ -109,10 +109,13 @@ typedef struct hprqp_params {
   double time_limit;         /* seconds, <= 0: none (Sec. 4.1 uses 3600) */
   int32_t iters_per_launch;  /* iterations captured per CUDA-graph launch, default 64 */
   int32_t autotune;          /* 1 (default): time the SpMV schedules (lanes per row 1-32,
-                                or the staged form that streams a chunk's entries as one
-                                range) at create and pick the fastest for each operator;
+                                the staged form that streams a chunk's entries as one range,
+                                or for A and A^T a SELL-32 copy) at create and pick the
+                                fastest for each operator;
                                 0: lanes per row from the mean row length; 2: the staged
-                                form for every CSR pass */
+                                form for every CSR pass; 3: the SELL-32 copy for the A and
+                                A^T passes (rows sorted by length inside each 256-row chunk,
+                                one row per lane), one lane per row elsewhere */
   int32_t verbose;           /* 0: silent */
   hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
   hprqp_free_fn free;

@@ -291,6 +291,59 @@ static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, 
   return zeros(h, &T.part, (size_t)T.b.ntile * (size_t)B.rows);
 }
 
+// SELL-32 copy of M for the row passes (sorting windows = the 256-row chunks of the row
+// kernels, so a chunk's slices hold exactly its rows): d.soff, d.sperm, d.sci, d.sv.
+static hprqp_status build_sell_rows(hprqp_handle* h, Csr& d, const HostCsr& M) {
+  const int64_t rows = M.rows, nsl = (rows + 31) / 32;
+  std::vector<int> off((size_t)nsl + 1), perm((size_t)nsl * 32, -1), slot((size_t)std::max<int64_t>(rows, 1));
+  std::vector<int> order;
+  int64_t tot = 0;
+  for (int64_t r0 = 0; r0 < rows; r0 += kChunk) {
+    const int64_t cnt = std::min<int64_t>(kChunk, rows - r0);
+    order.resize((size_t)cnt);
+    for (int64_t i = 0; i < cnt; i++) order[(size_t)i] = (int)(r0 + i);
+    auto len = [&](int r) { return M.rp[r + 1] - M.rp[r]; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return len(x) > len(y); });
+    for (int64_t i = 0; i < cnt; i += 32) {
+      const int64_t sl = (r0 + i) / 32;
+      int width = 0;
+      for (int l = 0; l < 32 && i + l < cnt; l++) {
+        const int r = order[(size_t)(i + l)];
+        perm[(size_t)sl * 32 + l] = r;
+        slot[(size_t)r] = (int)(sl * 32 + l);
+        width = std::max(width, len(r));
+      }
+      off[(size_t)sl] = (int)tot;
+      tot += (int64_t)width * 32;
+      if (tot >= ((int64_t)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "SELL copy: too many entries");
+    }
+  }
+  off[(size_t)nsl] = (int)tot;
+  std::vector<int> ci((size_t)std::max<int64_t>(tot, 1), 0);
+  std::vector<double> v((size_t)std::max<int64_t>(tot, 1), 0.0);
+  for (int64_t r = 0; r < rows; r++) {
+    const int sp = slot[(size_t)r];
+    const size_t base = (size_t)off[(size_t)(sp / 32)] + (size_t)(sp % 32);
+    for (int q = M.rp[r]; q < M.rp[r + 1]; q++) {
+      const size_t pos = base + (size_t)(q - M.rp[r]) * 32;
+      ci[pos] = M.ci[q];
+      v[pos] = M.v[q];
+    }
+  }
+  hprqp_status st;
+  int *doff, *dperm, *dci;
+  double* dv;
+  if ((st = upload(h, &doff, off)) || (st = upload(h, &dperm, perm)) || (st = upload(h, &dci, ci)) ||
+      (st = upload(h, &dv, v)))
+    return st;
+  CU(h, cudaStreamSynchronize(h->stream));   // the host vectors are released on return
+  d.soff = doff;
+  d.sperm = dperm;
+  d.sci = dci;
+  d.sv = dv;
+  return HPRQP_OK;
+}
+
 static hprqp_status upload_csr(hprqp_handle* h, Csr& d, const HostCsr& M) {
   d.rows = M.rows;
   d.cols = M.cols;
@@ -367,15 +420,18 @@ extern "C" void hprqp_destroy(hprqp_handle* h) { release(h); }
 static int tune_G(hprqp_handle* h, const Csr& M, int grid, double* x, double* y, int fallback) {
   if (M.rows == 0 || M.nnz == 0) return fallback;
   if (h->prm.autotune == 2) return 0;
+  if (h->prm.autotune == 3) return M.soff ? -1 : 1;
   if (!h->prm.autotune) {
     double avg = (double)M.nnz / (double)M.rows;
     return avg < 6 ? 1 : avg < 12 ? 2 : avg < 24 ? 4 : avg < 64 ? 8 : 32;
   }
-  // lanes per row (1-32) or 0: the staged form that streams each chunk's entries as a block
-  const int cand[7] = {0, 1, 2, 4, 8, 16, 32};
+  // lanes per row (1-32), 0: the staged form that streams each chunk's entries as a block,
+  // -1: the SELL copy (A and A^T)
+  const int cand[8] = {-1, 0, 1, 2, 4, 8, 16, 32};
   float best = 1e30f;
   int bestG = fallback;
   for (int G : cand) {
+    if (G == -1 && !M.soff) continue;
     launch_spmv_probe(M, G, grid, x, y, h->stream);
     float tot = 0;
     for (int r = 0; r < 3; r++) {
@@ -388,6 +444,9 @@ static int tune_G(hprqp_handle* h, const Csr& M, int grid, double* x, double* y,
       tot += ms;
     }
     if (cudaGetLastError() != cudaSuccess) continue;
+    // the probe is a bare SpMV; inside the row kernels the SELL form also frees the
+    // epilogue's loads from uncoalesced index traffic, so it wins ties within 10 %
+    if (G == -1) tot *= 0.9f;
     if (tot < best) {
       best = tot;
       bestG = G;
@@ -723,6 +782,11 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     if ((st = upload_csr(h, a.A, A))) return st;
     HostCsr AT = transpose(A);
     if ((st = upload_csr(h, a.AT, AT))) return st;
+    // SELL copies for the autotuner's choice (not for the persistent mode, which keeps lanes)
+    if (h->prm.launch_mode != 3 && h->prm.autotune != 0) {
+      if ((st = build_sell_rows(h, a.A, A))) return st;
+      if ((st = build_sell_rows(h, a.AT, AT))) return st;
+    }
   } else {
     a.A.cols = n;
     a.AT.cols = 0;

@@ -23,6 +23,12 @@ struct Csr {
   const int* rp = nullptr;
   const int* ci = nullptr;
   const double* v = nullptr;
+  // optional SELL-32 copy (A and A^T): rows sorted by length inside each 256-row chunk, slices
+  // of 32 rows, entry m of a slice's lane l at soff[slice] + 32 m + l, zero-padded
+  const int* soff = nullptr;    // slices + 1
+  const int* sperm = nullptr;   // slices * 32: row of each lane, -1 for padding
+  const int* sci = nullptr;
+  const double* sv = nullptr;
 };
 
 // Shared-memory-tiled copy of a factor term B_f (p x n) for products with one vector: t = B x

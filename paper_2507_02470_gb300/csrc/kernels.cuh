@@ -281,10 +281,57 @@ __device__ __forceinline__ void csr_chunk_staged(const Csr& M, int64_t row0, con
   }
 }
 
+// SELL form of the same row sums (G = -1, matrices with a SELL copy, single-term passes only:
+// add must be false): warp w of the block takes slice row0 / 32 + w, each lane one row of it,
+// so every load of indices and values is coalesced and every FMA works on 32 rows.
+template <int NR>
+__device__ __forceinline__ void csr_chunk_sell(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
+                                               const double* HPRQP_RESTRICT x1, double* rs0, double* rs1) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t sl = row0 / 32 + warp;
+  if (sl * 32 >= M.rows) return;   // the same for the whole warp
+  const L2Pol pol;
+  const int r = M.sperm[sl * 32 + lane];
+  const int b = M.soff[sl], e = M.soff[sl + 1];
+  double s0 = 0.0, s1 = 0.0;
+  int q = b + lane;
+  for (; q + 3 * 32 < e; q += 4 * 32) {
+    const int c0 = stream_i32(M.sci + q, pol), c1 = stream_i32(M.sci + q + 32, pol),
+              c2 = stream_i32(M.sci + q + 64, pol), c3 = stream_i32(M.sci + q + 96, pol);
+    const double v0 = stream_f64(M.sv + q, pol), v1 = stream_f64(M.sv + q + 32, pol),
+                 v2 = stream_f64(M.sv + q + 64, pol), v3 = stream_f64(M.sv + q + 96, pol);
+    const double a0 = gather_f64(x0 + c0, pol), a1 = gather_f64(x0 + c1, pol), a2 = gather_f64(x0 + c2, pol),
+                 a3 = gather_f64(x0 + c3, pol);
+    s0 = fma(v0, a0, s0);
+    s0 = fma(v1, a1, s0);
+    s0 = fma(v2, a2, s0);
+    s0 = fma(v3, a3, s0);
+    if (NR == 2) {
+      const double b0 = gather_f64(x1 + c0, pol), b1 = gather_f64(x1 + c1, pol), b2 = gather_f64(x1 + c2, pol),
+                   b3 = gather_f64(x1 + c3, pol);
+      s1 = fma(v0, b0, s1);
+      s1 = fma(v1, b1, s1);
+      s1 = fma(v2, b2, s1);
+      s1 = fma(v3, b3, s1);
+    }
+  }
+  for (; q < e; q += 32) {
+    const int c = stream_i32(M.sci + q, pol);
+    const double v = stream_f64(M.sv + q, pol);
+    s0 = fma(v, gather_f64(x0 + c, pol), s0);
+    if (NR == 2) s1 = fma(v, gather_f64(x1 + c, pol), s1);
+  }
+  if (r >= 0) {
+    rs0[r - row0] = s0;
+    if (NR == 2) rs1[r - row0] = s1;
+  }
+}
+
 template <int G, int NR>
 __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
                                           const double* HPRQP_RESTRICT x1, double* rs0, double* rs1, bool add) {
   if constexpr (G == 0) csr_chunk_staged<NR>(M, row0, x0, x1, rs0, rs1, add);
+  else if constexpr (G == -1) csr_chunk_sell<NR>(M, row0, x0, x1, rs0, rs1);
   else csr_chunk_lanes<G, NR>(M, row0, x0, x1, rs0, rs1, add);
 }
 
@@ -1073,10 +1120,19 @@ RowKernel row_kernel_q(int kind, int var, int G);
 RowKernel row_kernel_a(int kind, int var, int G);
 RowKernel row_kernel_at(int kind, int var, int G);
 
+// kinds whose CSR pass is one matrix with a SELL copy (A or A^T)
+constexpr bool sell_kind(int kind) {
+  return kind == K_A1 || kind == K_APPLY_A || kind == K_POWER_A || kind == K_AT || kind == K_APPLY_AT ||
+         kind == K_APPLY_AT_P;
+}
+
 template <int KIND>
 RowKernel pick_row(int var, int G) {
 #define HPRQP_ROW_G(VAR)                                        \
   switch (G) {                                                  \
+    case -1:                                                    \
+      if constexpr (sell_kind(KIND)) return k_rows<-1, KIND, VAR>; \
+      else return nullptr;                                      \
     case 0: return k_rows<0, KIND, VAR>;                        \
     case 1: return k_rows<1, KIND, VAR>;                        \
     case 2: return k_rows<2, KIND, VAR>;                        \

@@ -573,6 +573,7 @@ cudaError_t launch_pre_probe(const Args& a, int G, int grid, cudaStream_t s) {
 
 cudaError_t launch_spmv_probe(const Csr& M, int G, int grid, const double* x, double* y, cudaStream_t s) {
   switch (G) {
+    case -1: k_spmv_probe<-1><<<grid, kThreads, 0, s>>>(M, x, y); break;
     case 0: k_spmv_probe<0><<<grid, kThreads, 0, s>>>(M, x, y); break;
     case 1: k_spmv_probe<1><<<grid, kThreads, 0, s>>>(M, x, y); break;
     case 2: k_spmv_probe<2><<<grid, kThreads, 0, s>>>(M, x, y); break;

@@ -265,15 +265,18 @@ def _long_and_empty_rows():
 STAGED = dict(PROBLEMS, long_rows=_long_and_empty_rows())
 
 
+@pytest.mark.parametrize("tune", [2, 3])
 @pytest.mark.parametrize("name", list(STAGED))
-def test_staged_schedule_matches_oracle(pkg, name):
+def test_staged_schedule_matches_oracle(pkg, name, tune):
     """autotune = 2 runs every CSR pass in the staged chunk form (the block streams a chunk's
-    entries in windows, then each thread sums its own row): same products and iterates."""
+    entries in windows, then each thread sums its own row); autotune = 3 runs the A and A^T
+    passes from their SELL-32 copies (one row per lane, rows sorted by length inside each
+    256-row chunk): same products and iterates."""
     qp = STAGED[name]
     rng = np.random.default_rng(1)
     K = 50
     ref = oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K)
-    with pkg.Solver(qp, autotune=2, lambda_A=ref.lambda_A if qp.m else 0.0, lambda_Q=ref.lambda_Q) as s:
+    with pkg.Solver(qp, autotune=tune, lambda_A=ref.lambda_A if qp.m else 0.0, lambda_Q=ref.lambda_Q) as s:
         v = rng.standard_normal(qp.n)
         assert rel(s.apply("Q", v), oracle.qmul(qp, v)) <= 1e-13
         if qp.m:
