@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hprqp.h"
@@ -281,9 +282,9 @@ static hprqp_status build_sell(hprqp_handle* h, SellTiles& S, const HostCsr& M) 
 
 // Tiled copies of a factor term B (p x n) for the shared-memory products of tiled.cu: B tiled
 // over its columns (the entries of x), B^T over its columns (the entries of t = B x).
-static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, int sms) {
+static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, const HostCsr& BT, int sms) {
   hprqp_status st;
-  if ((st = build_sell(h, T.b, B)) || (st = build_sell(h, T.bt, transpose(B)))) return st;
+  if ((st = build_sell(h, T.b, B)) || (st = build_sell(h, T.bt, BT))) return st;
   T.p = B.rows;
   const int64_t nwin = (T.b.nsl + kSellWin / kSellC - 1) / (kSellWin / kSellC);
   // one wave of (tile, window range) blocks at one block per SM
@@ -292,51 +293,68 @@ static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, 
 }
 
 // SELL-32 copy of M for the row passes (sorting windows = the 256-row chunks of the row
-// kernels, so a chunk's slices hold exactly its rows): d.soff, d.sperm, d.sci, d.sv.
-static hprqp_status build_sell_rows(hprqp_handle* h, Csr& d, const HostCsr& M) {
+// kernels, so a chunk's slices hold exactly its rows): host arrays, then the upload.
+struct SellRows {
+  std::vector<int> off, perm, ci;
+  std::vector<double> v;
+  bool too_big = false;
+};
+static SellRows make_sell_rows(const HostCsr& M) {
+  SellRows S;
   const int64_t rows = M.rows, nsl = (rows + 31) / 32;
-  std::vector<int> off((size_t)nsl + 1), perm((size_t)nsl * 32, -1), slot((size_t)std::max<int64_t>(rows, 1));
-  std::vector<int> order;
+  S.off.assign((size_t)nsl + 1, 0);
+  S.perm.assign((size_t)nsl * 32, -1);
+  std::vector<int> slot((size_t)std::max<int64_t>(rows, 1)), order, cnt;
   int64_t tot = 0;
   for (int64_t r0 = 0; r0 < rows; r0 += kChunk) {
-    const int64_t cnt = std::min<int64_t>(kChunk, rows - r0);
-    order.resize((size_t)cnt);
-    for (int64_t i = 0; i < cnt; i++) order[(size_t)i] = (int)(r0 + i);
-    auto len = [&](int r) { return M.rp[r + 1] - M.rp[r]; };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return len(x) > len(y); });
-    for (int64_t i = 0; i < cnt; i += 32) {
+    const int64_t nr = std::min<int64_t>(kChunk, rows - r0);
+    // rows of the window by decreasing length, ties in row order (counting sort)
+    int lmax = 0;
+    for (int64_t r = r0; r < r0 + nr; r++) lmax = std::max(lmax, M.rp[r + 1] - M.rp[r]);
+    cnt.assign((size_t)lmax + 2, 0);
+    for (int64_t r = r0; r < r0 + nr; r++) cnt[(size_t)(lmax - (M.rp[r + 1] - M.rp[r])) + 1]++;
+    for (int l = 0; l <= lmax; l++) cnt[(size_t)l + 1] += cnt[(size_t)l];
+    order.assign((size_t)nr, 0);
+    for (int64_t r = r0; r < r0 + nr; r++) order[(size_t)cnt[(size_t)(lmax - (M.rp[r + 1] - M.rp[r]))]++] = (int)r;
+    for (int64_t i = 0; i < nr; i += 32) {
       const int64_t sl = (r0 + i) / 32;
       int width = 0;
-      for (int l = 0; l < 32 && i + l < cnt; l++) {
+      for (int l = 0; l < 32 && i + l < nr; l++) {
         const int r = order[(size_t)(i + l)];
-        perm[(size_t)sl * 32 + l] = r;
+        S.perm[(size_t)sl * 32 + l] = r;
         slot[(size_t)r] = (int)(sl * 32 + l);
-        width = std::max(width, len(r));
+        width = std::max(width, M.rp[r + 1] - M.rp[r]);
       }
-      off[(size_t)sl] = (int)tot;
+      S.off[(size_t)sl] = (int)tot;
       tot += (int64_t)width * 32;
-      if (tot >= ((int64_t)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "SELL copy: too many entries");
+      if (tot >= ((int64_t)1 << 31)) {
+        S.too_big = true;
+        return S;
+      }
     }
   }
-  off[(size_t)nsl] = (int)tot;
-  std::vector<int> ci((size_t)std::max<int64_t>(tot, 1), 0);
-  std::vector<double> v((size_t)std::max<int64_t>(tot, 1), 0.0);
+  S.off[(size_t)nsl] = (int)tot;
+  S.ci.assign((size_t)std::max<int64_t>(tot, 1), 0);
+  S.v.assign((size_t)std::max<int64_t>(tot, 1), 0.0);
   for (int64_t r = 0; r < rows; r++) {
     const int sp = slot[(size_t)r];
-    const size_t base = (size_t)off[(size_t)(sp / 32)] + (size_t)(sp % 32);
+    const size_t base = (size_t)S.off[(size_t)(sp / 32)] + (size_t)(sp % 32);
     for (int q = M.rp[r]; q < M.rp[r + 1]; q++) {
       const size_t pos = base + (size_t)(q - M.rp[r]) * 32;
-      ci[pos] = M.ci[q];
-      v[pos] = M.v[q];
+      S.ci[pos] = M.ci[q];
+      S.v[pos] = M.v[q];
     }
   }
+  return S;
+}
+static hprqp_status upload_sell_rows(hprqp_handle* h, Csr& d, const SellRows& S) {
+  if (S.too_big) return fail(h, HPRQP_INVALID_ARG, "SELL copy: too many entries");
   hprqp_status st;
   int *doff, *dperm, *dci;
   double* dv;
-  if ((st = upload(h, &doff, off)) || (st = upload(h, &dperm, perm)) || (st = upload(h, &dci, ci)) ||
-      (st = upload(h, &dv, v)))
+  if ((st = upload(h, &doff, S.off)) || (st = upload(h, &dperm, S.perm)) || (st = upload(h, &dci, S.ci)) ||
+      (st = upload(h, &dv, S.v)))
     return st;
-  CU(h, cudaStreamSynchronize(h->stream));   // the host vectors are released on return
   d.soff = doff;
   d.sperm = dperm;
   d.sci = dci;
@@ -784,8 +802,12 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     if ((st = upload_csr(h, a.AT, AT))) return st;
     // SELL copies for the autotuner's choice (not for the persistent mode, which keeps lanes)
     if (h->prm.launch_mode != 3 && h->prm.autotune != 0) {
-      if ((st = build_sell_rows(h, a.A, A))) return st;
-      if ((st = build_sell_rows(h, a.AT, AT))) return st;
+      SellRows sa, sat;
+      std::thread worker([&] { sa = make_sell_rows(A); });   // the two copies in parallel
+      sat = make_sell_rows(AT);
+      worker.join();
+      if ((st = upload_sell_rows(h, a.A, sa)) || (st = upload_sell_rows(h, a.AT, sat))) return st;
+      CU(h, cudaStreamSynchronize(h->stream));   // the host arrays are released below
     }
   } else {
     a.A.cols = n;
@@ -815,9 +837,11 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   int64_t toff = 0;
   QD.nfac = (int)facs.size();
+  std::vector<HostCsr> facts((size_t)QD.nfac);   // the transposes, kept for the tiled copies
   for (int f = 0; f < QD.nfac; f++) {
     if ((st = upload_csr(h, QD.fac[f], facs[f]))) return st;
-    HostCsr BT = transpose(facs[f]);
+    facts[f] = transpose(facs[f]);
+    const HostCsr& BT = facts[f];
     if ((st = upload_csr(h, QD.fact[f], BT))) return st;
     QD.toff[f] = toff;
     toff += facs[f].rows;
@@ -862,7 +886,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
       const bool fits = room && h->prm.launch_mode != 3 && kt <= 8 && kb * B.rows <= ((int64_t)1 << 28);
       const bool large = nnz >= 2000000 && nnz >= 8 * std::max<int64_t>(n, B.rows);
       if (!fits || !(h->prm.tiled_factor == 2 || (h->prm.tiled_factor == 1 && large))) continue;
-      if ((st = build_tiled(h, QD.tf[f], B, tsms))) return st;
+      if ((st = build_tiled(h, QD.tf[f], B, facts[f], tsms))) return st;
       QD.tiled[f] = 1;
       QD.uoff[f] = toff;
       toff += n;
