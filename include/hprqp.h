@@ -242,8 +242,9 @@ hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* in, double* 
 /* Runs `iters` (>= 1) inner steps of Algorithm 4 from the starting point, with lambda_A,
  * lambda_Q and sigma0 of the last hprqp_solve, as individual launches on the handle's stream
  * bracketed by CUDA events, and writes the mean duration (milliseconds) of each kernel kind
- * into ms[HPRQP_PROF_KINDS] (0 for kinds the problem does not use; the restart kinds are
- * averaged over the steps that restarted).  The iterate is left in an unspecified state:
+ * into ms[HPRQP_PROF_KINDS]: the step kinds over the plain steps (the steps with the R~ or the
+ * stopping test carry extra sums; over all steps when none was plain), the restart kinds
+ * over the steps that restarted, 0 for kinds the problem does not use.  The iterate is left in an unspecified state:
  * call hprqp_solve again before hprqp_get.  Requires a previous hprqp_solve. */
 hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms);
 

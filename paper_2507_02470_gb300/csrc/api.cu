@@ -222,14 +222,19 @@ static hprqp_status build_sell(hprqp_handle* h, SellTiles& S, const HostCsr& M) 
   std::vector<int> perm((size_t)nt * (size_t)nsl * kSellC, -1);
   std::vector<int> slot((size_t)nt * (size_t)rows);   // slice * 32 + lane of (tile, row)
   int64_t tot = 0;
-  std::vector<int> order;
+  std::vector<int> order, bucket;
   for (int k = 0; k < nt; k++) {
     const int* lk = len.data() + (size_t)k * (size_t)rows;
     for (int64_t r0 = 0; r0 < rows; r0 += kSellWin) {
       const int64_t cnt = std::min<int64_t>(kSellWin, rows - r0);
-      order.resize((size_t)cnt);
-      for (int64_t i = 0; i < cnt; i++) order[(size_t)i] = (int)(r0 + i);
-      std::stable_sort(order.begin(), order.end(), [lk](int x, int y) { return lk[x] > lk[y]; });
+      // rows of the window by decreasing entry count in the tile, ties in row order
+      int lmax = 0;
+      for (int64_t r = r0; r < r0 + cnt; r++) lmax = std::max(lmax, lk[r]);
+      bucket.assign((size_t)lmax + 2, 0);
+      for (int64_t r = r0; r < r0 + cnt; r++) bucket[(size_t)(lmax - lk[r]) + 1]++;
+      for (int l = 0; l <= lmax; l++) bucket[(size_t)l + 1] += bucket[(size_t)l];
+      order.assign((size_t)cnt, 0);
+      for (int64_t r = r0; r < r0 + cnt; r++) order[(size_t)bucket[(size_t)(lmax - lk[r])]++] = (int)r;
       for (int64_t i = 0; i < cnt; i += kSellC) {
         const int64_t sl = (r0 + i) / kSellC;
         int width = 0;
@@ -1767,6 +1772,8 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
   }
   double tot[HPRQP_PROF_KINDS] = {0};
   int cnt[HPRQP_PROF_KINDS] = {0};
+  double tot_all[HPRQP_PROF_KINDS] = {0};
+  int cnt_all[HPRQP_PROF_KINDS] = {0};
   cudaError_t err = cudaSuccess;
   Ctrl& C = *h->hctrl;
   for (int32_t i = 0; i < iters && err == cudaSuccess; i++) {
@@ -1790,8 +1797,15 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
     for (int k = 0; k < HPRQP_PROF_KINDS && err == cudaSuccess; k++) {
       float t = 0.f;
       if (cudaEventElapsedTime(&t, ev[k][0], ev[k][1]) == cudaSuccess) {
-        tot[k] += t;
-        cnt[k]++;
+        // step kernels: plain steps (the R~ and stopping-test variants carry extra sums);
+        // every step's times are kept for a run without a plain step
+        const bool plain_kind = k < HPRQP_PROF_RPRE;
+        if (!plain_kind || var == 0) {
+          tot[k] += t;
+          cnt[k]++;
+        }
+        tot_all[k] += t;
+        cnt_all[k]++;
       } else {
         cudaGetLastError();
       }
@@ -1802,7 +1816,8 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
     cudaEventDestroy(e[1]);
   }
   if (err != cudaSuccess) return fail(h, HPRQP_CUDA_ERROR, "profile: %s", cudaGetErrorString(err));
-  for (int k = 0; k < HPRQP_PROF_KINDS; k++) ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
+  for (int k = 0; k < HPRQP_PROF_KINDS; k++)
+    ms[k] = cnt[k] ? tot[k] / cnt[k] : cnt_all[k] ? tot_all[k] / cnt_all[k] : 0.0;
   h->solved = false;  // the iterate no longer belongs to a solve
   return HPRQP_OK;
 }
