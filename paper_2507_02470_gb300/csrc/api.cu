@@ -45,6 +45,7 @@ struct hprqp_handle {
   cudaGraphExec_t g_iter = nullptr;
   cudaGraphExec_t g_fixed = nullptr;   // fixed-schedule graph of fixed_L steps (conditional mode)
   int fixed_L = 0;
+  bool fixed_tried = false;
   cudaGraphExec_t g_pw[2] = {nullptr, nullptr};
   int pw_chunk = 16;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -998,7 +999,9 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     for (int f = 0; f < QD.nfac; f++)
       if (!big || QD.fact[f].nnz > big->nnz) big = &QD.fact[f];
     P.gQ = big ? tune_G(h, *big, P.gridN, ain, aout, 1) : 1;
-    if (QD.nfac > 0 && h->prm.autotune == 1) {
+    bool untiled = false;   // the probe below runs the one-vector pre-pass, which skips tiled terms
+    for (int f = 0; f < QD.nfac; f++) untiled = untiled || !QD.tiled[f];
+    if (QD.nfac > 0 && h->prm.autotune == 1 && untiled) {
       // lanes per factor row of the pre-pass, timed on the pre-pass itself
       float best = 1e30f;
       for (int G : {1, 4, 8, 32}) {
@@ -1137,6 +1140,13 @@ extern "C" hprqp_status hprqp_set_lambda(hprqp_handle* h, double lambda_A, doubl
 // R~-test and stopping-test periods, at most 1024 steps; left out when larger or when the
 // driver rejects it (the dynamic graph then runs every step).
 static void build_fixed(hprqp_handle* h) {
+  if (h->fixed_tried) return;
+  h->fixed_tried = true;
+  if (h->prm.launch_mode != 0 || !h->prm.fixed_schedule) return;
+  if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
   const int64_t ce = h->prm.check_every, re = h->prm.restart_off ? ce : h->prm.restart_every;
   int64_t a = re, b = ce;
   while (b) {
@@ -1146,19 +1156,27 @@ static void build_fixed(hprqp_handle* h) {
   }
   const int64_t L = re / a * ce;
   if (L > 1024) return;
-  cudaGraph_t g;
-  if (build_fixed_graph(h->args, h->plan, h->stream, h->side, (int)L, (int)re, (int)ce, &g) != cudaSuccess) {
-    cudaGetLastError();
+  // with programmatic launches first; without them if the driver rejects that graph
+  for (int attempt = 0; attempt < 2; attempt++) {
+    if (attempt == 1 && !h->prm.pdl) break;
+    h->plan.pdl = attempt == 0 && h->prm.pdl ? 1 : 0;
+    cudaGraph_t g;
+    if (build_fixed_graph(h->args, h->plan, h->stream, h->side, (int)L, (int)re, (int)ce, &g) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaError_t ie = cudaGraphInstantiate(&h->g_fixed, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      h->g_fixed = nullptr;
+      continue;
+    }
+    h->fixed_L = (int)L;
+    h->conditional = true;   // conditional nodes work on this device
     return;
   }
-  cudaError_t ie = cudaGraphInstantiate(&h->g_fixed, g, 0);
-  cudaGraphDestroy(g);
-  if (ie != cudaSuccess) {
-    cudaGetLastError();
-    h->g_fixed = nullptr;
-    return;
-  }
-  h->fixed_L = (int)L;
+  h->plan.pdl = 0;
 }
 
 static hprqp_status build_iter_graph(hprqp_handle* h) {
@@ -1176,7 +1194,6 @@ static hprqp_status build_iter_graph(hprqp_handle* h) {
       cudaGraphDestroy(g);
       if (ie == cudaSuccess) {
         h->conditional = true;
-        if (h->prm.fixed_schedule) build_fixed(h);
         return HPRQP_OK;
       }
       h->g_iter = nullptr;
@@ -1641,9 +1658,9 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   Range rg("hprqp_iterate");
   if (h->prm.launch_mode == 2) return solve_stream(h, t0, t1, lamA, lamQ, sigma);
   if (h->prm.launch_mode == 3) return solve_persist(h, t0, t1, lamA, lamQ, sigma);
-  if ((st = build_iter_graph(h))) return st;
   bool time_up = false;
   // ---- Algorithm 4 in launches of the fixed-schedule graph while fixed_L steps remain
+  build_fixed(h);
   int64_t k0 = 0;
   if (h->g_fixed && max_iter >= h->fixed_L) {
     for (; max_iter - k0 >= h->fixed_L; k0 += h->fixed_L) {
@@ -1660,8 +1677,9 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
     CU(h, launch_restart(a, h->plan, h->stream));
     h->launches += kernels_per_restart(a);
   }
-  // ---- the rest in launches of the dynamic graph (iters_per_launch steps); double-buffered
-  // done poll
+  // ---- the rest in launches of the dynamic graph (iters_per_launch steps, built when first
+  // needed); double-buffered done poll
+  if ((st = build_iter_graph(h))) return st;
   const int64_t per = h->prm.iters_per_launch;
   const int64_t max_launch = (max_iter - k0 + per - 1) / per + 2;
   const int64_t nodes = h->conditional ? 1 : per * kernels_per_iteration(a);
