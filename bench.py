@@ -421,12 +421,16 @@ STEP_SOURCES = ("core.cuh", "solver.cuh", "kernels.cuh", "solver.cu", "rows_q.cu
 
 
 def source_sha():
-    """Hash of the sources of the step kernels (a change to them voids recorded traffic)."""
+    """Hash of the sources of the step kernels, without their // comments and blank lines (a
+    change to the code voids recorded traffic; a change to a comment does not)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2507_02470_gb300", "csrc")
     for f in STEP_SOURCES:
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

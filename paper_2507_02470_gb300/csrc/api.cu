@@ -2,9 +2,9 @@
 //
 // Host responsibilities: validate and copy the problem (host or device inputs), build the
 // stored transposes A^T and B_f^T (counting sort by column, so the row order inside each
-// transposed row is fixed), pick the SpMV schedule, run the power method of Sec. 4.1, and
-// drive Algorithm 4 as a CUDA graph of `iters_per_launch` inner steps whose kernels stop
-// themselves once the device-side controller has set the done flag.
+// transposed row is fixed), build the SELL and tiled copies, pick the SpMV schedule, run the
+// power method of Sec. 4.1, and drive Algorithm 4 through CUDA graphs (solver.cu) whose kernels
+// stop themselves once the device-side controller has set the done flag.
 #include <cublas_v2.h>
 #include <nvtx3/nvToolsExt.h>
 

@@ -1,11 +1,16 @@
-// Launch sequences of the single-instance HPR-QP solver and the CUDA graph that runs them.
+// Launch sequences of the single-instance HPR-QP solver and the CUDA graphs that run them.
 //
-// Graph layout (one launch = iters_per_launch inner steps of Algorithm 4):
+// Fixed-schedule graph (one launch = L inner steps, L = lcm(restart_every, check_every)):
+//   dispatch -> step 1 -> ... -> step L, the variant of each step fixed by its position (R~
+// test at multiples of restart_every, stopping test at multiples of check_every); the step
+// after each R~ test is a SWITCH node (scheduled step / step with R~_{r,0} after a restart
+// without sigma update / restart pass of Algorithm 5 then that step / nothing once done).
+// Dynamic graph (one launch = iters_per_launch steps, for the iterations after the last whole
+// period):
 //   dispatch -> [SWITCH step 0] -> [IF restart 0] -> [SWITCH step 1] -> [IF restart 1] -> ...
-// Each SWITCH node has four bodies: a plain step, a step that evaluates R~ (restart test,
-// Sec. 3.2), a step that evaluates the stopping rule (Sec. 4.1), and an empty body taken once
-// the solve is done.  The controller in the last block of every step sets the value of its own
-// restart IF node and of the next SWITCH node with cudaGraphSetConditional, so the host only
+// each SWITCH with four bodies: plain step, step with the R~ test (Sec. 3.2), step with the
+// stopping rule (Sec. 4.1), empty once done.  In both, the controller in the last block of
+// every step sets the next conditional node with cudaGraphSetConditional, so the host only
 // polls a done flag between launches.
 #include <cublas_v2.h>
 
