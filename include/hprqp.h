@@ -116,7 +116,7 @@ typedef struct hprqp_params {
                                 form for every CSR pass; 3: the SELL-32 copy for the A and
                                 A^T passes (rows sorted by length inside each 256-row chunk,
                                 one row per lane), one lane per row elsewhere */
-  int32_t verbose;           /* 0: silent */
+  int32_t verbose;           /* 0: silent; 2: wall time of each phase of hprqp_create on stderr */
   hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
   hprqp_free_fn free;
   void* alloc_ctx;

@@ -583,10 +583,25 @@ static void scale_data(hprqp_handle* h, std::vector<double>& hc, std::vector<dou
   h->nc2 = nc2;
 }
 
+// verbose >= 2: wall time of each phase of hprqp_create on stderr (device work synchronised)
+struct PhaseClock {
+  hprqp_handle* h;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void mark(const char* name) {
+    if (h->prm.verbose < 2) return;
+    cudaStreamSynchronize(h->stream);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "hprqp_create: %-16s %8.2f ms\n", name,
+                 std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hprqp_qop* Q, const int32_t* A_rowptr,
                                 const int32_t* A_colidx, const double* A_vals, const double* c, const double* l,
                                 const double* u, const double* L, const double* U, int32_t phi, double lambda) {
   hprqp_status st;
+  PhaseClock clk{h};
   if (n <= 0 || m < 0) return fail(h, HPRQP_INVALID_ARG, "need n > 0 and m >= 0 (n=%lld, m=%lld)", (long long)n, (long long)m);
   if (n >= (int64_t)1 << 31 || m >= (int64_t)1 << 31) return fail(h, HPRQP_INVALID_ARG, "n and m must be < 2^31");
   if (phi < 0 || phi > 2) return fail(h, HPRQP_INVALID_ARG, "unknown phi kind %d", phi);
@@ -623,6 +638,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   if ((st = data_norms(h, hc, hl, hu))) return st;
 
+  clk.mark("vectors");
   // ---- A
   HostCsr A;
   A.rows = m;
@@ -636,6 +652,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     if ((st = check_csr(h, A, "A"))) return st;
   }
 
+  clk.mark("A");
   // ---- Q terms
   std::vector<double> qdiag;
   HostCsr qcsr;
@@ -744,6 +761,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
         }
   }
 
+  clk.mark("Q terms");
   // ---- preconditioning (Sec. 4.1: only when Q is explicit; the box-only phi keeps the
   // prox a plain clip in the scaled variables).  b_inf, c_inf of the stopping test stay those
   // of the original data; the sigma0 norms become those of the scaled data.
@@ -767,6 +785,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     scale_data(h, hc, hl, hu);
   }
 
+  clk.mark("preconditioning");
   // ---- device problem
   Args& a = h->args;
   std::memset(&a, 0, sizeof(a));
@@ -876,6 +895,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     toff += n;
     if ((st = blas_init(h))) return st;
   }
+  clk.mark("device problem");
   // ---- tiled copies of large factor terms: their one-vector products gather through shared
   // memory (tiled.cu); u = B_f^T B_f x goes to the intermediate buffers at uoff
   {
@@ -902,6 +922,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   QD.tlen = toff;
 
+  clk.mark("tiled copies");
   // ---- work vectors (all n- and m-vectors exist; unused ones stay zero)
   double** nvecs[] = {&V.x, &V.w, &V.Qw, &V.ATy, &V.x0, &V.w0, &V.Qw0, &V.ATy0, &V.xb, &V.wb, &V.Qwb, &V.ATyb,
                       &V.wh, &V.Qwh, &V.v, &V.zb, &V.Qxb};
@@ -923,6 +944,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   V.ain = ain;
   V.aout = aout;
 
+  clk.mark("work vectors");
   // ---- launch plan
   int dev = 0, sms = 0;
   CU(h, cudaGetDevice(&dev));
@@ -989,6 +1011,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   CU(h, cudaEventCreate(&h->ev[1]));
   CU(h, cudaStreamSynchronize(h->stream));
 
+  clk.mark("launch plan");
   // ---- schedule autotune (lanes per row for each CSR pass)
   {
     CU(h, cudaMemsetAsync(ain, 0, nm * sizeof(double), h->stream));
@@ -1024,6 +1047,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     CU(h, cudaGetLastError());
     CU(h, plan_plain_grids(a, P, sms));
   }
+  clk.mark("autotune");
   return HPRQP_OK;
 }
 
