@@ -16,11 +16,11 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/hprqp.h"
 #include "../../include/hprqp_learn.h"
+#include "sell_build.cuh"
 #include "solver.cuh"
 
 using namespace hprqp;
@@ -298,73 +298,31 @@ static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, 
   return zeros(h, &T.part, (size_t)T.b.ntile * (size_t)B.rows);
 }
 
-// SELL-32 copy of M for the row passes (sorting windows = the 256-row chunks of the row
-// kernels, so a chunk's slices hold exactly its rows): host arrays, then the upload.
-struct SellRows {
-  std::vector<int> off, perm, ci;
-  std::vector<double> v;
-  bool too_big = false;
-};
-static SellRows make_sell_rows(const HostCsr& M) {
-  SellRows S;
-  const int64_t rows = M.rows, nsl = (rows + 31) / 32;
-  S.off.assign((size_t)nsl + 1, 0);
-  S.perm.assign((size_t)nsl * 32, -1);
-  std::vector<int> slot((size_t)std::max<int64_t>(rows, 1)), order, cnt;
-  int64_t tot = 0;
-  for (int64_t r0 = 0; r0 < rows; r0 += kChunk) {
-    const int64_t nr = std::min<int64_t>(kChunk, rows - r0);
-    // rows of the window by decreasing length, ties in row order (counting sort)
-    int lmax = 0;
-    for (int64_t r = r0; r < r0 + nr; r++) lmax = std::max(lmax, M.rp[r + 1] - M.rp[r]);
-    cnt.assign((size_t)lmax + 2, 0);
-    for (int64_t r = r0; r < r0 + nr; r++) cnt[(size_t)(lmax - (M.rp[r + 1] - M.rp[r])) + 1]++;
-    for (int l = 0; l <= lmax; l++) cnt[(size_t)l + 1] += cnt[(size_t)l];
-    order.assign((size_t)nr, 0);
-    for (int64_t r = r0; r < r0 + nr; r++) order[(size_t)cnt[(size_t)(lmax - (M.rp[r + 1] - M.rp[r]))]++] = (int)r;
-    for (int64_t i = 0; i < nr; i += 32) {
-      const int64_t sl = (r0 + i) / 32;
-      int width = 0;
-      for (int l = 0; l < 32 && i + l < nr; l++) {
-        const int r = order[(size_t)(i + l)];
-        S.perm[(size_t)sl * 32 + l] = r;
-        slot[(size_t)r] = (int)(sl * 32 + l);
-        width = std::max(width, M.rp[r + 1] - M.rp[r]);
-      }
-      S.off[(size_t)sl] = (int)tot;
-      tot += (int64_t)width * 32;
-      if (tot >= ((int64_t)1 << 31)) {
-        S.too_big = true;
-        return S;
-      }
-    }
-  }
-  S.off[(size_t)nsl] = (int)tot;
-  S.ci.assign((size_t)std::max<int64_t>(tot, 1), 0);
-  S.v.assign((size_t)std::max<int64_t>(tot, 1), 0.0);
-  for (int64_t r = 0; r < rows; r++) {
-    const int sp = slot[(size_t)r];
-    const size_t base = (size_t)S.off[(size_t)(sp / 32)] + (size_t)(sp % 32);
-    for (int q = M.rp[r]; q < M.rp[r + 1]; q++) {
-      const size_t pos = base + (size_t)(q - M.rp[r]) * 32;
-      S.ci[pos] = M.ci[q];
-      S.v[pos] = M.v[q];
-    }
-  }
-  return S;
-}
-static hprqp_status upload_sell_rows(hprqp_handle* h, Csr& d, const SellRows& S) {
-  if (S.too_big) return fail(h, HPRQP_INVALID_ARG, "SELL copy: too many entries");
+// SELL-32 copy of a device CSR matrix for the row passes, built on the device (sorting
+// windows = the 256-row chunks of the row kernels, so a chunk's slices hold exactly its rows).
+static hprqp_status build_sell_rows(hprqp_handle* h, Csr& d) {
+  const int64_t nsl = (d.rows + 31) / 32;
   hprqp_status st;
-  int *doff, *dperm, *dci;
-  double* dv;
-  if ((st = upload(h, &doff, S.off)) || (st = upload(h, &dperm, S.perm)) || (st = upload(h, &dci, S.ci)) ||
-      (st = upload(h, &dv, S.v)))
+  void *perm, *width, *off, *total;
+  if ((st = dalloc(h, &perm, (size_t)nsl * 32 * sizeof(int))) || (st = dalloc(h, &width, (size_t)nsl * sizeof(int))) ||
+      (st = dalloc(h, &off, (size_t)(nsl + 1) * sizeof(int))) || (st = dalloc(h, &total, sizeof(long long))))
     return st;
-  d.soff = doff;
-  d.sperm = dperm;
-  d.sci = dci;
-  d.sv = dv;
+  CU(h, sell_layout(d, (int*)perm, (int*)width, (int*)off, (long long*)total, h->stream));
+  long long tot = 0;
+  CU(h, cudaMemcpyAsync(&tot, total, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (tot < 0 || tot >= ((long long)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "SELL copy: too many entries");
+  void *sci, *sv;
+  if ((st = dalloc(h, &sci, (size_t)std::max<long long>(tot, 1) * sizeof(int))) ||
+      (st = dalloc(h, &sv, (size_t)std::max<long long>(tot, 1) * sizeof(double))))
+    return st;
+  CU(h, cudaMemsetAsync(sci, 0, (size_t)std::max<long long>(tot, 1) * sizeof(int), h->stream));
+  CU(h, cudaMemsetAsync(sv, 0, (size_t)std::max<long long>(tot, 1) * sizeof(double), h->stream));
+  CU(h, sell_fill(d, (const int*)perm, (const int*)off, (int*)sci, (double*)sv, h->stream));
+  d.soff = (const int*)off;
+  d.sperm = (const int*)perm;
+  d.sci = (const int*)sci;
+  d.sv = (const double*)sv;
   return HPRQP_OK;
 }
 
@@ -827,12 +785,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     if ((st = upload_csr(h, a.AT, AT))) return st;
     // SELL copies for the autotuner's choice (not for the persistent mode, which keeps lanes)
     if (h->prm.launch_mode != 3 && h->prm.autotune != 0) {
-      SellRows sa, sat;
-      std::thread worker([&] { sa = make_sell_rows(A); });   // the two copies in parallel
-      sat = make_sell_rows(AT);
-      worker.join();
-      if ((st = upload_sell_rows(h, a.A, sa)) || (st = upload_sell_rows(h, a.AT, sat))) return st;
-      CU(h, cudaStreamSynchronize(h->stream));   // the host arrays are released below
+      if ((st = build_sell_rows(h, a.A)) || (st = build_sell_rows(h, a.AT))) return st;
     }
   } else {
     a.A.cols = n;

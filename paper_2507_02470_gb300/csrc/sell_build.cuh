@@ -1,0 +1,13 @@
+// Device-side construction of the SELL-32 copies used by the row kernels (sell_build.cu).
+#pragma once
+#include "core.cuh"
+
+namespace hprqp {
+
+// SELL-32 copy of a device CSR matrix (the layout of the row kernels' SELL schedule):
+// sell_layout fills perm (slices*32 ints), width (slices), off (slices+1) and *total (the
+// entry count); sell_fill then writes the entries into zeroed sci / sv of *total each
+cudaError_t sell_layout(const Csr& M, int* perm, int* width, int* off, long long* total, cudaStream_t s);
+cudaError_t sell_fill(const Csr& M, const int* perm, const int* off, int* sci, double* sv, cudaStream_t s);
+
+}  // namespace hprqp
