@@ -354,9 +354,9 @@ def algorithmic(qp, tiled=False):
             if t.kind != "factor":
                 continue
             nnz, kb, kt = int(t.rowptr[-1]), -(-n // TILE_W), -(-t.p // TILE_W)
-            # B x and B^T t at 10 B per entry, x once, kb partial rows written and read, t,
-            # u written once per tile of t and read back for every tile after the first
-            pre_bytes += 20 * nnz + 8 * n + 16 * kb * t.p + 8 * t.p + 8 * n * (2 * kt - 1)
+            # B x and B^T t at 10 B per entry, kb partial rows written and read, t, u written
+            # once per tile of t and read back for every tile after the first (x: below)
+            pre_bytes += 20 * nnz + 16 * kb * t.p + 8 * t.p + 8 * n * (2 * kt - 1)
             pre_flops += 2 * nnz + kb * t.p + (kt - 1) * n
     HA = m > 0
     zx_vec = (15 if HA else 11) if qp.qterms else 8

@@ -1,0 +1,50 @@
+"""Host-side pieces of bench.py (no GPU): the algorithmic byte / FP64 counts behind the
+roofline, and the source hash that keeps a recorded DRAM-traffic table tied to the kernel
+code it was measured on."""
+import os
+import shutil
+
+import numpy as np
+
+import bench
+import qpgen
+
+
+def test_tiled_factor_counts():
+    """Lasso-like problem (no A, Q = B^T B): the tiled pre-pass group reads B and B^T at 10 B
+    per entry, x once, the kb partial rows twice (written and read), t, and u once per tile of
+    t plus its re-reads; FP64: two FMAs per entry, the partial sums and the tile updates of u."""
+    qp = qpgen.lasso(p=30_000, q=60_000, density=5e-4, seed=2)
+    n = qp.n
+    t = [q for q in qp.qterms if q.kind == "factor"][0]
+    nnz, p = int(t.rowptr[-1]), t.p
+    kb, kt = -(-n // 25600), -(-p // 25600)
+    assert (kb, kt) == (3, 2)
+    b, f = bench.algorithmic(qp, tiled=True)["pre1"]
+    assert b == 20 * nnz + 8 * n + 16 * kb * p + 8 * p + 8 * n * (2 * kt - 1)
+    assert f == 2 * nnz + kb * p + (kt - 1) * n
+    # the row pass then only adds u; untiled it carries the B^T pass
+    bq, fq = bench.algorithmic(qp, tiled=True)["q1"]
+    bu, fu = bench.algorithmic(qp, tiled=False)["q1"]
+    assert bu - bq == 12 * nnz + 4 * n - 8 * n and fu - fq == nnz
+
+
+def test_zx_counts_match_the_eighteen_operations_per_coordinate():
+    qp = qpgen.large_cqp(n=10_000, m=5_000, seed=0)
+    b, f = bench.algorithmic(qp)["zx"]
+    assert f == 18 * qp.n and b == 8 * qp.n * (15 + 6)
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    src = os.path.join(bench.ROOT, "paper_2507_02470_gb300", "csrc")
+    dst = tmp_path / "paper_2507_02470_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.STEP_SOURCES:
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.source_sha()
+    k = dst / "kernels.cuh"
+    k.write_text(k.read_text() + "\n// a comment added at the end\n\n")
+    assert bench.source_sha() == h0
+    k.write_text(k.read_text() + "static int added_code = 1;\n")
+    assert bench.source_sha() != h0
