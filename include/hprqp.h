@@ -120,15 +120,19 @@ typedef struct hprqp_params {
   hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
   hprqp_free_fn free;
   void* alloc_ctx;
-  int32_t launch_mode;       /* 0 (default): CUDA graph whose conditional nodes pick each
-                                step's variant on the device; 1: graph without conditional
-                                nodes (variants read at run time inside the kernels);
+  int32_t launch_mode;       /* 0 (default): CUDA graphs with conditional nodes: whole check
+                                periods through a graph whose step variants are fixed by
+                                position (see fixed_schedule), the rest through a graph whose
+                                conditional nodes pick each step's variant on the device;
+                                1: graph without conditional nodes (variants read at run time
+                                inside the kernels);
                                 2: plain stream launches of the same step variants, chosen on
                                 the host after each step (for profilers that cannot follow
                                 conditional graph nodes; one host synchronisation per step);
                                 3: persistent solver, all passes of up to 4096 inner steps in
-                                one cooperative launch with grid barriers between passes (for
-                                small and mid-sized problems, where launch latency dominates) */
+                                one cooperative launch with grid barriers between passes (one
+                                launch per solve segment; slower than mode 0 on every
+                                configuration measured) */
   int32_t scaling;           /* 1 (default): the Sec. 4.1 preconditioning (10 Ruiz passes, then
                                 Pock-Chambolle with alpha = 1, on K = [Q A^T; A 0]) when Q is
                                 explicit (DIAG, CSR and DIA terms only) and phi is the box
