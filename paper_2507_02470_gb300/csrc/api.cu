@@ -286,11 +286,49 @@ static hprqp_status build_sell(hprqp_handle* h, SellTiles& S, const HostCsr& M) 
   return HPRQP_OK;
 }
 
-// Tiled copies of a factor term B (p x n) for the shared-memory products of tiled.cu: B tiled
-// over its columns (the entries of x), B^T over its columns (the entries of t = B x).
-static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, const HostCsr& BT, int sms) {
+// The same copy built on the device from the uploaded CSR matrix d (at most kMaxTilesDevice
+// column tiles); the host build above otherwise.
+static hprqp_status build_sell_dev(hprqp_handle* h, SellTiles& S, const Csr& d, const HostCsr& M) {
+  const int64_t rows = d.rows, nsl = (rows + 31) / 32;
+  const int nt = (int)std::max<int64_t>(1, (d.cols + kTileW - 1) / kTileW);
+  if (nt > kMaxTilesDevice || rows == 0) return build_sell(h, S, M);
   hprqp_status st;
-  if ((st = build_sell(h, T.b, B)) || (st = build_sell(h, T.bt, BT))) return st;
+  void *len, *perm, *slot, *width, *off, *total;
+  if ((st = dalloc(h, &len, (size_t)nt * rows * sizeof(int))) ||
+      (st = dalloc(h, &perm, (size_t)nt * nsl * 32 * sizeof(int))) ||
+      (st = dalloc(h, &slot, (size_t)nt * rows * sizeof(int))) ||
+      (st = dalloc(h, &width, (size_t)nt * nsl * sizeof(int))) ||
+      (st = dalloc(h, &off, (size_t)nt * (nsl + 1) * sizeof(int))) || (st = dalloc(h, &total, sizeof(long long))))
+    return st;
+  CU(h, tile_layout(d, kTileW, nt, (int*)len, (int*)perm, (int*)slot, (int*)width, (int*)off, (long long*)total,
+                    h->stream));
+  long long tot = 0;
+  CU(h, cudaMemcpyAsync(&tot, total, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (tot < 0 || tot >= ((long long)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "tiled factor copy: too many entries");
+  void *col, *val;
+  const size_t cnt = (size_t)std::max<long long>(tot, 1);
+  if ((st = dalloc(h, &col, cnt * sizeof(unsigned short))) || (st = dalloc(h, &val, cnt * sizeof(double)))) return st;
+  CU(h, cudaMemsetAsync(col, 0, cnt * sizeof(unsigned short), h->stream));
+  CU(h, cudaMemsetAsync(val, 0, cnt * sizeof(double), h->stream));
+  CU(h, tile_fill(d, kTileW, nt, (const int*)slot, (const int*)off, (unsigned short*)col, (double*)val, h->stream));
+  S.rows = rows;
+  S.ntile = nt;
+  S.nsl = nsl;
+  S.off = (const int*)off;
+  S.perm = (const int*)perm;
+  S.col = (const unsigned short*)col;
+  S.val = (const double*)val;
+  return HPRQP_OK;
+}
+
+// Tiled copies of a factor term B (p x n) for the shared-memory products of tiled.cu: B tiled
+// over its columns (the entries of x), B^T over its columns (the entries of t = B x); from
+// the device copies dB, dBT of B and B^T.
+static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, const HostCsr& BT, const Csr& dB,
+                                const Csr& dBT, int sms) {
+  hprqp_status st;
+  if ((st = build_sell_dev(h, T.b, dB, B)) || (st = build_sell_dev(h, T.bt, dBT, BT))) return st;
   T.p = B.rows;
   const int64_t nwin = (T.b.nsl + kSellWin / kSellC - 1) / (kSellWin / kSellC);
   // one wave of (tile, window range) blocks at one block per SM
@@ -865,7 +903,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
       const bool fits = room && h->prm.launch_mode != 3 && kt <= 8 && kb * B.rows <= ((int64_t)1 << 28);
       const bool large = nnz >= 2000000 && nnz >= 8 * std::max<int64_t>(n, B.rows);
       if (!fits || !(h->prm.tiled_factor == 2 || (h->prm.tiled_factor == 1 && large))) continue;
-      if ((st = build_tiled(h, QD.tf[f], B, facts[f], tsms))) return st;
+      if ((st = build_tiled(h, QD.tf[f], B, facts[f], QD.fac[f], QD.fact[f], tsms))) return st;
       QD.tiled[f] = 1;
       QD.uoff[f] = toff;
       toff += n;

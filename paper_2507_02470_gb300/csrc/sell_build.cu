@@ -90,4 +90,114 @@ cudaError_t sell_fill(const Csr& M, const int* perm, const int* off, int* sci, d
   return cudaGetLastError();
 }
 
+
+// ---- tiled SELL copies (SellTiles, tiled.cu): per column tile of width W, rows in windows of
+// kSellWin sorted by their entry count in the tile (ties by row), slices of 32, 16-bit
+// tile-local columns.  Same layout as a host build.
+
+// entry count of every (tile, row): len[k * rows + r] (zeroed beforehand)
+__global__ void k_tile_len(const int* __restrict__ rp, const int* __restrict__ ci, int64_t rows, int W,
+                           int* __restrict__ len) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += stride)
+    for (int q = rp[r]; q < rp[r + 1]; q++) len[(int64_t)(ci[q] / W) * rows + r]++;
+}
+
+// block (tile k, window w): rank of each row of the window by decreasing length (ties by
+// row); perm[k][position] = row, slot[k * rows + row] = position, width of each slice
+__global__ void k_tile_rank(const int* __restrict__ len, int64_t rows, int64_t nsl, int nwin,
+                            int* __restrict__ perm, int* __restrict__ slot, int* __restrict__ width) {
+  __shared__ int sl[kSellWin];
+  const int k = blockIdx.x / nwin, w = blockIdx.x % nwin;
+  const int64_t r0 = (int64_t)w * kSellWin;
+  const int cnt = (int)(rows - r0 < kSellWin ? rows - r0 : kSellWin);
+  const int* lk = len + (int64_t)k * rows;
+  for (int t = threadIdx.x; t < kSellWin; t += blockDim.x) sl[t] = t < cnt ? lk[r0 + t] : -1;
+  __syncthreads();
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int L = sl[t];
+    int rank = 0;
+    for (int u = 0; u < cnt; u++) rank += (sl[u] > L) || (sl[u] == L && u < t);
+    const int64_t pos = r0 + rank;
+    perm[(int64_t)k * nsl * 32 + pos] = (int)(r0 + t);
+    slot[(int64_t)k * rows + r0 + t] = (int)pos;
+    if (rank % 32 == 0) width[(int64_t)k * nsl + pos / 32] = L;
+  }
+}
+
+// off[k * (nsl + 1) + s]: entry offset of slice s of tile k, tiles one after the other;
+// off[k * (nsl + 1) + nsl]: the running total after tile k; *total: all entries (one block)
+__global__ void k_tile_scan(const int* __restrict__ width, int ntile, int64_t nsl, int* __restrict__ off,
+                            long long* __restrict__ total) {
+  __shared__ long long part[kThreads];
+  const int64_t all = (int64_t)ntile * nsl;
+  const int t = threadIdx.x;
+  const int64_t per = (all + kThreads - 1) / kThreads;
+  const int64_t b = t * per, e = b + per < all ? b + per : all;
+  long long sum = 0;
+  for (int64_t i = b; i < e; i++) sum += 32LL * width[i];
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    for (int i = 0; i < kThreads; i++) {
+      const long long v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  long long run = part[t];
+  for (int64_t i = b; i < e; i++) {
+    const int64_t k = i / nsl, s = i % nsl;
+    off[k * (nsl + 1) + s] = (int)run;
+    run += 32LL * width[i];
+    if (s == nsl - 1) off[k * (nsl + 1) + nsl] = (int)run;
+  }
+}
+
+// entries of each row into their tile's slice lanes, in row order (col / val zeroed)
+__global__ void k_tile_fill(const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                            int64_t rows, int W, int ntile, int64_t nsl, const int* __restrict__ slot,
+                            const int* __restrict__ off, unsigned short* __restrict__ col,
+                            double* __restrict__ val) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += stride) {
+    int m[kMaxTilesDevice];
+    for (int k = 0; k < ntile; k++) m[k] = 0;
+    for (int q = rp[r]; q < rp[r + 1]; q++) {
+      const int k = ci[q] / W;
+      const int p = slot[(int64_t)k * rows + r];
+      const int64_t pos = (int64_t)off[(int64_t)k * (nsl + 1) + p / 32] + (int64_t)m[k] * 32 + p % 32;
+      col[pos] = (unsigned short)(ci[q] - k * W);
+      val[pos] = v[q];
+      m[k]++;
+    }
+  }
+}
+
+cudaError_t tile_layout(const Csr& M, int W, int ntile, int* len, int* perm, int* slot, int* width, int* off,
+                        long long* total, cudaStream_t s) {
+  const int64_t rows = M.rows, nsl = (rows + 31) / 32;
+  const int nwin = (int)((rows + kSellWin - 1) / kSellWin);
+  cudaError_t e = cudaMemsetAsync(len, 0, (size_t)ntile * rows * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(perm, 0xff, (size_t)ntile * nsl * 32 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(width, 0, (size_t)ntile * nsl * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::min<int64_t>((rows + kThreads - 1) / kThreads, 152 * 8);
+  k_tile_len<<<blocks, kThreads, 0, s>>>(M.rp, M.ci, rows, W, len);
+  k_tile_rank<<<(unsigned)(ntile * nwin), kThreads, 0, s>>>(len, rows, nsl, nwin, perm, slot, width);
+  k_tile_scan<<<1, kThreads, 0, s>>>(width, ntile, nsl, off, total);
+  return cudaGetLastError();
+}
+
+cudaError_t tile_fill(const Csr& M, int W, int ntile, const int* slot, const int* off, unsigned short* col,
+                      double* val, cudaStream_t s) {
+  const int64_t rows = M.rows, nsl = (rows + 31) / 32;
+  const int blocks = (int)std::min<int64_t>((rows + kThreads - 1) / kThreads, 152 * 8);
+  k_tile_fill<<<blocks, kThreads, 0, s>>>(M.rp, M.ci, M.v, rows, W, ntile, nsl, slot, off, col, val);
+  return cudaGetLastError();
+}
+
 }  // namespace hprqp

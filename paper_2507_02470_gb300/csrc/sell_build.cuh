@@ -10,4 +10,14 @@ namespace hprqp {
 cudaError_t sell_layout(const Csr& M, int* perm, int* width, int* off, long long* total, cudaStream_t s);
 cudaError_t sell_fill(const Csr& M, const int* perm, const int* off, int* sci, double* sv, cudaStream_t s);
 
+// Tiled SELL copy (SellTiles) of a device CSR matrix over column tiles of width W (ntile <=
+// kMaxTilesDevice): tile_layout fills len and slot (ntile * rows), perm (ntile * slices * 32),
+// width (ntile * slices), off (ntile * (slices + 1)) and *total; tile_fill then writes the
+// entries into zeroed col / val of *total each.
+constexpr int kMaxTilesDevice = 64;
+cudaError_t tile_layout(const Csr& M, int W, int ntile, int* len, int* perm, int* slot, int* width, int* off,
+                        long long* total, cudaStream_t s);
+cudaError_t tile_fill(const Csr& M, int W, int ntile, const int* slot, const int* off, unsigned short* col,
+                      double* val, cudaStream_t s);
+
 }  // namespace hprqp
