@@ -155,8 +155,9 @@ typedef struct hprqp_params {
   int32_t tiled_factor;      /* factor terms B_f^T B_f: 1 (default) a large factor (>= 2e6
                                 entries, >= 8 per row and column) also gets a copy stored tile
                                 by tile, and the one-vector products B_f x, B_f^T t gather from
-                                shared-memory tiles; 2: every factor that fits; 0: never.  Not
-                                with launch_mode 3.  Sums in another order (rounding only) */
+                                shared-memory tiles; 2: every factor that fits (n up to 64
+                                tiles of 25,600 columns, p up to 8 tiles); 0: never.  Not with
+                                launch_mode 3.  Sums in another order (rounding only) */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */

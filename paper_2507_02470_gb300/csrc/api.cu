@@ -207,91 +207,16 @@ static HostCsr transpose(const HostCsr& M) {
   return T;
 }
 
-// SELL-32-512 copy of M tile by tile over its columns (tile k: columns [k W, (k+1) W),
-// W = kTileW): per tile, rows in windows of 512 sorted by their entry count in the tile
-// (ties by row), slices of 32 rows padded with zero values to the slice's longest row, a
-// row's entries in their order inside the row, column indices relative to the tile.
-static hprqp_status build_sell(hprqp_handle* h, SellTiles& S, const HostCsr& M) {
+// SELL-32-512 copy of the device CSR matrix d tile by tile over its columns (tile k: columns
+// [k W, (k+1) W), W = kTileW, at most kMaxTilesDevice tiles), built on the device: per tile,
+// rows in windows of 512 sorted by their entry count in the tile (ties by row), slices of 32
+// rows padded with zero values to the slice's longest row, a row's entries in their order
+// inside the row, column indices relative to the tile.
+static hprqp_status build_sell_dev(hprqp_handle* h, SellTiles& S, const Csr& d) {
   static_assert(kTileW <= 65536, "tile-local columns must fit 16 bits");
-  const int64_t rows = M.rows, W = kTileW;
-  const int nt = (int)std::max<int64_t>(1, (M.cols + W - 1) / W);
-  const int64_t nsl = (rows + kSellC - 1) / kSellC;
-  std::vector<int> len((size_t)nt * (size_t)rows, 0);
-  for (int64_t r = 0; r < rows; r++)
-    for (int q = M.rp[r]; q < M.rp[r + 1]; q++) len[(size_t)(M.ci[q] / W) * (size_t)rows + (size_t)r]++;
-  std::vector<int> off((size_t)nt * (size_t)(nsl + 1));
-  std::vector<int> perm((size_t)nt * (size_t)nsl * kSellC, -1);
-  std::vector<int> slot((size_t)nt * (size_t)rows);   // slice * 32 + lane of (tile, row)
-  int64_t tot = 0;
-  std::vector<int> order, bucket;
-  for (int k = 0; k < nt; k++) {
-    const int* lk = len.data() + (size_t)k * (size_t)rows;
-    for (int64_t r0 = 0; r0 < rows; r0 += kSellWin) {
-      const int64_t cnt = std::min<int64_t>(kSellWin, rows - r0);
-      // rows of the window by decreasing entry count in the tile, ties in row order
-      int lmax = 0;
-      for (int64_t r = r0; r < r0 + cnt; r++) lmax = std::max(lmax, lk[r]);
-      bucket.assign((size_t)lmax + 2, 0);
-      for (int64_t r = r0; r < r0 + cnt; r++) bucket[(size_t)(lmax - lk[r]) + 1]++;
-      for (int l = 0; l <= lmax; l++) bucket[(size_t)l + 1] += bucket[(size_t)l];
-      order.assign((size_t)cnt, 0);
-      for (int64_t r = r0; r < r0 + cnt; r++) order[(size_t)bucket[(size_t)(lmax - lk[r])]++] = (int)r;
-      for (int64_t i = 0; i < cnt; i += kSellC) {
-        const int64_t sl = (r0 + i) / kSellC;
-        int width = 0;
-        for (int l = 0; l < kSellC && i + l < cnt; l++) {
-          const int r = order[(size_t)(i + l)];
-          perm[((size_t)k * (size_t)nsl + (size_t)sl) * kSellC + l] = r;
-          slot[(size_t)k * (size_t)rows + (size_t)r] = (int)(sl * kSellC + l);
-          width = std::max(width, lk[r]);
-        }
-        off[(size_t)k * (size_t)(nsl + 1) + (size_t)sl] = (int)tot;
-        tot += (int64_t)width * kSellC;
-        if (tot >= ((int64_t)1 << 31)) return fail(h, HPRQP_INVALID_ARG, "tiled factor copy: too many entries");
-      }
-    }
-    off[(size_t)k * (size_t)(nsl + 1) + (size_t)nsl] = (int)tot;
-  }
-  std::vector<unsigned short> col((size_t)tot, 0);
-  std::vector<double> val((size_t)tot, 0.0);
-  std::vector<int> m((size_t)nt);
-  for (int64_t r = 0; r < rows; r++) {
-    std::fill(m.begin(), m.end(), 0);
-    for (int q = M.rp[r]; q < M.rp[r + 1]; q++) {
-      const int k = (int)(M.ci[q] / W);
-      const int sp = slot[(size_t)k * (size_t)rows + (size_t)r];
-      const size_t pos = (size_t)off[(size_t)k * (size_t)(nsl + 1) + (size_t)(sp / kSellC)] +
-                         (size_t)m[(size_t)k] * kSellC + (size_t)(sp % kSellC);
-      col[pos] = (unsigned short)(M.ci[q] - k * W);
-      val[pos] = M.v[q];
-      m[(size_t)k]++;
-    }
-  }
-  hprqp_status st;
-  int *d_off, *d_perm;
-  unsigned short* d_col;
-  double* d_val;
-  if ((st = upload(h, &d_off, off)) || (st = upload(h, &d_perm, perm)) || (st = upload(h, &d_col, col)) ||
-      (st = upload(h, &d_val, val)))
-    return st;
-  // the host vectors are released on return: finish the copies first
-  CU(h, cudaStreamSynchronize(h->stream));
-  S.rows = rows;
-  S.ntile = nt;
-  S.nsl = nsl;
-  S.off = d_off;
-  S.perm = d_perm;
-  S.col = d_col;
-  S.val = d_val;
-  return HPRQP_OK;
-}
-
-// The same copy built on the device from the uploaded CSR matrix d (at most kMaxTilesDevice
-// column tiles); the host build above otherwise.
-static hprqp_status build_sell_dev(hprqp_handle* h, SellTiles& S, const Csr& d, const HostCsr& M) {
   const int64_t rows = d.rows, nsl = (rows + 31) / 32;
   const int nt = (int)std::max<int64_t>(1, (d.cols + kTileW - 1) / kTileW);
-  if (nt > kMaxTilesDevice || rows == 0) return build_sell(h, S, M);
+  if (nt > kMaxTilesDevice || rows == 0) return fail(h, HPRQP_INVALID_ARG, "tiled factor copy: shape");
   hprqp_status st;
   void *len, *perm, *slot, *width, *off, *total;
   if ((st = dalloc(h, &len, (size_t)nt * rows * sizeof(int))) ||
@@ -325,15 +250,14 @@ static hprqp_status build_sell_dev(hprqp_handle* h, SellTiles& S, const Csr& d, 
 // Tiled copies of a factor term B (p x n) for the shared-memory products of tiled.cu: B tiled
 // over its columns (the entries of x), B^T over its columns (the entries of t = B x); from
 // the device copies dB, dBT of B and B^T.
-static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const HostCsr& B, const HostCsr& BT, const Csr& dB,
-                                const Csr& dBT, int sms) {
+static hprqp_status build_tiled(hprqp_handle* h, TiledFac& T, const Csr& dB, const Csr& dBT, int sms) {
   hprqp_status st;
-  if ((st = build_sell_dev(h, T.b, dB, B)) || (st = build_sell_dev(h, T.bt, dBT, BT))) return st;
-  T.p = B.rows;
+  if ((st = build_sell_dev(h, T.b, dB)) || (st = build_sell_dev(h, T.bt, dBT))) return st;
+  T.p = dB.rows;
   const int64_t nwin = (T.b.nsl + kSellWin / kSellC - 1) / (kSellWin / kSellC);
   // one wave of (tile, window range) blocks at one block per SM
   T.nrange = (int)std::max<int64_t>(1, std::min<int64_t>(sms / T.b.ntile, nwin));
-  return zeros(h, &T.part, (size_t)T.b.ntile * (size_t)B.rows);
+  return zeros(h, &T.part, (size_t)T.b.ntile * (size_t)dB.rows);
 }
 
 // SELL-32 copy of a device CSR matrix for the row passes, built on the device (sorting
@@ -853,11 +777,9 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   int64_t toff = 0;
   QD.nfac = (int)facs.size();
-  std::vector<HostCsr> facts((size_t)QD.nfac);   // the transposes, kept for the tiled copies
   for (int f = 0; f < QD.nfac; f++) {
     if ((st = upload_csr(h, QD.fac[f], facs[f]))) return st;
-    facts[f] = transpose(facs[f]);
-    const HostCsr& BT = facts[f];
+    const HostCsr BT = transpose(facs[f]);
     if ((st = upload_csr(h, QD.fact[f], BT))) return st;
     QD.toff[f] = toff;
     toff += facs[f].rows;
@@ -900,10 +822,11 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
       const HostCsr& B = facs[f];
       const int64_t nnz = B.rp[B.rows];
       const int64_t kb = (n + kTileW - 1) / kTileW, kt = (B.rows + kTileW - 1) / kTileW;
-      const bool fits = room && h->prm.launch_mode != 3 && kt <= 8 && kb * B.rows <= ((int64_t)1 << 28);
+      const bool fits = room && h->prm.launch_mode != 3 && kt <= 8 && kb <= kMaxTilesDevice &&
+                        kb * B.rows <= ((int64_t)1 << 28);
       const bool large = nnz >= 2000000 && nnz >= 8 * std::max<int64_t>(n, B.rows);
       if (!fits || !(h->prm.tiled_factor == 2 || (h->prm.tiled_factor == 1 && large))) continue;
-      if ((st = build_tiled(h, QD.tf[f], B, facts[f], QD.fac[f], QD.fact[f], tsms))) return st;
+      if ((st = build_tiled(h, QD.tf[f], QD.fac[f], QD.fact[f], tsms))) return st;
       QD.tiled[f] = 1;
       QD.uoff[f] = toff;
       toff += n;
