@@ -304,6 +304,33 @@ static hprqp_status upload_csr(hprqp_handle* h, Csr& d, const HostCsr& M) {
   return HPRQP_OK;
 }
 
+// Stored transpose of a matrix already on the device (d), built on the device in the order of
+// the host counting sort; the host transpose of M when a transposed row would hold more than
+// 2048 entries (the device sorts each row by insertion).
+static hprqp_status upload_transpose(hprqp_handle* h, Csr& t, const Csr& d, const HostCsr& M) {
+  hprqp_status st;
+  void *rp, *mx;
+  if ((st = dalloc(h, &rp, (size_t)(d.cols + 1) * sizeof(int))) || (st = dalloc(h, &mx, sizeof(int)))) return st;
+  CU(h, transpose_layout(d, (int*)rp, (int*)mx, h->stream));
+  int maxlen = 0;
+  CU(h, cudaMemcpyAsync(&maxlen, mx, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (maxlen > 2048) return upload_csr(h, t, transpose(M));
+  void *cur, *ci, *v;
+  if ((st = dalloc(h, &cur, (size_t)std::max<int64_t>(d.cols, 1) * sizeof(int))) ||
+      (st = dalloc(h, &ci, (size_t)std::max<int64_t>(d.nnz, 1) * sizeof(int))) ||
+      (st = dalloc(h, &v, (size_t)std::max<int64_t>(d.nnz, 1) * sizeof(double))))
+    return st;
+  CU(h, transpose_fill(d, (const int*)rp, (int*)cur, (int*)ci, (double*)v, h->stream));
+  t.rows = d.cols;
+  t.cols = d.rows;
+  t.nnz = d.nnz;
+  t.rp = (const int*)rp;
+  t.ci = (const int*)ci;
+  t.v = (const double*)v;
+  return HPRQP_OK;
+}
+
 // ------------------------------------------------------------------------------------ defaults
 extern "C" void hprqp_default_params(hprqp_params* p) {
   if (!p) return;
@@ -743,8 +770,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   if (m > 0) {
     if ((st = upload_csr(h, a.A, A))) return st;
-    HostCsr AT = transpose(A);
-    if ((st = upload_csr(h, a.AT, AT))) return st;
+    if ((st = upload_transpose(h, a.AT, a.A, A))) return st;
     // SELL copies for the autotuner's choice (not for the persistent mode, which keeps lanes)
     if (h->prm.launch_mode != 3 && h->prm.autotune != 0) {
       if ((st = build_sell_rows(h, a.A)) || (st = build_sell_rows(h, a.AT))) return st;
@@ -779,8 +805,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   QD.nfac = (int)facs.size();
   for (int f = 0; f < QD.nfac; f++) {
     if ((st = upload_csr(h, QD.fac[f], facs[f]))) return st;
-    const HostCsr BT = transpose(facs[f]);
-    if ((st = upload_csr(h, QD.fact[f], BT))) return st;
+    if ((st = upload_transpose(h, QD.fact[f], QD.fac[f], facs[f]))) return st;
     QD.toff[f] = toff;
     toff += facs[f].rows;
   }

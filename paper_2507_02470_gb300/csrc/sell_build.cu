@@ -200,4 +200,117 @@ cudaError_t tile_fill(const Csr& M, int W, int ntile, const int* slot, const int
   return cudaGetLastError();
 }
 
+// ---- transpose of a CSR matrix on the device, with the layout of the host counting sort
+// (entries of each transposed row in increasing original row order)
+__global__ void k_tr_count(const int* __restrict__ ci, int64_t nnz, int* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += stride)
+    atomicAdd(cnt + ci[q] + 1, 1);
+}
+
+// in-place inclusive scan of rp[0..len) (rp[0] = 0) and the largest difference (one block)
+__global__ void k_tr_scan(int* __restrict__ rp, int64_t len, int* __restrict__ maxlen) {
+  __shared__ long long part[kThreads];
+  __shared__ int mx[kThreads];
+  const int t = threadIdx.x;
+  const int64_t per = (len + kThreads - 1) / kThreads;
+  const int64_t b = t * per, e = b + per < len ? b + per : len;
+  long long sum = 0;
+  int m = 0;
+  for (int64_t i = b; i < e; i++) {
+    sum += rp[i];
+    m = rp[i] > m ? rp[i] : m;
+  }
+  part[t] = sum;
+  mx[t] = m;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    int mm = 0;
+    for (int i = 0; i < kThreads; i++) {
+      const long long v = part[i];
+      part[i] = run;
+      run += v;
+      mm = mx[i] > mm ? mx[i] : mm;
+    }
+    *maxlen = mm;
+  }
+  __syncthreads();
+  long long run = part[t];
+  for (int64_t i = b; i < e; i++) {
+    run += rp[i];
+    rp[i] = (int)run;
+  }
+}
+
+// every entry into its column's segment at a free place (any order), keyed by its index q
+__global__ void k_tr_fill(const int* __restrict__ ci, const double* __restrict__ v, int64_t nnz,
+                          const int* __restrict__ rpT, int* __restrict__ cur, int* __restrict__ ciT,
+                          double* __restrict__ vT) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += stride) {
+    const int c = ci[q];
+    const int pos = rpT[c] + atomicAdd(cur + c, 1);
+    ciT[pos] = (int)q;
+    vT[pos] = v[q];
+  }
+}
+
+// the entry index q of every place -> its row (binary search in the row pointers)
+__global__ void k_tr_rows(const int* __restrict__ rp, int64_t rows, int64_t nnz, int* __restrict__ ciT) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz; i += stride) {
+    const int q = ciT[i];
+    int64_t lo = 0, hi = rows - 1;   // the last row r with rp[r] <= q
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) / 2;
+      if (rp[mid] <= q) lo = mid;
+      else hi = mid - 1;
+    }
+    ciT[i] = (int)lo;
+  }
+}
+
+// each transposed row by increasing entry index, i.e. by row and then by place in the row:
+// the order of the host counting sort (insertion sort; the keys are distinct)
+__global__ void k_tr_sort(const int* __restrict__ rpT, int64_t cols, int* __restrict__ ciT, double* __restrict__ vT) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cols; c += stride) {
+    const int b = rpT[c], e = rpT[c + 1];
+    for (int i = b + 1; i < e; i++) {
+      const int key = ciT[i];
+      const double val = vT[i];
+      int j = i - 1;
+      while (j >= b && ciT[j] > key) {
+        ciT[j + 1] = ciT[j];
+        vT[j + 1] = vT[j];
+        j--;
+      }
+      ciT[j + 1] = key;
+      vT[j + 1] = val;
+    }
+  }
+}
+
+cudaError_t transpose_layout(const Csr& M, int* rpT, int* maxlen, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(rpT, 0, (size_t)(M.cols + 1) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::min<int64_t>((M.nnz + kThreads - 1) / kThreads + 1, 152 * 8);
+  if (M.nnz > 0) k_tr_count<<<blocks, kThreads, 0, s>>>(M.ci, M.nnz, rpT);
+  k_tr_scan<<<1, kThreads, 0, s>>>(rpT, M.cols + 1, maxlen);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_fill(const Csr& M, const int* rpT, int* cur, int* ciT, double* vT, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cur, 0, (size_t)(M.cols > 0 ? M.cols : 1) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (M.nnz == 0) return cudaSuccess;
+  const int qb = (int)std::min<int64_t>((M.nnz + kThreads - 1) / kThreads + 1, 152 * 8);
+  const int cb = (int)std::min<int64_t>((M.cols + kThreads - 1) / kThreads + 1, 152 * 8);
+  k_tr_fill<<<qb, kThreads, 0, s>>>(M.ci, M.v, M.nnz, rpT, cur, ciT, vT);
+  k_tr_sort<<<cb, kThreads, 0, s>>>(rpT, M.cols, ciT, vT);
+  k_tr_rows<<<qb, kThreads, 0, s>>>(M.rp, M.rows, M.nnz, ciT);
+  return cudaGetLastError();
+}
+
 }  // namespace hprqp

@@ -20,4 +20,11 @@ cudaError_t tile_layout(const Csr& M, int W, int ntile, int* len, int* perm, int
 cudaError_t tile_fill(const Csr& M, int W, int ntile, const int* slot, const int* off, unsigned short* col,
                       double* val, cudaStream_t s);
 
+// Transpose T (cols x rows) of a device CSR matrix M, each row of T in increasing row order of
+// M: transpose_layout fills rpT (cols + 1) and *maxlen (the longest row of T); transpose_fill
+// then writes ciT / vT (M.nnz each), sorting each row of T by insertion (use the host
+// transpose when *maxlen is large).
+cudaError_t transpose_layout(const Csr& M, int* rpT, int* maxlen, cudaStream_t s);
+cudaError_t transpose_fill(const Csr& M, const int* rpT, int* cur, int* ciT, double* vT, cudaStream_t s);
+
 }  // namespace hprqp
