@@ -1,8 +1,8 @@
 // C ABI of the single-instance HPR-QP solver (include/hprqp.h).
 //
-// Host responsibilities: validate and copy the problem (host or device inputs), build the
-// stored transposes A^T and B_f^T (counting sort by column, so the row order inside each
-// transposed row is fixed), build the SELL and tiled copies, pick the SpMV schedule, run the
+// Host responsibilities: validate and copy the problem (host or device inputs), have the
+// device build the stored transposes A^T and B_f^T (each transposed row in increasing original
+// row order) and the SELL and tiled copies (sell_build.cu), pick the SpMV schedule, run the
 // power method of Sec. 4.1, and drive Algorithm 4 through CUDA graphs (solver.cu) whose kernels
 // stop themselves once the device-side controller has set the done flag.
 #include <cublas_v2.h>
