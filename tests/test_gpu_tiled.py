@@ -69,8 +69,8 @@ def test_tiled_converges_like_the_csr_path_and_the_oracle(pkg, name):
 
 
 def test_tiled_is_chosen_for_large_factors_only(pkg):
-    """The default (tiled_factor = 1) tiles the Lasso factor of the benchmark size but not the
-    small S of the config-1 CQP (the autotuner's lanes report is unaffected)."""
+    """The default (tiled_factor = 1) tiles a Lasso factor of 3.6e6 entries but not the factor
+    of the n = 6e4 CQP (1.2e6 entries, below the 2e6 threshold)."""
     big = qpgen.lasso(p=30_000, q=60_000, density=2e-3, seed=1)   # 3.6e6 entries, 60 per column
     small = PROBLEMS["cqp"]
     with pkg.Solver(big) as s1, pkg.Solver(big, tiled_factor=0) as s0:
