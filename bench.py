@@ -64,7 +64,8 @@ def _oracle_one(args):
 
 
 def run_batched(args, rank, world, dist=None):
-    """Config 3: the portfolio batch in one persistent launch, against the plain solver."""
+    """The batch of portfolio CQPs (n from 50 to 5000, m = 11) in one persistent launch, against
+    the plain solver."""
     import torch
     import paper_2507_02470_gb300 as pkg
     count = args.c3_count
@@ -143,7 +144,7 @@ def run_batched(args, rank, world, dist=None):
 
 
 def run_learned(args, rank, world):
-    """Config 4: learned warm start on the parametric family (n=1e5, m=5e4) against the plain
+    """Learned warm start on the parametric family (n=1e5, m=5e4) against the plain
     solver started from the origin, both on the GPU."""
     import torch
     import paper_2507_02470_gb300 as pkg
