@@ -2,7 +2,7 @@
 // one vector (every inner step except stopping tests, the restart pass, apply, power method):
 //
 //   k_tb    partial t_k = B_f[:, tile k] x_k  block (k, g): column tile k of x (kTileW entries)
-//                                             in shared memory, windows of range g of B_f's rows
+//                                             in shared memory, share g of the tile's slices
 //   k_tsum  t = sum_k t_k                     in tile order (deterministic)
 //   k_tbt   u = B_f^T t                       one pass per tile of t: every block holds the tile
 //                                             in shared memory and adds its rows' part to u
@@ -12,6 +12,7 @@
 // these products.  Here each lane owns a row of a 32-row slice (SELL-32 with rows sorted by
 // length inside windows of 512): the loads are coalesced, every FMA instruction works on 32
 // rows with little padding and no shuffle reduction, and the gathers hit shared memory.
+// Padding entries hold the value 0 at column 0 and are skipped by the lane's own length test.
 // u goes to the intermediate buffer at uoff, where the row pass adds it.
 #include "kernels.cuh"
 
