@@ -12,7 +12,7 @@
 // these products.  Here each lane owns a row of a 32-row slice (SELL-32 with rows sorted by
 // length inside windows of 512): the loads are coalesced, every FMA instruction works on 32
 // rows with little padding and no shuffle reduction, and the gathers hit shared memory.
-// Padding entries hold the value 0 at column 0 and are skipped by the lane's own length test.
+// Padding entries hold the value 0 at column 0: they add 0 * tab[0] (0 for a finite iterate).
 // u goes to the intermediate buffer at uoff, where the row pass adds it.
 #include "kernels.cuh"
 
