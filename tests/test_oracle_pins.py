@@ -11,6 +11,7 @@ import os
 import numpy as np
 import pytest
 import scipy.optimize as so
+import scipy.sparse as sp
 
 import oracle
 import qpgen
@@ -619,3 +620,107 @@ def test_qap_relaxation_bound_below_brute_force_optimum():
     assert qpb >= qp.qap_bound_const - 1e-6        # Qhat is PSD
     X = s.x.reshape(d, d, order="F")
     assert np.allclose(X.sum(axis=0), 1, atol=1e-6) and np.allclose(X.sum(axis=1), 1, atol=1e-6)
+
+
+# ------------------------------------------------------------------ operator products
+def _dense_by_entries(qp):
+    """A and Q assembled entry by entry from the stored arrays, one loop per storage form:
+    CSR row i lists (colidx[k], vals[k]) for k in [rowptr[i], rowptr[i+1]); a band term holds
+    Q[i][i+o] = Q[i+o][i] = diags[k][i] for offset o = offsets[k]; a factor term (sparse B or
+    dense F, p x n) contributes sum over rows r of B[r]^T B[r]; a diagonal term d[j] at (j, j)."""
+    n, m = qp.n, qp.m
+    A = np.zeros((m, n))
+    for i in range(m):
+        for k in range(qp.A_rowptr[i], qp.A_rowptr[i + 1]):
+            A[i, qp.A_colidx[k]] += qp.A_vals[k]
+    Q = np.zeros((n, n))
+    for t in qp.qterms:
+        if t.kind == "diag":
+            for j in range(n):
+                Q[j, j] += t.dense[j]
+        elif t.kind == "csr":
+            for i in range(n):
+                for k in range(t.rowptr[i], t.rowptr[i + 1]):
+                    Q[i, t.colidx[k]] += t.vals[k]
+        elif t.kind == "dia":
+            for k, o in enumerate(t.offsets):
+                for i in range(n - o):
+                    Q[i, i + o] += t.diags[k][i]
+                    if o:
+                        Q[i + o, i] += t.diags[k][i]
+        elif t.kind in ("factor", "dense_factor"):
+            for r in range(t.p):
+                row = np.zeros(n)
+                if t.kind == "factor":
+                    for k in range(t.rowptr[r], t.rowptr[r + 1]):
+                        row[t.colidx[k]] += t.vals[k]
+                else:
+                    row[:] = np.asarray(t.dense).reshape(t.p, n)[r]
+                for j1 in range(n):
+                    for j2 in range(n):
+                        Q[j1, j2] += row[j1] * row[j2]
+        else:
+            raise ValueError(t.kind)
+    return A, Q
+
+
+def _all_term_kinds(n=11, m=6, seed=5):
+    """A QP whose Q sums one term of every stored kind (diagonal, CSR, band with offsets
+    0, 1 and 3, sparse factor, dense factor); A with an empty row and a repeated column."""
+    rng = np.random.default_rng(seed)
+    Ad = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.5)
+    Ad[2] = 0.0
+    Ad[4, 7] = 3.0
+    rp, ci, va = qpgen.csr_from_scipy(sp.csr_matrix(Ad))
+    G = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.4)
+    S = G + G.T
+    srp = [0]; sci = []; sva = []
+    for i in range(n):
+        for j in range(n):
+            if S[i, j] != 0.0:
+                sci.append(j); sva.append(S[i, j])
+        srp.append(len(sci))
+    offs = np.array([0, 1, 3], np.int32)
+    diags = rng.uniform(-1, 1, (3, n))
+    B = rng.standard_normal((4, n)) * (rng.random((4, n)) < 0.5)
+    brp = [0]; bci = []; bva = []
+    for r in range(4):
+        for j in range(n):
+            if B[r, j] != 0.0:
+                bci.append(j); bva.append(B[r, j])
+        brp.append(len(bci))
+    F = rng.standard_normal((3, n))
+    terms = [
+        qpgen.QTerm("diag", dense=rng.uniform(0.5, 1.5, n)),
+        qpgen.QTerm("csr", rowptr=np.array(srp, np.int32), colidx=np.array(sci, np.int32),
+                    vals=np.array(sva)),
+        qpgen.QTerm("dia", offsets=offs, diags=diags),
+        qpgen.QTerm("factor", p=4, rowptr=np.array(brp, np.int32), colidx=np.array(bci, np.int32),
+                    vals=np.array(bva)),
+        qpgen.QTerm("dense_factor", p=3, dense=np.ascontiguousarray(F)),
+    ]
+    inf = np.inf
+    return qpgen.QP(n, m, rp, ci, va, rng.standard_normal(n), np.full(m, -inf), np.full(m, inf),
+                    np.full(n, -inf), np.full(n, inf), 0, 0.0, terms, name="all_term_kinds")
+
+
+def test_operator_products_of_every_term_kind_match_their_entries():
+    """The oracle's Q v, A v and A^T y (the products every step of Algorithm 4 is built from)
+    equal the matrices written out entry by entry from each storage form's definition, term
+    by term and summed."""
+    qp = _all_term_kinds()
+    A, Q = _dense_by_entries(qp)
+    assert np.allclose(Q, Q.T)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        v = rng.standard_normal(qp.n)
+        y = rng.standard_normal(qp.m)
+        np.testing.assert_allclose(oracle.qmul(qp, v), Q @ v, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(oracle.amul(qp, v), A @ v, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(oracle.atmul(qp, y), A.T @ y, rtol=1e-12, atol=1e-12)
+    for t in qp.qterms:
+        one = qpgen.QP(**{**qp.__dict__, "qterms": [t]})
+        _, Qt = _dense_by_entries(one)
+        v = rng.standard_normal(qp.n)
+        np.testing.assert_allclose(oracle.qmul(one, v), Qt @ v, rtol=1e-12, atol=1e-12,
+                                   err_msg=t.kind)
