@@ -724,3 +724,73 @@ def test_operator_products_of_every_term_kind_match_their_entries():
         v = rng.standard_normal(qp.n)
         np.testing.assert_allclose(oracle.qmul(one, v), Qt @ v, rtol=1e-12, atol=1e-12,
                                    err_msg=t.kind)
+
+
+def _support_by_lp(w, lo, hi):
+    """sup over the box [lo, hi] of <w, s>, computed by an LP solver (finite by construction)."""
+    if w.size == 0:
+        return 0.0
+    r = so.linprog(-w, bounds=list(zip(np.where(np.isfinite(lo), lo, None),
+                                       np.where(np.isfinite(hi), hi, None))), method="highs")
+    assert r.status == 0
+    return -r.fun
+
+
+@pytest.mark.parametrize("phi", ["box", "l1"])
+@pytest.mark.parametrize("dominant", ["Ax or Qx", "b", "c", "A*y"])
+def test_stopping_measures_at_a_point_away_from_the_solution(phi, dominant):
+    """eta_p, eta_d, eta_gap of the Sec. 4.1 stopping rule at an arbitrary (x, y, z): the
+    projection onto K and both support functions (delta*_K(-y) = sup_{s in K} <-y, s>,
+    phi*(-z) = sup_{x in C} <-z, x> for the box) evaluated by an LP solver, the norms and
+    denominators as printed.  y and z carry signs that keep the supports finite, with zero
+    multipliers on some infinite bounds (those contribute 0).  Each variant scales one
+    quantity so that it is the largest term of its denominator."""
+    qp = _all_term_kinds(n=11, m=6, seed=9)
+    rng = np.random.default_rng(4)
+    n, m = qp.n, qp.m
+    qp.l = rng.uniform(-2, 0, m); qp.u = qp.l + rng.uniform(0, 2, m)
+    qp.l[[1, 4]] = -np.inf; qp.u[[2, 4]] = np.inf; qp.u[5] = qp.l[5]
+    if dominant == "b":
+        qp.l[0], qp.u[0] = -400.0, -399.0          # ||b|| = 400 and row 0 violated
+    if dominant == "c":
+        qp.c = qp.c * 1e3
+    y = rng.standard_normal(m) * (1e3 if dominant == "A*y" else 1.0)
+    y[~np.isfinite(qp.l)] = -np.abs(y[~np.isfinite(qp.l)])      # y_i > 0 needs l_i finite
+    y[~np.isfinite(qp.u)] = np.abs(y[~np.isfinite(qp.u)])       # y_i < 0 needs u_i finite
+    y[4] = 0.0                                                   # free row: zero multiplier
+    if phi == "box":
+        qp.L = rng.uniform(-3, -1, n); qp.U = rng.uniform(1, 3, n)
+        qp.L[[0, 6]] = -np.inf; qp.U[[3, 6]] = np.inf
+        x = np.clip(rng.standard_normal(n) * 2, qp.L, qp.U)
+        z = rng.standard_normal(n)
+        z[~np.isfinite(qp.L)] = -np.abs(z[~np.isfinite(qp.L)])
+        z[~np.isfinite(qp.U)] = np.abs(z[~np.isfinite(qp.U)])
+        z[6] = 0.0
+        phi_x = 0.0
+        phi_conj = _support_by_lp(-z, qp.L, qp.U)
+    else:
+        qp.phi = qpgen.PHI_L1; qp.lam = 0.7
+        qp.L = np.full(n, -np.inf); qp.U = np.full(n, np.inf)
+        x = rng.standard_normal(n)
+        z = rng.uniform(-qp.lam, qp.lam, n)                      # phi*(-z) = 0 on |z| <= lambda
+        phi_x = qp.lam * np.abs(x).sum()
+        phi_conj = 0.0
+    A, Q = _dense_by_entries(qp)
+    Ax, Qx, Aty = A @ x, Q @ x, A.T @ y
+    b = np.maximum(np.where(np.isfinite(qp.l), np.abs(qp.l), 0.0),
+                   np.where(np.isfinite(qp.u), np.abs(qp.u), 0.0))
+    terms_p = {"b": np.abs(b).max(), "Ax": np.abs(Ax).max()}
+    terms_d = {"c": np.abs(qp.c).max(), "A*y": np.abs(Aty).max(), "Qx": np.abs(Qx).max()}
+    if dominant in ("b", "c", "A*y"):
+        big = terms_p if dominant == "b" else terms_d
+        assert max(big, key=big.get) == dominant
+    eta_p = np.abs(Ax - np.clip(Ax, qp.l, qp.u)).max() / (1 + max(terms_p.values()))
+    eta_d = np.abs(-Qx + Aty + z - qp.c).max() / (1 + max(terms_d.values()))
+    supK = _support_by_lp(-y, qp.l, qp.u)
+    P = 0.5 * x @ Qx + qp.c @ x + phi_x
+    Dv = -0.5 * x @ Qx - supK - phi_conj
+    eta_gap = abs(P - Dv) / (1 + max(abs(P), abs(0.5 * x @ Qx + supK + phi_conj)))
+    e, pobj, dobj = oracle.eta(qp, x, y, z)
+    np.testing.assert_allclose(e, [eta_p, eta_d, eta_gap], rtol=1e-10)
+    assert pobj == pytest.approx(P, rel=1e-12) and dobj == pytest.approx(Dv, rel=1e-10)
+    assert min(e) > 1e-4                     # a point away from the solution: every term counts
