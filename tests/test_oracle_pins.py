@@ -794,3 +794,38 @@ def test_stopping_measures_at_a_point_away_from_the_solution(phi, dominant):
     np.testing.assert_allclose(e, [eta_p, eta_d, eta_gap], rtol=1e-10)
     assert pobj == pytest.approx(P, rel=1e-12) and dobj == pytest.approx(Dv, rel=1e-10)
     assert min(e) > 1e-4                     # a point away from the solution: every term counts
+
+
+@pytest.mark.parametrize("form", ["csr", "dia"])
+def test_scaling_closed_form_when_ruiz_is_already_at_its_fixed_point(form):
+    """Q = [[1, 1], [1, 1/4]] (m = 0): every column of K already has infinity norm 1, so the ten
+    Ruiz passes leave d = 1, and the Pock-Chambolle pass (alpha = 1) divides by the square roots
+    of the column 1-norms 2 and 5/4: d = (1/sqrt 2, 1/sqrt 1.25).  Taking the 1-norm in the Ruiz
+    passes, or the infinity norm in the last one, gives another d."""
+    Qd = np.array([[1.0, 1.0], [1.0, 0.25]])
+    if form == "csr":
+        qp = qpgen.from_dense(Qd, np.array([1.0, -1.0]), L=np.array([-1.0, -1.0]), U=np.array([1.0, 1.0]))
+    else:
+        qp = qpgen.from_dense(None, np.array([1.0, -1.0]), L=np.array([-1.0, -1.0]), U=np.array([1.0, 1.0]))
+        qp.qterms = [qpgen.QTerm("dia", offsets=np.array([0, 1], np.int32),
+                                 diags=np.array([[1.0, 0.25], [1.0, 0.0]]))]
+    d, e, ok = oracle.scaling(qp)
+    assert ok and e.size == 0
+    np.testing.assert_allclose(d, [1 / np.sqrt(2.0), 1 / np.sqrt(1.25)], rtol=1e-15)
+
+
+def test_scaling_closed_form_with_one_entry_per_column():
+    """K = [Q A^T; A 0] with one nonzero per column (Q diagonal on the columns A does not touch,
+    A a scaled partial permutation): the first Ruiz pass makes every entry +-1 and no later pass
+    changes it, so d_j = 1/sqrt|q_j| on Q's columns and d_j = e_i = 1/sqrt|a_ij| on A's
+    (both start at 1 and are divided by the same root)."""
+    n, m = 5, 3
+    q = np.array([0.0, 4.0, 0.0, 0.0, 0.09])
+    A = np.zeros((m, n))
+    A[0, 2], A[1, 0], A[2, 3] = -25.0, 0.01, 2.0
+    qp = qpgen.from_dense(np.diag(q), np.ones(n), A=A, l=-np.ones(m), u=np.ones(m),
+                          L=-np.ones(n), U=np.ones(n), q_kind="diag")
+    d, e, ok = oracle.scaling(qp)
+    assert ok
+    np.testing.assert_allclose(d, [10.0, 0.5, 0.2, 1 / np.sqrt(2.0), 1 / 0.3], rtol=1e-14)
+    np.testing.assert_allclose(e, [0.2, 10.0, 1 / np.sqrt(2.0)], rtol=1e-14)
