@@ -356,6 +356,9 @@ def test_power_method_estimates():
     assert eq <= lq * (1 + 1e-9) and eq >= lq * (1 - 1e-6)
     s = oracle.solve(qp, max_iter=1)
     assert s.lambda_A >= la and s.lambda_Q >= lq  # default safety factor keeps lambda >= lambda_1
+    # the safety factor: lambda = 1.01 x the estimate, which stops within 1e-4 below lambda_1 here
+    assert 1.0099 <= s.lambda_A / la <= 1.0100 + 1e-12
+    assert 1.0099 <= s.lambda_Q / lq <= 1.0100 + 1e-12
 
 
 # ------------------------------------------------------------------ restart bookkeeping (Sec. 3.2)
