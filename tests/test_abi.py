@@ -79,3 +79,15 @@ def test_create_without_gpu_fails_cleanly(lib):
     qp = qpgen.random_small(n=4, m=2, seed=0)
     with pytest.raises(pkg.HPRQPError):
         pkg.Solver(qp)
+
+
+@pytest.mark.parametrize("bad", [dict(check_every=0), dict(restart_every=0), dict(iters_per_launch=0),
+                                 dict(iters_per_launch=4097), dict(launch_mode=4), dict(method=3)])
+def test_out_of_range_parameters_are_rejected_before_any_device_work(lib, bad):
+    """Parameter ranges are checked first, so the answer is INVALID_ARG with a message naming
+    the ranges, on a machine with or without a GPU."""
+    import qpgen
+    qp = qpgen.random_small(n=4, m=2, seed=0)
+    with pytest.raises(pkg.HPRQPError) as e:
+        pkg.Solver(qp, **bad)
+    assert e.value.status == 4 and "check_every" in str(e.value)
