@@ -511,7 +511,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4", "qap"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4", "qap"],
+                    help="c0: CQP n=1e3, m=500 (Q = M^T M, M 100 x 1e3); c1 (default): CQP n=1e6, "
+                         "m=5e5 (A 6 per row, Q pentadiagonal + S^T S); c2: Lasso, B 5e4 x 5e5 "
+                         "Bernoulli(5e-4); c3: 4096 portfolio CQPs, n in [50, 5000], batched; "
+                         "c4: learned warm start on a family of CQPs n=1e5, m=5e4; qap: QAP "
+                         "relaxation, d=256 (n=65,536)")
     ap.add_argument("--c4-train", type=int, default=2000)
     ap.add_argument("--c4-test", type=int, default=100)
     ap.add_argument("--c4-epochs", type=int, default=30)

@@ -17,7 +17,9 @@ import sys
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c4"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c4"],
+                    help="c0: CQP n=1e3, m=500; c1: CQP n=1e6, m=5e5; c2: Lasso 5e4 x 5e5; "
+                         "c4: CQP n=1e5, m=5e4 (the learned warm start's family base)")
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--warm-iters", type=int, default=20, help="iterations of the solve before profiling")
     ap.add_argument("--autotune", type=int, default=1,

@@ -74,7 +74,8 @@ class CsrSpMV:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c1", choices=["c1", "c4"])
+    ap.add_argument("--workload", default="c1", choices=["c1", "c4"],
+                    help="c1: A of the CQP n=1e6, m=5e5; c4: A of the CQP n=1e5, m=5e4")
     ap.add_argument("--reps", type=int, default=30)
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
