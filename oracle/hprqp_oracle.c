@@ -152,13 +152,17 @@ static double conj_phi(const orc_problem* P, const double* z) {
   }
   if (P->phi == ORC_PHI_L1) return 0.0; /* indicator of [-lam, lam]^n, z bar lies inside */
   /* lam|x| + delta_[L,U]: per coordinate sup_{x in [L,U]} (-z x - lam |x|), a concave
-     piecewise-linear function: the sup is at a finite end point, at 0, or +inf. */
+     piecewise-linear function: the sup is at a finite end point or at 0 when z lies in the
+     domain, i.e. z <= lam if L = -inf and z >= -lam if U = +inf.  zbar is a subgradient of
+     phi at xbar (eq. (3.1)), so it lies there in exact arithmetic; (xbar - r_z)/sigma can
+     cross the edge by rounding, so an infinite side takes z on its edge (as the pure l1
+     case above, whose conjugate is 0 on [-lam, lam], does). */
   for (int64_t j = 0; j < P->n; j++) {
     double zj = z[j], Lj = P->L[j], Uj = P->U[j], lam = P->lambda, best = -INFINITY;
+    if (!isfinite(Lj) && zj > lam) zj = lam;
+    if (!isfinite(Uj) && zj < -lam) zj = -lam;
     if (isfinite(Lj)) best = fmax(best, -zj * Lj - lam * fabs(Lj));
-    else if (zj > lam) return INFINITY;
     if (isfinite(Uj)) best = fmax(best, -zj * Uj - lam * fabs(Uj));
-    else if (-zj - lam > 0.0) return INFINITY;
     if (Lj <= 0.0 && Uj >= 0.0) best = fmax(best, 0.0);
     s += best;
   }

@@ -120,8 +120,11 @@ __device__ __forceinline__ double prox_phi(int phi, double r, double L, double U
   return iclamp(s, L, U);
 }
 
-// phi^*(-z) contribution of one coordinate (0 * inf = 0; +inf when z points past an
-// infinite bound, which a Prox output cannot do)
+// phi^*(-z) contribution of one coordinate (0 * inf = 0 for the box).  For lam|x| + the box,
+// sup over [L, U] of (-z x - lam |x|): a finite end point or 0, given z <= lam where L = -inf
+// and z >= -lam where U = +inf.  zbar from the prox (eq. (3.1)) meets that in exact
+// arithmetic but can cross the edge by rounding, so an infinite side puts z on its edge (the
+// pure l1 term, 0 on [-lam, lam], makes the same assumption).
 __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, double U, double lam) {
   if (phi == PHI_L1) return 0.0;
   if (phi == PHI_BOX) {
@@ -130,11 +133,11 @@ __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, dou
     else if (ilt0(z)) t = -U * z;
     return t;
   }
+  if (iisinf(L) && z > lam) z = lam;
+  if (iisinf(U) && z < -lam) z = -lam;
   double best = -INFINITY;
   if (!iisinf(L)) best = imax(best, -z * L - lam * iabs(L));
-  else if (z > lam) return INFINITY;
   if (!iisinf(U)) best = imax(best, -z * U - lam * iabs(U));
-  else if (-z - lam > 0.0) return INFINITY;
   if (L <= 0.0 && U >= 0.0) best = imax(best, 0.0);
   return best;
 }

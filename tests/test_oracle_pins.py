@@ -93,6 +93,30 @@ def test_l1_box_separable():
     np.testing.assert_allclose(s.x, np.clip(soft / q, L, U), atol=1e-8)
 
 
+def test_l1_with_unbounded_sides_closed_form():
+    """lam|x| + the indicator of [L, U] with infinite sides (x >= 0 as in a nonnegative Lasso,
+    x <= U, and both sides free), diagonal Q: the solution is clip(soft(-c, lam)/q, L, U)
+    coordinate by coordinate, and the solve must stop on the Sec. 4.1 rule (the dual value
+    phi*(-zbar) stays finite on the unbounded sides)."""
+    rng = np.random.default_rng(7)
+    n = 40
+    q = rng.uniform(0.5, 2.0, n)
+    c = 2 * rng.standard_normal(n)
+    L = np.where(np.arange(n) % 4 == 0, 0.0, -np.inf)
+    U = np.where(np.arange(n) % 4 == 1, 0.4, np.inf)
+    L[2::4], U[2::4] = -0.3, 0.3
+    lam = 0.3
+    qp = qpgen.from_dense(np.diag(q), c, L=L, U=U, phi="l1_box", lam=lam, q_kind="diag")
+    s = _solve(qp)
+    assert s.status == "converged"
+    soft = np.sign(-c) * np.maximum(np.abs(c) - lam, 0)
+    xs = np.clip(soft / q, L, U)
+    np.testing.assert_allclose(s.x, xs, atol=1e-8)
+    assert np.count_nonzero(xs[L == 0.0] > 0) >= 3     # interior points on a side with U = inf
+    p_star = 0.5 * q @ xs**2 + c @ xs + lam * np.abs(xs).sum()
+    assert s.pobj == pytest.approx(p_star, rel=1e-8)
+
+
 def test_lp_special_case_matches_linprog():
     # Q = 0, phi = delta_C: HPR-QP reduces to HPR-LP (Sec. 2.2 remark); compare the
     # optimal value with an LP library (HiGHS through scipy)
