@@ -14,7 +14,9 @@
  * Conventions for every entry point:
  *   - Pointers to problem data may point to host memory or to device memory of the current
  *     CUDA device; the library detects which (cudaPointerGetAttributes) and copies.
- *   - Infinite bounds are IEEE +-INFINITY.  NaN anywhere in the data is an error.
+ *   - Infinite bounds are IEEE +-INFINITY: l, L may be -INFINITY and u, U +INFINITY
+ *     (Sec. 1); l = +INFINITY or u = -INFINITY (an empty row set), L = +INFINITY or
+ *     U = -INFINITY are errors.  NaN anywhere in the data is an error.
  *   - Index arrays are int32, CSR row pointers start at 0 and are non-decreasing, column
  *     indices lie in [0, ncols).  Row entries need not be sorted.
  *   - Functions never abort or exit; they return a status and, on failure, record a message
@@ -36,7 +38,8 @@ typedef enum hprqp_status {
   HPRQP_MAX_ITER = 1,        /* iteration limit reached; the last bar iterate is kept */
   HPRQP_TIME_LIMIT = 2,      /* wall-clock limit reached */
   HPRQP_NUMERICAL_ERROR = 3, /* NaN/Inf appeared in the iteration or its residuals */
-  HPRQP_INVALID_ARG = 4,     /* bad sizes, bounds with l > u or L > U, NaN, bad CSR */
+  HPRQP_INVALID_ARG = 4,     /* bad sizes, bounds with l > u, L > U or an infinite bound on
+                                the wrong side, NaN, bad CSR */
   HPRQP_CUDA_ERROR = 5,      /* a CUDA runtime call failed (message in last_error) */
   HPRQP_TIMEOUT = 6,         /* a bounded device wait gave up (batched queue) */
   HPRQP_OOM = 7              /* device allocation failed */
@@ -215,8 +218,8 @@ void hprqp_default_params(hprqp_params* p);
  * All inputs are copied (host or device, detected per pointer); the caller keeps ownership
  * of its buffers and may free them after the call.  params may be NULL (defaults).
  * Builds A^T (and B^T for every FACTOR term) on the device.
- * Returns HPRQP_INVALID_ARG for inconsistent sizes, NaN, l > u, L > U, non-monotone row
- * pointers or out-of-range column indices; HPRQP_OOM / HPRQP_CUDA_ERROR on device failure.
+ * Returns HPRQP_INVALID_ARG for inconsistent sizes, NaN, l > u, L > U, l or L = +INFINITY,
+ * u or U = -INFINITY, non-monotone row pointers or out-of-range column indices; HPRQP_OOM / HPRQP_CUDA_ERROR on device failure.
  * On failure *h is set to NULL and nothing is leaked. */
 hprqp_status hprqp_create(hprqp_handle** h, int64_t n, int64_t m, const hprqp_qop* Q,
                           const int32_t* A_rowptr, const int32_t* A_colidx, const double* A_vals,

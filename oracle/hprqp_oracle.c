@@ -402,14 +402,19 @@ void orc_default_params(orc_params* p) {
 
 static int bad_double(double v) { return isnan(v); }
 
+/* [lo, hi] as the paper admits it (Sec. 1): lo in R u {-inf}, hi in R u {+inf}, lo <= hi */
+static int bad_interval(double lo, double hi) {
+  return bad_double(lo) || bad_double(hi) || lo > hi || lo == INFINITY || hi == -INFINITY;
+}
+
 static int validate(const orc_problem* P, const orc_params* prm) {
   if (P->n <= 0 || P->m < 0 || prm->max_iter < 1 || !(prm->tol > 0.0)) return 0;
   if (prm->check_every < 1 || prm->restart_every < 1) return 0;
   for (int64_t j = 0; j < P->n; j++) {
-    if (!isfinite(P->c[j]) || bad_double(P->L[j]) || bad_double(P->U[j]) || P->L[j] > P->U[j]) return 0;
+    if (!isfinite(P->c[j]) || bad_interval(P->L[j], P->U[j])) return 0;
   }
   for (int64_t i = 0; i < P->m; i++)
-    if (bad_double(P->l[i]) || bad_double(P->u[i]) || P->l[i] > P->u[i]) return 0;
+    if (bad_interval(P->l[i], P->u[i])) return 0;
   if (P->m > 0 && P->A_rowptr[0] != 0) return 0;
   for (int64_t i = 0; i < P->m; i++) {
     if (P->A_rowptr[i + 1] < P->A_rowptr[i]) return 0;

@@ -436,8 +436,9 @@ static hprqp_status data_norms(hprqp_handle* h, const std::vector<double>& hc, c
     if (!std::isfinite(hc[j])) return fail(h, HPRQP_INVALID_ARG, "c[%lld] is not finite", (long long)j);
   double nb2 = 0, bi = 0;
   for (size_t i = 0; i < hl.size(); i++) {
-    if (std::isnan(hl[i]) || std::isnan(hu[i]) || hl[i] > hu[i])
-      return fail(h, HPRQP_INVALID_ARG, "row bound %lld: need l <= u, no NaN", (long long)i);
+    // K = {y real : l <= y <= u} (Sec. 1): l = +inf or u = -inf leaves it empty
+    if (std::isnan(hl[i]) || std::isnan(hu[i]) || hl[i] > hu[i] || hl[i] == INFINITY || hu[i] == -INFINITY)
+      return fail(h, HPRQP_INVALID_ARG, "row bound %lld: need l <= u, l < +inf, u > -inf, no NaN", (long long)i);
     double bl = std::isfinite(hl[i]) ? std::fabs(hl[i]) : 0.0;
     double bu = std::isfinite(hu[i]) ? std::fabs(hu[i]) : 0.0;
     double b = std::max(bl, bu);
@@ -580,8 +581,9 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     hU.assign(n, INFINITY);
   }
   for (int64_t j = 0; j < n; j++) {
-    if (std::isnan(hL[j]) || std::isnan(hU[j]) || hL[j] > hU[j])
-      return fail(h, HPRQP_INVALID_ARG, "box bound %lld: need L <= U, no NaN", (long long)j);
+    // L in (R u {-inf})^n, U in (R u {+inf})^n (Sec. 1)
+    if (std::isnan(hL[j]) || std::isnan(hU[j]) || hL[j] > hU[j] || hL[j] == INFINITY || hU[j] == -INFINITY)
+      return fail(h, HPRQP_INVALID_ARG, "box bound %lld: need L <= U, L < +inf, U > -inf, no NaN", (long long)j);
   }
   if ((st = data_norms(h, hc, hl, hu))) return st;
 

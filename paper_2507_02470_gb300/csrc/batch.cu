@@ -770,14 +770,15 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
     double nc2 = 0, ci = 0, nb2 = 0, bi = 0;
     for (int64_t j = 0; j < n; j++) {
       const double cj = c[I.on + j], Lj = L[I.on + j], Uj = U[I.on + j];
-      if (!std::isfinite(cj) || std::isnan(Lj) || std::isnan(Uj) || Lj > Uj)
+      if (!std::isfinite(cj) || std::isnan(Lj) || std::isnan(Uj) || Lj > Uj || Lj == INFINITY || Uj == -INFINITY)
         return bfail(b, HPRQP_INVALID_ARG, "instance %d: bad c or box at %lld", i, (long long)j);
       nc2 += cj * cj;
       ci = std::max(ci, std::fabs(cj));
     }
     for (int64_t r = 0; r < m; r++) {
       const double lr = l[I.om + r], ur = u[I.om + r];
-      if (std::isnan(lr) || std::isnan(ur) || lr > ur) return bfail(b, HPRQP_INVALID_ARG, "instance %d: bad row bounds", i);
+      if (std::isnan(lr) || std::isnan(ur) || lr > ur || lr == INFINITY || ur == -INFINITY)
+        return bfail(b, HPRQP_INVALID_ARG, "instance %d: bad row bounds", i);
       const double bb = std::max(std::isfinite(lr) ? std::fabs(lr) : 0.0, std::isfinite(ur) ? std::fabs(ur) : 0.0);
       nb2 += bb * bb;
       bi = std::max(bi, bb);

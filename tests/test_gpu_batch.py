@@ -100,3 +100,10 @@ def test_batch_rejects_bad_input(pkg):
     bad = qpgen.QP(**{**bad.__dict__, "l": bad.u + 1.0})
     with pytest.raises(pkg.HPRQPError):
         pkg.BatchSolver([bad])
+    # an empty box side: L = U = +inf on one coordinate (L in R u {-inf}, Sec. 1)
+    ok = qpgen.portfolio(2, n=60)
+    L, U = ok.L.copy(), ok.U.copy()
+    L[5] = U[5] = np.inf
+    with pytest.raises(pkg.HPRQPError) as e:
+        pkg.BatchSolver([ok, qpgen.QP(**{**ok.__dict__, "L": L, "U": U})])
+    assert e.value.status == 4

@@ -165,11 +165,24 @@ def test_invalid_arguments(pkg):
     ci = qp.A_colidx.copy(); ci[-1] = 99
     with pytest.raises(pkg.HPRQPError):
         pkg.Solver(qpgen.QP(**{**qp.__dict__, "A_colidx": ci}))
+    # an infinite bound on the wrong side (l = u = +inf is an empty row set, Sec. 1); the
+    # other bound moves with it, so that lo <= hi still holds
+    for lo, hi, idx, v in (("l", "u", 0, np.inf), ("l", "u", 2, -np.inf),
+                           ("L", "U", 1, np.inf), ("L", "U", 3, -np.inf)):
+        a, b = getattr(qp, lo).copy(), getattr(qp, hi).copy()
+        a[idx] = b[idx] = v
+        with pytest.raises(pkg.HPRQPError) as e:
+            pkg.Solver(qpgen.QP(**{**qp.__dict__, lo: a, hi: b}))
+        assert e.value.status == 4, (lo, v)
     with pkg.Solver(qp) as s:
         with pytest.raises(pkg.HPRQPError):
             s.solve(tol=1e-8, max_iter=0)
         with pytest.raises(pkg.HPRQPError):
             s.solve(tol=-1.0, max_iter=10)
+        l_bad, u_bad = qp.l.copy(), qp.u.copy()
+        l_bad[0] = u_bad[0] = np.inf
+        with pytest.raises(pkg.HPRQPError):
+            s.set_data(l=l_bad, u=u_bad)
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3])

@@ -486,6 +486,13 @@ def test_invalid_inputs_rejected():
     ci = qp.A_colidx.copy(); ci[0] = qp.n
     assert oracle.solve(qpgen.QP(**{**qp.__dict__, "A_colidx": ci})).status == "invalid_arg"
     assert oracle.solve(qp, max_iter=0).status == "invalid_arg"
+    # infinite bounds on the wrong side: l, L in R u {-inf}, u, U in R u {+inf} (Sec. 1);
+    # the other bound moves with it, so that lo <= hi still holds
+    for lo, hi, idx, v in (("l", "u", 0, np.inf), ("l", "u", 1, -np.inf),
+                           ("L", "U", 2, np.inf), ("L", "U", 3, -np.inf)):
+        a, b = getattr(qp, lo).copy(), getattr(qp, hi).copy()
+        a[idx] = b[idx] = v
+        assert oracle.solve(qpgen.QP(**{**qp.__dict__, lo: a, hi: b})).status == "invalid_arg", (lo, v)
 
 
 def test_tolerance_ladder_marks_where_looser_solves_stop():
