@@ -5,6 +5,7 @@ import os
 import shutil
 
 import numpy as np
+import pytest
 
 import bench
 import qpgen
@@ -48,3 +49,33 @@ def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.source_sha() == h0
     k.write_text(k.read_text() + "static int added_code = 1;\n")
     assert bench.source_sha() != h0
+
+
+def test_roofline_takes_the_slowest_kernel_and_the_larger_fraction():
+    """The roofline object: the kernel with the largest mean time, achieved = algorithmic count
+    / time, frac against the measured HBM copy rate or the FP64 issue peak (152 SMs x 32/19
+    lanes per clock x the maximum clock), whichever fraction is larger, and that kernel's
+    recorded DRAM traffic."""
+    qp = qpgen.large_cqp(n=10_000, m=5_000, seed=0)
+    alg = bench.algorithmic(qp)
+    pk = {"hbm_gbs": 6786.2, "sm_max_mhz": 2070.0}
+    prof = {"zx": 0.0005, "q1": 0.0004, "a1": 0.0002, "at": 0.0003, "q2": 0.0003, "pre1": 0.0001,
+            "pre2": 0.0001, "restart": 0.0}
+    r = bench.roofline(prof, qp, pk, "measured", {"zx": 1.5e6, "q1": 2.0e6})
+    assert r["kernel"] == "zx" and r["traffic"] == 1.5e6
+    b, f = alg["zx"]
+    gbs, fp64 = b / 0.5e-6 / 1e9, f / 0.5e-6 / 1e9
+    fp64_peak = 152 * 32 / 19 * 2070e6 / 1e9
+    assert fp64_peak == pytest.approx(529.9, abs=0.1)
+    assert r["alg_bytes"] == b and r["alg_fp64"] == f
+    if fp64 / fp64_peak > gbs / 6786.2:
+        assert r["bound"] == "alu" and r["frac"] == pytest.approx(fp64 / fp64_peak, abs=1e-4)
+        assert r["hbm_frac"] == pytest.approx(gbs / 6786.2, abs=1e-4)
+    else:
+        assert r["bound"] == "hbm" and r["frac"] == pytest.approx(gbs / 6786.2, abs=1e-4)
+    # a slower row pass takes over the line; the HBM bound wins when its fraction is larger
+    prof["a1"] = 0.01
+    r = bench.roofline(prof, qp, pk, "measured", None)
+    assert r["kernel"] == "a1" and r["traffic"] is None
+    b, f = alg["a1"]
+    assert (r["bound"] == "hbm") == (b / 1e-5 / 1e9 / 6786.2 >= f / 1e-5 / 1e9 / fp64_peak)
