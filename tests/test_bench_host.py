@@ -79,3 +79,24 @@ def test_roofline_takes_the_slowest_kernel_and_the_larger_fraction():
     assert r["kernel"] == "a1" and r["traffic"] is None
     b, f = alg["a1"]
     assert (r["bound"] == "hbm") == (b / 1e-5 / 1e9 / 6786.2 >= f / 1e-5 / 1e9 / fp64_peak)
+
+
+def test_clock_summary_median_and_throttle_reasons():
+    """nvidia-smi rows (index, SM MHz, max SM MHz, power, active mask, hw_slowdown,
+    hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap): the median SM clock, the maximum,
+    and the reasons seen Active at least once ('Not Active' is not a reason; '[N/A]' clocks are
+    skipped)."""
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["unsampled"]
+    na, act = "Not Active", "Active"
+    cs.samples = [
+        ["0", "2070", "2070", "900.1", "0x0", na, na, na, na],
+        ["0", "1980", "2070", "1390.5", "0x4", na, na, na, act],
+        ["0", "[N/A]", "2070", "1000.0", "0x0", na, na, na, na],
+        ["0", "2010", "2070", "1200.0", "0x0", na, na, na, na],
+    ]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2010.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 4
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.samples.append(["0", "1500", "2070", "1400.0", "0x48", na, act, na, na])
+    assert cs.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
