@@ -99,6 +99,7 @@ void orc_qmul(const orc_problem* P, const double* v, double* out) {
   }
 }
 
+/* A v: the linear operator of the constraint Ax in K (Sec. 1), stored as CSR. */
 void orc_amul(const orc_problem* P, const double* v, double* out) {
   for (int64_t i = 0; i < P->m; i++) {
     double s = 0.0;
@@ -107,6 +108,7 @@ void orc_amul(const orc_problem* P, const double* v, double* out) {
   }
 }
 
+/* A^* y: the adjoint (transpose) of A, formed from the same CSR arrays row by row. */
 void orc_atmul(const orc_problem* P, const double* v, double* out) {
   for (int64_t j = 0; j < P->n; j++) out[j] = 0.0;
   for (int64_t i = 0; i < P->m; i++)
