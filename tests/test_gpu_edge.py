@@ -5,7 +5,9 @@ indicator, more rows than columns, a ragged size (n = 257: one 256-row chunk and
 a single row, lam = 0 for the l1 term, and lam|x| plus a box with infinite sides (the dual
 value phi*(-zbar) on an unbounded side).  First iterates to 1e-10 relative, the converged
 objective to 1e-6 with the stopping rule recomputed by the oracle, and one separable problem
-with a closed-form solution (a nonnegative l1 term among others).
+with a closed-form solution (a nonnegative l1 term among others).  Also the run-time controls:
+a time-limit stop (zbar formed at hprqp_get), hprqp_profile, and the dynamic graph's chunk
+length (iters_per_launch).
 """
 import numpy as np
 import pytest
@@ -114,3 +116,56 @@ def test_l1_with_unbounded_sides_closed_form(pkg):
         x, *_ = s.get()
     soft = np.sign(-c) * np.maximum(np.abs(c) - lam, 0)
     np.testing.assert_allclose(x, np.clip(soft / q, L, U), atol=1e-8)
+
+
+def _plain():
+    return qpgen.plain_cqp(n=300, m=150, seed=3, q_rows=30, a_density=0.05, q_density=0.1)
+
+
+def test_time_limit_stops_between_launches_with_a_consistent_zbar(pkg):
+    """time_limit stops the solve after the launch in which it expires; hprqp_get then forms
+    zbar = (xbar - r_z)/sigma from the stored iterate.  With restarts off and sigma fixed the
+    run is compared with the oracle's run of the same length."""
+    qp = _plain()
+    lam = oracle.solve(qp, tol=1e-30, max_iter=1)
+    kw = dict(restart_off=1, sigma_fixed=1)
+    with pkg.Solver(qp, lambda_A=lam.lambda_A, lambda_Q=lam.lambda_Q, time_limit=0.02, **kw) as s:
+        assert s.solve(tol=1e-30, max_iter=10**8) == "time_limit"
+        x, y, z, w, k = s.get()
+    it = k["iters"]
+    assert 0 < it < 10**8 and k["status"] == "time_limit"
+    ref = oracle.solve(qp, tol=1e-30, max_iter=it, lambda_A=lam.lambda_A, lambda_Q=lam.lambda_Q, **kw)
+    assert rel(x, ref.x) <= 1e-8 and rel(y, ref.y) <= 1e-8 and rel(z, ref.z) <= 1e-8, it
+
+
+def test_profile_reports_every_step_kernel_and_leaves_no_solution(pkg):
+    qp = _plain()
+    with pkg.Solver(qp) as s:
+        with pytest.raises(pkg.HPRQPError):
+            s.profile(iters=5)                       # needs a solve first
+        s.solve(tol=1e-30, max_iter=1)
+        prof = s.profile(iters=12)
+        for kind in ("zx", "pre1", "q1", "a1", "at", "pre2", "q2"):
+            assert 0.0 < prof[kind] < 100.0, (kind, prof)
+        with pytest.raises(pkg.HPRQPError):
+            s.get()                                  # the iterate no longer belongs to a solve
+        assert s.solve(tol=1e-8) == "converged"
+
+
+@pytest.mark.parametrize("per", [1, 7])
+def test_iters_per_launch_changes_nothing(pkg, per):
+    """The dynamic graph in chunks of 1 or 7 steps runs the same kernels in the same order as in
+    chunks of 64: identical iterates (fixed schedules: autotune = 0)."""
+    qp = _plain()
+    out = {}
+    for p in (per, 64):
+        with pkg.Solver(qp, autotune=0, fixed_schedule=0, iters_per_launch=p) as s:
+            s.solve(tol=1e-30, max_iter=50)
+            x50, y50, *_ = s.get()
+            assert s.solve(tol=1e-8) == "converged"
+            x, y, z, w, k = s.get()
+            out[p] = (x50, y50, x, y, k["iters"])
+    a, b = out[per], out[64]
+    for u, v in zip(a[:4], b[:4]):
+        assert np.array_equal(u, v)
+    assert a[4] == b[4]
