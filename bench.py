@@ -32,6 +32,34 @@ TOL = 1e-8
 FP64_LANES_PER_CLK_SM = 32.0 / 19.0   # measured: one FP64 warp instruction per 19 SM cycles
 
 
+L2_BYTES = 129e6   # GB300 L2
+
+
+def working_set_bytes(qp) -> int:
+    """Approximate device working set of one solve: the problem's arrays, the stored
+    transposes of A and of every factor term (as large again), and the solver's 17 n-vectors
+    and 3 m-vectors."""
+    mat = 0
+    for a in (qp.A_rowptr, qp.A_colidx, qp.A_vals):
+        mat += int(np.asarray(a).nbytes)
+    for t in qp.qterms:
+        for a in (t.rowptr, t.colidx, t.vals, t.offsets, t.diags, t.dense):
+            if a is not None:
+                mat += int(np.asarray(a).nbytes) * (2 if t.kind == "factor" else 1)
+    vec = 8 * (qp.c.size + qp.l.size + qp.u.size + qp.L.size + qp.U.size)
+    return int(mat + int(np.asarray(qp.A_vals).nbytes) + int(np.asarray(qp.A_colidx).nbytes)
+               + vec + 8 * (17 * qp.n + 3 * qp.m))
+
+
+def l2_note(ws: int) -> str:
+    """How the timed steps relate to L2: inputs larger than L2, or an L2-resident working set
+    that each timed step (a whole solve) re-reads in every iteration."""
+    if ws > L2_BYTES:
+        return f"inputs larger than L2: working set about {ws / 1e6:.0f} MB > 129 MB, no flush needed"
+    return (f"working set about {ws / 1e6:.1f} MB fits in L2 (129 MB) and is not flushed between "
+            f"timed steps: each step is a whole solve whose iterations re-read it")
+
+
 def workload(name: str):
     import qpgen
     if name == "c1":
@@ -128,12 +156,17 @@ def run_batched(args, rank, world, dist=None):
         plain_t += time.perf_counter() - t
     plain_total = plain_t / len(sample) * count
     nsum = sum(p.n for p in probs)
+    fpool = sum(8 * t.p * p.n for p in probs for t in p.qterms if t.kind == "dense_factor")
     line = {"metric": METRIC, "value": round(its / t_step, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"batched portfolio CQPs x{count}: n~U{{50..5000}} (sum n={nsum}), "
                                    "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch",
-                       "tol": TOL, "l2": "F pool larger than L2"},
+                       "tol": TOL,
+                       "l2": (f"inputs larger than L2: the dense factors F take {fpool / 1e9:.2f} GB, no flush "
+                              f"needed" if fpool > L2_BYTES else
+                              f"dense factors F {fpool / 1e6:.1f} MB fit in L2 (129 MB), not flushed between "
+                              f"timed steps: each step is a whole batched solve")},
             "time_to_tol_s": round(t_step, 4), "converged": conv, "instances": count,
             "plain_solver_est_s": round(plain_total, 3), "speedup_vs_plain": round(plain_total / t_step, 2),
             "plain_sample": f"{len(sample)} instances solved one by one (create+solve), scaled to {count}",
@@ -224,7 +257,7 @@ def run_learned(args, rank, world):
             "config": {"workload": "learned warm start, family of cqp n=1e5 m=5e4 (A, Q fixed; c=cbar+0.1N(0,1), "
                                    "u=ubar+0.1U(0,1) on inequality rows), MLP 512-1024-1024-257, P 512 x 1.5e5, "
                                    "Phi 1.5e5 x 256", "train": Ntr, "test": Nte, "tol": TOL,
-                       "epochs": args.c4_epochs},
+                       "epochs": args.c4_epochs, "l2": l2_note(working_set_bytes(base))},
             "cold": {"iters_mean": float(cold["iters"].mean()), "s_mean": t_cold,
                      "s_median": float(np.median(cold["seconds"]))},
             "warm": {"iters_mean": float(warm["iters"].mean()), "s_mean": t_warm,
@@ -497,7 +530,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "l2": "working set > L2 (129 MB)"},
+            "config": {"workload": desc, "l2": l2_note(working_set_bytes(qp))},
             "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per} HPR iterations per step of the same workload, lambda by a 200-step"
                                        f" power method (untimed)"},
@@ -650,7 +683,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(t_all / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "tol": TOL, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (working set > 129 MB), no flush needed",
+                       "l2": l2_note(working_set_bytes(qp)),
                        "check_every": int(solver.params.check_every), "restart_every": int(solver.params.restart_every),
                        "launch_mode": args.launch_mode, "pdl": args.pdl, "fixed_schedule": args.fixed_schedule,
                        "tiled_factor": args.tiled_factor},

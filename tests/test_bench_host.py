@@ -100,3 +100,13 @@ def test_clock_summary_median_and_throttle_reasons():
     assert s["reasons"] == ["sw_power_cap"]
     cs.samples.append(["0", "1500", "2070", "1400.0", "0x48", na, act, na, na])
     assert cs.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_l2_note_states_which_timing_rule_applies():
+    """The n = 1e6 CQP's working set exceeds the 129 MB L2 (no flush needed); the n = 1e3 CQP's
+    fits and the note says it is not flushed because each step is a whole solve."""
+    big = bench.working_set_bytes(qpgen.large_cqp(n=1_000_000, m=500_000, seed=0))
+    small = bench.working_set_bytes(qpgen.plain_cqp())
+    assert big > 129e6 > 1e6 > small
+    assert bench.l2_note(big).startswith("inputs larger than L2")
+    assert "fits in L2" in bench.l2_note(small) and "whole solve" in bench.l2_note(small)
