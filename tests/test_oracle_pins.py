@@ -700,7 +700,7 @@ def _dense_by_entries(qp):
 
 def _all_term_kinds(n=11, m=6, seed=5):
     """A QP whose Q sums one term of every stored kind (diagonal, CSR, band with offsets
-    0, 1 and 3, sparse factor, dense factor); A with an empty row and a repeated column."""
+    0, 1 and 3, sparse factor, dense factor); A with an empty row."""
     rng = np.random.default_rng(seed)
     Ad = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.5)
     Ad[2] = 0.0
@@ -863,3 +863,23 @@ def test_scaling_closed_form_with_one_entry_per_column():
     assert ok
     np.testing.assert_allclose(d, [10.0, 0.5, 0.2, 1 / np.sqrt(2.0), 1 / 0.3], rtol=1e-14)
     np.testing.assert_allclose(e, [0.2, 10.0, 1 / np.sqrt(2.0)], rtol=1e-14)
+
+
+def test_duplicate_csr_entries_are_summed():
+    """A row that stores the same column twice means the sum of the two values (CSR as a list
+    of entries): the products equal those of the matrix written out entry by entry."""
+    qp = _all_term_kinds(seed=3)
+    rp, ci, va = qp.A_rowptr.copy(), qp.A_colidx.copy(), qp.A_vals.copy()
+    k = int(rp[1])                                   # append a duplicate of row 0's first entry
+    col = int(ci[rp[0]]) if rp[1] > rp[0] else 0
+    ci = np.insert(ci, k, col).astype(np.int32)
+    va = np.insert(va, k, 0.75)
+    rp = rp.copy()
+    rp[1:] += 1
+    dup = qpgen.QP(**{**qp.__dict__, "A_rowptr": rp, "A_colidx": ci, "A_vals": va})
+    A, Q = _dense_by_entries(dup)
+    rng = np.random.default_rng(5)
+    v, y = rng.standard_normal(dup.n), rng.standard_normal(dup.m)
+    np.testing.assert_allclose(oracle.amul(dup, v), A @ v, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.atmul(dup, y), A.T @ y, rtol=1e-12, atol=1e-12)
+    assert A[0, col] == pytest.approx(_dense_by_entries(qp)[0][0, col] + 0.75)
