@@ -242,9 +242,10 @@ hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_iter);
  * caller buffers (host or device; any may be NULL) and fills kkt (may be NULL). */
 hprqp_status hprqp_get(hprqp_handle* h, double* x, double* y, double* z, double* w, hprqp_kkt* kkt);
 
-/* Applies one linear operator of the problem to a vector (for tests and benchmarks):
- * op 0: out = A in (in: n, out: m); 1: out = A^T in (in: m, out: n); 2: out = Q in (n -> n).
- * in/out may be host or device pointers. */
+/* Applies one linear operator of problem (1.1) (Sec. 1) to a vector (for tests and
+ * benchmarks): op 0: out = A in (in: n, out: m); 1: out = A^T in (in: m, out: n);
+ * 2: out = Q in (n -> n).  in/out may be host or device pointers; with preconditioning they
+ * are in the original variables. */
 hprqp_status hprqp_apply(hprqp_handle* h, int32_t op, const double* in, double* out);
 
 /* Runs `iters` (>= 1) inner steps of Algorithm 4 from the starting point, with lambda_A,
@@ -322,18 +323,23 @@ typedef struct hprqp_batch hprqp_batch;
  * is ignored). */
 hprqp_status hprqp_batch_create(hprqp_batch** b, int32_t count, const hprqp_problem* probs,
                                 const hprqp_params* params);
-/* Solves every instance to max(eta_p, eta_d, eta_gap) <= tol or max_iter iterations.  Returns
- * HPRQP_OK when all converged, HPRQP_MAX_ITER when some did not, an error status otherwise. */
+/* Runs Algorithm 4 on every instance until its Sec. 4.1 stopping rule,
+ * max(eta_p, eta_d, eta_gap) <= tol, holds or max_iter iterations have run.  Returns HPRQP_OK
+ * when all converged, HPRQP_MAX_ITER when some did not, an error status otherwise. */
 hprqp_status hprqp_batch_solve(hprqp_batch* b, double tol, int64_t max_iter);
-/* Bar iterate and residuals of instance i (any output may be NULL; host or device). */
+/* The bar iterate (xbar, ybar, zbar) of instance i, the output of Algorithm 4, and its
+ * stopping-rule values (Sec. 4.1); any output may be NULL; host or device. */
 hprqp_status hprqp_batch_get(hprqp_batch* b, int32_t i, double* x, double* y, double* z, hprqp_kkt* kkt);
-/* Wall time (seconds) of the last hprqp_batch_solve and the number of kernel launches in it. */
+/* Bookkeeping, with no counterpart in the paper: the wall time (seconds) of the last
+ * hprqp_batch_solve and the number of kernel launches in it; destroy (NULL is a no-op);
+ * the message of the last failure on the batch ("" if none; b = NULL gives the last failure
+ * of hprqp_batch_create in this thread). */
 hprqp_status hprqp_batch_stats(hprqp_batch* b, double* seconds, int64_t* kernel_launches);
 void hprqp_batch_destroy(hprqp_batch* b);
 const char* hprqp_batch_last_error(const hprqp_batch* b);
 
-/* Message of the last failure on this handle ("" if none); h may be NULL for the last
- * failure of hprqp_create in this thread. */
+/* Bookkeeping, with no counterpart in the paper: the message of the last failure on this
+ * handle ("" if none); h may be NULL for the last failure of hprqp_create in this thread. */
 const char* hprqp_last_error(const hprqp_handle* h);
 
 #ifdef __cplusplus
