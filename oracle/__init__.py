@@ -62,7 +62,8 @@ class _Params(C.Structure):
                 ("halpern_total", C.c_int32), ("sigma_golden", C.c_int32), ("restart_off", C.c_int32),
                 ("sigma_fixed", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32), ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("trace_len", C.c_int64), ("trace_x", C.c_void_p), ("trace_y", C.c_void_p),
-                ("trace_R", C.c_void_p), ("trace_sigma", C.c_void_p), ("trace_restart", C.c_void_p)]
+                ("trace_R", C.c_void_p), ("trace_sigma", C.c_void_p), ("trace_restart", C.c_void_p),
+                ("trace_w", C.c_void_p)]
 
 
 class _Result(C.Structure):
@@ -201,6 +202,7 @@ def solve(qp, trace_len: int = 0, x0=None, y0=None, **kw) -> Solution:
     tr = None
     if trace_len > 0:
         tr = {"x": np.zeros((trace_len, qp.n)), "y": np.zeros((trace_len, max(qp.m, 1))),
+              "w": np.zeros((trace_len, qp.n)),
               "R": np.full(trace_len, np.nan), "sigma": np.zeros(trace_len),
               "restart": np.zeros(trace_len, np.int32)}
         p.trace_len = trace_len
@@ -209,6 +211,7 @@ def solve(qp, trace_len: int = 0, x0=None, y0=None, **kw) -> Solution:
         p.trace_R = tr["R"].ctypes.data
         p.trace_sigma = tr["sigma"].ctypes.data
         p.trace_restart = tr["restart"].ctypes.data
+        p.trace_w = tr["w"].ctypes.data
     r = _Result()
     x = np.zeros(qp.n); y = np.zeros(max(qp.m, 1)); z = np.zeros(qp.n); w = np.zeros(qp.n)
     L.orc_solve(P.ref, C.byref(p), C.byref(r), x.ctypes.data, y.ctypes.data, z.ctypes.data, w.ctypes.data)

@@ -14,6 +14,7 @@
  */
 #include "hprqp_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -157,12 +158,21 @@ static double conj_phi(const orc_problem* P, const double* z) {
      piecewise-linear function: the sup is at a finite end point or at 0 when z lies in the
      domain, i.e. z <= lam if L = -inf and z >= -lam if U = +inf.  zbar is a subgradient of
      phi at xbar (eq. (3.1)), so it lies there in exact arithmetic; (xbar - r_z)/sigma can
-     cross the edge by rounding, so an infinite side takes z on its edge (as the pure l1
-     case above, whose conjugate is 0 on [-lam, lam], does). */
+     cross the edge by rounding, so on an infinite side a z within 64 ulps of the edge
+     (relative to max(1, lam)) is taken on the edge (as the pure l1 case above, whose
+     conjugate is 0 on [-lam, lam], does).  A z further out is outside the domain: the
+     conjugate is +inf. */
+  const double edge = 64.0 * DBL_EPSILON * fmax(1.0, P->lambda);
   for (int64_t j = 0; j < P->n; j++) {
     double zj = z[j], Lj = P->L[j], Uj = P->U[j], lam = P->lambda, best = -INFINITY;
-    if (!isfinite(Lj) && zj > lam) zj = lam;
-    if (!isfinite(Uj) && zj < -lam) zj = -lam;
+    if (!isfinite(Lj) && zj > lam) {
+      if (zj - lam > edge) return INFINITY;
+      zj = lam;
+    }
+    if (!isfinite(Uj) && zj < -lam) {
+      if (-lam - zj > edge) return INFINITY;
+      zj = -lam;
+    }
     if (isfinite(Lj)) best = fmax(best, -zj * Lj - lam * fabs(Lj));
     if (isfinite(Uj)) best = fmax(best, -zj * Uj - lam * fabs(Uj));
     if (Lj <= 0.0 && Uj >= 0.0) best = fmax(best, 0.0);
@@ -572,6 +582,8 @@ static int solve_core(const orc_problem* P, const orc_params* prm, orc_result* r
     if (k < prm->trace_len) {
       if (prm->trace_x)
         for (int64_t j = 0; j < n; j++) prm->trace_x[k * n + j] = d ? d[j] * xb[j] : xb[j];
+      if (prm->trace_w)
+        for (int64_t j = 0; j < n; j++) prm->trace_w[k * n + j] = d ? d[j] * wb[j] : wb[j];
       if (prm->trace_y && m > 0)
         for (int64_t i = 0; i < m; i++) prm->trace_y[k * m + i] = e ? e[i] * yb[i] : yb[i];
       if (prm->trace_R) prm->trace_R[k] = R;

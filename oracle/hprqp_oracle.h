@@ -77,6 +77,7 @@ typedef struct {
   double* trace_R;           /* trace_len : R~ (NaN where not evaluated) */
   double* trace_sigma;       /* trace_len : sigma used in the iteration */
   int32_t* trace_restart;    /* trace_len : 1 if the iteration ended with a restart */
+  double* trace_w;           /* trace_len x n : wbar_Q */
 } orc_params;
 
 typedef struct {

@@ -123,8 +123,9 @@ __device__ __forceinline__ double prox_phi(int phi, double r, double L, double U
 // phi^*(-z) contribution of one coordinate (0 * inf = 0 for the box).  For lam|x| + the box,
 // sup over [L, U] of (-z x - lam |x|): a finite end point or 0, given z <= lam where L = -inf
 // and z >= -lam where U = +inf.  zbar from the prox (eq. (3.1)) meets that in exact
-// arithmetic but can cross the edge by rounding, so an infinite side puts z on its edge (the
-// pure l1 term, 0 on [-lam, lam], makes the same assumption).
+// arithmetic but can cross the edge by rounding, so on an infinite side a z within 64 ulps of
+// the edge (relative to max(1, lam)) is put on the edge (the pure l1 term, 0 on [-lam, lam],
+// makes the same assumption); a z further out is outside the domain and gives +inf.
 __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, double U, double lam) {
   if (phi == PHI_L1) return 0.0;
   if (phi == PHI_BOX) {
@@ -133,8 +134,15 @@ __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, dou
     else if (ilt0(z)) t = -U * z;
     return t;
   }
-  if (iisinf(L) && z > lam) z = lam;
-  if (iisinf(U) && z < -lam) z = -lam;
+  const double edge = 64.0 * 2.220446049250313e-16 * fmax(1.0, lam);
+  if (iisinf(L) && z > lam) {
+    if (z - lam > edge) return INFINITY;
+    z = lam;
+  }
+  if (iisinf(U) && z < -lam) {
+    if (-lam - z > edge) return INFINITY;
+    z = -lam;
+  }
   double best = -INFINITY;
   if (!iisinf(L)) best = imax(best, -z * L - lam * iabs(L));
   if (!iisinf(U)) best = imax(best, -z * U - lam * iabs(U));

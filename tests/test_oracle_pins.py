@@ -117,6 +117,29 @@ def test_l1_with_unbounded_sides_closed_form():
     assert s.pobj == pytest.approx(p_star, rel=1e-8)
 
 
+def test_l1_box_conjugate_on_unbounded_sides():
+    """phi*(-z) for lam|x| + the indicator of [L, U] (the Sec. 4.1 dual objective): per
+    coordinate sup over [L, U] of (-z x - lam|x|), finite only for z <= lam where L = -inf and
+    z >= -lam where U = +inf.  A z a few ulps past that edge (rounding of zbar) is taken on the
+    edge; a z further out gives +inf, i.e. the dual value -inf."""
+    lam = 0.5
+    L = np.array([-np.inf, 0.0, -1.0])
+    U = np.array([1.0, np.inf, 2.0])
+    qp = qpgen.from_dense(np.eye(3), np.zeros(3), L=L, U=U, phi="l1_box", lam=lam, q_kind="diag")
+    x = np.zeros(3)
+    z_edge = np.array([lam, -lam, -0.7])
+    # closed form per coordinate: max over the finite end points and 0 (0 lies in every [L, U])
+    expect = -(0.0 + 0.0 + max(0.7 * -1.0 - lam * 1.0, 0.7 * 2.0 - lam * 2.0, 0.0))
+    _, _, d_edge = oracle.eta(qp, x, np.zeros(0), z_edge)
+    assert d_edge == pytest.approx(expect, abs=1e-15)
+    z_ulp = np.array([np.nextafter(lam, 1.0), np.nextafter(-lam, -1.0), -0.7])
+    _, _, d_ulp = oracle.eta(qp, x, np.zeros(0), z_ulp)
+    assert d_ulp == d_edge
+    for z_far in (np.array([lam + 1e-6, -lam, -0.7]), np.array([lam, -lam - 1e-6, -0.7])):
+        _, _, d_far = oracle.eta(qp, x, np.zeros(0), z_far)
+        assert np.isneginf(d_far), d_far
+
+
 def test_lp_special_case_matches_linprog():
     # Q = 0, phi = delta_C: HPR-QP reduces to HPR-LP (Sec. 2.2 remark); compare the
     # optimal value with an LP library (HiGHS through scipy)
@@ -366,6 +389,60 @@ def test_sigma_update_smoothing():
     assert oracle.sigma_update(1e-30, 1e-40, 0.0, 1.0, 0.0, 7.0, False) == pytest.approx(1.0, rel=1e-14)
     # only theta1, theta2 are floored: theta2 = 4e-12 with theta1 floored gives sqrt(4) = 2
     assert oracle.sigma_update(0.0, 4e-12, 0.0, 1.0, 0.0, 7.0, False) == pytest.approx(2.0, rel=1e-12)
+
+
+def _sigma_by_derivative_root(t1, t2, t3, lq):
+    """argmin of f(s) = t1 s + t2/s + s^2 t3/(1 + lq s) (eq. (3.12)) as the root of
+    f'(s) = t1 - t2/s^2 + t3 s (2 + lq s)/(1 + lq s)^2, which increases on s > 0 (f is
+    strictly convex, Sec. 3.3), found by scipy's brentq: independent of the oracle's search."""
+    fp = lambda s: t1 - t2 / s ** 2 + t3 * s * (2.0 + lq * s) / (1.0 + lq * s) ** 2
+    hi = np.sqrt(t2 / t1)          # f'(hi) >= 0: the t3 term is non-negative
+    if fp(hi) == 0.0:
+        return hi
+    lo = hi
+    while fp(lo) > 0.0:
+        lo *= 0.5
+    return so.brentq(fp, lo, hi, xtol=1e-300, rtol=1e-15, maxiter=1000)
+
+
+@pytest.mark.parametrize("seed,q_kind,rank", [(0, "csr", 3), (1, "factor", 2), (2, "csr", 5), (3, "dense_factor", 1)])
+def test_theta_tilde_and_sigma_update_at_every_restart(seed, q_kind, rank):
+    """Algorithm 5 at every restart, recomputed from the traced iterates: theta~ of eq. (3.11)
+    from the bar iterate ubar^{r,tau_r} of the restarting step and the anchor u^{r,0} (the origin
+    for r = 0, then the bar iterate of the previous restart, u^{r+1,0} = ubar^{r,tau_r}), with A and
+    Q dense; the floors on theta~_1, theta~_2; the minimiser of eq. (3.12); beta =
+    exp(-R~_{r,tau_r-1}/R~_{0,tau_0-1}) and the log-linear smoothing with sigma_r.  A wrong
+    anchor (current instead of u^{r,0}) or a sign error in any theta~ term changes sigma_{r+1}."""
+    qp = qpgen.random_small(n=7, m=4, seed=seed, q_kind=q_kind, q_rank=rank, eq_rows=1, box=(-1.0, 1.0))
+    A, Q = D.dense_of(qp)
+    assert np.linalg.matrix_rank(Q) == rank < qp.n   # rank-deficient Q: w lives in Range(Q)
+    K = 800
+    s = oracle.solve(qp, tol=1e-30, max_iter=K, restart_every=1, check_every=K, trace_len=K, scaling=0)
+    tr = s.trace
+    lamA, lamQ = s.lambda_A, s.lambda_Q
+    rest = [k for k in np.nonzero(tr["restart"])[0] if k + 1 < len(tr["sigma"])]
+    assert len(rest) >= 4
+    x0, w0, y0 = np.zeros(qp.n), np.zeros(qp.n), np.zeros(qp.m)
+    R_first = None
+    cross_seen = False
+    for k in rest:
+        xb, wb, yb = tr["x"][k], tr["w"][k], tr["y"][k]
+        dy, dw, dx = yb - y0, wb - w0, xb - x0
+        Atdy = A.T @ dy
+        th1 = lamA * (dy @ dy) + lamQ * (dw @ Q @ dw) - 2.0 * ((Q @ dw) @ Atdy)
+        th2 = dx @ dx
+        th3 = Atdy @ Q @ Atdy
+        cross_seen |= abs((Q @ dw) @ Atdy) > 1e-6 * max(th1, 1e-12)
+        th1, th2 = max(th1, 1e-12), max(th2, 1e-12)
+        s_new = _sigma_by_derivative_root(th1, th2, th3, lamQ)
+        R = tr["R"][k]
+        if R_first is None:
+            R_first = R
+        beta = np.exp(-(R / R_first if R_first > 0 else 0.0))
+        expect = np.exp(beta * np.log(s_new) + (1.0 - beta) * np.log(tr["sigma"][k]))
+        assert tr["sigma"][k + 1] == pytest.approx(expect, rel=1e-12), k
+        x0, w0, y0 = xb, wb, yb
+    assert cross_seen   # the cross term <Q dw, A^* dy> took part in at least one update
 
 
 # ------------------------------------------------------------------ power method (Sec. 4.1)
