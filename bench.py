@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-8 rel-KKT, HPR iters/s, HBM GB/s; batched & learned vs plain GPU"
 UNIT = "HPR iterations/s"
 TOL = 1e-8
-FP64_LANES_PER_CLK_SM = 32.0 / 19.0   # measured: one FP64 warp instruction per 19 SM cycles
 
 
 L2_BYTES = 129e6   # GB300 L2
@@ -114,11 +113,26 @@ def run_batched(args, rank, world, dist=None):
                          f"process on {len(sample)} host cores, {dt:.1f} s"}
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     pkg.build()
-    seed0 = rank * count
+    r = measure_batched(pkg, torch, count, rank * count, args.steps, args.warmup, args.plain_sample, dist)
+    line = {"metric": METRIC, "value": r["hpr_its_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(r["time_to_tol_s"] * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": r.pop("workload"), "tol": TOL, "l2": r.pop("l2")},
+            **{k: v for k, v in r.items() if k not in ("hpr_its_per_s",)},
+            "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batched(pkg, torch, count, seed0, steps, warmup, plain_sample, dist=None):
+    """The batch of `count` portfolio CQPs (seeds seed0.., n from 50 to 5000, m = 11) solved to
+    1e-8 in one persistent launch per solve (warm-up solves first: the first one runs the
+    autotuner), timed with CUDA events on its stream; then the plain single-instance solver on a
+    sample of the same instances (create + solve each), scaled to the batch."""
     probs = portfolio_batch(count, seed0)
     stream = torch.cuda.Stream()
     b = pkg.BatchSolver(probs, stream=stream.cuda_stream)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.solve(tol=TOL)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     its = 0
@@ -129,8 +143,8 @@ def run_batched(args, rank, world, dist=None):
         torch.cuda.synchronize()
         ev0.record(stream)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            st = b.solve(tol=TOL)
+        for _ in range(steps):
+            b.solve(tol=TOL)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -139,41 +153,35 @@ def run_batched(args, rank, world, dist=None):
         its += k["iters"]
         conv += k["status"] == "converged"
     dev_s = ev0.elapsed_time(ev1) / 1e3
-    # replicas: each rank solved its own 4096 instances; slowest rank's time, all ranks' iterations
-    t_all, its_all = aggregate(dist, max(dev_s, wall), float(its) * args.steps, "cuda")
-    t_step = t_all / args.steps
-    its = its_all / args.steps
-    # the plain single-instance solver on a sample of the same instances (create + solve each)
-    sample = list(range(0, count, max(1, count // args.plain_sample)))[:args.plain_sample]
-    plain_t, plain_its = 0.0, 0
+    # replicas: each rank solved its own instances; slowest rank's time, all ranks' iterations
+    t_all, its_all = aggregate(dist, max(dev_s, wall), float(its) * steps, "cuda")
+    t_step = t_all / steps
+    its = its_all / steps
+    sample = list(range(0, count, max(1, count // plain_sample)))[:plain_sample]
+    plain_t = 0.0
     for i in sample:
         torch.cuda.synchronize()
         t = time.perf_counter()
         with pkg.Solver(probs[i], stream=stream.cuda_stream) as s:
             s.solve(tol=TOL)
-            plain_its += s.kkt()["iters"]
         torch.cuda.synchronize()
         plain_t += time.perf_counter() - t
     plain_total = plain_t / len(sample) * count
     nsum = sum(p.n for p in probs)
     fpool = sum(8 * t.p * p.n for p in probs for t in p.qterms if t.kind == "dense_factor")
-    line = {"metric": METRIC, "value": round(its / t_step, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batched portfolio CQPs x{count}: n~U{{50..5000}} (sum n={nsum}), "
-                                   "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch",
-                       "tol": TOL,
-                       "l2": (f"inputs larger than L2: the dense factors F take {fpool / 1e9:.2f} GB, no flush "
-                              f"needed" if fpool > L2_BYTES else
-                              f"dense factors F {fpool / 1e6:.1f} MB fit in L2 (129 MB), not flushed between "
-                              f"timed steps: each step is a whole batched solve")},
-            "time_to_tol_s": round(t_step, 4), "converged": conv, "instances": count,
-            "plain_solver_est_s": round(plain_total, 3), "speedup_vs_plain": round(plain_total / t_step, 2),
-            "plain_sample": f"{len(sample)} instances solved one by one (create+solve), scaled to {count}",
-            "clocks": clocks.summary(), "gpu_launches": args.steps, "cpu_baseline": cpu}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    sched = b.stats()
     b.close()
+    return {"workload": f"batched portfolio CQPs x{count}: n~U{{50..5000}} (sum n={nsum}), "
+                        "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch",
+            "l2": (f"inputs larger than L2: the dense factors F take {fpool / 1e9:.2f} GB, no flush needed"
+                   if fpool > L2_BYTES else
+                   f"dense factors F {fpool / 1e6:.1f} MB fit in L2 (129 MB), not flushed between timed steps: "
+                   f"each step is a whole batched solve"),
+            "hpr_its_per_s": round(its / t_step, 3), "time_to_tol_s": round(t_step, 4), "converged": conv,
+            "instances": count, "plain_solver_est_s": round(plain_total, 3),
+            "speedup_vs_plain": round(plain_total / t_step, 2),
+            "plain_sample": f"{len(sample)} instances solved one by one (create+solve), scaled to {count}",
+            "clocks": clocks.summary(), "gpu_launches": int(sched["kernel_launches"]) * steps}
 
 
 def run_learned(args, rank, world):
@@ -347,17 +355,12 @@ class ClockSampler:
 TILE_W = 25600   # entries of x (or t) per shared-memory tile in the tiled factor products
 
 
-def algorithmic(qp, tiled=False):
-    """Algorithmic HBM bytes and FP64 instructions per launch of each kernel kind (one
-    non-checking inner step; vectors counted once per pass, CSR at 12 B/nnz + 4 B/row,
-    band at 8 B per stored diagonal entry).  tiled: the factor terms run as shared-memory
-    tiled products (10 B per entry, per-tile partial sums of B x, u = B^T t tile by tile),
-    all inside the pre-pass group, and the row pass only adds u."""
-    n, m = qp.n, qp.m
-    nnzA = int(qp.A_rowptr[-1]) if m else 0
-    q_bytes = 0
-    q_flops = 0
-    fac_nnz = 0
+def _q_terms(qp, tiled):
+    """HBM bytes and FP64 operations of one row pass over Q's stored terms (CSR 12 B/entry +
+    4 B/row, band 8 B per stored diagonal entry, dense factors 8 B/entry), and the factor
+    entries that a pre-pass handles."""
+    n = qp.n
+    q_bytes = q_flops = fac_nnz = 0
     for t in qp.qterms:
         if t.kind == "dia":
             q_bytes += 8 * len(t.offsets) * n
@@ -374,14 +377,36 @@ def algorithmic(qp, tiled=False):
         elif t.kind == "factor":
             fac_nnz += int(t.rowptr[-1])
             q_bytes += 12 * int(t.rowptr[-1]) + 4 * n   # B^T pass (rows n)
-            q_flops += int(t.rowptr[-1])
+            q_flops += int(t.rowptr[-1]) + n            # entries, and adding the term to the row
         elif t.kind == "dense_factor":
             q_bytes += 8 * t.p * n
             q_flops += t.p * n
         elif t.kind == "qap":
-            q_bytes += 8 * n            # the product formed by cuBLAS before the pass, added in it
+            q_bytes += 8 * n            # the product formed before the pass, added in it
+            q_flops += n
+    return q_bytes, q_flops, fac_nnz
+
+
+def algorithmic(qp, tiled=False):
+    """Algorithmic HBM bytes and FP64 operations (lane instructions) per launch of each kernel
+    kind of a plain inner step: every vector counted once per pass, the stored operators as in
+    _q_terms; tiled: the factor terms run as shared-memory tiled products (10 B per entry,
+    per-tile partial sums of B x, u = B^T t tile by tile), all inside the pre-pass group, and
+    the row pass only adds u.  ath / prew / q2h are the fused passes that end a plain step of
+    the fixed-schedule graph (they replace at / pre2 / q2 and the next step's zx)."""
+    n, m = qp.n, qp.m
+    nnzA = int(qp.A_rowptr[-1]) if m else 0
+    q_bytes, q_flops, fac_nnz = _q_terms(qp, tiled)
     pre_bytes = 12 * fac_nnz + 4 * sum(t.p + 1 for t in qp.qterms if t.kind == "factor")
     pre_flops = fac_nnz
+    qap_bytes = qap_flops = 0
+    for t in qp.qterms:
+        if t.kind == "qap":
+            # Ahat X (d^3 FMAs), then [T1 | S | X] [Bhat; -X; -T] (3 d^3): the four d x d
+            # matrices, x twice, T1 written and read, the result written
+            d = int(round(np.sqrt(n)))
+            qap_bytes += 8 * 9 * d * d
+            qap_flops += 4 * d ** 3
     if tiled:
         pre_bytes, pre_flops = 0, 0
         for t in qp.qterms:
@@ -392,42 +417,104 @@ def algorithmic(qp, tiled=False):
             # once per tile of t and read back for every tile after the first (x: below)
             pre_bytes += 20 * nnz + 16 * kb * t.p + 8 * t.p + 8 * n * (2 * kt - 1)
             pre_flops += 2 * nnz + kb * t.p + (kt - 1) * n
+    pre_bytes += qap_bytes
+    pre_flops += qap_flops
     HA = m > 0
     zx_vec = (15 if HA else 11) if qp.qterms else 8
-    zx_out = 6 if HA else 5
+    zx_out = 7 if HA else 6
     out = {
+        # x, w, Qw, A^*y: Halpern (3 each); g (2), r_z, what, wbar_{1/2} (2)
         "zx": (8 * n * (zx_vec + zx_out), 18 * n),
         "pre1": (pre_bytes + 8 * n, pre_flops),
-        "q1": (q_bytes + 8 * n * (1 + 3 + 1), q_flops + 3 * n),
+        # Q wbar_{1/2}; reads wbar_{1/2}, Q w, what; writes v = what + sigma (Q w - Q wbar_{1/2})
+        "q1": (q_bytes + 8 * n * 4, q_flops + 2 * n),
         "a1": (12 * nnzA + 4 * m + 8 * n + 8 * m * 6, nnzA + 6 * m),
         "at": (12 * nnzA + 4 * n + 8 * m + 8 * n * 4, nnzA + 2 * n),
         "pre2": (pre_bytes + 8 * n, pre_flops),
         "q2": (q_bytes + 8 * n * 2, q_flops),
+        # A^T ybar; reads A^*y, A^*y0, wbar_{1/2}, w, w0; writes A^*y, w; wbar (2), Halpern (3 + 3)
+        "ath": (12 * nnzA + 4 * n + 8 * m + 8 * n * 7, nnzA + 8 * n),
+        "prew": (pre_bytes + 8 * n, pre_flops),
+        # Q w; reads w, what, x0, A^*y, c, L, U; writes Q w, what, wbar_{1/2}; x Halpern (2),
+        # g (2), r_z, what, wbar_{1/2} (2)
+        "q2h": (q_bytes + 8 * n * 10, q_flops + 8 * n),
     }
     return out
 
 
-def roofline(prof, qp, pk, pk_src, traffic, tiled=False):
+def iteration_bytes(qp):
+    """Algorithmic HBM bytes of one HPR iteration by the per-iteration count of the hot-path
+    scope (each stored operator read once per application: A and A^T, Q twice; row pointers;
+    26 n-vector and 8 m-vector FP64 passes):
+    12 (nnz A + nnz A^T) + 2 bytes(Q) + 4 (2m + 2n) + 8 (26 n + 8 m)."""
+    n, m = qp.n, qp.m
+    nnzA = int(qp.A_rowptr[-1]) if m else 0
+    qb = 0
+    for t in qp.qterms:
+        if t.kind == "dia":
+            qb += 8 * len(t.offsets) * n
+        elif t.kind == "diag":
+            qb += 8 * n
+        elif t.kind == "csr":
+            qb += 12 * int(t.rowptr[-1])
+        elif t.kind == "factor":
+            qb += 24 * int(t.rowptr[-1]) + 4 * (t.p + 1)   # B and B^T
+        elif t.kind == "dense_factor":
+            qb += 16 * t.p * n
+        elif t.kind == "qap":
+            qb += 8 * 4 * int(round(np.sqrt(n))) ** 2
+    return 24 * nnzA + 2 * qb + 4 * (2 * m + 2 * n) + 8 * (26 * n + 8 * m)
+
+
+def fp64_peak(pk):
+    """FP64 lane operations per second of the whole GPU: the issue rate measured now by the
+    library's probe (hprqp_fp64_rate: full-warp FP64 FMA, lanes per SM clock) x SMs x the
+    maximum SM clock.  Returns (G ops/s, lanes per clock per SM, source)."""
+    import paper_2507_02470_gb300 as pkg
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    r = max((pkg.fp64_rate(0, 32) for _ in range(3)), key=lambda d: d["lanes_per_clk"])
+    clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    g = props.multi_processor_count * r["lanes_per_clk"] * clk / 1e9
+    return g, r["lanes_per_clk"], (f"measured in this run: hprqp_fp64_rate {r['lanes_per_clk']:.4f} lanes/clk/SM "
+                                   f"x {props.multi_processor_count} SMs x {clk / 1e6:.0f} MHz max clock "
+                                   f"(probe at {r['sm_mhz']:.0f} MHz)")
+
+
+def roofline(prof, qp, pk, pk_src, traffic, tiled=False, iter_s=None, fp64=None):
+    """Roofline of the dominant kernel (the longest mean CUDA-event duration over plain steps)
+    by its algorithmic bytes and FP64 operations per launch, against the measured HBM copy rate
+    and the FP64 issue peak; plus the whole iteration by iteration_bytes() over the measured
+    time per iteration (iter_s)."""
     alg = algorithmic(qp, tiled)
-    name = max((k for k in prof if k in alg and prof[k] > 0), key=lambda k: prof[k])
+    kinds = [k for k in prof if k in alg and prof[k] > 0]
+    if prof.get("q2h", 0) > 0:
+        # fused steps: a plain step runs pre1, q1, a1, ath, prew, q2h; zx, at, pre2 and q2 run
+        # only around the R~ and stopping tests (about one step in ten)
+        kinds = [k for k in kinds if k in ("pre1", "q1", "a1", "ath", "prew", "q2h")]
+    name = max(kinds, key=lambda k: prof[k])
     ms = prof[name]
     b, f = alg[name]
     gbs = b / (ms * 1e-3) / 1e9
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    fp64_peak = 152 * FP64_LANES_PER_CLK_SM * clk / 1e9       # G FP64 instr/s
-    fp64 = f / (ms * 1e-3) / 1e9
-    frac_h, frac_a = gbs / hbm, fp64 / fp64_peak
+    fp64_g, lanes, fp64_src = fp64 if fp64 else (float("nan"), float("nan"), "not measured")
+    ops = f / (ms * 1e-3) / 1e9
+    frac_h, frac_a = gbs / hbm, ops / fp64_g
     if frac_a > frac_h:
-        r = {"bound": "alu", "achieved": round(fp64, 2), "peak": round(fp64_peak, 2), "unit": "G FP64 instr/s",
+        r = {"bound": "alu", "achieved": round(ops, 2), "peak": round(fp64_g, 2), "unit": "G FP64 ops/s",
              "frac": round(frac_a, 4), "hbm_frac": round(frac_h, 4)}
     else:
         r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(frac_h, 4),
              "alu_frac": round(frac_a, 4)}
-    r.update({"kernel": name, "ms_per_launch": round(ms, 5), "alg_bytes": int(b), "alg_fp64": int(f),
-              "peak_source": f"hbm {pk_src}; fp64 derived (152 SMs x 32/19 lanes/clk x max clock)",
-              "traffic": traffic.get(name) if traffic else None,
+    tr = traffic.get(name) if traffic else None
+    r.update({"traffic": tr, "kernel": name, "ms_per_launch": round(ms, 5), "alg_bytes": int(b), "alg_fp64": int(f),
+              "peak_source": f"hbm {pk_src} (MEASURED_PEAKS.json, of measured); fp64 {fp64_src}",
               "all_kernels_ms": {k: round(v, 5) for k, v in prof.items() if v > 0}})
+    if iter_s:
+        ib = iteration_bytes(qp)
+        r["iteration"] = {"alg_bytes": int(ib), "us": round(iter_s * 1e6, 2),
+                          "achieved_gbs": round(ib / iter_s / 1e9, 1),
+                          "hbm_frac": round(ib / iter_s / 1e9 / hbm, 4)}
     return r
 
 
@@ -560,6 +647,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--extensions", type=int, default=1,
+                    help="1: the default line also measures the batched form (4096 portfolio QPs in one "
+                         "launch against the plain solver) as its 'batched' key; 0: skip")
     ap.add_argument("--launch-mode", type=int, default=0,
                     help="0 conditional CUDA graph (default), 1 flat graph, 2 stream launches (for profilers)")
     ap.add_argument("--pdl", type=int, default=1,
@@ -642,7 +732,9 @@ def main():
     prof = solver.profile(iters=40)
     pk, pk_src = peaks()
     nfac = sum(1 for t in qp.qterms if t.kind == "factor")
-    roof = roofline(prof, qp, pk, pk_src, traffic_table(args.workload), tiled=nfac > 0 and kk["tiled_terms"] == nfac)
+    iter_s = statistics.median((k["solve_seconds"] - k["power_seconds"]) / k["iters"] for k in kkts)
+    roof = roofline(prof, qp, pk, pk_src, traffic_table(args.workload), tiled=nfac > 0 and kk["tiled_terms"] == nfac,
+                    iter_s=iter_s, fp64=fp64_peak(pk))
 
     # end to end through the C ABI with host buffers: create (H2D), solve, get (D2H)
     host = {k: (torch.from_numpy(np.ascontiguousarray(v)).pin_memory() if isinstance(v, np.ndarray) else v)
@@ -674,6 +766,15 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "note": "hprqp_create from host arrays + solve + hprqp_get, per solve"}
 
+    # the batched form against the plain solver (row a10 of the hot path), compact
+    batched = None
+    if args.extensions:
+        solver.close()
+        r = measure_batched(pkg, torch, args.c3_count, rank * args.c3_count, 1, 1, args.plain_sample, dist)
+        batched = {k: r[k] for k in ("instances", "converged", "time_to_tol_s", "hpr_its_per_s",
+                                     "plain_solver_est_s", "speedup_vs_plain", "plain_sample", "gpu_launches")}
+        batched["workload"] = r["workload"]
+        batched["timing"] = "one warm-up solve (it runs the autotuner), then one timed solve of the whole batch"
     if rank == 0:
         cpu = None
         if not args.no_cpu:
@@ -697,6 +798,8 @@ def main():
             "clocks": clocks.summary(), "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         }
+        if batched:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
     solver.close()
     if dist:

@@ -57,7 +57,8 @@ typedef enum hprqp_qkind {
   HPRQP_Q_QAP = 6            /* Q vec(X) += vec(Ahat X Bhat - S X - X T) for d x d X with
                                 n = d^2, vec(X)[i + j d] = X[i][j] (the QAP relaxation of
                                 Sec. 4.5): p = d, dense = Ahat, Bhat, S, T (symmetric d x d,
-                                4 d^2 values one after another); applied with cuBLAS DGEMMs;
+                                4 d^2 values one after another); applied as two FP64
+                                contractions, Ahat X then [Ahat X | S | X][Bhat; -X; -T];
                                 at most one such term; not with launch_mode 3 */
 } hprqp_qkind;
 
@@ -161,6 +162,18 @@ typedef struct hprqp_params {
                                 shared-memory tiles; 2: every factor that fits (n up to 64
                                 tiles of 25,600 columns, p up to 8 tiles); 0: never.  Not with
                                 launch_mode 3.  Sums in another order (rounding only) */
+  int32_t fused_steps;       /* 1 (default; fixed-schedule graph, Q and A present): a plain step
+                                followed by a Halpern step ends with two fused passes, A^T ybar
+                                with the Halpern update of (w_Q, A^* y), then Q w of the new
+                                iterate with the next step's elementwise pass of eqs. (3.1)-(3.3),
+                                so that step runs no separate elementwise kernel; Q w is then
+                                formed directly instead of by the Halpern recurrence of its
+                                image (rounding only).  0: every step runs all five passes */
+  int32_t factor_inline;     /* factor terms B_f^T B_f without a tiled copy: 1 (default) a thin
+                                factor (sum over B's rows of their squared lengths <= n / 2)
+                                has the inner step's products t = B x formed inside the Q row
+                                pass from B's rows, with no separate pre-pass launch; 2: every
+                                such factor; 0: never.  Sums in another order (rounding only) */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
@@ -204,7 +217,11 @@ enum {
   HPRQP_PROF_Q2 = 6,         /* Q wbar, R~ / stopping sums, controller */
   HPRQP_PROF_RPRE = 7,       /* restart: B_f d, F_g d */
   HPRQP_PROF_RESTART = 8,    /* restart: theta~ of eq. (3.11), Algorithm 5 */
-  HPRQP_PROF_KINDS = 9
+  HPRQP_PROF_ATH = 9,        /* fused: A^T ybar, wbar, then the next Halpern update of w_Q, A^* y */
+  HPRQP_PROF_PREW = 10,      /* fused: B_f w_Q, F_g w_Q of the new iterate */
+  HPRQP_PROF_Q2H = 11,       /* fused: Q w_Q of the new iterate, the next step's Halpern update of
+                                x and eqs. (3.1)-(3.3), controller */
+  HPRQP_PROF_KINDS = 12
 };
 
 typedef struct hprqp_handle hprqp_handle;
@@ -262,10 +279,10 @@ hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms);
 hprqp_status hprqp_history(hprqp_handle* h, hprqp_check* out, int32_t cap, int32_t* count);
 
 /* Allocation-free power method.  The paper has no counterpart to this entry point; it exists
- * for callers that cannot allocate device memory at the moment they need lambda_A: code that
- * runs while a stream is being captured into a CUDA graph (allocations are not allowed then),
- * real-time loops that must not allocate after start-up, and processes whose device memory is
- * owned entirely by another allocator.
+ * for callers that cannot allocate device memory at the moment they need lambda_A: real-time
+ * loops that must not allocate after start-up (an allocation may block), and processes whose
+ * device memory is owned entirely by another allocator (a framework's pool that leaves nothing
+ * for cudaMalloc).
  *
  * Computes lambda_A = safety * lambda_1(A A^*) exactly as hprqp_solve does (same start vector,
  * Rayleigh quotient and stopping rule: relative change <= tol, at most max_iter steps) and
@@ -276,9 +293,10 @@ hprqp_status hprqp_history(hprqp_handle* h, hprqp_check* out, int32_t cap, int32
  * file-scope device array sized for m, n <= HPRQP_NOALLOC_MAX_DIM, which every GPU that loads
  * the library keeps until the process exits (about 3.2 MB).  Larger m or n return
  * HPRQP_INVALID_ARG.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
- * the array; calls that overlap on the GPU race with each other.  The call returns after the
- * estimate has been copied to the host. */
+ * (cudaGetSymbolAddress).  All calls share the array; calls that overlap on the GPU race with
+ * each other.  The call synchronizes `stream` (it copies the row-pointer ends and the
+ * convergence flag to the host), so it cannot be used on a stream that is being captured into a
+ * CUDA graph.  It returns after the estimate has been copied to the host. */
 #define HPRQP_NOALLOC_MAX_DIM 131072
 hprqp_status hprqp_power_noalloc(int64_t m, int64_t n, const int32_t* A_rowptr, const int32_t* A_colidx,
                                  const double* A_vals, const int32_t* AT_rowptr, const int32_t* AT_colidx,
@@ -287,6 +305,24 @@ hprqp_status hprqp_power_noalloc(int64_t m, int64_t n, const int32_t* A_rowptr, 
 
 /* Releases all device memory of the handle.  NULL is ignored. */
 void hprqp_destroy(hprqp_handle* h);
+
+/* Bookkeeping, with no counterpart in the paper: the device memory the handle holds, by the
+ * path it came from.  out[0], out[1]: allocations and bytes obtained through the allocator
+ * hooks of hprqp_params (alloc/free); out[2], out[3]: allocations and bytes obtained with
+ * cudaMalloc (when no hook is set).  Host pointer to 4 int64 values. */
+hprqp_status hprqp_memory_stats(const hprqp_handle* h, int64_t* out);
+
+/* Measurement utility with no counterpart in the paper: the issue rate of one arithmetic
+ * operation on the current device, the roof that bounds this library's FP64 kernels on
+ * GB300.  op: 0 FP64 FMA, 1 FP64 add, 2 FP64 multiply, 3 FP32 FMA (for comparison).
+ * A full wave of 256-thread blocks (all resident at once) runs eight independent chains of
+ * the operation per thread with the first `lanes` (1..32) lanes of each warp active.
+ * Outputs (host pointers): *lanes_per_clk = thread operations per SM clock per SM (from the
+ * blocks' clock64 spans); *sm_mhz = the SM clock during the run (clock64 cycles over the
+ * CUDA-event duration); *ops_per_s = thread operations per second for the whole device.
+ * sm_mhz and ops_per_s may be NULL.  Allocates and frees two small buffers; synchronizes
+ * the device's legacy default stream.  HPRQP_INVALID_ARG for op or lanes out of range. */
+hprqp_status hprqp_fp64_rate(int32_t op, int32_t lanes, double* lanes_per_clk, double* sm_mhz, double* ops_per_s);
 
 /* ------------------------------------------------------------------------------------------
  * Batched solver: many independent instances of eq. (1.1), each run through Algorithm 4 with

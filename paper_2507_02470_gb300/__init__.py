@@ -5,7 +5,8 @@ this package holds its sources (``csrc/``), the build step (``build``) and a thi
 binding (``Solver`` and the raw ``lib()`` entry points).
 """
 from .build import build  # noqa: F401
-from ._lib import (BatchSolver, HPRQPError, Solver, default_params, lib, lib_path,  # noqa: F401
+from ._lib import (BatchSolver, HPRQPError, Solver, default_params, fp64_rate, lib, lib_path,  # noqa: F401
                    STATUS_NAMES)
 
-__all__ = ["build", "Solver", "BatchSolver", "HPRQPError", "default_params", "lib", "lib_path", "STATUS_NAMES"]
+__all__ = ["build", "Solver", "BatchSolver", "HPRQPError", "default_params", "fp64_rate", "lib", "lib_path",
+           "STATUS_NAMES"]

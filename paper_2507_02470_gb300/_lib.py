@@ -48,7 +48,7 @@ class hprqp_params(C.Structure):
                 ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("launch_mode", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32),
                 ("pdl", C.c_int32), ("fixed_schedule", C.c_int32),
-                ("tiled_factor", C.c_int32)]
+                ("tiled_factor", C.c_int32), ("fused_steps", C.c_int32), ("factor_inline", C.c_int32)]
 
 
 class hprqp_kkt(C.Structure):
@@ -105,6 +105,8 @@ SIGNATURES = [
     ("hprqp_set_data", C.c_int, [_vp, _vp, _vp, _vp]),
     ("hprqp_history", C.c_int, [_vp, _vp, _i32, C.POINTER(_i32)]),
     ("hprqp_set_lambda", C.c_int, [_vp, _dbl, _dbl]),
+    ("hprqp_fp64_rate", C.c_int, [_i32, _i32, C.POINTER(_dbl), C.POINTER(_dbl), C.POINTER(_dbl)]),
+    ("hprqp_memory_stats", C.c_int, [_vp, _vp]),
     # learned warm start (include/hprqp_learn.h)
     ("hprqp_gemm_bf16", C.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     ("hprqp_learn_check", C.c_int, []),
@@ -171,17 +173,41 @@ def default_params() -> hprqp_params:
     return p
 
 
+def fp64_rate(op=0, lanes=32):
+    """Issue rate of one arithmetic operation on the current device (hprqp_fp64_rate):
+    op 0 FP64 FMA, 1 FP64 add, 2 FP64 multiply, 3 FP32 FMA.  Returns a dict with the thread
+    operations per SM clock per SM, the SM clock (MHz) during the run and the device-wide
+    thread operations per second."""
+    r, mhz, ops = C.c_double(), C.c_double(), C.c_double()
+    st = lib().hprqp_fp64_rate(int(op), int(lanes), C.byref(r), C.byref(mhz), C.byref(ops))
+    if st != HPRQP_OK:
+        raise HPRQPError(st, "hprqp_fp64_rate failed")
+    return {"lanes_per_clk": r.value, "sm_mhz": mhz.value, "ops_per_s": ops.value}
+
+
+def _torch_cuda() -> bool:
+    try:
+        import torch
+        return bool(torch.cuda.is_available())
+    except Exception:
+        return False
+
+
 class _TorchAllocator:
-    """Routes the library's device allocations through PyTorch's caching allocator."""
+    """Routes the library's device allocations through PyTorch's caching allocator (blocks
+    tied to the handle's stream; the handle synchronizes that stream before it frees them)."""
 
     def __init__(self):
         import torch
 
         self.torch = torch
+        self.count = 0
 
         def _alloc(nbytes, ctx, stream):
             try:
-                return self.torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+                p = self.torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+                self.count += 1
+                return p
             except Exception:
                 return None
 
@@ -200,7 +226,7 @@ class Solver:
     dense); arrays may be numpy (host) or torch CUDA tensors (device).
     """
 
-    def __init__(self, qp, stream=None, torch_alloc=False, **params):
+    def __init__(self, qp, stream=None, torch_alloc=None, **params):
         L = lib()
         self._keep = []
         p = default_params()
@@ -211,6 +237,10 @@ class Solver:
         if stream is not None:
             p.stream = int(stream)
         self._alloc = None
+        # device memory through PyTorch's caching allocator unless the caller says otherwise
+        # (torch_alloc=False: the library's own cudaMalloc path)
+        if torch_alloc is None:
+            torch_alloc = _torch_cuda()
         if torch_alloc:
             self._alloc = _TorchAllocator()
             p.alloc = self._alloc.alloc
@@ -301,6 +331,13 @@ class Solver:
         self._check(lib().hprqp_get(self.h, None, None, None, None, C.byref(k)))
         return k.as_dict()
 
+    def memory_stats(self):
+        """Device memory the handle holds, by path (hprqp_memory_stats)."""
+        out = np.zeros(4, np.int64)
+        self._check(lib().hprqp_memory_stats(self.h, _ptr(out)))
+        return {"hook_allocs": int(out[0]), "hook_bytes": int(out[1]), "cudamalloc_allocs": int(out[2]),
+                "cudamalloc_bytes": int(out[3])}
+
     def history(self, cap=512):
         """The stopping tests of the last solve (oldest first) as a list of dicts."""
         buf = (hprqp_check * cap)()
@@ -316,7 +353,7 @@ class Solver:
         self._check(lib().hprqp_apply(self.h, code, _ptr(v), _ptr(out)))
         return out
 
-    PROFILE_KINDS = ["zx", "pre1", "q1", "a1", "at", "pre2", "q2", "restart_pre", "restart"]
+    PROFILE_KINDS = ["zx", "pre1", "q1", "a1", "at", "pre2", "q2", "restart_pre", "restart", "ath", "prew", "q2h"]
 
     def profile(self, iters=20):
         """Mean per-kernel durations (ms) of `iters` inner steps, timed with CUDA events."""
@@ -372,7 +409,7 @@ class BatchSolver:
     parameters."""
 
     def __init__(self, problems, stream=None, x0=None, y0=None, sigma0=None, lambda_A=None, lambda_Q=None,
-                 **params):
+                 torch_alloc=None, **params):
         L = lib()
         keep = []
 
@@ -396,6 +433,13 @@ class BatchSolver:
             setattr(p, k, v)
         if stream is not None:
             p.stream = int(stream)
+        self._alloc = None
+        if torch_alloc is None:
+            torch_alloc = _torch_cuda()
+        if torch_alloc:   # device memory through PyTorch's caching allocator, as for Solver
+            self._alloc = _TorchAllocator()
+            p.alloc = self._alloc.alloc
+            p.free = self._alloc.free
         self.params = p
         cnt = len(problems)
         arr = (hprqp_problem * cnt)()

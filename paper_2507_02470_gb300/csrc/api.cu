@@ -5,7 +5,6 @@
 // row order) and the SELL and tiled copies (sell_build.cu), pick the SpMV schedule, run the
 // power method of Sec. 4.1, and drive Algorithm 4 through CUDA graphs (solver.cu) whose kernels
 // stop themselves once the device-side controller has set the done flag.
-#include <cublas_v2.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
@@ -45,6 +44,8 @@ struct hprqp_handle {
   cudaGraphExec_t g_iter = nullptr;
   cudaGraphExec_t g_fixed = nullptr;   // fixed-schedule graph of fixed_L steps (conditional mode)
   int fixed_L = 0;
+  int fixed_kernels = 0;          // kernels of one fixed-graph launch without restarts
+  int64_t fixed_steps = 0;        // inner steps run through the fixed graph in this solve
   bool fixed_tried = false;
   cudaGraphExec_t g_pw[2] = {nullptr, nullptr};
   int pw_chunk = 16;
@@ -54,6 +55,8 @@ struct hprqp_handle {
   int last_status = -1;
   bool solved = false;
   int64_t launches = 0;
+  // device memory of the handle by path: the allocator hooks, or cudaMalloc
+  int64_t hook_count = 0, hook_bytes = 0, rt_count = 0, rt_bytes = 0;
   double last_lamA = 0, last_lamQ = 0, last_sigma0 = 1;
   cudaStream_t side = nullptr;   // captures the bodies of the conditional nodes
   bool conditional = false;      // the iteration graph selects step variants on the device
@@ -62,8 +65,6 @@ struct hprqp_handle {
   bool scaled = false;
   std::vector<double> hd, he;
   double *ux = nullptr, *uy = nullptr, *uz = nullptr, *uw = nullptr;
-  void* blas = nullptr;            // cuBLAS handle (QAP term only)
-  void* blas_ws = nullptr;
   // primal HPR methods (Appendix A): state allocated at their first solve
   bool primal_ready = false;
   double *px = nullptr, *ps = nullptr, *py = nullptr, *pv = nullptr, *pt = nullptr;
@@ -132,12 +133,16 @@ static hprqp_status dalloc(hprqp_handle* h, void** p, size_t bytes) {
   if (h->prm.alloc) {
     *p = h->prm.alloc(bytes, h->prm.alloc_ctx, h->stream);
     if (!*p) return fail(h, HPRQP_OOM, "allocator hook returned NULL for %zu bytes", bytes);
+    h->hook_count++;
+    h->hook_bytes += (int64_t)bytes;
   } else {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(h, HPRQP_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
+    h->rt_count++;
+    h->rt_bytes += (int64_t)bytes;
   }
   h->allocs.push_back({*p, bytes});
   return HPRQP_OK;
@@ -357,6 +362,8 @@ extern "C" void hprqp_default_params(hprqp_params* p) {
   p->pdl = 1;
   p->fixed_schedule = 1;
   p->tiled_factor = 1;
+  p->fused_steps = 1;
+  p->factor_inline = 1;
 }
 
 extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
@@ -366,7 +373,6 @@ extern "C" const char* hprqp_last_error(const hprqp_handle* h) {
 static void release(hprqp_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
   if (h->g_iter) cudaGraphExecDestroy(h->g_iter);
   if (h->g_fixed) cudaGraphExecDestroy(h->g_fixed);
   for (auto& g : h->g_pw)
@@ -386,6 +392,15 @@ static void release(hprqp_handle* h) {
 }
 
 extern "C" void hprqp_destroy(hprqp_handle* h) { release(h); }
+
+extern "C" hprqp_status hprqp_memory_stats(const hprqp_handle* h, int64_t* out) {
+  if (!h || !out) return HPRQP_INVALID_ARG;
+  out[0] = h->hook_count;
+  out[1] = h->hook_bytes;
+  out[2] = h->rt_count;
+  out[3] = h->rt_bytes;
+  return HPRQP_OK;
+}
 
 // ------------------------------------------------------------------------------------ autotune
 static int tune_G(hprqp_handle* h, const Csr& M, int grid, double* x, double* y, int fallback) {
@@ -457,19 +472,20 @@ static hprqp_status data_norms(hprqp_handle* h, const std::vector<double>& hc, c
   return HPRQP_OK;
 }
 
-// cuBLAS handle with a fixed workspace (the products are captured into CUDA graphs)
-static hprqp_status blas_init(hprqp_handle* h) {
-  if (h->blas) return HPRQP_OK;
-  cublasHandle_t b;
-  if (cublasCreate(&b) != CUBLAS_STATUS_SUCCESS) return fail(h, HPRQP_CUDA_ERROR, "cublasCreate failed");
-  h->blas = b;
-  const size_t ws = (size_t)32 << 20;
+// Scratch of the QAP term's split contractions (qap.cu): partial tiles and per-tile counters
+static hprqp_status qap_scratch(hprqp_handle* h, QDev& QD) {
+  int dev = 0, sms = 0;
+  CU(h, cudaGetDevice(&dev));
+  CU(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t d = QD.qap_d, tiles_i = (d + 31) / 32;
+  QD.qap_splits = qap_splits(d, sms);
   void* p = nullptr;
-  hprqp_status st = dalloc(h, &p, ws);
-  if (st) return st;
-  h->blas_ws = p;
-  if (cublasSetWorkspace(b, p, ws) != CUBLAS_STATUS_SUCCESS) return fail(h, HPRQP_CUDA_ERROR, "cublasSetWorkspace failed");
-  h->plan.blas = b;
+  hprqp_status st;
+  if ((st = dalloc(h, &p, sizeof(double) * (size_t)QD.qap_splits * d * d))) return st;
+  QD.qap_part = (double*)p;
+  if ((st = dalloc(h, &p, sizeof(unsigned) * (size_t)(tiles_i * tiles_i)))) return st;
+  CU(h, cudaMemsetAsync(p, 0, sizeof(unsigned) * (size_t)(tiles_i * tiles_i), h->stream));
+  QD.qap_count = (unsigned*)p;
   return HPRQP_OK;
 }
 
@@ -793,11 +809,15 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   if (!dia_off.empty()) {
     QD.ndia = (int)dia_off.size();
+    // stored by increasing offset: the main diagonal, if present, comes first (q_local peels it)
+    std::vector<int> ord(dia_off.size());
+    for (size_t k = 0; k < ord.size(); k++) ord[k] = (int)k;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return dia_off[a] < dia_off[b]; });
     std::vector<double> all;
     all.reserve((size_t)QD.ndia * n);
     for (int k = 0; k < QD.ndia; k++) {
-      QD.dia_off[k] = dia_off[k];
-      all.insert(all.end(), dia_vals[k].begin(), dia_vals[k].end());
+      QD.dia_off[k] = dia_off[ord[k]];
+      all.insert(all.end(), dia_vals[ord[k]].begin(), dia_vals[ord[k]].end());
     }
     double* d;
     if ((st = upload(h, &d, all))) return st;
@@ -833,7 +853,7 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     QD.qap_in = qin;
     QD.qap_off = toff;
     toff += n;
-    if ((st = blas_init(h))) return st;
+    if ((st = qap_scratch(h, QD))) return st;
   }
   clk.mark("device problem");
   // ---- tiled copies of large factor terms: their one-vector products gather through shared
@@ -861,12 +881,30 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     }
     if (any) CU(h, tiled_setup());
   }
+  // ---- thin factor terms: the inner step forms (B x)_r inside the Q row pass from row r of B.
+  // The extra gathers per row of Q are sum_r len(r)^2 / n (every entry of B^T's row j re-reads
+  // a whole row of B); at most 1/2 per row the pass saves the pre-pass launch and its latency
+  // (S of the n = 1e6 CQP: 1e4 rows of 3, 0.09 per row)
+  for (int f = 0; f < QD.nfac; f++) {
+    if (QD.tiled[f] || h->prm.factor_inline == 0) continue;
+    const HostCsr& B = facs[f];
+    double sq = 0.0;
+    for (int64_t r = 0; r < B.rows; r++) {
+      const double len = (double)(B.rp[r + 1] - B.rp[r]);
+      sq += len * len;
+    }
+    if (h->prm.factor_inline == 2 || sq <= 0.5 * (double)n) QD.inl[f] = 1;
+    // a SELL-32 copy of B^T packs the few rows that carry entries of each 256-row chunk into
+    // one warp's slice, so the on-demand products run on full warps instead of one lane per warp
+    if (QD.inl[f] && h->prm.launch_mode != 3 && h->prm.autotune != 0)
+      if ((st = build_sell_rows(h, QD.fact[f]))) return st;
+  }
   QD.tlen = toff;
 
   clk.mark("tiled copies");
   // ---- work vectors (all n- and m-vectors exist; unused ones stay zero)
   double** nvecs[] = {&V.x, &V.w, &V.Qw, &V.ATy, &V.x0, &V.w0, &V.Qw0, &V.ATy0, &V.xb, &V.wb, &V.Qwb, &V.ATyb,
-                      &V.wh, &V.Qwh, &V.v, &V.zb, &V.Qxb};
+                      &V.wh, &V.Qwh, &V.v, &V.zb, &V.Qxb, &V.xh};
   for (double** p : nvecs)
     if ((st = zeros(h, p, n))) return st;
   double** mvecs[] = {&V.y, &V.y0, &V.yb};
@@ -963,6 +1001,13 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     for (int f = 0; f < QD.nfac; f++)
       if (!big || QD.fact[f].nnz > big->nnz) big = &QD.fact[f];
     P.gQ = big ? tune_G(h, *big, P.gridN, ain, aout, 1) : 1;
+    // Q's CSR-like parts are only thin factors with SELL copies: their on-demand products decide
+    // the schedule (the bare-SpMV probe cannot see them), the SELL form
+    {
+      bool only_inl = QD.nfac > 0 && !QD.csr.rows;
+      for (int f = 0; f < QD.nfac; f++) only_inl = only_inl && (QD.tiled[f] || (QD.inl[f] && QD.fact[f].soff));
+      if (only_inl && h->prm.autotune == 1) P.gQ = -1;
+    }
     bool untiled = false;   // the probe below runs the one-vector pre-pass, which skips tiled terms
     for (int f = 0; f < QD.nfac; f++) untiled = untiled || !QD.tiled[f];
     if (QD.nfac > 0 && h->prm.autotune == 1 && untiled) {
@@ -987,6 +1032,8 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     CU(h, cudaStreamSynchronize(h->stream));
     CU(h, cudaGetLastError());
     CU(h, plan_plain_grids(a, P, sms));
+    // plain steps of the fixed-schedule graph end with the fused passes (need Q and A)
+    P.fuse = (h->prm.fused_steps != 0 && QD.present() && m > 0) ? 1 : 0;
   }
   clk.mark("autotune");
   return HPRQP_OK;
@@ -1126,7 +1173,8 @@ static void build_fixed(hprqp_handle* h) {
     if (attempt == 1 && !h->prm.pdl) break;
     h->plan.pdl = attempt == 0 && h->prm.pdl ? 1 : 0;
     cudaGraph_t g;
-    if (build_fixed_graph(h->args, h->plan, h->stream, h->side, (int)L, (int)re, (int)ce, &g) != cudaSuccess) {
+    if (build_fixed_graph(h->args, h->plan, h->stream, h->side, (int)L, (int)re, (int)ce, &g, &h->fixed_kernels) !=
+        cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -1600,6 +1648,7 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   const bool HQ = a.Q.present(), HA = h->m > 0;
   CU(h, cudaSetDevice(h->dev));
   h->launches = 0;
+  h->fixed_steps = 0;
   // ---- lambda_A >= lambda_1(AA^*), lambda_Q >= lambda_1(Q) (Sec. 4.1)
   double lamA = 0.0, lamQ = 0.0;
   if (HA) {
@@ -1630,7 +1679,8 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   if (h->g_fixed && max_iter >= h->fixed_L) {
     for (; max_iter - k0 >= h->fixed_L; k0 += h->fixed_L) {
       CU(h, cudaGraphLaunch(h->g_fixed, h->stream));
-      h->launches += 1;
+      h->launches += h->fixed_kernels;
+      h->fixed_steps += h->fixed_L;
       CU(h, cudaMemcpyAsync(&h->hflags[0], &h->dctrl->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
       CU(h, cudaStreamSynchronize(h->stream));
       if (h->hflags[0]) return finish_solve(h, t0, t1, lamA, lamQ, sigma, false);
@@ -1698,9 +1748,10 @@ static hprqp_status finish_solve(hprqp_handle* h, std::chrono::steady_clock::tim
   K.lambda_Q = lamQ;
   K.solve_seconds = std::chrono::duration<double>(t2 - t0).count();
   K.power_seconds = std::chrono::duration<double>(t1 - t0).count();
-  // conditional graph and stream launches: only the variants taken ran kernels
+  // conditional graph and stream launches: only the variants taken ran kernels (the fixed graph's
+  // launches were counted as launched, restarts apart)
   if (h->conditional || h->prm.launch_mode == 2)
-    h->launches += C.k * kernels_per_step(a) + C.r * kernels_per_restart(a);
+    h->launches += std::max<int64_t>(0, C.k - h->fixed_steps) * kernels_per_step(a) + C.r * kernels_per_restart(a);
   K.kernel_launches = h->launches;
   K.status = status;
   // tolerance ladder: iterations and time (power method + device time since the first step)
@@ -1759,6 +1810,7 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
   int cnt_all[HPRQP_PROF_KINDS] = {0};
   cudaError_t err = cudaSuccess;
   Ctrl& C = *h->hctrl;
+  bool k1 = true;   // false: the previous step's fused pass ran this step's k_zx
   for (int32_t i = 0; i < iters && err == cudaSuccess; i++) {
     // the variant the device controller would select for this step
     const int var = C.done ? 3 : C.ttest ? 2 : C.rtest ? 1 : 0;
@@ -1769,7 +1821,18 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
       cudaEventCreate(&e[0]);
       cudaEventCreate(&e[1]);
     }
-    err = launch_step_var(h->args, h->plan, h->stream, var, ev);
+    // as in the fixed-schedule graph: a plain step that is not the last one profiled ends with
+    // the fused passes, for the variant the controller will give the next step (no restart can
+    // follow a plain step: k and t advance by one)
+    int fuse_next = -1;
+    if (h->plan.fuse && var == 0 && i + 1 < iters) {
+      const long long k2 = C.k + 2;
+      const bool nr = !C.restart_off && k2 % C.restart_every == 0;
+      const bool nt = k2 % C.check_every == 0 || k2 >= C.max_iter;
+      fuse_next = nt ? 2 : nr ? 1 : 0;
+    }
+    err = launch_step_fused(h->args, h->plan, h->stream, var, k1, fuse_next, ev);
+    k1 = fuse_next < 0;
     if (err == cudaSuccess) err = cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
     if (err == cudaSuccess && C.restart_pending && !C.done) {
@@ -1782,7 +1845,7 @@ extern "C" hprqp_status hprqp_profile(hprqp_handle* h, int32_t iters, double* ms
       if (cudaEventElapsedTime(&t, ev[k][0], ev[k][1]) == cudaSuccess) {
         // step kernels: plain steps (the R~ and stopping-test variants carry extra sums);
         // every step's times are kept for a run without a plain step
-        const bool plain_kind = k < HPRQP_PROF_RPRE;
+        const bool plain_kind = k < HPRQP_PROF_RPRE || k >= HPRQP_PROF_ATH;
         if (!plain_kind || var == 0) {
           tot[k] += t;
           cnt[k]++;

@@ -75,16 +75,25 @@ struct QDev {
   const double* dense[kMaxDense] = {nullptr};   // F_g row-major p x n
   int64_t toff[kMaxFac + kMaxDense] = {0};
   // QAP term (Sec. 4.5): Ahat, Bhat, S, T (d x d each, contiguous); its product Q_qap x is
-  // formed before a pass (cuBLAS) into the intermediate buffer at qap_off, like B_f x
+  // formed before a pass (the FP64 contractions of qap.cu) into the intermediate buffer at
+  // qap_off, like B_f x
   int64_t qap_d = 0;
   const double* qap = nullptr;
-  double* qap_tmp = nullptr;    // d x d scratch
+  double* qap_tmp = nullptr;    // d x d scratch (Ahat X)
   double* qap_in = nullptr;     // n scratch (restart difference)
+  double* qap_part = nullptr;   // qap_splits x d x d partial tiles of a split contraction
+  unsigned* qap_count = nullptr;   // one counter per 32 x 32 tile of the result
+  int qap_splits = 1;           // blocks sharing the K range of one tile
   int64_t qap_off = 0;
   // factor terms with a tiled copy: their one-vector products (t = B x, then u = B^T t into
   // the intermediate buffer at uoff) run in the tiled kernels; the two-vector products of a
   // stopping test keep the CSR pre-pass and row pass
   int tiled[kMaxFac] = {0};
+  // thin factor terms (few rows of B meet any row of B^T: sum over B's rows of their squared
+  // lengths is small against n): the inner step's products form (B x)_r from row r of B inside
+  // the row pass that needs it, with no pre-pass; other products (apply, power method, restart
+  // difference) still use the pre-pass
+  int inl[kMaxFac] = {0};
   TiledFac tf[kMaxFac];
   int64_t uoff[kMaxFac] = {0};
   int64_t tfd = 0;              // intermediate rows of the factor and dense terms

@@ -71,6 +71,31 @@ __device__ __forceinline__ int stream_i32(const int* p, const L2Pol& q) {
 }
 #endif
 
+// The value a CSR pass multiplies entry (i, c) with: the c-th element of a vector in memory, or,
+// for a thin factor term B (see QDev::inl), (B x)_c formed from row c of B on demand (entries
+// in stored order), so that the pass needs no pre-pass writing t = B x first.
+struct GatherX {
+  const double* p;
+  __device__ __forceinline__ double operator()(int c, const L2Pol& pol) const { return gather_f64(p + c, pol); }
+};
+struct FacRowX {
+  const int* rp;
+  const int* ci;
+  const double* v;
+  const double* x;
+  __device__ __forceinline__ double operator()(int c, const L2Pol& pol) const {
+    const int b = rp[c], e = rp[c + 1];
+    double s = 0.0;
+    for (int k = b; k < e; k++) s = fma(v[k], gather_f64(x + ci[k], pol), s);
+    return s;
+  }
+};
+
+template <class X>
+constexpr bool kOnDemand = false;
+template <>
+constexpr bool kOnDemand<FacRowX> = true;
+
 // Conditional-node handles set by the controller (graph mode); zero flags when unused.
 struct Handles {
   unsigned long long sw_next = 0;   // SWITCH node of the next inner step
@@ -152,10 +177,9 @@ __device__ __forceinline__ double conj_phi_term(int phi, double z, double L, dou
 
 // ------------------------------------------------------------------------------------ CSR pass
 // Row sums of a chunk of kChunk rows, G lanes per row, into shared rs0/rs1 (add: accumulate).
-template <int G, int NR>
-__device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
-                                                const double* HPRQP_RESTRICT x1, double* rs0, double* rs1,
-                                                bool add) {
+template <int G, int NR, class X0, class X1>
+__device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, const X0& x0, const X1& x1, double* rs0,
+                                                double* rs1, bool add) {
   const int lane = threadIdx.x % G;
   const int grp = threadIdx.x / G;
   constexpr int NG = kThreads / G;
@@ -164,7 +188,17 @@ __device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, cons
   for (int rr = grp; rr < kChunk; rr += NG) {
     const int64_t row = row0 + rr;
     double s0 = 0.0, s1 = 0.0;
-    if (row < M.rows) {
+    if (row < M.rows && kOnDemand<X0>) {
+      // values formed on demand (thin factor): rows of B^T hold a few entries at most, so one
+      // entry at a time, with no unrolled loads to keep in registers
+      const int b = stream_i32(M.rp + row, pol), e = stream_i32(M.rp + row + 1, pol);
+      for (int k = b + lane; k < e; k += G) {
+        const int c = stream_i32(M.ci + k, pol);
+        const double v = stream_f64(M.v + k, pol);
+        s0 = fma(v, x0(c, pol), s0);
+        if (NR == 2) s1 = fma(v, x1(c, pol), s1);
+      }
+    } else if (row < M.rows) {
       const int b = stream_i32(M.rp + row, pol), e = stream_i32(M.rp + row + 1, pol);
       int k = b + lane;
       for (; k + 3 * G < e; k += 4 * G) {
@@ -172,15 +206,13 @@ __device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, cons
                   c2 = stream_i32(M.ci + k + 2 * G, pol), c3 = stream_i32(M.ci + k + 3 * G, pol);
         const double v0 = stream_f64(M.v + k, pol), v1 = stream_f64(M.v + k + G, pol),
                      v2 = stream_f64(M.v + k + 2 * G, pol), v3 = stream_f64(M.v + k + 3 * G, pol);
-        const double a0 = gather_f64(x0 + c0, pol), a1 = gather_f64(x0 + c1, pol), a2 = gather_f64(x0 + c2, pol),
-                     a3 = gather_f64(x0 + c3, pol);
+        const double a0 = x0(c0, pol), a1 = x0(c1, pol), a2 = x0(c2, pol), a3 = x0(c3, pol);
         s0 = fma(v0, a0, s0);
         s0 = fma(v1, a1, s0);
         s0 = fma(v2, a2, s0);
         s0 = fma(v3, a3, s0);
         if (NR == 2) {
-          const double b0 = gather_f64(x1 + c0, pol), b1 = gather_f64(x1 + c1, pol), b2 = gather_f64(x1 + c2, pol),
-                       b3 = gather_f64(x1 + c3, pol);
+          const double b0 = x1(c0, pol), b1 = x1(c1, pol), b2 = x1(c2, pol), b3 = x1(c3, pol);
           s1 = fma(v0, b0, s1);
           s1 = fma(v1, b1, s1);
           s1 = fma(v2, b2, s1);
@@ -197,16 +229,16 @@ __device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, cons
         const double v0 = stream_f64(M.v + k, pol);
         const double v1 = h1 ? stream_f64(M.v + k + G, pol) : 0.0;
         const double v2 = h2 ? stream_f64(M.v + k + 2 * G, pol) : 0.0;
-        const double a0 = gather_f64(x0 + c0, pol);
-        const double a1 = h1 ? gather_f64(x0 + c1, pol) : 0.0;
-        const double a2 = h2 ? gather_f64(x0 + c2, pol) : 0.0;
+        const double a0 = x0(c0, pol);
+        const double a1 = h1 ? x0(c1, pol) : 0.0;
+        const double a2 = h2 ? x0(c2, pol) : 0.0;
         s0 = fma(v0, a0, s0);
         if (h1) s0 = fma(v1, a1, s0);
         if (h2) s0 = fma(v2, a2, s0);
         if (NR == 2) {
-          const double b0 = gather_f64(x1 + c0, pol);
-          const double b1 = h1 ? gather_f64(x1 + c1, pol) : 0.0;
-          const double b2 = h2 ? gather_f64(x1 + c2, pol) : 0.0;
+          const double b0 = x1(c0, pol);
+          const double b1 = h1 ? x1(c1, pol) : 0.0;
+          const double b2 = h2 ? x1(c2, pol) : 0.0;
           s1 = fma(v0, b0, s1);
           if (h1) s1 = fma(v1, b1, s1);
           if (h2) s1 = fma(v2, b2, s1);
@@ -234,10 +266,9 @@ __device__ __forceinline__ void csr_chunk_lanes(const Csr& M, int64_t row0, cons
 // entries are latency-bound in the lane form, which walks index -> gather row after row; here
 // one such round trip serves up to kWin entries of many rows.
 constexpr int kWin = 1024;
-template <int NR>
-__device__ __forceinline__ void csr_chunk_staged(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
-                                                 const double* HPRQP_RESTRICT x1, double* rs0, double* rs1,
-                                                 bool add) {
+template <int NR, class X0, class X1>
+__device__ __forceinline__ void csr_chunk_staged(const Csr& M, int64_t row0, const X0& x0, const X1& x1, double* rs0,
+                                                 double* rs1, bool add) {
   __shared__ int srp[kChunk + 1];
   __shared__ double sv[kWin];
   __shared__ double sx[NR][kWin];
@@ -266,8 +297,8 @@ __device__ __forceinline__ void csr_chunk_staged(const Csr& M, int64_t row0, con
 #pragma unroll
     for (int q = 0; q < kPer; q++) {
       const int i = t + q * kThreads;
-      g0[q] = i < wn ? gather_f64(x0 + c[q], pol) : 0.0;
-      if (NR == 2) g1[q] = i < wn ? gather_f64(x1 + c[q], pol) : 0.0;
+      g0[q] = i < wn ? x0(c[q], pol) : 0.0;
+      if (NR == 2) g1[q] = i < wn ? x1(c[q], pol) : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < kPer; q++) {
@@ -292,12 +323,12 @@ __device__ __forceinline__ void csr_chunk_staged(const Csr& M, int64_t row0, con
   }
 }
 
-// SELL form of the same row sums (G = -1, matrices with a SELL copy, single-term passes only:
-// add must be false): warp w of the block takes slice row0 / 32 + w, each lane one row of it,
-// so every load of indices and values is coalesced and every FMA works on 32 rows.
-template <int NR>
-__device__ __forceinline__ void csr_chunk_sell(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
-                                               const double* HPRQP_RESTRICT x1, double* rs0, double* rs1) {
+// SELL form of the same row sums (G = -1, matrices with a SELL copy): warp w of the block takes
+// slice row0 / 32 + w, each lane one row of it, so every load of indices and values is
+// coalesced and every FMA works on 32 rows.
+template <int NR, class X0, class X1>
+__device__ __forceinline__ void csr_chunk_sell(const Csr& M, int64_t row0, const X0& x0, const X1& x1, double* rs0,
+                                               double* rs1, bool add) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t sl = row0 / 32 + warp;
   if (sl * 32 >= M.rows) return;   // the same for the whole warp
@@ -311,15 +342,13 @@ __device__ __forceinline__ void csr_chunk_sell(const Csr& M, int64_t row0, const
               c2 = stream_i32(M.sci + q + 64, pol), c3 = stream_i32(M.sci + q + 96, pol);
     const double v0 = stream_f64(M.sv + q, pol), v1 = stream_f64(M.sv + q + 32, pol),
                  v2 = stream_f64(M.sv + q + 64, pol), v3 = stream_f64(M.sv + q + 96, pol);
-    const double a0 = gather_f64(x0 + c0, pol), a1 = gather_f64(x0 + c1, pol), a2 = gather_f64(x0 + c2, pol),
-                 a3 = gather_f64(x0 + c3, pol);
+    const double a0 = x0(c0, pol), a1 = x0(c1, pol), a2 = x0(c2, pol), a3 = x0(c3, pol);
     s0 = fma(v0, a0, s0);
     s0 = fma(v1, a1, s0);
     s0 = fma(v2, a2, s0);
     s0 = fma(v3, a3, s0);
     if (NR == 2) {
-      const double b0 = gather_f64(x1 + c0, pol), b1 = gather_f64(x1 + c1, pol), b2 = gather_f64(x1 + c2, pol),
-                   b3 = gather_f64(x1 + c3, pol);
+      const double b0 = x1(c0, pol), b1 = x1(c1, pol), b2 = x1(c2, pol), b3 = x1(c3, pol);
       s1 = fma(v0, b0, s1);
       s1 = fma(v1, b1, s1);
       s1 = fma(v2, b2, s1);
@@ -329,27 +358,42 @@ __device__ __forceinline__ void csr_chunk_sell(const Csr& M, int64_t row0, const
   for (; q < e; q += 32) {
     const int c = stream_i32(M.sci + q, pol);
     const double v = stream_f64(M.sv + q, pol);
-    s0 = fma(v, gather_f64(x0 + c, pol), s0);
-    if (NR == 2) s1 = fma(v, gather_f64(x1 + c, pol), s1);
+    s0 = fma(v, x0(c, pol), s0);
+    if (NR == 2) s1 = fma(v, x1(c, pol), s1);
   }
   if (r >= 0) {
-    rs0[r - row0] = s0;
-    if (NR == 2) rs1[r - row0] = s1;
+    rs0[r - row0] = add ? rs0[r - row0] + s0 : s0;
+    if (NR == 2) rs1[r - row0] = add ? rs1[r - row0] + s1 : s1;
   }
 }
 
+// Row sums of a chunk in the schedule G; a matrix without a SELL copy takes one lane per row
+// where G asks for the SELL form.
+template <int G, int NR, class X0, class X1>
+__device__ __forceinline__ void csr_chunk_x(const Csr& M, int64_t row0, const X0& x0, const X1& x1, double* rs0,
+                                            double* rs1, bool add) {
+  if constexpr (G == 0) {
+    csr_chunk_staged<NR>(M, row0, x0, x1, rs0, rs1, add);
+  } else if constexpr (G == -1) {
+    if (M.soff) csr_chunk_sell<NR>(M, row0, x0, x1, rs0, rs1, add);
+    else csr_chunk_lanes<1, NR>(M, row0, x0, x1, rs0, rs1, add);
+  } else {
+    csr_chunk_lanes<G, NR>(M, row0, x0, x1, rs0, rs1, add);
+  }
+}
 template <int G, int NR>
 __device__ __forceinline__ void csr_chunk(const Csr& M, int64_t row0, const double* HPRQP_RESTRICT x0,
                                           const double* HPRQP_RESTRICT x1, double* rs0, double* rs1, bool add) {
-  if constexpr (G == 0) csr_chunk_staged<NR>(M, row0, x0, x1, rs0, rs1, add);
-  else if constexpr (G == -1) csr_chunk_sell<NR>(M, row0, x0, x1, rs0, rs1);
-  else csr_chunk_lanes<G, NR>(M, row0, x0, x1, rs0, rs1, add);
+  csr_chunk_x<G, NR>(M, row0, GatherX{x0}, GatherX{x1}, rs0, rs1, add);
 }
 
 // All CSR-like parts of Q (explicit CSR and every B_f^T with its intermediate t_f) for a chunk.
+// inl: the pass belongs to an inner step, where a thin factor term (Q.inl) forms t_f = B_f x on
+// demand from B_f's rows (x = x0, and x1 for the second vector) instead of reading t.
 template <int G, int NR>
 __device__ __forceinline__ void q_csr_chunk(const QDev& Q, int64_t row0, const double* x0, const double* x1,
-                                            const double* t0, const double* t1, double* rs0, double* rs1) {
+                                            const double* t0, const double* t1, double* rs0, double* rs1,
+                                            bool inl = false) {
   bool add = false;
   if (Q.csr.rows) {
     csr_chunk<G, NR>(Q.csr, row0, x0, x1, rs0, rs1, false);
@@ -357,7 +401,12 @@ __device__ __forceinline__ void q_csr_chunk(const QDev& Q, int64_t row0, const d
   }
   for (int f = 0; f < Q.nfac; f++) {
     if (NR == 1 && Q.tiled[f]) continue;   // B_f^T t_f formed by the tiled kernels (q_local)
-    csr_chunk<G, NR>(Q.fact[f], row0, t0 + Q.toff[f], NR == 2 ? t1 + Q.toff[f] : nullptr, rs0, rs1, add);
+    if (inl && Q.inl[f]) {
+      const Csr& B = Q.fac[f];
+      csr_chunk_x<G, NR>(Q.fact[f], row0, FacRowX{B.rp, B.ci, B.v, x0}, FacRowX{B.rp, B.ci, B.v, x1}, rs0, rs1, add);
+    } else {
+      csr_chunk<G, NR>(Q.fact[f], row0, t0 + Q.toff[f], NR == 2 ? t1 + Q.toff[f] : nullptr, rs0, rs1, add);
+    }
     add = true;
   }
   if (!add) {
@@ -374,14 +423,23 @@ __device__ __forceinline__ double q_local(const QDev& Q, int64_t j, const double
                                           const double* HPRQP_RESTRICT t, bool with_dense, bool tiled_u) {
   double acc = 0.0;
   if (Q.diag) acc = Q.diag[j] * x[j];
-  for (int k = 0; k < Q.ndia; k++) {
-    const int o = Q.dia_off[k];
-    const double* d = Q.dia + (size_t)k * Q.n;
-    if (o == 0) {
-      acc = fma(d[j], x[j], acc);
-    } else {
-      if (j + o < Q.n) acc = fma(d[j], x[j + o], acc);
-      if (j - o >= 0) acc = fma(d[j - o], x[j - o], acc);
+  if (Q.ndia) {
+    // diagonals stored by increasing offset: the main diagonal, if present, is the first
+    int k = 0;
+    if (Q.dia_off[0] == 0) {
+      acc = fma(Q.dia[j], x[j], acc);
+      k = 1;
+    }
+    for (; k < Q.ndia; k++) {
+      const int o = Q.dia_off[k];
+      const double* d = Q.dia + (size_t)k * Q.n;
+      // entries past either end of the band contribute 0: the operands are selected rather than
+      // the FMAs predicated, so every lane of the warp issues the same two FMAs
+      const bool up = j + o < Q.n, dn = j - o >= 0;
+      const double du = up ? d[j] : 0.0, xu = up ? x[j + o] : 0.0;
+      const double dd = dn ? d[j - o] : 0.0, xd = dn ? x[j - o] : 0.0;
+      acc = fma(du, xu, acc);
+      acc = fma(dd, xd, acc);
     }
   }
   if (Q.qap_d) acc += t[Q.qap_off + j];   // (Q_qap x)_j, formed before the pass
@@ -467,6 +525,7 @@ __device__ __forceinline__ void zx_body(const Args& a) {
     if (ttest) V.zb[j] = (xbar - rz) * inv_sigma;
     // eq. (3.3)
     const double xh = fma(2.0, xbar, -x);
+    V.xh[j] = xh;
     if (HQ) whout[j] = fma(c2, xh, c1 * w);
     else if (HA) V.v[j] = xh;
   }
@@ -480,22 +539,22 @@ __global__ void __launch_bounds__(kThreads) k_zx(Args a) {
 
 // ------------------------------------------------------------------------------------ factor pre-pass
 // t = B_f x for every factor term (G lanes per row), t = F_g x for every dense term (one warp
-// per row).  which: 0 -> x = wbar_{1/2} (and xbar on stopping tests) into t1; 1 -> x = wbar into
-// t2; 2 -> x = A^*ybar - A^*y^{r,0} into t2 (restart); 3 -> x = ain into t1 (apply);
-// 4 -> x = pv into t1 (power method).  TT: 0 one vector, 1 two (stopping test), 2 read C->ttest.
+// per row), x selected by `which` (PreSrc): wbar_{1/2} (and xbar on stopping tests), wbar, the
+// restart difference A^*ybar - A^*y^{r,0}, the apply input, the power-method vector, or w_Q.
+// TT: 0 one vector, 1 two (stopping test), 2 read C->ttest.
 template <int G, int TT>
 __device__ __forceinline__ void pre_body(const Args& a, int which) {
   const Ctrl* HPRQP_RESTRICT C = a.C;
-  if (which <= 2 && C->done) return;
+  if (pre_in_step(which) && C->done) return;
   if (which == 2 && !C->restart_pending) return;
   if (which == 4 && C->pw_done) return;
   const QDev& Q = a.Q;
   const Vec& V = a.V;
   const bool two = (which == 0) && (TT == 1 || (TT == 2 && C->ttest));
-  const double* x0 = which == 0 ? (a.m > 0 ? V.wh : V.wb) : which == 1 ? V.wb : which == 3 ? a.V.ain
-                     : which == 4 ? V.pv : nullptr;
+  const double* x0 = which == PRE_WH ? (a.m > 0 ? V.wh : V.wb) : which == PRE_WB ? V.wb : which == PRE_AIN ? a.V.ain
+                     : which == PRE_PV ? V.pv : which == PRE_W ? V.w : nullptr;
   const double* x1 = V.xb;
-  double* t = (which == 0 || which >= 3) ? V.t1 : V.t2;
+  double* t = pre_into_t1(which) ? V.t1 : V.t2;
   const int nt = Q.nfac + Q.ndense;
   const int64_t ffac = Q.nfac ? Q.toff[Q.nfac - 1] + Q.fac[Q.nfac - 1].rows : 0;  // rows of factor terms
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -511,8 +570,10 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
       int term = 0;
       if (r < ffac)
         while (term + 1 < Q.nfac && r >= Q.toff[term + 1]) term++;
-      // one-vector products of a tiled factor are formed by the tiled kernels
-      const bool mine = r < ffac && !(Q.tiled[term] && !two);
+      // one-vector products of a tiled factor are formed by the tiled kernels; the step's
+      // products of a thin factor are formed inside the row pass (q_csr_chunk)
+      const bool step_src = which == PRE_WH || which == PRE_WB || which == PRE_W;
+      const bool mine = r < ffac && !(Q.tiled[term] && !two) && !(Q.inl[term] && step_src);
       if (mine) {
         const Csr& B = Q.fac[term];
         const int64_t rl = r - Q.toff[term];
@@ -703,9 +764,7 @@ __device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const doub
     C.t = 0;
     C.r++;
   } else {
-    const double i = C.halpern_total ? (double)C.k : (double)C.t;
-    C.ha = 1.0 / (i + 2.0);
-    C.hb = (i + 1.0) / (i + 2.0);
+    halpern_weights(C, C.ha, C.hb);
     C.mode = 1;
     C.t++;
   }
@@ -800,22 +859,27 @@ __device__ __forceinline__ void end_iteration(EndTerms& T, const Args& a, const 
 template <int G, int KIND, int VAR>
 __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
   Ctrl* HPRQP_RESTRICT C = a.C;
-  if (KIND <= K_Q2 && C->done) return;
+  if (step_kind(KIND) && C->done) return;
   if ((KIND == K_POWER_Q || KIND == K_POWER_A || KIND == K_APPLY_AT_P) && C->pw_done) return;
   __shared__ double rs0[kChunk];
   __shared__ double rs1[kChunk];
   const Vec& V = a.V;
   const QDev& Q = a.Q;
   const bool HQ = Q.present(), HA = a.m > 0;
+  // the fused passes belong to a plain step; their VAR is the variant of the next step
+  constexpr bool FUSED = (KIND == K_ATH || KIND == K_Q2H);
   const bool ttest = (KIND <= K_Q2) ? var_ttest<VAR>(C) : false;
   const bool rtest = (KIND <= K_Q2) ? var_rtest<VAR>(C) : false;
-  constexpr bool RED = (VAR != VAR_PLAIN);   // the variant carries reduction code
+  constexpr bool RED = (VAR != VAR_PLAIN) && !FUSED;   // the variant carries reduction code
   const int64_t rows = (KIND == K_A1 || KIND == K_APPLY_A || KIND == K_POWER_A) ? a.m : a.n;
   const int64_t nchunks = (rows + kChunk - 1) / kChunk;
   const double sigma = C->sigma, s = C->s, slA = C->slA, inv_slA = C->inv_slA;
   const int mode = C->mode;
-  const double ha = C->ha, hb = C->hb;
-  const bool last_of_iter = (KIND == K_Q2) || (KIND == K_Q1 && !HA) || (KIND == K_AT && !HQ);
+  double ha = C->ha, hb = C->hb;
+  // the fused passes apply the Halpern step that follows this one (the controller sets the
+  // same weights at the end of this step)
+  if (FUSED) halpern_weights(*C, ha, hb);
+  const bool last_of_iter = (KIND == K_Q2) || (KIND == K_Q2H) || (KIND == K_Q1 && !HA) || (KIND == K_AT && !HQ);
   EndTerms T;
   T.zero();
   double y3[kW3] = {0.0, 0.0, 0.0, 0.0};
@@ -826,10 +890,12 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
     // ---- phase 1: CSR row sums into shared memory
     if (KIND == K_Q1) {
       const double* src = HA ? V.wh : V.wb;
-      if (RED && ttest) q_csr_chunk<G, 2>(Q, row0, src, V.xb, V.t1, V.t1 + Q.tlen, rs0, rs1);
-      else q_csr_chunk<G, 1>(Q, row0, src, nullptr, V.t1, nullptr, rs0, rs1);
+      if (RED && ttest) q_csr_chunk<G, 2>(Q, row0, src, V.xb, V.t1, V.t1 + Q.tlen, rs0, rs1, true);
+      else q_csr_chunk<G, 1>(Q, row0, src, nullptr, V.t1, nullptr, rs0, rs1, true);
     } else if (KIND == K_Q2) {
-      q_csr_chunk<G, 1>(Q, row0, V.wb, nullptr, V.t2, nullptr, rs0, rs1);
+      q_csr_chunk<G, 1>(Q, row0, V.wb, nullptr, V.t2, nullptr, rs0, rs1, true);
+    } else if (KIND == K_Q2H) {
+      q_csr_chunk<G, 1>(Q, row0, V.w, nullptr, V.t2, nullptr, rs0, rs1, true);
     } else if (KIND == K_APPLY_Q) {
       q_csr_chunk<G, 1>(Q, row0, V.ain, nullptr, V.t1, nullptr, rs0, rs1);
     } else if (KIND == K_POWER_Q) {
@@ -841,7 +907,7 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
       csr_chunk<G, 1>(a.A, row0, V.ain, nullptr, rs0, rs1, false);
     } else if (KIND == K_POWER_A) {
       csr_chunk<G, 1>(a.A, row0, V.ptmp, nullptr, rs0, rs1, false);
-    } else if (KIND == K_AT) {
+    } else if (KIND == K_AT || KIND == K_ATH) {
       csr_chunk<G, 1>(a.AT, row0, V.yb, nullptr, rs0, rs1, false);
     } else if (KIND == K_APPLY_AT) {
       csr_chunk<G, 1>(a.AT, row0, V.ain, nullptr, rs0, rs1, false);
@@ -859,8 +925,7 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
         if (RED && ttest) V.Qxb[j] = rs1[threadIdx.x] + q_local(Q, j, V.xb, V.t1 + Q.tlen, true, false);
         if (HA) {
           // v = what + sigma (Q w - Q wbar_{1/2})   (eq. (3.5), second form)
-          const double xh = fma(2.0, V.xb[j], -V.x[j]);
-          V.v[j] = fma(sigma, V.Qw[j] - qwh, xh);
+          V.v[j] = fma(sigma, V.Qw[j] - qwh, V.xh[j]);
           if (RED && rtest) V.Qwh[j] = qwh;
         } else {
           V.Qwb[j] = qwh;  // m = 0: wbar = wbar_{1/2}
@@ -870,6 +935,25 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
         const double qwb = r0 + q_local(Q, j, V.wb, V.t2, true, true);
         V.Qwb[j] = qwb;
         if (RED) end_row(T, a, j, rtest, ttest, HQ, HA, qwb);
+      } else if (KIND == K_Q2H) {
+        // Q w of the new iterate (K_ATH wrote w), then the next step's elementwise pass: the
+        // Halpern step on x with 2 xbar - x = what, eqs. (3.1)-(3.3) as in k_zx
+        const double qw = r0 + q_local(Q, j, V.w, V.t2, true, true);
+        V.Qw[j] = qw;
+        const double x = fma(hb, V.xh[j], ha * V.x0[j]);
+        double g = -V.c[j];
+        g -= qw;
+        g += V.ATy[j];
+        const double rz = fma(sigma, g, x);
+        const double xbar = prox_phi(a.phi, rz, V.L[j], V.U[j], C->tau);
+        const double xh = fma(2.0, xbar, -x);
+        V.xh[j] = xh;
+        V.wh[j] = fma(C->c2, xh, C->c1 * V.w[j]);
+        if (VAR != VAR_PLAIN) {   // the next step evaluates R~ or the stopping rule
+          V.xb[j] = xbar;
+          V.x[j] = x;
+        }
+        if (VAR == VAR_T) V.zb[j] = (xbar - rz) * C->inv_sigma;
       } else if (KIND == K_A1) {
         // Halpern / restart on y, then eq. (3.5)
         double y;
@@ -909,6 +993,13 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
         } else if (RED) {
           end_row(T, a, j, rtest, ttest, HQ, HA, 0.0);
         }
+      } else if (KIND == K_ATH) {
+        // wbar as in K_AT, then the Halpern step of the next iteration on w_Q and A^* y,
+        // u = 1/(i+2) u^{r,0} + (i+1)/(i+2) (2 ubar - u); wbar and A^* ybar stay in registers
+        const double aty = V.ATy[j];
+        const double wb = fma(s, r0 - aty, V.wh[j]);
+        V.ATy[j] = fma(hb, fma(2.0, r0, -aty), ha * V.ATy0[j]);
+        V.w[j] = fma(hb, fma(2.0, wb, -V.w[j]), ha * V.w0[j]);
       } else if (KIND == K_APPLY_Q) {
         V.aout[j] = r0 + q_local(Q, j, V.ain, V.t1, true, true);
       } else if (KIND == K_APPLY_A || KIND == K_APPLY_AT) {
@@ -969,7 +1060,8 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
 template <int G, int KIND, int VAR>
 // plain steps keep six blocks per SM resident (at most 40 registers): their passes are
 // latency-bound gathers, so occupancy matters more than a few extra registers
-__global__ void __launch_bounds__(kThreads, VAR == VAR_PLAIN ? 6 : 1) k_rows(Args a, Handles hd) {
+__global__ void __launch_bounds__(kThreads, (VAR == VAR_PLAIN || KIND == K_ATH || KIND == K_Q2H) ? 6 : 1)
+    k_rows(Args a, Handles hd) {
   pdl_enter();
   rows_body<G, KIND, VAR>(a, hd);
 }
@@ -1131,10 +1223,12 @@ RowKernel row_kernel_q(int kind, int var, int G);
 RowKernel row_kernel_a(int kind, int var, int G);
 RowKernel row_kernel_at(int kind, int var, int G);
 
-// kinds whose CSR pass is one matrix with a SELL copy (A or A^T)
+// kinds whose CSR passes may run from SELL copies (A, A^T, thin factor transposes); a matrix
+// without a copy takes one lane per row in the same pass
 constexpr bool sell_kind(int kind) {
   return kind == K_A1 || kind == K_APPLY_A || kind == K_POWER_A || kind == K_AT || kind == K_APPLY_AT ||
-         kind == K_APPLY_AT_P;
+         kind == K_APPLY_AT_P || kind == K_ATH || kind == K_Q1 || kind == K_Q2 || kind == K_Q2H ||
+         kind == K_APPLY_Q || kind == K_POWER_Q;
 }
 
 template <int KIND>
@@ -1152,7 +1246,15 @@ RowKernel pick_row(int var, int G) {
     case 16: return k_rows<16, KIND, VAR>;                      \
     default: return k_rows<32, KIND, VAR>;                      \
   }
-  if constexpr (KIND > K_Q2) {
+  if constexpr (KIND == K_ATH) {
+    HPRQP_ROW_G(VAR_PLAIN)
+  } else if constexpr (KIND == K_Q2H) {
+    switch (var) {
+      case VAR_PLAIN: { HPRQP_ROW_G(VAR_PLAIN) }
+      case VAR_R: { HPRQP_ROW_G(VAR_R) }
+      default: { HPRQP_ROW_G(VAR_T) }
+    }
+  } else if constexpr (KIND > K_Q2) {
     HPRQP_ROW_G(VAR_PLAIN)
   } else {
     switch (var) {

@@ -1,17 +1,20 @@
 // hprqp_power_noalloc: the power-method estimate of lambda_A without any device allocation.
 //
-// Some callers cannot allocate device memory when they need this estimate: code that runs
-// while a stream is being captured into a CUDA graph (allocation calls are not allowed then),
-// real-time loops that must not allocate after start-up, and processes whose device memory is
-// owned entirely by another allocator.  This entry point therefore keeps its work vectors, its
-// per-block partial sums and its control scalars in one file-scope device array of fixed size;
-// the caller only passes the matrix (and its transpose) and receives the estimate.
+// Some callers cannot allocate device memory when they need this estimate: real-time loops
+// that must not allocate after start-up (an allocation can block on the device or the
+// driver), and processes whose device memory is owned entirely by another allocator (a
+// framework's pool that leaves nothing for cudaMalloc).  This entry point therefore keeps its
+// work vectors, its per-block partial sums and its control scalars in one file-scope device
+// array of fixed size; the caller only passes the matrix (and its transpose) and receives the
+// estimate.
 //
 // The array lives in every GPU that loads the library until the process exits.  Its device
-// address is looked up once per device with cudaGetSymbolAddress (the first call on a device
-// does that look-up, so it should come before any stream capture).  All calls share the array:
-// two calls that overlap on the GPU race with each other.  Every call initialises the parts it
-// reads (control block, start vector) before using them.
+// address is looked up once per device with cudaGetSymbolAddress, by the first call on that
+// device.  All calls share the array: two calls that overlap on the GPU race with each other.
+// Every call initialises the parts it reads (control block, start vector) before using them.
+// The call reads the two row-pointer ends and polls the convergence flag with copies to the
+// host followed by a synchronisation of its stream, so it cannot run on a stream that is being
+// captured into a CUDA graph.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -226,7 +229,11 @@ extern "C" hprqp_status hprqp_power_noalloc(int64_t m, int64_t n, const int32_t*
   const int G = avg < 12 ? 1 : avg < 48 ? 4 : 32;
   double state = 0.0;
   const int64_t chunk = 16;
-  for (int64_t done_iters = 0; done_iters < max_iter + chunk; done_iters += chunk) {
+  // launch rounds of `chunk` steps until the device flag says finished; the kernels stop by
+  // themselves after max_iter steps, so max_iter / chunk + 2 rounds always reach that flag
+  // (written without max_iter + chunk, which overflows for max_iter near INT64_MAX)
+  const int64_t rounds = max_iter / chunk + 2;
+  for (int64_t r = 0; r < rounds; r++) {
     for (int64_t i = 0; i < chunk; i++) {
       cudaError_t e = G == 1 ? na_pass<1>(s, A, AT, gm, gn, ge, m, max_iter, tol, st)
                       : G == 4 ? na_pass<4>(s, A, AT, gm, gn, ge, m, max_iter, tol, st)

@@ -12,8 +12,6 @@
 // stopping rule (Sec. 4.1), empty once done.  In both, the controller in the last block of
 // every step sets the next conditional node with cudaGraphSetConditional, so the host only
 // polls a done flag between launches.
-#include <cublas_v2.h>
-
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -25,7 +23,8 @@
 namespace hprqp {
 
 static RowKernel rowk(int kind, int var, int G) {
-  if (kind == K_Q1 || kind == K_Q2 || kind == K_APPLY_Q || kind == K_POWER_Q) return row_kernel_q(kind, var, G);
+  if (kind == K_Q1 || kind == K_Q2 || kind == K_APPLY_Q || kind == K_POWER_Q || kind == K_Q2H)
+    return row_kernel_q(kind, var, G);
   if (kind == K_A1 || kind == K_APPLY_A || kind == K_POWER_A) return row_kernel_a(kind, var, G);
   return row_kernel_at(kind, var, G);
 }
@@ -65,20 +64,6 @@ static ZxKernel zxk(int var) {
 
 
 // ------------------------------------------------------------------------------------ QAP term
-// out = vec(Ahat X Bhat - S X - X T) for X = reshape(x, d, d) column-major (Sec. 4.5); all
-// four matrices symmetric, so row- and column-major storage coincide.
-static cudaError_t qap_product(const QDev& Q, cublasHandle_t b, const double* x, double* out) {
-  const int d = (int)Q.qap_d;
-  const double *Ah = Q.qap, *Bh = Q.qap + (size_t)d * d, *S = Q.qap + 2 * (size_t)d * d, *T = Q.qap + 3 * (size_t)d * d;
-  const double one = 1.0, zero = 0.0, mone = -1.0;
-  cublasStatus_t st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &one, Ah, d, x, d, &zero, Q.qap_tmp, d);
-  if (st == CUBLAS_STATUS_SUCCESS)
-    st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &one, Q.qap_tmp, d, Bh, d, &zero, out, d);
-  if (st == CUBLAS_STATUS_SUCCESS) st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &mone, S, d, x, d, &one, out, d);
-  if (st == CUBLAS_STATUS_SUCCESS) st = cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, d, d, d, &mone, x, d, T, d, &one, out, d);
-  return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
-}
-
 __global__ void k_qap_diff(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
                            int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -88,20 +73,18 @@ __global__ void k_qap_diff(const double* __restrict__ a, const double* __restric
 cudaError_t launch_qap(const Args& a, const Plan& p, int which, int tt, cudaStream_t s) {
   const QDev& Q = a.Q;
   if (!Q.qap_d) return cudaSuccess;
-  cublasHandle_t b = (cublasHandle_t)p.blas;
-  if (!b || cublasSetStream(b, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorNotReady;
   const Vec& V = a.V;
-  double* t = (which == 0 || which >= 3) ? V.t1 : V.t2;
-  const double* x = which == 0 ? (a.m > 0 ? V.wh : V.wb) : which == 1 ? V.wb : which == 3 ? V.ain : which == 4 ? V.pv
-                                                                                                     : Q.qap_in;
+  double* t = pre_into_t1(which) ? V.t1 : V.t2;
+  const double* x = which == PRE_WH ? (a.m > 0 ? V.wh : V.wb) : which == PRE_WB ? V.wb : which == PRE_AIN ? V.ain
+                    : which == PRE_PV ? V.pv : which == PRE_W ? V.w : Q.qap_in;
   if (which == 2) {
     const int blocks = (int)std::min<int64_t>((a.n + kThreads - 1) / kThreads, 152 * 8);
     k_qap_diff<<<blocks, kThreads, 0, s>>>(V.ATyb, V.ATy0, Q.qap_in, a.n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = qap_product(Q, b, x, t + Q.qap_off);
-  if (e == cudaSuccess && which == 0 && tt != 0) e = qap_product(Q, b, V.xb, t + Q.tlen + Q.qap_off);
+  cudaError_t e = qap_apply(Q, x, t + Q.qap_off, Q.qap_splits, s);
+  if (e == cudaSuccess && which == 0 && tt != 0) e = qap_apply(Q, V.xb, t + Q.tlen + Q.qap_off, Q.qap_splits, s);
   return e;
 }
 
@@ -129,10 +112,12 @@ struct Seq {
   bool pdl;
   bool prev = false;
   cudaError_t e = cudaSuccess;
+  int count = 0;   // kernels launched through this sequence
   template <typename... P, typename... A>
   void operator()(void (*k)(P...), int grid, A&&... args) {
     if (e == cudaSuccess) e = launch_k(pdl && prev, k, grid, s, std::forward<A>(args)...);
     prev = true;
+    count++;
   }
   void other() { prev = false; }
 };
@@ -142,9 +127,13 @@ struct Seq {
 static bool pre_has_work(const Args& a, int which, int tt) {
   if (!a.Q.has_fd()) return false;
   if (a.Q.ndense) return true;
-  for (int f = 0; f < a.Q.nfac; f++)
-    if (!a.Q.tiled[f]) return true;
-  return which == 0 && tt != 0;
+  const bool step = which == PRE_WH || which == PRE_WB || which == PRE_W;
+  bool tiled = false;
+  for (int f = 0; f < a.Q.nfac; f++) {
+    if (!a.Q.tiled[f] && !(step && a.Q.inl[f])) return true;
+    tiled = tiled || a.Q.tiled[f];
+  }
+  return which == PRE_WH && tt != 0 && tiled;
 }
 static int tiled_terms(const Args& a) {
   int c = 0;
@@ -152,10 +141,21 @@ static int tiled_terms(const Args& a) {
   return c;
 }
 
+// Shape of an inner step in the fixed-schedule graph.  k1: the step begins with its own k_zx
+// (false when the step before ran it in K_Q2H); fuse_next >= 0 (plain steps only): the step
+// ends with K_ATH and K_Q2H, which run the elementwise pass of the next step, a step of variant
+// fuse_next; k1_after >= 0: the step ends with the next step's k_zx in that variant.
+struct StepShape {
+  bool k1 = true;
+  int fuse_next = -1;
+  int k1_after = -1;
+  int* kernels = nullptr;   // optional: receives += the number of kernels the step launches
+};
+
 // One inner step in variant `var`; the last kernel of the step receives the handles.  chained:
 // the previous node on s is this library's kernel (its first kernel may then launch early too).
 cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, const Handles& hd,
-                        cudaEvent_t (*ev)[2], bool chained = false) {
+                        cudaEvent_t (*ev)[2], bool chained = false, StepShape sh = StepShape()) {
   const bool HQ = a.Q.present(), HA = a.m > 0, pre = a.Q.has_pre();
   const Handles none;
   const int tt = var == VAR_T ? 1 : var == VAR_RUNTIME ? 2 : 0;
@@ -163,7 +163,7 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   const bool pl = var == VAR_PLAIN && p.wZX > 0;
   Seq L{s, p.pdl != 0 && !ev};
   L.prev = chained;
-  // the products that precede a Q pass: CSR pre-pass, tiled factor kernels, QAP DGEMMs
+  // the products that precede a Q pass: CSR pre-pass, tiled factor kernels, QAP contractions
   auto pre_pass = [&](int which, int ptt) -> cudaError_t {
     if (pre_has_work(a, which, ptt)) L(prek(p.gPre, ptt), p.gridPre, a, which);
     if (L.e != cudaSuccess) return L.e;
@@ -172,15 +172,18 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
       const cudaError_t te = launch_tiled(a, p, which, ptt, s, &nt);
       if (te != cudaSuccess) return te;
       if (nt) L.prev = true;
+      L.count += nt;
     }
     if (a.Q.qap_d) {
       L.other();
       const cudaError_t qe = launch_qap(a, p, which, ptt, s);
       if (qe != cudaSuccess) return qe;
+      L.count += 2 + (which == PRE_WH && ptt != 0 ? 2 : 0);
     }
     return cudaSuccess;
   };
-  TIMED(0, L(zxk(var), pl ? p.wZX : p.gridE, a));
+  const bool fused = sh.fuse_next >= 0 && var == VAR_PLAIN && HQ && HA;
+  if (sh.k1) TIMED(0, L(zxk(var), pl ? p.wZX : p.gridE, a));
   if (HQ) {
     if (pre) {
       if (ev) cudaEventRecord(ev[1][0], s);
@@ -192,6 +195,19 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
   }
   if (HA) {
     TIMED(3, L(rowk(K_A1, var, p.gA), pl ? p.wA1 : p.gridM, a, none));
+    if (fused) {
+      TIMED(9, L(rowk(K_ATH, VAR_PLAIN, p.gAT), p.wATH, a, none));
+      if (pre) {
+        if (ev) cudaEventRecord(ev[10][0], s);
+        const cudaError_t pe = pre_pass(PRE_W, 0);
+        if (pe != cudaSuccess) return pe;
+        if (ev) cudaEventRecord(ev[10][1], s);
+      }
+      TIMED(11, L(rowk(K_Q2H, sh.fuse_next, p.gQ), p.wQ2H, a, hd));
+      if (sh.kernels) *sh.kernels += L.count;
+      if (L.e != cudaSuccess) return L.e;
+      return cudaGetLastError();
+    }
     TIMED(4, L(rowk(K_AT, var, p.gAT), pl ? p.wAT : p.gridN, a, HQ ? none : hd));
     if (HQ) {
       if (pre) {
@@ -207,6 +223,8 @@ cudaError_t launch_step(const Args& a, const Plan& p, cudaStream_t s, int var, c
     // neither operator: the controller still needs its (empty-operator) pass
     TIMED(4, L(rowk(K_AT, var, p.gAT), p.gridN, a, hd));
   }
+  if (sh.k1_after >= 0) L(zxk(sh.k1_after), sh.k1_after == VAR_PLAIN && p.wZX > 0 ? p.wZX : p.gridE, a);
+  if (sh.kernels) *sh.kernels += L.count;
   if (L.e != cudaSuccess) return L.e;
   return cudaGetLastError();
 }
@@ -250,6 +268,8 @@ cudaError_t plan_plain_grids(const Args& a, Plan& p, int sms) {
   p.wQ2 = wave((const void*)rowk(K_Q2, VAR_PLAIN, p.gQ), chN);
   p.wAT = wave((const void*)rowk(K_AT, VAR_PLAIN, p.gAT), chN);
   p.wA1 = wave((const void*)rowk(K_A1, VAR_PLAIN, p.gA), std::max<int64_t>(chM, 1));
+  p.wATH = wave((const void*)rowk(K_ATH, VAR_PLAIN, p.gAT), chN);
+  p.wQ2H = wave((const void*)rowk(K_Q2H, VAR_PLAIN, p.gQ), chN);
   return cudaGetLastError();
 }
 
@@ -287,10 +307,18 @@ cudaError_t launch_step_var(const Args& a, const Plan& p, cudaStream_t s, int va
   return launch_step(a, p, s, var, Handles(), ev);
 }
 
+cudaError_t launch_step_fused(const Args& a, const Plan& p, cudaStream_t s, int var, bool k1, int fuse_next,
+                              cudaEvent_t (*ev)[2]) {
+  StepShape sh;
+  sh.k1 = k1;
+  sh.fuse_next = fuse_next;
+  return launch_step(a, p, s, var, Handles(), ev, false, sh);
+}
+
 // kernels before a Q pass of a plain step: the factor pre-pass, the tiled factor kernels and
-// the four DGEMMs of a QAP product
+// the two contractions of a QAP product
 static int pre_kernels(const Args& a) {
-  return (pre_has_work(a, 1, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 4 : 0);
+  return (pre_has_work(a, 1, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 2 : 0);
 }
 
 int kernels_per_step(const Args& a) {
@@ -303,7 +331,7 @@ int kernels_per_step(const Args& a) {
 }
 int kernels_per_restart(const Args& a) {
   return 1 + ((a.Q.present() && a.m > 0 && a.Q.has_pre())
-                  ? (pre_has_work(a, 2, 0) ? 1 : 0) + 2 * tiled_terms(a) + (a.Q.qap_d ? 5 : 0)
+                  ? (pre_has_work(a, 2, 0) ? 1 : 0) + 2 * tiled_terms(a) + (a.Q.qap_d ? 3 : 0)
                   : 0);
 }
 int kernels_per_iteration(const Args& a) { return kernels_per_step(a) + kernels_per_restart(a); }
@@ -404,12 +432,27 @@ cudaError_t build_conditional_graph(const Args& a, const Plan& p, cudaStream_t s
 // restart pass of Algorithm 5 runs and the next step records R~_{r,0}), is one SWITCH node
 // after every R~ test; the dynamic graph above spends a SWITCH and an IF node on every step.
 cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int L, int re, int ce,
-                              cudaGraph_t* out) {
+                              cudaGraph_t* out, int* kernels) {
+  int nk = 0;   // kernels of one launch in which no restart happens (body 0 of every SWITCH)
   auto sR = [&](int q) { return q % re == 0; };
   auto sT = [&](int q) { return q % ce == 0; };
   auto is_sw = [&](int q) { return sR(q == 1 ? L : q - 1); };
   auto var0 = [&](int q) { return sT(q) ? (int)VAR_T : sR(q) ? (int)VAR_R : (int)VAR_PLAIN; };
   auto varR = [&](int q) { return sT(q) ? (int)VAR_T : (int)VAR_R; };
+  // With p.fuse, a step followed by a step without a SWITCH node (no restart can happen in
+  // between) runs that step's k_zx at its end: a plain step in K_Q2H, another variant as a
+  // separate launch; the step after it then starts with K2.  The step after a SWITCH node (or
+  // the first of the graph) runs its own k_zx in every body.
+  auto next_sw = [&](int q) { return q == L ? true : is_sw(q + 1); };
+  auto shape = [&](int q, int v) {
+    StepShape sh;
+    sh.k1 = !(p.fuse && q > 1 && !is_sw(q));
+    if (p.fuse && !next_sw(q)) {
+      if (v == VAR_PLAIN) sh.fuse_next = var0(q + 1);
+      else sh.k1_after = var0(q + 1);
+    }
+    return sh;
+  };
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
   cudaStreamCaptureStatus st;
@@ -435,7 +478,9 @@ cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cuda
     }
     if (!is_sw(q)) {
       // directly after the previous step's last kernel unless that step sat in a SWITCH body
-      e = launch_step(a, p, s, var0(q), hd, nullptr, q > 1 && !is_sw(q - 1));
+      StepShape sh = shape(q, var0(q));
+      sh.kernels = &nk;
+      e = launch_step(a, p, s, var0(q), hd, nullptr, q > 1 && !is_sw(q - 1), sh);
       continue;
     }
     cudaGraph_t bodies[4];
@@ -444,7 +489,10 @@ cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cuda
       e = cudaStreamBeginCaptureToGraph(s2, bodies[v], nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
       if (e != cudaSuccess) break;
       cudaError_t le = v == 2 ? launch_restart(a, p, s2, nullptr) : cudaSuccess;
-      if (le == cudaSuccess) le = launch_step(a, p, s2, v == 0 ? var0(q) : varR(q), hd, nullptr);
+      const int vv = v == 0 ? var0(q) : varR(q);
+      StepShape sh = shape(q, vv);
+      if (v == 0) sh.kernels = &nk;
+      if (le == cudaSuccess) le = launch_step(a, p, s2, vv, hd, nullptr, false, sh);
       cudaGraph_t tmp;
       e = cudaStreamEndCapture(s2, &tmp);
       if (le != cudaSuccess) e = le;
@@ -460,6 +508,7 @@ cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cuda
     return e;
   }
   *out = gout;
+  if (kernels) *kernels = nk + 1;   // + the dispatch kernel
   return cudaSuccess;
 }
 
@@ -511,7 +560,7 @@ cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStrea
 
 int kernels_per_power_iter(const Args& a, int which) {
   if (which == 0) return 4;
-  return 3 + (pre_has_work(a, 4, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 4 : 0);
+  return 3 + (pre_has_work(a, 4, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 2 : 0);
 }
 
 cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s) {

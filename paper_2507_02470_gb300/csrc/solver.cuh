@@ -10,6 +10,7 @@ struct Vec {
   double *x0, *w0, *Qw0, *ATy0;
   double *xb, *wb, *Qwb, *ATyb;
   double *wh, *Qwh, *v, *zb, *Qxb;
+  double* xh;                 // what = 2 xbar - x of eq. (3.3), read by the Q wbar_{1/2} pass
   double *y, *y0, *yb;
   const double *c, *L, *U, *l, *u;
   double *t1, *t2;            // factor intermediates (2 * tlen each)
@@ -43,8 +44,24 @@ struct Args {
 };
 
 // Row-kernel kinds
+// K_ATH, K_Q2H: the last two passes of a plain step whose successor starts with a Halpern step
+// (no restart is possible after a plain step): K_ATH is K_AT followed by the Halpern update of
+// (w_Q, A^* y); K_Q2H forms Q w of the new iterate directly (instead of Q wbar and the Halpern
+// recurrence of the image) and runs the next step's elementwise pass (Halpern on x, eqs.
+// (3.1)-(3.3)) in its epilogue, so that step needs no k_zx.
 enum Kind { K_Q1 = 0, K_A1 = 1, K_AT = 2, K_Q2 = 3, K_APPLY_Q = 4, K_APPLY_A = 5, K_APPLY_AT = 6,
-            K_POWER_Q = 7, K_POWER_A = 8, K_APPLY_AT_P = 9 };
+            K_POWER_Q = 7, K_POWER_A = 8, K_APPLY_AT_P = 9, K_ATH = 10, K_Q2H = 11 };
+// kinds that run inside an inner step (they return once the solve is done)
+__host__ __device__ constexpr bool step_kind(int k) { return k <= K_Q2 || k == K_ATH || k == K_Q2H; }
+
+// Intermediate products formed before a Q pass (factor pre-pass, tiled factor kernels, QAP
+// product), by source vector: 0 wbar_{1/2} (and xbar on stopping tests), 1 wbar, 2 the restart
+// difference A^* ybar - A^* y^{r,0}, 3 the apply input, 4 the power-method vector, 5 w_Q (the
+// new Halpern iterate, for K_Q2H).  Sources 0, 3 and 4 fill t1, the others t2.
+enum PreSrc { PRE_WH = 0, PRE_WB = 1, PRE_RDIFF = 2, PRE_AIN = 3, PRE_PV = 4, PRE_W = 5 };
+__host__ __device__ constexpr bool pre_into_t1(int which) { return which == PRE_WH || which == PRE_AIN || which == PRE_PV; }
+// sources used by the inner step (idle once the solve is done)
+__host__ __device__ constexpr bool pre_in_step(int which) { return which <= PRE_RDIFF || which == PRE_W; }
 
 // Launch plan chosen at create time (lanes per row of each CSR pass, grid sizes).
 struct Plan {
@@ -52,14 +69,25 @@ struct Plan {
   int gridN = 0, gridM = 0, gridE = 0, gridPre = 0;   // blocks of the n-row, m-row, elementwise, pre kernels
   // blocks of the plain (non-reducing) step variants: one full wave at the occupancy of each
   // kernel; the reducing variants keep gridN/gridM/gridE, which size the partial-sum regions
-  int wZX = 0, wQ1 = 0, wA1 = 0, wAT = 0, wQ2 = 0;
+  int wZX = 0, wQ1 = 0, wA1 = 0, wAT = 0, wQ2 = 0, wATH = 0, wQ2H = 0;
+  // fixed-schedule graph: plain steps end with K_ATH + K_Q2H, which run the next step's
+  // elementwise pass (requires Q and A)
+  int fuse = 0;
   int gridP = 0;   // blocks of the persistent (cooperative) solver
   int gridT = 0;   // blocks of the tiled B^T t kernel
-  void* blas = nullptr;   // cuBLAS handle for a QAP term's products
   // programmatic dependent launch between consecutive kernels of a step (each kernel waits for
   // its predecessor with griddepcontrol.wait, so only its launch overlaps the predecessor's end)
   int pdl = 0;
 };
+
+// Halpern weights 1/(i+2), (i+1)/(i+2) of the step after the current one (Algorithm 4; i the
+// inner counter t, or k with halpern_total), evaluated before the controller advances t and k.
+// The controller and the fused passes use this one expression, so their weights agree bit for bit.
+__host__ __device__ inline void halpern_weights(const Ctrl& C, double& ha, double& hb) {
+  const double i = C.halpern_total ? (double)C.k : (double)C.t;
+  ha = 1.0 / (i + 2.0);
+  hb = (i + 1.0) / (i + 2.0);
+}
 
 // sigma and the scalars derived from it (host and device use the same arithmetic)
 __host__ __device__ inline void set_sigma(Ctrl& C, double sigma) {
@@ -79,13 +107,19 @@ __host__ __device__ inline void set_sigma(Ctrl& C, double sigma) {
 // device at run time.  ev (optional) receives CUDA events around each kernel kind.
 cudaError_t launch_step_var(const Args& a, const Plan& p, cudaStream_t s, int var, cudaEvent_t (*ev)[2] = nullptr);
 cudaError_t launch_iteration(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
+// One inner step as the fixed-schedule graph runs it: k1 false when the previous step's K_Q2H
+// ran this step's elementwise pass; fuse_next >= 0 (plain steps, p.fuse): end with K_ATH and
+// K_Q2H for a next step of that variant.
+cudaError_t launch_step_fused(const Args& a, const Plan& p, cudaStream_t s, int var, bool k1, int fuse_next,
+                              cudaEvent_t (*ev)[2] = nullptr);
 cudaError_t launch_restart(const Args& a, const Plan& p, cudaStream_t s, cudaEvent_t (*ev)[2] = nullptr);
 cudaError_t build_conditional_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int steps,
                                     cudaGraph_t* out);
 // Graph of L steps whose variants are fixed by position (R~ test every re, stopping test
 // every ce steps; L a multiple of both), one SWITCH node after each R~ test for the restart.
+// *kernels (optional) receives the number of kernels one launch runs when no restart happens.
 cudaError_t build_fixed_graph(const Args& a, const Plan& p, cudaStream_t s, cudaStream_t s2, int L, int re, int ce,
-                              cudaGraph_t* out);
+                              cudaGraph_t* out, int* kernels = nullptr);
 int kernels_per_step(const Args& a);
 int kernels_per_restart(const Args& a);
 int kernels_per_iteration(const Args& a);
@@ -127,6 +161,11 @@ cudaError_t primal_eta(const double* xb, const double* Qxb, const double* ATyb, 
 // The QAP term's product(s) before a pass that needs them (which as for k_pre; tt: 0 one
 // vector, 1 or 2 also x-bar for the stopping test); no-op without a QAP term.
 cudaError_t launch_qap(const Args& a, const Plan& p, int which, int tt, cudaStream_t s);
+// qap.cu: out = vec(Ahat X Bhat - S X - X T) for x = vec(X) (two kernels), and the K-range
+// split that keeps about two blocks per SM busy for a d x d product
+constexpr int kQapMaxSplits = 8;
+cudaError_t qap_apply(const QDev& Q, const double* x, double* out, int splits, cudaStream_t s);
+int qap_splits(int64_t d, int sms);
 // Records the device time stamp of the start of the iteration (tolerance ladder).
 cudaError_t launch_stamp(const Args& a, cudaStream_t s);
 // Fills the plain-variant grids of p from the occupancy of those kernels (after gQ, gA, gAT).

@@ -26,7 +26,7 @@ namespace {
 // Same early exits as the CSR pre-pass; two-vector passes (stopping tests) take the CSR path.
 template <int TT>
 __device__ __forceinline__ bool tiled_idle(const Ctrl* C, int which) {
-  if (which <= 2 && C->done) return true;
+  if (pre_in_step(which) && C->done) return true;
   if (which == 2 && !C->restart_pending) return true;
   if (which == 4 && C->pw_done) return true;
   return which == 0 && (TT == 1 || (TT == 2 && C->ttest));
@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tb(Args a, int which, int f) {
   const int k = (int)(blockIdx.x % (unsigned)M.ntile), g = (int)(blockIdx.x / (unsigned)M.ntile);
   const int64_t c0 = (int64_t)k * kTileW;
   const int cw = (int)(n - c0 < (int64_t)kTileW ? n - c0 : (int64_t)kTileW);
-  const double* x0 = which == 0 ? (a.m > 0 ? V.wh : V.wb) : which == 1 ? V.wb : which == 3 ? V.ain : V.pv;
+  const double* x0 = which == PRE_WH ? (a.m > 0 ? V.wh : V.wb) : which == PRE_WB ? V.wb : which == PRE_AIN ? V.ain
+                     : which == PRE_W ? V.w : V.pv;
   if (which == 2) {   // restart: the difference of two vectors
     for (int i = threadIdx.x; i < cw; i += blockDim.x) sx[i] = V.ATyb[c0 + i] - V.ATy0[c0 + i];
     __syncthreads();
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_tsum(Args a, int which, int f) {
   const TiledFac& T = a.Q.tf[f];
   const int64_t p = T.p;
   const int kb = T.b.ntile;
-  double* t = ((which == 0 || which >= 3) ? a.V.t1 : a.V.t2) + a.Q.toff[f];
+  double* t = (pre_into_t1(which) ? a.V.t1 : a.V.t2) + a.Q.toff[f];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p; r += stride) {
     double s = 0.0;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(kTThreads, 1) k_tbt(Args a, int which, int f) 
   const SellTiles& M = T.bt;
   const Vec& V = a.V;
   const int64_t p = T.p;
-  double* tb = which == 1 ? V.t2 : V.t1;
+  double* tb = pre_into_t1(which) ? V.t1 : V.t2;
   const double* tv = tb + a.Q.toff[f];
   double* u = tb + a.Q.uoff[f];
   // this block's share: whole windows (a window holds the same rows in every tile, sorted

@@ -26,6 +26,10 @@ def main(argv=None):
                     help="SpMV schedule: 1 timed choice, 0 lanes from row length, 2 staged chunks")
     ap.add_argument("--tiled-factor", type=int, default=1,
                     help="shared-memory-tiled factor products: 1 auto, 0 off, 2 forced")
+    ap.add_argument("--factor-inline", type=int, default=1,
+                    help="thin factor products formed inside the Q pass: 1 auto, 0 off (pre-pass), 2 forced")
+    ap.add_argument("--fused-steps", type=int, default=1,
+                    help="plain steps end with the fused passes (1) or run all five passes (0)")
     args = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -37,7 +41,8 @@ def main(argv=None):
           "c1": lambda: qpgen.large_cqp(n=1_000_000, m=500_000, seed=0),
           "c2": lambda: qpgen.lasso(),
           "c4": lambda: qpgen.param_family_base(n=100_000, m=50_000, seed=0)}[args.workload]()
-    with pkg.Solver(qp, launch_mode=2, autotune=args.autotune, tiled_factor=args.tiled_factor) as s:
+    with pkg.Solver(qp, launch_mode=2, autotune=args.autotune, tiled_factor=args.tiled_factor,
+                    factor_inline=args.factor_inline, fused_steps=args.fused_steps) as s:
         s.solve(tol=1e-30, max_iter=args.warm_iters)
         k = s.kkt()
         ms = s.profile(iters=args.iters)

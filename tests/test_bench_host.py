@@ -24,16 +24,31 @@ def test_tiled_factor_counts():
     b, f = bench.algorithmic(qp, tiled=True)["pre1"]
     assert b == 20 * nnz + 8 * n + 16 * kb * p + 8 * p + 8 * n * (2 * kt - 1)
     assert f == 2 * nnz + kb * p + (kt - 1) * n
-    # the row pass then only adds u; untiled it carries the B^T pass
+    # the row pass then only adds u; untiled it carries the B^T pass (entries, and adding the
+    # term to each row: one FP64 operation per row either way)
     bq, fq = bench.algorithmic(qp, tiled=True)["q1"]
     bu, fu = bench.algorithmic(qp, tiled=False)["q1"]
-    assert bu - bq == 12 * nnz + 4 * n - 8 * n and fu - fq == nnz
+    assert bu - bq == 12 * nnz + 4 * n - 8 * n and fu - fq == nnz + n
 
 
 def test_zx_counts_match_the_eighteen_operations_per_coordinate():
+    # reads x, w, Qw, A^*y with their anchors and bar values, c, L, U; writes x, w, Qw, A^*y,
+    # xbar, what, wbar_{1/2}
     qp = qpgen.large_cqp(n=10_000, m=5_000, seed=0)
     b, f = bench.algorithmic(qp)["zx"]
-    assert f == 18 * qp.n and b == 8 * qp.n * (15 + 6)
+    assert f == 18 * qp.n and b == 8 * qp.n * (15 + 7)
+
+
+def test_fused_pass_counts():
+    # ath: A^T ybar (12 B/entry, 4 B/row, ybar gathered once), 5 n-vector reads and 2 writes;
+    # q2h: the Q pass plus 7 reads and 3 writes, 8 FP64 operations per coordinate beyond Q
+    qp = qpgen.large_cqp(n=10_000, m=5_000, seed=0)
+    n, m, nnzA = qp.n, qp.m, int(qp.A_rowptr[-1])
+    alg = bench.algorithmic(qp)
+    assert alg["ath"] == (12 * nnzA + 4 * n + 8 * m + 8 * n * 7, nnzA + 8 * n)
+    bq, fq = alg["q2"]
+    bh, fh = alg["q2h"]
+    assert bh - bq == 8 * n * 8 and fh - fq == 8 * n
 
 
 def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
@@ -53,32 +68,47 @@ def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
 
 def test_roofline_takes_the_slowest_kernel_and_the_larger_fraction():
     """The roofline object: the kernel with the largest mean time, achieved = algorithmic count
-    / time, frac against the measured HBM copy rate or the FP64 issue peak (152 SMs x 32/19
-    lanes per clock x the maximum clock), whichever fraction is larger, and that kernel's
-    recorded DRAM traffic."""
+    / time, frac against the measured HBM copy rate or the FP64 issue peak (the probe's lanes
+    per clock x SMs x the maximum clock, passed in), whichever fraction is larger, and that
+    kernel's recorded DRAM traffic; the whole iteration by the hot-path byte count."""
     qp = qpgen.large_cqp(n=10_000, m=5_000, seed=0)
     alg = bench.algorithmic(qp)
     pk = {"hbm_gbs": 6786.2, "sm_max_mhz": 2070.0}
+    fp64_peak = 152 * 1.6817 * 2070e6 / 1e9
+    fp64 = (fp64_peak, 1.6817, "probe")
     prof = {"zx": 0.0005, "q1": 0.0004, "a1": 0.0002, "at": 0.0003, "q2": 0.0003, "pre1": 0.0001,
             "pre2": 0.0001, "restart": 0.0}
-    r = bench.roofline(prof, qp, pk, "measured", {"zx": 1.5e6, "q1": 2.0e6})
+    r = bench.roofline(prof, qp, pk, "measured", {"zx": 1.5e6, "q1": 2.0e6}, iter_s=2e-6, fp64=fp64)
     assert r["kernel"] == "zx" and r["traffic"] == 1.5e6
     b, f = alg["zx"]
-    gbs, fp64 = b / 0.5e-6 / 1e9, f / 0.5e-6 / 1e9
-    fp64_peak = 152 * 32 / 19 * 2070e6 / 1e9
-    assert fp64_peak == pytest.approx(529.9, abs=0.1)
+    gbs, ops = b / 0.5e-6 / 1e9, f / 0.5e-6 / 1e9
     assert r["alg_bytes"] == b and r["alg_fp64"] == f
-    if fp64 / fp64_peak > gbs / 6786.2:
-        assert r["bound"] == "alu" and r["frac"] == pytest.approx(fp64 / fp64_peak, abs=1e-4)
+    if ops / fp64_peak > gbs / 6786.2:
+        assert r["bound"] == "alu" and r["frac"] == pytest.approx(ops / fp64_peak, abs=1e-4)
         assert r["hbm_frac"] == pytest.approx(gbs / 6786.2, abs=1e-4)
     else:
         assert r["bound"] == "hbm" and r["frac"] == pytest.approx(gbs / 6786.2, abs=1e-4)
+    ib = bench.iteration_bytes(qp)
+    assert r["iteration"]["alg_bytes"] == ib
+    assert r["iteration"]["hbm_frac"] == pytest.approx(ib / 2e-6 / 1e9 / 6786.2, abs=1e-4)
     # a slower row pass takes over the line; the HBM bound wins when its fraction is larger
     prof["a1"] = 0.01
-    r = bench.roofline(prof, qp, pk, "measured", None)
-    assert r["kernel"] == "a1" and r["traffic"] is None
+    r = bench.roofline(prof, qp, pk, "measured", None, fp64=fp64)
+    assert r["kernel"] == "a1" and r["traffic"] is None and "iteration" not in r
     b, f = alg["a1"]
     assert (r["bound"] == "hbm") == (b / 1e-5 / 1e9 / 6786.2 >= f / 1e-5 / 1e9 / fp64_peak)
+
+
+def test_iteration_bytes_of_the_large_cqp():
+    """The per-iteration byte count of the n = 1e6, m = 5e5 CQP: A and A^T (3e6 entries each at
+    12 B), Q twice (three stored diagonals, S and S^T with 3e4 entries), row pointers at 4 B,
+    26 n-vector and 8 m-vector passes: about 0.38 GB."""
+    qp = qpgen.large_cqp(n=1_000_000, m=500_000, seed=0)
+    n, m = 1_000_000, 500_000
+    q = 8 * 3 * n + 24 * 30_000 + 4 * (10_000 + 1)
+    expect = 24 * 3_000_000 + 2 * q + 4 * (2 * m + 2 * n) + 8 * (26 * n + 8 * m)
+    assert bench.iteration_bytes(qp) == expect
+    assert 0.37e9 < expect < 0.40e9
 
 
 def test_clock_summary_median_and_throttle_reasons():

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import qpgen
+from tests.parity import close  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +31,8 @@ def pkg():
 
 
 def mixed_batch():
-    probs = [qpgen.portfolio(s, n=n) for s, n in ((1, 50), (2, 130), (3, 700), (4, 1500), (5, 61))]
+    # portfolio instances at both ends of the configured U{50..5000} (n = 5000: F is 250 x 5000)
+    probs = [qpgen.portfolio(s, n=n) for s, n in ((1, 50), (2, 130), (3, 700), (4, 1500), (5, 61), (6, 5000))]
     probs.append(qpgen.random_small(n=40, m=12, seed=8, q_kind="csr", density=0.3))
     probs.append(qpgen.random_small(n=30, m=6, seed=9, q_kind="dense_factor", q_rank=7, phi="l1_box", lam=0.2))
     return probs
@@ -48,9 +50,9 @@ def test_batch_first_iterates(pkg):
             for i, (qp, ref) in enumerate(zip(probs, refs)):
                 x, y, z, kkt = b.get(i)
                 assert kkt["iters"] == k, (i, kkt)
-                assert rel(x, ref.trace["x"][k - 1]) <= ITER_TOL, (i, k)
+                assert close(x, ref.trace["x"][k - 1]) <= ITER_TOL, (i, k)
                 if qp.m:
-                    assert rel(y, ref.trace["y"][k - 1]) <= ITER_TOL, (i, k)
+                    assert close(y, ref.trace["y"][k - 1]) <= ITER_TOL, (i, k)
 
 
 def test_batch_converged(pkg):

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import qpgen
+from tests.parity import close  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -79,9 +80,9 @@ def test_edge_first_iterates(pkg, name):
         for k in (1, 2, 10, 11, 50):
             s.solve(tol=1e-30, max_iter=k)
             x, y, *_ = s.get()
-            assert rel(x, ref.trace["x"][k - 1]) <= 1e-10, (name, k)
+            assert close(x, ref.trace["x"][k - 1]) <= 1e-10, (name, k)
             if qp.m:
-                assert rel(y, ref.trace["y"][k - 1]) <= 1e-10, (name, k)
+                assert close(y, ref.trace["y"][k - 1]) <= 1e-10, (name, k)
 
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
@@ -135,7 +136,7 @@ def test_time_limit_stops_between_launches_with_a_consistent_zbar(pkg):
     it = k["iters"]
     assert 0 < it < 10**8 and k["status"] == "time_limit"
     ref = oracle.solve(qp, tol=1e-30, max_iter=it, lambda_A=lam.lambda_A, lambda_Q=lam.lambda_Q, **kw)
-    assert rel(x, ref.x) <= 1e-8 and rel(y, ref.y) <= 1e-8 and rel(z, ref.z) <= 1e-8, it
+    assert close(x, ref.x) <= 1e-8 and close(y, ref.y) <= 1e-8 and close(z, ref.z) <= 1e-8, it
 
 
 def test_profile_reports_every_step_kernel_and_leaves_no_solution(pkg):
