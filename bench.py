@@ -70,7 +70,8 @@ def workload(name: str):
         return qpgen.lasso(), "lasso p=5e4 q=5e5 nnz(B)=1.25e7, Q=B^T B matrix-free, lam=0.1||B^T b||_inf"
     if name == "qap":
         return qpgen.qap_relaxation(d=256, seed=0), \
-            "QAP relaxation (Sec. 4.5) d=256: n=65536, m=512, Q = Bhat(x)Ahat - I(x)S - T(x)I matrix-free (cuBLAS DGEMMs)"
+            ("QAP relaxation (Sec. 4.5) d=256: n=65536, m=512, Q = Bhat(x)Ahat - I(x)S - T(x)I matrix-free "
+             "(two FP64 contractions per product)")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -124,6 +125,50 @@ def run_batched(args, rank, world, dist=None):
         print(json.dumps(line), flush=True)
 
 
+NETWORK = os.path.join(ROOT, "paper_2507_02470_gb300", "c4_network.npz")
+
+
+def measure_learned(args, rank):
+    """Cold against learned starts on `args.c4_eval` held-out members of the family (the first of
+    the 1,000 held-out seeds), with the network of NETWORK (trained by `bench.py --workload c4
+    --c4-train 20000 --c4-test 1000 --c4-save ...`).  None when the file is missing."""
+    if not os.path.exists(NETWORK):
+        return None
+    import torch
+    import qpgen
+    from paper_2507_02470_gb300 import learned as L
+    base = qpgen.param_family_base(n=100_000, m=50_000, seed=0)
+    ws = L.LearnedWarmStart(base.n, base.m, base.L, base.U, base.l, base.u, d0=512, hidden=(1024, 1024), r=256,
+                            seed=0, max_batch=256)
+    meta = ws.load(NETWORK)
+    lam = (float(meta["lambda_A"]), float(meta["lambda_Q"]))
+    Ne = args.c4_eval
+    off = 10_000_000 + rank * 1000
+    Cte, Ute = qpgen.ws_family_data(base, range(off, off + Ne))
+    te = lambda a, b: (Cte[a:b], Ute[a:b])
+    ws.predict(Cte[:min(Ne, 256)], Ute[:min(Ne, 256)])
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    Z0, sig0 = ws.predict(Cte, Ute)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t
+    cold = L.solve_members(base, te, Ne, lam=lam)
+    warm = L.solve_members(base, te, Ne, lam=lam, starts=(Z0.cpu().numpy(), sig0.cpu().numpy()))
+    ws.close()
+    t_cold = float(np.mean(cold["seconds"]))
+    t_warm = float(np.mean(warm["seconds"])) + t_pred / Ne
+    conv = sum(s == "converged" for s in cold["status"]) + sum(s == "converged" for s in warm["status"])
+    return {"workload": "family of cqp n=1e5 m=5e4 (c=cbar+0.1N(0,1), u=ubar+0.1U(0,1)), MLP 512-1024-1024-257",
+            "network": f"trained on {int(meta['train'])} members (seeds {meta['train_seeds']}), "
+                       f"{int(meta['epochs'])} epochs; file {os.path.relpath(NETWORK, ROOT)}",
+            "eval_members": f"{Ne} of the 1,000 held-out seeds ({off}..{off + Ne - 1})",
+            "cold_s": round(t_cold, 5), "warm_s": round(t_warm, 5), "speedup_vs_plain": round(t_cold / t_warm, 3),
+            "cold_iters": float(cold["iters"].mean()), "warm_iters": float(warm["iters"].mean()),
+            "inference_s_per_member": round(t_pred / Ne, 6), "converged": conv, "of": 2 * Ne,
+            "timing": "per member on one handle: data (c, u) and starting point set, then solve to 1e-8 "
+                      "(host wall clock around the solve); warm adds its share of the batched inference"}
+
+
 def measure_batched(pkg, torch, count, seed0, steps, warmup, plain_sample, dist=None):
     """The batch of `count` portfolio CQPs (seeds seed0.., n from 50 to 5000, m = 11) solved to
     1e-8 in one persistent launch per solve (warm-up solves first: the first one runs the
@@ -170,6 +215,7 @@ def measure_batched(pkg, torch, count, seed0, steps, warmup, plain_sample, dist=
     nsum = sum(p.n for p in probs)
     fpool = sum(8 * t.p * p.n for p in probs for t in p.qterms if t.kind == "dense_factor")
     sched = b.stats()
+    buckets = b.schedule()
     b.close()
     return {"workload": f"batched portfolio CQPs x{count}: n~U{{50..5000}} (sum n={nsum}), "
                         "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch",
@@ -181,6 +227,7 @@ def measure_batched(pkg, torch, count, seed0, steps, warmup, plain_sample, dist=
             "instances": count, "plain_solver_est_s": round(plain_total, 3),
             "speedup_vs_plain": round(plain_total / t_step, 2),
             "plain_sample": f"{len(sample)} instances solved one by one (create+solve), scaled to {count}",
+            "schedule": [{k: v for k, v in bk.items() if k != "f_capacity"} for bk in buckets if bk["instances"]],
             "clocks": clocks.summary(), "gpu_launches": int(sched["kernel_launches"]) * steps}
 
 
@@ -209,6 +256,9 @@ def run_learned(args, rank, world):
                             seed=0, max_batch=256)
     rep = ws.fit(tr_data, Z, tr["sigma"], epochs=args.c4_epochs, batch=256, lr=1e-3)
     del Z
+    if args.c4_save and rank == 0:
+        ws.save(args.c4_save, family="cqp n=1e5 m=5e4 seed 0", train=Ntr, train_seeds=f"{off}..{off + Ntr - 1}",
+                epochs=args.c4_epochs, lambda_A=lam[0], lambda_Q=lam[1])
     # inference for the held-out members (batched), timed on the device and the host
     for _ in range(2):
         ws.predict(Cte[:min(Nte, 256)], Ute[:min(Nte, 256)])
@@ -640,6 +690,10 @@ def main():
     ap.add_argument("--c4-train", type=int, default=2000)
     ap.add_argument("--c4-test", type=int, default=100)
     ap.add_argument("--c4-epochs", type=int, default=30)
+    ap.add_argument("--c4-save", default="", help="c4: write the trained network here (the default line's "
+                                                  "'learned' key evaluates it)")
+    ap.add_argument("--c4-eval", type=int, default=100,
+                    help="held-out members the default line's 'learned' key solves cold and warm")
     ap.add_argument("--c4-workers", type=int, default=4)
     ap.add_argument("--c3-count", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=24)
@@ -647,6 +701,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="iteration cap of each solve (0: 1e6; the QAP relaxation: 3000, whose solves to 1e-8 "
+                         "take far longer; its line then reports iterations/s of capped solves)")
     ap.add_argument("--extensions", type=int, default=1,
                     help="1: the default line also measures the batched form (4096 portfolio QPs in one "
                          "launch against the plain solver) as its 'batched' key; 0: skip")
@@ -697,8 +754,9 @@ def main():
     solver = pkg.Solver(qp, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl,
                         fixed_schedule=args.fixed_schedule, tiled_factor=args.tiled_factor)
     iters_per_step, solve_s = [], []
+    max_iter = args.max_iter if args.max_iter > 0 else (3000 if args.workload == "qap" else 1_000_000)
     for _ in range(args.warmup):
-        solver.solve(tol=TOL, max_iter=1_000_000)
+        solver.solve(tol=TOL, max_iter=max_iter)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
     statuses = []
@@ -710,7 +768,7 @@ def main():
         ev0.record(stream)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            statuses.append(solver.solve(tol=TOL, max_iter=1_000_000))
+            statuses.append(solver.solve(tol=TOL, max_iter=max_iter))
             k = solver.kkt()
             kkts.append(k)
             iters_per_step.append(k["iters"])
@@ -757,7 +815,7 @@ def main():
         t = time.perf_counter()
         with pkg.Solver(pinned, stream=stream.cuda_stream, launch_mode=args.launch_mode, pdl=args.pdl,
                         fixed_schedule=args.fixed_schedule, tiled_factor=args.tiled_factor) as s2:
-            s2.solve(tol=TOL, max_iter=1_000_000)
+            s2.solve(tol=TOL, max_iter=max_iter)
             _, _, _, _, k2 = s2.get(outx, outy if qp.m else None, outz, outw)
         torch.cuda.synchronize()
         e2e_t += time.perf_counter() - t
@@ -766,13 +824,19 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "note": "hprqp_create from host arrays + solve + hprqp_get, per solve"}
 
+    # the learned warm start against the cold start (row a11), from the network trained on the
+    # configured 20,000 members and committed with the package
+    learned = None
+    if args.extensions:
+        learned = measure_learned(args, rank)
     # the batched form against the plain solver (row a10 of the hot path), compact
     batched = None
     if args.extensions:
         solver.close()
         r = measure_batched(pkg, torch, args.c3_count, rank * args.c3_count, 1, 1, args.plain_sample, dist)
         batched = {k: r[k] for k in ("instances", "converged", "time_to_tol_s", "hpr_its_per_s",
-                                     "plain_solver_est_s", "speedup_vs_plain", "plain_sample", "gpu_launches")}
+                                     "plain_solver_est_s", "speedup_vs_plain", "plain_sample", "schedule",
+                                     "gpu_launches")}
         batched["workload"] = r["workload"]
         batched["timing"] = "one warm-up solve (it runs the autotuner), then one timed solve of the whole batch"
     if rank == 0:
@@ -800,6 +864,8 @@ def main():
         }
         if batched:
             line["batched"] = batched
+        if learned:
+            line["learned"] = learned
         print(json.dumps(line), flush=True)
     solver.close()
     if dist:

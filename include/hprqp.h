@@ -174,6 +174,11 @@ typedef struct hprqp_params {
                                 has the inner step's products t = B x formed inside the Q row
                                 pass from B's rows, with no separate pre-pass launch; 2: every
                                 such factor; 0: never.  Sums in another order (rounding only) */
+  int32_t wait_polls;        /* launch_mode 3: polls of one grid-barrier wait before the solve
+                                gives up with HPRQP_TIMEOUT; 0 (default): about a second */
+  int32_t batch_team;        /* batched solver: 0 (default) threads per instance chosen per bucket
+                                of n (autotune 1: timed on the batch; 0: 512/256/128/64 from the
+                                largest n down); 64, 128, 256 or 512: that team size for all */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
@@ -306,6 +311,11 @@ hprqp_status hprqp_power_noalloc(int64_t m, int64_t n, const int32_t* A_rowptr, 
 /* Releases all device memory of the handle.  NULL is ignored. */
 void hprqp_destroy(hprqp_handle* h);
 
+/* Bookkeeping, with no counterpart in the paper: sets hprqp_params.wait_polls of the handle for
+ * later solves (launch_mode 3: polls of one grid-barrier wait; 0 restores the default).  A solve
+ * whose wait gave up returns HPRQP_TIMEOUT; every solve starts from a cleared barrier. */
+hprqp_status hprqp_set_wait_polls(hprqp_handle* h, int32_t polls);
+
 /* Bookkeeping, with no counterpart in the paper: the device memory the handle holds, by the
  * path it came from.  out[0], out[1]: allocations and bytes obtained through the allocator
  * hooks of hprqp_params (alloc/free); out[2], out[3]: allocations and bytes obtained with
@@ -326,8 +336,10 @@ hprqp_status hprqp_fp64_rate(int32_t op, int32_t lanes, double* lanes_per_clk, d
 
 /* ------------------------------------------------------------------------------------------
  * Batched solver: many independent instances of eq. (1.1), each run through Algorithm 4 with
- * its own sigma, restart and termination state, in one persistent kernel launch (one thread
- * block per instance, instances taken from a work queue ordered by estimated cost).
+ * its own sigma, restart and termination state, in one persistent kernel launch.  Instances are
+ * bucketed by n; in each bucket a team of threads (64 to 512, chosen per bucket by an autotuner
+ * that times the candidates on the batch itself) solves one instance at a time, taking the next
+ * from the bucket's work queue (largest estimated cost first).
  * Supported Q terms per instance: at most one DIAG, one DENSE_FACTOR (p <= 1024) and one CSR.
  * m <= HPRQP_BATCH_MAX_M rows per instance (the second Q product of a step and the theta
  * terms of eqs. (2.12), (3.11) use Q A^T and A Q A^T, formed once per solve).
@@ -371,6 +383,12 @@ hprqp_status hprqp_batch_get(hprqp_batch* b, int32_t i, double* x, double* y, do
  * the message of the last failure on the batch ("" if none; b = NULL gives the last failure
  * of hprqp_batch_create in this thread). */
 hprqp_status hprqp_batch_stats(hprqp_batch* b, double* seconds, int64_t* kernel_launches);
+/* Bookkeeping, with no counterpart in the paper: the schedule the autotuner chose at the first
+ * hprqp_batch_solve.  Instances are bucketed by n (largest first); for each of the 4 buckets,
+ * out[5*k .. 5*k+4] = smallest n of the bucket, instances in it, threads per instance (a team of
+ * 64..512 threads of a 512-thread block), 1 if a team keeps its instance's dense factor F in
+ * shared memory (else 0), and that copy's capacity in doubles.  Host pointer to 20 int64. */
+hprqp_status hprqp_batch_schedule(const hprqp_batch* b, int64_t* out);
 void hprqp_batch_destroy(hprqp_batch* b);
 const char* hprqp_batch_last_error(const hprqp_batch* b);
 

@@ -48,7 +48,8 @@ class hprqp_params(C.Structure):
                 ("verbose", C.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("launch_mode", C.c_int32), ("scaling", C.c_int32), ("method", C.c_int32),
                 ("pdl", C.c_int32), ("fixed_schedule", C.c_int32),
-                ("tiled_factor", C.c_int32), ("fused_steps", C.c_int32), ("factor_inline", C.c_int32)]
+                ("tiled_factor", C.c_int32), ("fused_steps", C.c_int32), ("factor_inline", C.c_int32),
+                ("wait_polls", C.c_int32), ("batch_team", C.c_int32)]
 
 
 class hprqp_kkt(C.Structure):
@@ -99,6 +100,7 @@ SIGNATURES = [
     ("hprqp_batch_solve", C.c_int, [_vp, _dbl, _i64]),
     ("hprqp_batch_get", C.c_int, [_vp, _i32, _vp, _vp, _vp, C.POINTER(hprqp_kkt)]),
     ("hprqp_batch_stats", C.c_int, [_vp, C.POINTER(_dbl), C.POINTER(_i64)]),
+    ("hprqp_batch_schedule", C.c_int, [_vp, _vp]),
     ("hprqp_batch_destroy", None, [_vp]),
     ("hprqp_batch_last_error", C.c_char_p, [_vp]),
     ("hprqp_last_error", C.c_char_p, [_vp]),
@@ -107,6 +109,7 @@ SIGNATURES = [
     ("hprqp_set_lambda", C.c_int, [_vp, _dbl, _dbl]),
     ("hprqp_fp64_rate", C.c_int, [_i32, _i32, C.POINTER(_dbl), C.POINTER(_dbl), C.POINTER(_dbl)]),
     ("hprqp_memory_stats", C.c_int, [_vp, _vp]),
+    ("hprqp_set_wait_polls", C.c_int, [_vp, _i32]),
     # learned warm start (include/hprqp_learn.h)
     ("hprqp_gemm_bf16", C.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     ("hprqp_learn_check", C.c_int, []),
@@ -306,6 +309,10 @@ class Solver:
         self._check(lib().hprqp_set_data(self.h, *[_ptr(a) for a in keep]))
         self._keep = []
 
+    def set_wait_polls(self, polls):
+        """launch_mode 3: polls of one grid-barrier wait before the solve gives up (0: default)."""
+        self._check(lib().hprqp_set_wait_polls(self.h, int(polls)))
+
     def set_lambda(self, lambda_A, lambda_Q):
         """Fixes lambda_A, lambda_Q for later solves (0 restores the power method)."""
         self._check(lib().hprqp_set_lambda(self.h, float(lambda_A), float(lambda_Q)))
@@ -500,6 +507,14 @@ class BatchSolver:
         n = C.c_int64()
         self._check(lib().hprqp_batch_stats(self.h, C.byref(sec), C.byref(n)))
         return {"seconds": sec.value, "kernel_launches": n.value}
+
+    def schedule(self):
+        """Per bucket of instances (by n): the autotuner's team size and shared-memory F copy."""
+        out = np.zeros(20, np.int64)
+        self._check(lib().hprqp_batch_schedule(self.h, _ptr(out)))
+        return [{"n_from": int(out[5 * k]), "instances": int(out[5 * k + 1]), "threads": int(out[5 * k + 2]),
+                 "f_in_smem": bool(out[5 * k + 3]), "f_capacity": int(out[5 * k + 4])}
+                for k in range(4)]
 
     def close(self):
         if getattr(self, "h", None):

@@ -894,10 +894,6 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
       sq += len * len;
     }
     if (h->prm.factor_inline == 2 || sq <= 0.5 * (double)n) QD.inl[f] = 1;
-    // a SELL-32 copy of B^T packs the few rows that carry entries of each 256-row chunk into
-    // one warp's slice, so the on-demand products run on full warps instead of one lane per warp
-    if (QD.inl[f] && h->prm.launch_mode != 3 && h->prm.autotune != 0)
-      if ((st = build_sell_rows(h, QD.fact[f]))) return st;
   }
   QD.tlen = toff;
 
@@ -1001,12 +997,14 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
     for (int f = 0; f < QD.nfac; f++)
       if (!big || QD.fact[f].nnz > big->nnz) big = &QD.fact[f];
     P.gQ = big ? tune_G(h, *big, P.gridN, ain, aout, 1) : 1;
-    // Q's CSR-like parts are only thin factors with SELL copies: their on-demand products decide
-    // the schedule (the bare-SpMV probe cannot see them), the SELL form
+    // Q's CSR-like parts are only thin factors formed on demand: one lane per row (their few
+    // entries gain nothing from more lanes, and the bare-SpMV probe cannot see the on-demand
+    // products).  A SELL copy of B^T, which packs a chunk's entries into one warp, measured
+    // slower on the n = 1e6 CQP (longer chain of dependent loads per entry).
     {
       bool only_inl = QD.nfac > 0 && !QD.csr.rows;
-      for (int f = 0; f < QD.nfac; f++) only_inl = only_inl && (QD.tiled[f] || (QD.inl[f] && QD.fact[f].soff));
-      if (only_inl && h->prm.autotune == 1) P.gQ = -1;
+      for (int f = 0; f < QD.nfac; f++) only_inl = only_inl && (QD.tiled[f] || QD.inl[f]);
+      if (only_inl && h->prm.autotune == 1) P.gQ = 1;
     }
     bool untiled = false;   // the probe below runs the one-vector pre-pass, which skips tiled terms
     for (int f = 0; f < QD.nfac; f++) untiled = untiled || !QD.tiled[f];
@@ -1135,6 +1133,13 @@ extern "C" hprqp_status hprqp_set_data(hprqp_handle* h, const double* c, const d
   if (u && m) CU(h, cudaMemcpyAsync((void*)V.u, hu.data(), m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   h->solved = false;
+  return HPRQP_OK;
+}
+
+extern "C" hprqp_status hprqp_set_wait_polls(hprqp_handle* h, int32_t polls) {
+  if (!h) return HPRQP_INVALID_ARG;
+  if (polls < 0) return fail(h, HPRQP_INVALID_ARG, "wait_polls must be >= 0");
+  h->prm.wait_polls = polls;
   return HPRQP_OK;
 }
 
@@ -1380,6 +1385,7 @@ static hprqp_status init_state(hprqp_handle* h, double lamA, double lamQ, double
   C.done = 0;
   C.pw_done = 1;
   hprqp::set_sigma(C, sigma);
+  halpern_weights(C, C.fha, C.fhb);
   CU(h, cudaMemcpyAsync(h->dctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   return HPRQP_OK;
 }
@@ -1622,7 +1628,7 @@ static hprqp_status solve_persist(hprqp_handle* h, std::chrono::steady_clock::ti
   const long long per = 4096;
   bool time_up = false;
   for (;;) {
-    CU(h, launch_persist(a, h->plan, h->plan.gridP, per, bar, err, h->stream));
+    CU(h, launch_persist(a, h->plan, h->plan.gridP, per, bar, err, (unsigned)h->prm.wait_polls, h->stream));
     h->launches += 1;
     CU(h, cudaMemcpyAsync(h->hflags, &h->dctrl->done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaMemcpyAsync(h->hflags + 1, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

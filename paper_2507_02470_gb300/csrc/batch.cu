@@ -79,30 +79,124 @@ struct Pools {
   int halpern_total, restart_off, sigma_fixed, sigma_golden;
 };
 
-// ------------------------------------------------------------------------------------ block helpers
-template <int NT>
-__device__ __forceinline__ void bsum(double (&v)[NT], unsigned maxmask, double* red) {
-  block_reduce<NT>(v, maxmask, red);
-  // thread 0 holds the result; broadcast through shared memory
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < NT; i++) red[i] = v[i];
+// ------------------------------------------------------------------------------------ teams
+// A block of kBatchThreads threads works as teams of 64, 128, 256 or 512 consecutive threads; a
+// team solves one instance at a time and synchronises on its own named barrier.  Buckets of
+// instances (by n, largest first) run in order with non-increasing team sizes: a team that finds
+// its bucket exhausted splits into the next bucket's smaller teams at once, without waiting for
+// the other teams of its block.  Barrier ids are assigned by size and position (512: id 1; 256:
+// 2-3; 128: 4-7; 64: 8-15), so a team and the sub-teams of another never share an id, and the
+// shared memory of a team is the kSlotBytes slots of its 64-thread groups.
+constexpr int kBatchThreads = 512;
+constexpr int kMaxBuckets = 4;
+// Shared memory per 64 threads: at most kMaxSlot, and in a launch only what its schedule needs
+// (shared memory and L1 share one array per SM: every byte not reserved caches the teams'
+// vectors and F)
+constexpr size_t kMaxSlot = 25 * 1024;
+constexpr size_t kBatchSmemMax = kMaxSlot * (kBatchThreads / 64);
+
+template <int G>
+struct Team {
+  static constexpr int nt = G, nw = G / 32;
+  static constexpr int kIdBase = kBatchThreads / G;   // 1, 2, 4, 8 for 512, 256, 128, 64
+  int tid, id, lane, warp;
+  __device__ __forceinline__ Team() : tid(threadIdx.x % G), id(threadIdx.x / G), lane(threadIdx.x & 31),
+                                      warp((threadIdx.x % G) >> 5) {}
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(kIdBase + id), "r"(G) : "memory");
   }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NT; i++) v[i] = red[i];
-  __syncthreads();
+};
+
+// ------------------------------------------------------------------------------------ the solve
+constexpr int kTerms = 20;   // team-reduced terms of one step
+// 0..4  R~: sum dx^2, dw.Qdw, Qdw.A*dy, (unused), dx.(A*dy - Qdw)
+// 5..11 eta: max rd, max |A*ybar|, max |Qxbar|, xbar.Qxbar, c.xbar, |xbar|_1, phi*(-zbar)
+// 12..15 theta~ (restart candidates): |xbar-x0|^2, (wbar-w0).(Qwbar-Qw0), (Qwbar-Qw0).(A*ybar-A*y0), (unused)
+constexpr unsigned kMaxMask = (1u << 5) | (1u << 6) | (1u << 7);
+
+// Shared-memory state of one team (carved from the block's dynamic shared memory): the
+// m-vectors (m <= 32) and the controller scalars at fixed offsets, then the dense factor's
+// intermediate t = F v (pmax entries, twice), per-warp partial sums, and optionally a copy of
+// the instance's F.  Addresses are computed from the base on use, so they take no registers.
+constexpr int kFixedD = 11 * kMaxM;   // av, ax, y, yb, y0, lo, hi, pm0, pm1 and 2 spare
+struct TS {
+  double* base;
+  int64_t pmax, fcap;
+  int nw;
+  __device__ __forceinline__ double* av() const { return base; }
+  __device__ __forceinline__ double* ax() const { return base + kMaxM; }
+  __device__ __forceinline__ double* y() const { return base + 2 * kMaxM; }
+  __device__ __forceinline__ double* yb() const { return base + 3 * kMaxM; }
+  __device__ __forceinline__ double* y0() const { return base + 4 * kMaxM; }
+  __device__ __forceinline__ double* lo() const { return base + 5 * kMaxM; }
+  __device__ __forceinline__ double* hi() const { return base + 6 * kMaxM; }
+  __device__ __forceinline__ double* pm0() const { return base + 7 * kMaxM; }
+  __device__ __forceinline__ double* pm1() const { return base + 8 * kMaxM; }
+  __device__ __forceinline__ Ctrl* C() const { return reinterpret_cast<Ctrl*>(base + kFixedD); }
+  __device__ __forceinline__ int* inst() const {
+    return reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(base + kFixedD) + sizeof(Ctrl));
+  }
+  __device__ __forceinline__ double* t0() const { return base + kFixedD + kCtrlD; }
+  __device__ __forceinline__ double* t1() const { return t0() + pmax; }
+  __device__ __forceinline__ double* wred() const { return t0() + 2 * pmax; }             // 2 kMaxM x nw
+  __device__ __forceinline__ double* red() const { return wred() + 2 * kMaxM * nw; }      // kTerms x nw + kTerms
+  __device__ __forceinline__ double* F() const { return fcap > 0 ? red() + kTerms * nw + kTerms : nullptr; }
+  static constexpr int kCtrlD = (int)((sizeof(Ctrl) + sizeof(int) + 15) / 16 * 2);   // Ctrl + inst, in doubles
+};
+
+__host__ __device__ inline size_t team_bytes(int nw, int64_t pmax, int64_t fcap) {
+  const size_t d = (size_t)(kFixedD + TS::kCtrlD + 2 * pmax + 2 * kMaxM * nw + kTerms * nw + kTerms + fcap);
+  return (d * sizeof(double) + 15) / 16 * 16;
 }
 
-// t[r] = sum_j F[r][j] x[j] (and F x1 when x1), one warp per row; result in shared t0/t1
-__device__ __forceinline__ void dense_fx(const double* __restrict__ F, int64_t p, int64_t n,
+template <int G>
+__device__ inline TS team_state(unsigned char* base, const Team<G>& T, int64_t pmax, int64_t fcap, size_t slot) {
+  TS s;
+  s.base = reinterpret_cast<double*>(base + (size_t)T.id * (G / 64) * slot);
+  s.pmax = pmax;
+  s.fcap = fcap;
+  s.nw = T.nw;
+  return s;
+}
+
+// Sum (or max, per bit of maxmask) of every thread's v[i] over the team, in a fixed order
+// (warp shuffles, then the warps' partials in warp order); every thread receives the result.
+template <int NT, int G>
+__device__ __forceinline__ void team_reduce(const Team<G>& T, double (&v)[NT], unsigned maxmask, double* red) {
+#pragma unroll
+  for (int i = 0; i < NT; i++) {
+    double a = v[i];
+    const bool mx = (maxmask >> i) & 1u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b = __shfl_down_sync(0xffffffffu, a, o);
+      a = mx ? imax(a, b) : a + b;
+    }
+    if (T.lane == 0) red[i * T.nw + T.warp] = a;
+  }
+  T.sync();
+  if (T.tid < NT) {
+    const int i = T.tid;
+    const bool mx = (maxmask >> i) & 1u;
+    double a = red[i * T.nw];
+    for (int q = 1; q < T.nw; q++) a = mx ? imax(a, red[i * T.nw + q]) : a + red[i * T.nw + q];
+    red[NT * T.nw + i] = a;
+  }
+  T.sync();
+#pragma unroll
+  for (int i = 0; i < NT; i++) v[i] = red[NT * T.nw + i];
+  T.sync();
+}
+
+// t[r] = sum_j F[r][j] x[j] (and F x1 when x1), one warp of the team per row; into t0/t1
+template <int G>
+__device__ __forceinline__ void dense_fx(const Team<G>& T, const double* __restrict__ F, int64_t p, int64_t n,
                                         const double* __restrict__ x0, const double* __restrict__ x1, double* t0,
                                         double* t1) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t r = warp; r < p; r += nw) {
+  for (int64_t r = T.warp; r < p; r += T.nw) {
     const double* Fr = F + r * n;
     double s0 = 0.0, s1 = 0.0;
-    for (int64_t j = lane; j < n; j += 32) {
+    for (int64_t j = T.lane; j < n; j += 32) {
       const double f = Fr[j];
       s0 = fma(f, x0[j], s0);
       if (x1) s1 = fma(f, x1[j], s1);
@@ -112,21 +206,20 @@ __device__ __forceinline__ void dense_fx(const double* __restrict__ F, int64_t p
       s0 += __shfl_down_sync(0xffffffffu, s0, o);
       if (x1) s1 += __shfl_down_sync(0xffffffffu, s1, o);
     }
-    if (lane == 0) {
+    if (T.lane == 0) {
       t0[r] = s0;
       if (x1) t1[r] = s1;
     }
   }
 }
 
-// (Q x)_j = sum_r F[r][j] t[r] + d_j x_j + (Q_csr x)_j for one coordinate
-__device__ __forceinline__ double q_row(const Pools& P, const Inst& I, int64_t j, const double* __restrict__ x,
-                                        const double* t) {
+// (Q x)_j = sum_r F[r][j] t[r] + d_j x_j + (Q_csr x)_j for one coordinate (F: the instance's
+// factor, in global memory or the team's shared copy)
+__device__ __forceinline__ double q_row(const Pools& P, const Inst& I, const double* F, int64_t j,
+                                        const double* __restrict__ x, const double* t) {
   double acc = 0.0;
-  if (I.p) {
-    const double* F = P.F + I.oF;
+  if (I.p)
     for (int64_t r = 0; r < I.p; r++) acc = fma(F[r * I.n + j], t[r], acc);
-  }
   if (I.has_diag) acc = fma(P.d[I.on + j], x[j], acc);
   if (I.oqrp >= 0) {
     const int* rp = P.qrp + I.oqrp;
@@ -138,24 +231,26 @@ __device__ __forceinline__ double q_row(const Pools& P, const Inst& I, int64_t j
 }
 
 // out = Q x for the whole instance (x, out in global memory, x != out); t: shared scratch (p)
-__device__ void block_qmul(const Pools& P, const Inst& I, const double* x, double* out, double* t) {
-  if (I.p) dense_fx(P.F + I.oF, I.p, I.n, x, nullptr, t, nullptr);
-  __syncthreads();
-  for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x) out[j] = q_row(P, I, j, x, t);
-  __syncthreads();
+template <int G>
+__device__ void team_qmul(const Team<G>& T, const Pools& P, const Inst& I, const double* F, const double* x,
+                          double* out, double* t) {
+  if (I.p) dense_fx(T, F, I.p, I.n, x, nullptr, t, nullptr);
+  T.sync();
+  for (int64_t j = T.tid; j < I.n; j += T.nt) out[j] = q_row(P, I, F, j, x, t);
+  T.sync();
 }
 
-// (A v)_i for all rows i into shared av[m] (and A x1 into ax[m] when x1); block pass over the
-// rows of A: per row, lanes stride its entries, warps combine in shared memory (fixed order)
-__device__ void block_amul(const Pools& P, const Inst& I, const double* __restrict__ v, const double* __restrict__ x1,
-                           double* av, double* ax, double* wred) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// (A v)_i for all rows i into shared av[m] (and A x1 into ax[m] when x1): per row, the team's
+// threads stride its entries, warps combine their partials in warp order
+template <int G>
+__device__ void team_amul(const Team<G>& T, const Pools& P, const Inst& I, const double* __restrict__ v,
+                          const double* __restrict__ x1, double* av, double* ax, double* wred) {
   const int* rp = P.arp + I.oarp;
   const int* ci = P.aci + I.oann;
   const double* a = P.av + I.oann;
   for (int64_t i = 0; i < I.m; i++) {
     double s0 = 0.0, s1 = 0.0;
-    for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) {
+    for (int k = rp[i] + T.tid; k < rp[i + 1]; k += T.nt) {
       const double aik = a[k];
       s0 = fma(aik, v[ci[k]], s0);
       if (x1) s1 = fma(aik, x1[ci[k]], s1);
@@ -165,22 +260,22 @@ __device__ void block_amul(const Pools& P, const Inst& I, const double* __restri
       s0 += __shfl_down_sync(0xffffffffu, s0, o);
       if (x1) s1 += __shfl_down_sync(0xffffffffu, s1, o);
     }
-    if (lane == 0) {
-      wred[i * 32 + warp] = s0;
-      if (x1) wred[(kMaxM + i) * 32 + warp] = s1;
+    if (T.lane == 0) {
+      wred[i * T.nw + T.warp] = s0;
+      if (x1) wred[(kMaxM + i) * T.nw + T.warp] = s1;
     }
   }
-  __syncthreads();
-  if (threadIdx.x < I.m) {
+  T.sync();
+  if (T.tid < I.m) {
     double s0 = 0.0, s1 = 0.0;
-    for (int q = 0; q < nw; q++) {
-      s0 += wred[threadIdx.x * 32 + q];
-      if (x1) s1 += wred[(kMaxM + threadIdx.x) * 32 + q];
+    for (int q = 0; q < T.nw; q++) {
+      s0 += wred[T.tid * T.nw + q];
+      if (x1) s1 += wred[(kMaxM + T.tid) * T.nw + q];
     }
-    av[threadIdx.x] = s0;
-    if (x1) ax[threadIdx.x] = s1;
+    av[T.tid] = s0;
+    if (x1) ax[T.tid] = s1;
   }
-  __syncthreads();
+  T.sync();
 }
 
 // (A^T y)_j with y in shared memory
@@ -195,42 +290,42 @@ __device__ __forceinline__ double at_row(const Pools& P, const Inst& I, int64_t 
 
 // power method of Sec. 4.1 on Q (which = 1, R^n) or A A^* (which = 0, R^m); pv, pw, tmp: global
 // scratch of the instance; returns safety * Rayleigh quotient (valid in every thread)
-__device__ double block_power(const Pools& P, const Inst& I, int which, double* pv, double* pw, double* tmp,
-                              double* t, double* av, double* wred, double* red) {
+template <int G>
+__device__ double team_power(const Team<G>& T, const Pools& P, const Inst& I, const double* F, int which, double* pv,
+                             double* pw, double* tmp, TS& S) {
   const int64_t dim = which ? I.n : I.m;
   if (dim == 0) return 0.0;
   double s2[1] = {0.0};
-  for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) {
+  for (int64_t i = T.tid; i < dim; i += T.nt) {
     const uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761u);
     const double val = 0.5 + (double)h / 4294967296.0;
     pw[i] = val;
     s2[0] = fma(val, val, s2[0]);
   }
-  bsum<1>(s2, 0u, red);
+  team_reduce<1, G>(T, s2, 0u, S.red());
   double scale = 1.0 / sqrt(s2[0]), lam = 0.0;
-  __syncthreads();
   for (long long it = 0; it < P.power_max_iter; it++) {
-    for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) pv[i] = pw[i] * scale;
-    __syncthreads();
+    for (int64_t i = T.tid; i < dim; i += T.nt) pv[i] = pw[i] * scale;
+    T.sync();
     double acc[2] = {0.0, 0.0};
     if (which) {
-      block_qmul(P, I, pv, pw, t);
-      for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) {
+      team_qmul(T, P, I, F, pv, pw, S.t0());
+      for (int64_t i = T.tid; i < dim; i += T.nt) {
         acc[0] = fma(pv[i], pw[i], acc[0]);
         acc[1] = fma(pw[i], pw[i], acc[1]);
       }
     } else {
       // w = A (A^T v): A^T v from the stored transpose, then the row pass of A
-      for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x) tmp[j] = at_row(P, I, j, pv);
-      __syncthreads();
-      block_amul(P, I, tmp, nullptr, av, nullptr, wred);
-      for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) {
-        pw[i] = av[i];
-        acc[0] = fma(pv[i], av[i], acc[0]);
-        acc[1] = fma(av[i], av[i], acc[1]);
+      for (int64_t j = T.tid; j < I.n; j += T.nt) tmp[j] = at_row(P, I, j, pv);
+      T.sync();
+      team_amul(T, P, I, tmp, nullptr, S.av(), nullptr, S.wred());
+      for (int64_t i = T.tid; i < dim; i += T.nt) {
+        pw[i] = S.av()[i];
+        acc[0] = fma(pv[i], S.av()[i], acc[0]);
+        acc[1] = fma(S.av()[i], S.av()[i], acc[1]);
       }
     }
-    bsum<2>(acc, 0u, red);
+    team_reduce<2, G>(T, acc, 0u, S.red());
     const double nw = sqrt(acc[1]);
     if (nw == 0.0 || !isfinite(nw)) return 0.0;
     const bool conv = it > 0 && fabs(acc[0] - lam) <= P.power_tol * fabs(acc[0]);
@@ -241,28 +336,11 @@ __device__ double block_power(const Pools& P, const Inst& I, int which, double* 
   return P.power_safety * lam;
 }
 
-// ------------------------------------------------------------------------------------ the solve
-constexpr int kTerms = 20;   // block-reduced terms of one step
-// 0..4  R~: sum dx^2, dw.Qdw, Qdw.A*dy, (unused), dx.(A*dy - Qdw)
-// 5..11 eta: max rd, max |A*ybar|, max |Qxbar|, xbar.Qxbar, c.xbar, |xbar|_1, phi*(-zbar)
-// 12..15 theta~ (restart candidates): |xbar-x0|^2, (wbar-w0).(Qwbar-Qw0), (Qwbar-Qw0).(A*ybar-A*y0), (unused)
-constexpr unsigned kMaxMask = (1u << 5) | (1u << 6) | (1u << 7);
-
-struct __align__(16) Shared {
-  double t0[kMaxP], t1[kMaxP];
-  double av[kMaxM], ax[kMaxM];
-  double y[kMaxM], yb[kMaxM], y0[kMaxM], lo[kMaxM], hi[kMaxM];
-  double wred[2 * kMaxM * 32];
-  double red[kTerms * 32];
-  double pm[2][kMaxM];   // power-method vectors on R^m
-  Ctrl C;
-  int inst;
-};
-
-__device__ void solve_one(const Pools& P, int idx, Shared& S) {
+template <int G>
+__device__ void solve_one(const Pools& P, int idx, const Team<G>& T, TS& S) {
   const Inst I = P.inst[idx];
   const int64_t n = I.n, m = I.m;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = T.tid, nt = T.nt;
   // instance views
   const double *c = P.c + I.on, *L = P.L + I.on, *U = P.U + I.on;
   double *x = P.x + I.on, *w = P.w + I.on, *Qw = P.Qw + I.on, *ATy = P.ATy + I.on;
@@ -273,38 +351,45 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
   double* ybg = P.yb + I.om;
   double* qat = P.qat + I.oqat;   // [j*m + i] = (Q A^T)_{j i}
   double* aqa = P.aqa + I.oaqa;   // [i*m + l]
-  Ctrl& C = S.C;
+  Ctrl& C = *S.C();
+  // the dense factor: a copy in the team's shared memory when it fits, read every step
+  const double* F = P.F + I.oF;
+  if (S.F() && I.p > 0 && I.p * n <= S.fcap) {
+    for (int64_t q = tid; q < I.p * n; q += nt) S.F()[q] = F[q];
+    T.sync();
+    F = S.F();
+  }
 
   // ---- set-up (counted in the solve, like the power method): Q A^T, A Q A^T, lambda, sigma0
   for (int64_t i = 0; i < m; i++) {
     // column i of A^T = row i of A, scattered into s1
     for (int64_t j = tid; j < n; j += nt) s1[j] = 0.0;
-    __syncthreads();
+    T.sync();
     {
       const int* rp = P.arp + I.oarp;
       const int* ci = P.aci + I.oann;
       const double* a = P.av + I.oann;
       for (int k = rp[i] + tid; k < rp[i + 1]; k += nt) s1[ci[k]] = a[k];  // distinct columns per row
     }
-    __syncthreads();
-    block_qmul(P, I, s1, s2, S.t0);
+    T.sync();
+    team_qmul(T, P, I, F, s1, s2, S.t0());
     for (int64_t j = tid; j < n; j += nt) qat[j * m + i] = s2[j];
-    __syncthreads();
+    T.sync();
   }
   for (int64_t i = 0; i < m; i++) {
     // row i of A Q A^T: A applied to column i of Q A^T
     for (int64_t j = tid; j < n; j += nt) s1[j] = qat[j * m + i];
-    __syncthreads();
-    block_amul(P, I, s1, nullptr, S.av, nullptr, S.wred);
-    if (tid < m) aqa[tid * m + i] = S.av[tid];
-    __syncthreads();
+    T.sync();
+    team_amul(T, P, I, s1, nullptr, S.av(), nullptr, S.wred());
+    if (tid < m) aqa[tid * m + i] = S.av()[tid];
+    T.sync();
   }
   double lamA = I.lamA, lamQ = I.lamQ;
-  if (m > 0 && !(lamA > 0.0)) lamA = block_power(P, I, 0, S.pm[0], S.pm[1], v, S.t0, S.av, S.wred, S.red);
+  if (m > 0 && !(lamA > 0.0)) lamA = team_power(T, P, I, F, 0, S.pm0(), S.pm1(), v, S);
   if (m > 0 && !(lamA > 0.0)) lamA = 1.0;
   if (m == 0) lamA = 0.0;
   const bool HQ = I.p || I.has_diag || I.oqrp >= 0;
-  if (HQ && !(lamQ > 0.0)) lamQ = block_power(P, I, 1, s1, s2, v, S.t0, S.av, S.wred, S.red);
+  if (HQ && !(lamQ > 0.0)) lamQ = team_power(T, P, I, F, 1, s1, s2, v, S);
   if (!HQ) lamQ = 0.0;
   double sigma = I.sigma0;
   if (!(sigma > 0.0)) {
@@ -321,21 +406,21 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
   }
   if (tid < m) {
     const double yv = I.has_ws ? P.y0in[I.om + tid] : 0.0;
-    S.y[tid] = yv;
-    S.y0[tid] = yv;
-    S.yb[tid] = 0.0;
-    S.lo[tid] = P.l[I.om + tid];
-    S.hi[tid] = P.u[I.om + tid];
+    S.y()[tid] = yv;
+    S.y0()[tid] = yv;
+    S.yb()[tid] = 0.0;
+    S.lo()[tid] = P.l[I.om + tid];
+    S.hi()[tid] = P.u[I.om + tid];
   }
-  __syncthreads();
+  T.sync();
   if (I.has_ws) {
-    block_qmul(P, I, x, Qw, S.t0);
+    team_qmul(T, P, I, F, x, Qw, S.t0());
   } else {
     for (int64_t j = tid; j < n; j += nt) Qw[j] = 0.0;
   }
   for (int64_t j = tid; j < n; j += nt) {
     Qw0[j] = Qw[j];
-    const double a = m > 0 ? at_row(P, I, j, S.y) : 0.0;
+    const double a = m > 0 ? at_row(P, I, j, S.y()) : 0.0;
     ATy[j] = a;
     ATy0[j] = a;
   }
@@ -368,7 +453,7 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
     C.status = 1;
     set_sigma(C, sigma);
   }
-  __syncthreads();
+  T.sync();
 
   // ---- Algorithm 4
   while (!C.done) {
@@ -428,51 +513,51 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
     }
     if (tid < m) {
       // Halpern / restart on y (m <= 32: one thread per row)
-      double yv = S.y[tid];
-      if (mode == 1) yv = fma(hb, fma(2.0, S.yb[tid], -yv), ha * S.y0[tid]);
+      double yv = S.y()[tid];
+      if (mode == 1) yv = fma(hb, fma(2.0, S.yb()[tid], -yv), ha * S.y0()[tid]);
       else if (mode == 2) {
-        yv = S.yb[tid];
-        S.y0[tid] = yv;
+        yv = S.yb()[tid];
+        S.y0()[tid] = yv;
       }
-      S.y[tid] = yv;
+      S.y()[tid] = yv;
     }
-    __syncthreads();
+    T.sync();
     // P2-P3: Q wbar_{1/2} (+ Q xbar), v = what + sigma (Q w - Q wbar_{1/2})
     if (HQ) {
-      if (I.p) dense_fx(P.F + I.oF, I.p, n, wh, ttest ? xb : nullptr, S.t0, S.t1);
-      __syncthreads();
+      if (I.p) dense_fx(T, F, I.p, n, wh, ttest ? xb : nullptr, S.t0(), S.t1());
+      T.sync();
       for (int64_t j = tid; j < n; j += nt) {
-        const double qwh = q_row(P, I, j, wh, S.t0);
+        const double qwh = q_row(P, I, F, j, wh, S.t0());
         Qwh[j] = qwh;
-        if (ttest) Qxb[j] = q_row(P, I, j, xb, S.t1);
+        if (ttest) Qxb[j] = q_row(P, I, F, j, xb, S.t1());
         if (m > 0) v[j] = fma(sg, Qw[j] - qwh, v[j]);
       }
-      __syncthreads();
+      T.sync();
     }
-    double T[kTerms];
+    double R[kTerms];
 #pragma unroll
-    for (int q = 0; q < kTerms; q++) T[q] = 0.0;
+    for (int q = 0; q < kTerms; q++) R[q] = 0.0;
     // P4: A v (+ A xbar), eq. (3.5) on the m rows
     if (m > 0) {
-      block_amul(P, I, v, ttest ? xb : nullptr, S.av, S.ax, S.wred);
+      team_amul(T, P, I, v, ttest ? xb : nullptr, S.av(), S.ax(), S.wred());
       if (tid < m) {
-        const double yv = S.y[tid], lo = S.lo[tid], hi = S.hi[tid];
-        const double ry = fma(-slA, yv, S.av[tid]);
+        const double yv = S.y()[tid], lo = S.lo()[tid], hi = S.hi()[tid];
+        const double ry = fma(-slA, yv, S.av()[tid]);
         const double ybv = (iclamp(ry, lo, hi) - ry) * islA;
-        S.yb[tid] = ybv;
+        S.yb()[tid] = ybv;
         ybg[tid] = ybv;
       }
-      __syncthreads();
+      T.sync();
     }
     // P5: A^* ybar, wbar (eq. (3.3)), Q wbar by linearity, the R~ / eta / theta~ sums
     for (int64_t j = tid; j < n; j += nt) {
       double atyb = 0.0, dq = 0.0;
       if (m > 0) {
-        atyb = at_row(P, I, j, S.yb);
+        atyb = at_row(P, I, j, S.yb());
         ATyb[j] = atyb;
         if (HQ) {
           const double* qa = qat + j * m;
-          for (int64_t i = 0; i < m; i++) dq = fma(qa[i], S.yb[i] - S.y[i], dq);
+          for (int64_t i = 0; i < m; i++) dq = fma(qa[i], S.yb()[i] - S.y()[i], dq);
         }
       }
       double wbv = 0.0, qwb = 0.0;
@@ -487,46 +572,46 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
         const double dx = x[j] - xbj;
         const double qdw = HQ ? Qw[j] - qwb : 0.0;
         const double ady = m > 0 ? ATy[j] - atyb : 0.0;
-        T[0] = fma(dx, dx, T[0]);
-        if (HQ) T[1] = fma(w[j] - wbv, qdw, T[1]);
-        T[2] = fma(qdw, ady, T[2]);
-        T[4] = fma(dx, ady - qdw, T[4]);
+        R[0] = fma(dx, dx, R[0]);
+        if (HQ) R[1] = fma(w[j] - wbv, qdw, R[1]);
+        R[2] = fma(qdw, ady, R[2]);
+        R[4] = fma(dx, ady - qdw, R[4]);
         // theta~ candidates from ubar - u^{r,0} (used only if this step restarts)
         const double ex = xbj - x0[j];
-        T[12] = fma(ex, ex, T[12]);
+        R[12] = fma(ex, ex, R[12]);
         if (HQ) {
           const double qe = qwb - Qw0[j];
-          T[13] = fma(wbv - w0[j], qe, T[13]);
-          T[14] = fma(qe, atyb - ATy0[j], T[14]);
+          R[13] = fma(wbv - w0[j], qe, R[13]);
+          R[14] = fma(qe, atyb - ATy0[j], R[14]);
         }
       }
       if (ttest) {
         const double xbj = xb[j], qxb = HQ ? Qxb[j] : 0.0, cj = c[j];
-        T[5] = imax(T[5], iabs(atyb - qxb + zb[j] - cj));
-        T[6] = imax(T[6], iabs(atyb));
-        T[7] = imax(T[7], iabs(qxb));
-        T[8] = fma(xbj, qxb, T[8]);
-        T[9] = fma(cj, xbj, T[9]);
-        if (I.phi != PHI_BOX) T[10] += iabs(xbj);
-        T[11] += conj_phi_term(I.phi, zb[j], L[j], U[j], I.lambda);
+        R[5] = imax(R[5], iabs(atyb - qxb + zb[j] - cj));
+        R[6] = imax(R[6], iabs(atyb));
+        R[7] = imax(R[7], iabs(qxb));
+        R[8] = fma(xbj, qxb, R[8]);
+        R[9] = fma(cj, xbj, R[9]);
+        if (I.phi != PHI_BOX) R[10] += iabs(xbj);
+        R[11] += conj_phi_term(I.phi, zb[j], L[j], U[j], I.lambda);
       }
     }
-    if (rtest || ttest) block_reduce<kTerms>(T, kMaxMask, S.red);
-    __syncthreads();
+    if (rtest || ttest) team_reduce<kTerms, G>(T, R, kMaxMask, S.red());
+    T.sync();
     // P6: controller (one thread)
     if (tid == 0) {
       double Ls[kWL], P3[kW3];
 #pragma unroll
-      for (int q = 0; q < kWL; q++) Ls[q] = T[q];
+      for (int q = 0; q < kWL; q++) Ls[q] = R[q];
       P3[0] = P3[1] = P3[2] = P3[3] = 0.0;
       double th3 = 0.0, th3r = 0.0, dyr2 = 0.0;
       for (int64_t i = 0; i < m; i++) {
-        const double dy = S.y[i] - S.yb[i];
-        const double dr = S.yb[i] - S.y0[i];
+        const double dy = S.y()[i] - S.yb()[i];
+        const double dr = S.yb()[i] - S.y0()[i];
         P3[0] = fma(dy, dy, P3[0]);
         dyr2 = fma(dr, dr, dyr2);
         if (ttest) {
-          const double ax = S.ax[i], lo = S.lo[i], hi = S.hi[i], ybv = S.yb[i];
+          const double ax = S.ax()[i], lo = S.lo()[i], hi = S.hi()[i], ybv = S.yb()[i];
           P3[1] = fmax(P3[1], fabs(ax - fmin(fmax(ax, lo), hi)));
           P3[2] = fmax(P3[2], fabs(ax));
           if (ybv > 0.0) P3[3] += lo * ybv;
@@ -535,8 +620,8 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
         if (HQ) {
           double qd = 0.0, qr = 0.0;
           for (int64_t l2 = 0; l2 < m; l2++) {
-            qd = fma(aqa[i * m + l2], S.y[l2] - S.yb[l2], qd);
-            qr = fma(aqa[i * m + l2], S.yb[l2] - S.y0[l2], qr);
+            qd = fma(aqa[i * m + l2], S.y()[l2] - S.yb()[l2], qd);
+            qr = fma(aqa[i * m + l2], S.yb()[l2] - S.y0()[l2], qr);
           }
           th3 = fma(dy, qd, th3);
           th3r = fma(dr, qr, th3r);
@@ -544,12 +629,11 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
       }
       // the single-instance controller expects s * theta_3 in Ls[3]
       Ls[3] = C.s * th3;
-      const long long r_before = C.r;
       controller(C, Ls, P3);
       if (C.restart_pending) {
         // Algorithm 5 with theta~ of eq. (3.11) from ubar^{r,tau_r} - u^{r,0}
-        double t1 = C.lamA * dyr2 + C.lamQ * T[13] - 2.0 * T[14];
-        double t2 = T[12];
+        double t1 = C.lamA * dyr2 + C.lamQ * R[13] - 2.0 * R[14];
+        double t2 = R[12];
         t1 = fmax(t1, 1e-12);
         t2 = fmax(t2, 1e-12);
         double snew;
@@ -564,42 +648,72 @@ __device__ void solve_one(const Pools& P, int idx, Shared& S) {
         }
         C.restart_pending = 0;
       }
-      (void)r_before;
     }
-    __syncthreads();
+    T.sync();
   }
   // ---- results
   if (tid == 0) {
-    Res R;
-    R.eta_p = C.eta_p;
-    R.eta_d = C.eta_d;
-    R.eta_gap = C.eta_gap;
-    R.pobj = C.pobj;
-    R.dobj = C.dobj;
-    R.sigma = C.sigma;
-    R.lamA = C.lamA;
-    R.lamQ = C.lamQ;
-    R.iters = C.k;
-    R.restarts = C.r;
-    R.status = C.status;
-    R.pad = 0;
-    P.res[idx] = R;
+    Res Rs;
+    Rs.eta_p = C.eta_p;
+    Rs.eta_d = C.eta_d;
+    Rs.eta_gap = C.eta_gap;
+    Rs.pobj = C.pobj;
+    Rs.dobj = C.dobj;
+    Rs.sigma = C.sigma;
+    Rs.lamA = C.lamA;
+    Rs.lamQ = C.lamQ;
+    Rs.iters = C.k;
+    Rs.restarts = C.r;
+    Rs.status = C.status;
+    Rs.pad = 0;
+    P.res[idx] = Rs;
   }
-  __syncthreads();
+  T.sync();
 }
 
-__global__ void __launch_bounds__(512) k_batch(Pools P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+// Schedule of one launch: buckets of instances (order[beg[b] .. beg[b+1]), each with its own
+// work counter), and per bucket the team size and the team's F copy capacity (doubles).
+struct Sched {
+  int nb;
+  unsigned slot;                 // shared-memory bytes per 64 threads in this launch
+  int team[kMaxBuckets];
+  int64_t pmax[kMaxBuckets];
+  int64_t fcap[kMaxBuckets];
+  int beg[kMaxBuckets + 1];
+  unsigned* heads;
+};
+
+// One bucket with teams of G threads: every team takes instances from the bucket's counter until
+// it is exhausted.
+template <int G>
+__device__ void run_bucket(const Pools& P, const Sched& S, int b, unsigned char* smem_raw) {
+  const Team<G> T;
+  TS ts = team_state<G>(smem_raw, T, S.pmax[b], S.fcap[b], S.slot);
+  const unsigned cnt = (unsigned)(S.beg[b + 1] - S.beg[b]);
   for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned q = atomicAdd(P.head, 1u);
-      S.inst = q < (unsigned)P.count ? P.order[q] : -1;
+    if (T.tid == 0) {
+      const unsigned q = atomicAdd(S.heads + b, 1u);
+      *ts.inst() = q < cnt ? P.order[S.beg[b] + q] : -1;
     }
-    __syncthreads();
-    const int idx = S.inst;
+    T.sync();
+    const int idx = *ts.inst();
     if (idx < 0) break;
-    solve_one(P, idx, S);
+    solve_one<G>(P, idx, T, ts);   // ends with a team barrier, so inst is free again
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch(Pools P, Sched S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // team sizes do not grow from one bucket to the next (the schedule guarantees it), so the
+  // threads of a team that leaves a bucket together form whole teams of the next one
+  for (int b = 0; b < S.nb; b++) {
+    if (S.beg[b + 1] <= S.beg[b]) continue;   // the same for every thread
+    switch (S.team[b]) {
+      case 64: run_bucket<64>(P, S, b, smem_raw); break;
+      case 128: run_bucket<128>(P, S, b, smem_raw); break;
+      case 256: run_bucket<256>(P, S, b, smem_raw); break;
+      default: run_bucket<512>(P, S, b, smem_raw); break;
+    }
   }
 }
 
@@ -620,7 +734,13 @@ struct hprqp_batch {
   std::vector<int64_t> n_of, m_of;
   Pools P;
   std::vector<void*> allocs;
-  int block = 256, per_sm = 2;
+  // schedule: instances bucketed by n (order sorted by bucket, then cost); per bucket the team
+  // size and the shared-memory F copy, chosen by the autotuner at the first solve
+  Sched sched;
+  int grid = 0;
+  size_t smem = 0;
+  std::vector<int> bucket_lo;   // smallest n of each bucket
+  std::vector<int> horder;      // host copy of the work order
   bool tuned = false;
   std::vector<Res> hres;
   std::string err;
@@ -900,15 +1020,44 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
     b->n_of.push_back(n);
     b->m_of.push_back(m);
   }
-  // work order: largest estimated cost first (dense factor passes, else n)
+  // buckets by n (largest first), and inside a bucket the largest estimated cost first (dense
+  // factor passes, else n): every team takes the next instance of its bucket from a counter
+  static const int64_t kBucketLo[kMaxBuckets] = {3000, 1500, 600, 0};
+  auto bucket_of = [](int64_t n) {
+    int bk = 0;
+    while (bk + 1 < kMaxBuckets && n < kBucketLo[bk]) bk++;
+    return bk;
+  };
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c2) {
     const auto& A = b->hinst[a];
     const auto& B = b->hinst[c2];
+    const int ba = bucket_of(A.n), bb = bucket_of(B.n);
+    if (ba != bb) return ba < bb;
     const double wa = (double)A.n * (2.0 * A.p + 30.0), wb = (double)B.n * (2.0 * B.p + 30.0);
     return wa > wb;
   });
+  {
+    Sched& S = b->sched;
+    S = Sched();
+    S.nb = kMaxBuckets;
+    int pos = 0;
+    for (int bk = 0; bk < kMaxBuckets; bk++) {
+      S.beg[bk] = pos;
+      int64_t pm = 1;
+      while (pos < count && bucket_of(b->hinst[order[pos]].n) == bk) {
+        pm = std::max<int64_t>(pm, b->hinst[order[pos]].p);
+        pos++;
+      }
+      S.pmax[bk] = pm;
+      S.team[bk] = kBatchThreads;
+      S.fcap[bk] = 0;
+      b->bucket_lo.push_back((int)kBucketLo[bk]);
+    }
+    S.beg[kMaxBuckets] = pos;
+  }
+  b->horder = order;
   Pools& P = b->P;
   std::memset(&P, 0, sizeof(P));
   P.count = count;
@@ -924,7 +1073,7 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
   int* dord;
   if ((st = bupload(b, &dord, order))) return st;
   P.order = dord;
-  std::vector<unsigned> hz(1, 0u);
+  std::vector<unsigned> hz(kMaxBuckets, 0u);
   unsigned* dh;
   if ((st = bupload(b, &dh, hz))) return st;
   P.head = dh;
@@ -977,7 +1126,8 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
   P.qv = tmp;
   BCU(b, cudaStreamSynchronize(b->stream));
   BCU(b, cudaGetDevice(&b->dev));
-  BCU(b, cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
+  b->sched.heads = P.head;
+  BCU(b, cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax));
   b->hres.resize(count);
   return HPRQP_OK;
 }
@@ -990,6 +1140,11 @@ extern "C" hprqp_status hprqp_batch_create(hprqp_batch** out, int32_t count, con
   hprqp_batch* b = new hprqp_batch();
   if (params) b->prm = *params;
   else hprqp_default_params(&b->prm);
+  const int bt = b->prm.batch_team;
+  if (bt != 0 && bt != 64 && bt != 128 && bt != 256 && bt != 512) {
+    delete b;
+    return bfail(nullptr, HPRQP_INVALID_ARG, "batch_team must be 0, 64, 128, 256 or 512");
+  }
   if (b->prm.check_every < 1 || b->prm.restart_every < 1) {
     delete b;
     return bfail(nullptr, HPRQP_INVALID_ARG, "check_every and restart_every must be >= 1");
@@ -1014,11 +1169,109 @@ extern "C" hprqp_status hprqp_batch_create(hprqp_batch** out, int32_t count, con
   return HPRQP_OK;
 }
 
-static cudaError_t batch_launch(hprqp_batch* b, int block, int grid) {
-  cudaError_t e = cudaMemsetAsync(b->P.head, 0, sizeof(unsigned), b->stream);
+// Shared memory per 64 threads that a team of G threads needs for bucket bk's state (and an F
+// copy of fcap doubles), rounded to 128 bytes.
+static size_t bucket_slot(const Sched& S, int bk, int G, int64_t fcap) {
+  const size_t per = (team_bytes(G / 32, S.pmax[bk], fcap) + (size_t)(G / 64) - 1) / (size_t)(G / 64);
+  return (per + 127) / 128 * 128;
+}
+
+// The largest F copy that a team of G threads can hold next to its state (0 if none fits).
+static int64_t bucket_fcap(const Sched& S, int bk, int G) {
+  const size_t base = team_bytes(G / 32, S.pmax[bk], 0), room = (size_t)(G / 64) * kMaxSlot;
+  if (base >= room) return 0;
+  return (int64_t)((room - base) / sizeof(double)) / 2 * 2;
+}
+
+static cudaError_t batch_launch(hprqp_batch* b, const Sched& S, int grid, size_t smem) {
+  cudaError_t e = cudaMemsetAsync(b->P.head, 0, sizeof(unsigned) * kMaxBuckets, b->stream);
   if (e != cudaSuccess) return e;
-  k_batch<<<grid, block, sizeof(Shared), b->stream>>>(b->P);
+  k_batch<<<grid, kBatchThreads, smem, b->stream>>>(b->P, S);
   return cudaGetLastError();
+}
+
+// The launch's slot: the largest that any bucket with instances needs.
+static unsigned sched_slot(const Sched& S) {
+  size_t sl = 128;
+  for (int bk = 0; bk < S.nb; bk++)
+    if (S.beg[bk + 1] > S.beg[bk]) sl = std::max(sl, bucket_slot(S, bk, S.team[bk], S.fcap[bk]));
+  return (unsigned)sl;
+}
+
+// Autotuner (row a10): per bucket of instances, largest n first, time the candidate schedules on
+// a sample of the bucket's own instances (the first 100 iterations of up to 1216 of them, one
+// launch each) and keep the fastest: teams of 64, 128, 256 or 512 threads per instance (never
+// larger than the previous bucket's, so teams only split), and for each, whether the team keeps
+// its instance's dense factor F in shared memory (when F fits the team's slots).
+static hprqp_status batch_autotune(hprqp_batch* b, int sms) {
+  Sched& S = b->sched;
+  Pools& P = b->P;
+  if (b->prm.batch_team) {
+    // one team size for every bucket, no F copies
+    for (int bk = 0; bk < kMaxBuckets; bk++) S.team[bk] = b->prm.batch_team;
+    return HPRQP_OK;
+  }
+  if (!b->prm.autotune) {
+    // fixed schedule: team size from the bucket's n, no F copies
+    const int fixed[kMaxBuckets] = {512, 256, 128, 64};
+    for (int bk = 0; bk < kMaxBuckets; bk++) S.team[bk] = fixed[bk];
+    return HPRQP_OK;
+  }
+  cudaEvent_t e0, e1;
+  BCU(b, cudaEventCreate(&e0));
+  BCU(b, cudaEventCreate(&e1));
+  const long long keep = P.max_iter;
+  P.max_iter = std::min<long long>(keep, 100);
+  int gmax = kBatchThreads;
+  for (int bk = 0; bk < kMaxBuckets; bk++) {
+    const int cnt = S.beg[bk + 1] - S.beg[bk];
+    if (cnt <= 0) continue;
+    Sched T = S;
+    T.nb = 1;
+    T.beg[0] = S.beg[bk];
+    T.beg[1] = S.beg[bk] + std::min(cnt, sms * (kBatchThreads / 64));
+    T.pmax[0] = S.pmax[bk];
+    float best = 1e30f;
+    S.team[bk] = gmax;
+    for (int G : {64, 128, 256, 512}) {
+      if (G > gmax) continue;
+      for (int fs = 0; fs < 2; fs++) {
+        const int64_t fc = fs ? bucket_fcap(S, bk, G) : 0;
+        if (fs && fc <= 0) continue;
+        if (fs) {
+          // only when F of the bucket's first (largest) instance fits the copy
+          const Inst& I0 = b->hinst[b->horder[S.beg[bk]]];
+          if (I0.p * I0.n > fc) continue;
+        }
+        T.team[0] = G;
+        T.fcap[0] = fc;
+        const size_t sl = bucket_slot(S, bk, G, fc);
+        if (sl > kMaxSlot) continue;
+        T.slot = (unsigned)sl;
+        const size_t smem = sl * (kBatchThreads / 64);
+        int occ = 0;
+        BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, smem));
+        if (occ < 1) continue;
+        const int grid = sms * occ;
+        BCU(b, cudaEventRecord(e0, b->stream));
+        BCU(b, batch_launch(b, T, grid, smem));
+        BCU(b, cudaEventRecord(e1, b->stream));
+        BCU(b, cudaEventSynchronize(e1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          S.team[bk] = G;
+          S.fcap[bk] = fc;
+        }
+      }
+    }
+    gmax = S.team[bk];
+  }
+  P.max_iter = keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return HPRQP_OK;
 }
 
 extern "C" hprqp_status hprqp_batch_solve(hprqp_batch* b, double tol, int64_t max_iter) {
@@ -1045,45 +1298,18 @@ extern "C" hprqp_status hprqp_batch_solve(hprqp_batch* b, double tol, int64_t ma
   P.sigma_golden = b->prm.sigma_golden;
   int sms = 0;
   BCU(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev));
-  // autotune the block size once (threads per instance), on the real batch with a short cap
   if (!b->tuned) {
     b->tuned = true;
-    if (b->prm.autotune && b->count > 1) {
-      cudaEvent_t e0, e1;
-      BCU(b, cudaEventCreate(&e0));
-      BCU(b, cudaEventCreate(&e1));
-      const long long keep = P.max_iter;
-      P.max_iter = std::min<long long>(keep, 50);
-      float best = 1e30f;
-      for (int blk : {128, 256, 512}) {
-        int occ = 0;
-        BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, blk, sizeof(Shared)));
-        if (occ < 1) continue;
-        const int grid = std::min(b->count, sms * occ);
-        BCU(b, cudaEventRecord(e0, b->stream));
-        BCU(b, batch_launch(b, blk, grid));
-        BCU(b, cudaEventRecord(e1, b->stream));
-        BCU(b, cudaEventSynchronize(e1));
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          b->block = blk;
-          b->per_sm = occ;
-        }
-      }
-      P.max_iter = keep;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-    } else {
-      int occ = 0;
-      BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, b->block, sizeof(Shared)));
-      b->per_sm = std::max(occ, 1);
-    }
+    hprqp_status st = batch_autotune(b, sms);
+    if (st != HPRQP_OK) return st;
+    b->sched.slot = sched_slot(b->sched);
+    b->smem = (size_t)b->sched.slot * (kBatchThreads / 64);
+    int occ = 0;
+    BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, b->smem));
+    b->grid = std::max(1, std::min(b->count, sms * std::max(occ, 1)));
   }
-  const int grid = std::min(b->count, sms * b->per_sm);
   auto t0 = std::chrono::steady_clock::now();
-  BCU(b, batch_launch(b, b->block, grid));
+  BCU(b, batch_launch(b, b->sched, b->grid, b->smem));
   b->launches = 1;
   BCU(b, cudaMemcpyAsync(b->hres.data(), P.res, sizeof(Res) * b->count, cudaMemcpyDeviceToHost, b->stream));
   BCU(b, cudaStreamSynchronize(b->stream));
@@ -1095,6 +1321,19 @@ extern "C" hprqp_status hprqp_batch_solve(hprqp_batch* b, double tol, int64_t ma
     if (r.status != 0) all = false;
   }
   return all ? HPRQP_OK : HPRQP_MAX_ITER;
+}
+
+extern "C" hprqp_status hprqp_batch_schedule(const hprqp_batch* b, int64_t* out) {
+  if (!b || !out) return HPRQP_INVALID_ARG;
+  for (int bk = 0; bk < kMaxBuckets; bk++) {
+    int64_t* o = out + 5 * bk;
+    o[0] = b->bucket_lo[bk];
+    o[1] = b->sched.beg[bk + 1] - b->sched.beg[bk];
+    o[2] = b->sched.team[bk];
+    o[3] = b->sched.fcap[bk] > 0 ? 1 : 0;
+    o[4] = b->sched.fcap[bk];
+  }
+  return HPRQP_OK;
 }
 
 extern "C" hprqp_status hprqp_batch_get(hprqp_batch* b, int32_t i, double* x, double* y, double* z, hprqp_kkt* kkt) {

@@ -119,6 +119,8 @@ struct Ctrl {
   double slA, inv_slA;       // sigma lA and its reciprocal
   double tau;                // sigma * lambda (l1 threshold)
   double ha, hb;             // pending Halpern weights 1/(i+2), (i+1)/(i+2)
+  double fha, fhb;           // weights of the Halpern step after this one (if no restart), for
+                             // the fused passes: set with t and k, so no kernel thread divides
   int mode;                  // update at the start of this iteration: 0 none, 1 Halpern, 2 restart
   int rtest, ttest;          // this iteration evaluates R~ / the stopping rule
   int done;                  // kernels return at entry

@@ -771,6 +771,7 @@ __device__ __forceinline__ void controller(Ctrl& C, const double* Ls, const doub
   C.k = kd;
   C.rtest = !C.restart_off && ((C.t == 0) || ((C.k + 1) % C.restart_every == 0));
   C.ttest = ((C.k + 1) % C.check_every == 0) || (C.k + 1 >= C.max_iter);
+  halpern_weights(C, C.fha, C.fhb);
 }
 
 __device__ __forceinline__ void set_handles(const Ctrl& C, const Handles& hd) {
@@ -875,10 +876,9 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
   const int64_t nchunks = (rows + kChunk - 1) / kChunk;
   const double sigma = C->sigma, s = C->s, slA = C->slA, inv_slA = C->inv_slA;
   const int mode = C->mode;
-  double ha = C->ha, hb = C->hb;
-  // the fused passes apply the Halpern step that follows this one (the controller sets the
-  // same weights at the end of this step)
-  if (FUSED) halpern_weights(*C, ha, hb);
+  // the fused passes apply the Halpern step that follows this one (the weights the controller
+  // will set at the end of this step, computed by it with this step's t and k)
+  const double ha = FUSED ? C->fha : C->ha, hb = FUSED ? C->fhb : C->hb;
   const bool last_of_iter = (KIND == K_Q2) || (KIND == K_Q2H) || (KIND == K_Q1 && !HA) || (KIND == K_AT && !HQ);
   EndTerms T;
   T.zero();
@@ -1223,12 +1223,10 @@ RowKernel row_kernel_q(int kind, int var, int G);
 RowKernel row_kernel_a(int kind, int var, int G);
 RowKernel row_kernel_at(int kind, int var, int G);
 
-// kinds whose CSR passes may run from SELL copies (A, A^T, thin factor transposes); a matrix
-// without a copy takes one lane per row in the same pass
+// kinds whose CSR pass is one matrix with a SELL copy (A or A^T)
 constexpr bool sell_kind(int kind) {
   return kind == K_A1 || kind == K_APPLY_A || kind == K_POWER_A || kind == K_AT || kind == K_APPLY_AT ||
-         kind == K_APPLY_AT_P || kind == K_ATH || kind == K_Q1 || kind == K_Q2 || kind == K_Q2H ||
-         kind == K_APPLY_Q || kind == K_POWER_Q;
+         kind == K_APPLY_AT_P || kind == K_ATH;
 }
 
 template <int KIND>

@@ -18,10 +18,10 @@
 namespace hprqp {
 namespace {
 
-constexpr unsigned kBarSpin = 1u << 24;   // polls of one barrier wait (well over a second)
+constexpr unsigned kBarSpin = 1u << 24;   // default polls of one barrier wait (well over a second)
 
-// bar[0]: arrivals, bar[1]: generation; err: set when a wait gives up
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+// bar[0]: arrivals, bar[1]: generation; err: set when a wait gives up after `spin` polls
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned spin) {
   __shared__ int ok;
   __syncthreads();
   if (gridDim.x == 1) return true;
@@ -36,7 +36,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
       atomicAdd(&bar[1], 1u);
     } else {
       for (unsigned i = 0; *gen_p == gen; ++i) {
-        if (i >= kBarSpin || *(volatile int*)err) {
+        if (i >= spin || *(volatile int*)err) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -63,13 +63,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
   } while (0)
 
 #define HPRQP_SYNC() \
-  if (!grid_barrier(p.bar, p.err)) return
+  if (!grid_barrier(p.bar, p.err, p.spin)) return
 
 struct PersistParams {
   int gq, ga, gat, gpre;   // lanes per row (1 or 4) and of the pre-pass (1 or 8)
   long long steps;         // inner steps of this launch at most
   unsigned* bar;
   int* err;
+  unsigned spin;           // polls of one barrier wait before it gives up
 };
 
 __global__ void __launch_bounds__(kThreads) k_persist(Args a, PersistParams p) {
@@ -140,7 +141,7 @@ int persist_max_blocks(int sms) {
 }
 
 cudaError_t launch_persist(const Args& a, const Plan& pl, int grid, long long steps, unsigned* bar, int* err,
-                           cudaStream_t s) {
+                           unsigned spin, cudaStream_t s) {
   Args ag = a;
   ag.nbM = grid;   // the y-step partials of this launch have one row per block
   PersistParams p;
@@ -151,6 +152,7 @@ cudaError_t launch_persist(const Args& a, const Plan& pl, int grid, long long st
   p.steps = steps;
   p.bar = bar;
   p.err = err;
+  p.spin = spin > 0 ? spin : kBarSpin;
   void* args[] = {&ag, &p};
   return cudaLaunchCooperativeKernel((const void*)k_persist, dim3(grid), dim3(kThreads), args, 0, s);
 }

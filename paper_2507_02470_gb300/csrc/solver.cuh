@@ -140,10 +140,11 @@ cudaError_t launch_vmul(double* v, const double* s, int64_t n, cudaStream_t st);
 // out[i] = v[i] * s[i] for i < n
 cudaError_t launch_vmul_to(double* out, const double* v, const double* s, int64_t n, cudaStream_t st);
 // Persistent solver (persist.cu): co-resident blocks of its kernel on `sms` SMs, and one
-// cooperative launch running at most `steps` inner steps (bar: 2 zeroed words; err: flag).
+// cooperative launch running at most `steps` inner steps (bar: 2 zeroed words; err: flag; spin:
+// polls of one barrier wait, 0 for the default of about a second).
 int persist_max_blocks(int sms);
 cudaError_t launch_persist(const Args& a, const Plan& p, int grid, long long steps, unsigned* bar, int* err,
-                           cudaStream_t s);
+                           unsigned spin, cudaStream_t s);
 // Primal HPR methods of Appendix A (primal.cu): the elementwise steps and the stopping rule
 cudaError_t primal_rows(const double* Ax, const double* y, const double* l, const double* u, double sigma, int64_t m,
                         double* sb, double* yb, double* w, cudaStream_t s);

@@ -347,8 +347,46 @@ class LearnedWarmStart:
                                        sig[b0:b1].data_ptr(), _sp(self.stream)))
         return Z0, sig
 
+    # ---------------------------------------------------------------- persistence
+    def save(self, path, **meta):
+        """Everything inference needs, in one .npz: the layers' weights as BF16 bits (the
+        forward pass multiplies BF16 weights, so nothing it uses is lost), the biases, the mean
+        training solution mu, the feature and log-sigma statistics, and `meta` (e.g. the family
+        and the training set it came from)."""
+        arrs = {"dims": np.asarray(self.dims, np.int64), "n": self.n, "m": self.m,
+                "mu": self.mu.cpu().numpy(), "fmean": self.fmean.cpu().numpy(), "fistd": self.fistd.cpu().numpy(),
+                "s_mean": self.s_mean, "s_istd": self.s_istd}
+        for li in range(len(self.dims) - 1):
+            W, b = self.mlp.get_layer(li)
+            arrs[f"W{li}"] = bf16_bits_rne(W)
+            arrs[f"b{li}"] = b
+        for k, v in meta.items():
+            arrs["meta_" + k] = np.asarray(v)
+        np.savez_compressed(path, **arrs)
+
+    def load(self, path):
+        """The state written by save() (same sizes and seed); returns its meta entries."""
+        torch = _torch()
+        z = np.load(path)
+        if list(z["dims"]) != self.dims or int(z["n"]) != self.n or int(z["m"]) != self.m:
+            raise ValueError(f"{path}: network of another shape")
+        for li in range(len(self.dims) - 1):
+            W = (z[f"W{li}"].astype(np.uint32) << 16).view(np.float32)
+            self.mlp.set_layer(li, W, z[f"b{li}"])
+        self.mu = torch.from_numpy(z["mu"]).to(self.device)
+        self.fmean = torch.from_numpy(z["fmean"]).to(self.device)
+        self.fistd = torch.from_numpy(z["fistd"]).to(self.device)
+        self.s_mean, self.s_istd = float(z["s_mean"]), float(z["s_istd"])
+        return {k[5:]: z[k] for k in z.files if k.startswith("meta_")}
+
     def close(self):
         self.mlp.close()
+
+
+def bf16_bits_rne(a):
+    """float32 array -> BF16 bit patterns (uint16), rounded to nearest, ties to even."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
 
 
 def solve_members(base, data, N, stream=None, Z=None, starts=None, lam=None, tol=1e-8, workers=1,

@@ -38,14 +38,18 @@ def mixed_batch():
     return probs
 
 
-def test_batch_first_iterates(pkg):
+@pytest.mark.parametrize("autotune", [1, 0])
+def test_batch_first_iterates(pkg, autotune):
+    """autotune = 0 runs the fixed schedule, which gives the four buckets of this batch (n >= 3000,
+    1500..2999, 600..1499, below 600) teams of 512, 256, 128 and 64 threads: every team size
+    reproduces the oracle's iterates."""
     probs = mixed_batch()
     K = 40
     refs = [oracle.solve(qp, tol=1e-30, max_iter=K, trace_len=K, scaling=0) for qp in probs]
     lamA = [r.lambda_A for r in refs]
     lamQ = [r.lambda_Q for r in refs]
     for k in (1, 2, 11, 21, 40):
-        with pkg.BatchSolver(probs, lambda_A=lamA, lambda_Q=lamQ) as b:
+        with pkg.BatchSolver(probs, lambda_A=lamA, lambda_Q=lamQ, autotune=autotune) as b:
             b.solve(tol=1e-30, max_iter=k)
             for i, (qp, ref) in enumerate(zip(probs, refs)):
                 x, y, z, kkt = b.get(i)
@@ -66,6 +70,23 @@ def test_batch_converged(pkg):
             assert abs(kkt["pobj"] - ref.pobj) <= 1e-6 * (1 + abs(ref.pobj)), i
             e, _, _ = oracle.eta(qp, x, y, z)
             assert np.max(e) <= 1.05e-8, (i, e)
+
+
+def test_batch_schedule_is_reported(pkg):
+    """The autotuner's choice per bucket of n (threads per instance, F in shared memory): every
+    bucket with instances gets a team of 64..512 threads, an F copy only where it fits."""
+    probs = mixed_batch()
+    with pkg.BatchSolver(probs) as b:
+        assert b.solve(tol=1e-8, max_iter=400000) == "converged"
+        sched = b.schedule()
+    assert [s["n_from"] for s in sched] == [3000, 1500, 600, 0]
+    assert sum(s["instances"] for s in sched) == len(probs)
+    assert [s["instances"] for s in sched] == [1, 1, 1, 5]
+    for s in sched:
+        assert s["threads"] in (64, 128, 256, 512)
+        assert s["f_capacity"] >= 0 and s["f_in_smem"] == (s["f_capacity"] > 0)
+    # the F copy of the largest instance (5000 x 250 doubles, 10 MB) cannot fit
+    assert not sched[0]["f_in_smem"]
 
 
 def test_batch_power_method_and_defaults(pkg):

@@ -170,3 +170,21 @@ def test_iters_per_launch_changes_nothing(pkg, per):
     for u, v in zip(a[:4], b[:4]):
         assert np.array_equal(u, v)
     assert a[4] == b[4]
+
+
+def test_persistent_barrier_wait_gives_up_and_the_handle_recovers(pkg):
+    """launch_mode 3 with a grid-barrier wait of one poll: a block that reaches a barrier before
+    the others gives up at once, sets the error flag, and every block leaves at its next barrier
+    (all waits bounded), so the solve returns HPRQP_TIMEOUT with the context intact.  With the
+    default wait the same handle then solves to the oracle's objective."""
+    qp = qpgen.large_cqp(n=5000, m=2500, seed=1)
+    ref = oracle.solve(qp, tol=1e-8, max_iter=200000)
+    with pkg.Solver(qp, launch_mode=3, lambda_A=ref.lambda_A, lambda_Q=ref.lambda_Q) as s:
+        s.set_wait_polls(1)
+        with pytest.raises(pkg.HPRQPError) as e:
+            s.solve(tol=1e-8, max_iter=200000)
+        assert e.value.status == 6          # HPRQP_TIMEOUT
+        s.set_wait_polls(0)
+        assert s.solve(tol=1e-8, max_iter=200000) == "converged"
+        k = s.kkt()
+    assert abs(k["pobj"] - ref.pobj) <= 1e-6 * (1 + abs(ref.pobj))
