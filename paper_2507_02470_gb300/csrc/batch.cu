@@ -150,7 +150,7 @@ __host__ __device__ inline size_t team_bytes(int nw, int64_t pmax, int64_t fcap)
 }
 
 template <int G>
-__device__ inline TS team_state(unsigned char* base, const Team<G>& T, int64_t pmax, int64_t fcap, size_t slot) {
+__device__ inline TS team_state(unsigned char* base, const Team<G> T, int64_t pmax, int64_t fcap, size_t slot) {
   TS s;
   s.base = reinterpret_cast<double*>(base + (size_t)T.id * (G / 64) * slot);
   s.pmax = pmax;
@@ -162,7 +162,7 @@ __device__ inline TS team_state(unsigned char* base, const Team<G>& T, int64_t p
 // Sum (or max, per bit of maxmask) of every thread's v[i] over the team, in a fixed order
 // (warp shuffles, then the warps' partials in warp order); every thread receives the result.
 template <int NT, int G>
-__device__ __forceinline__ void team_reduce(const Team<G>& T, double (&v)[NT], unsigned maxmask, double* red) {
+__device__ __forceinline__ void team_reduce(const Team<G> T, double (&v)[NT], unsigned maxmask, double* red) {
 #pragma unroll
   for (int i = 0; i < NT; i++) {
     double a = v[i];
@@ -190,7 +190,7 @@ __device__ __forceinline__ void team_reduce(const Team<G>& T, double (&v)[NT], u
 
 // t[r] = sum_j F[r][j] x[j] (and F x1 when x1), one warp of the team per row; into t0/t1
 template <int G>
-__device__ __forceinline__ void dense_fx(const Team<G>& T, const double* __restrict__ F, int64_t p, int64_t n,
+__device__ __forceinline__ void dense_fx(const Team<G> T, const double* __restrict__ F, int64_t p, int64_t n,
                                         const double* __restrict__ x0, const double* __restrict__ x1, double* t0,
                                         double* t1) {
   for (int64_t r = T.warp; r < p; r += T.nw) {
@@ -232,7 +232,7 @@ __device__ __forceinline__ double q_row(const Pools& P, const Inst& I, const dou
 
 // out = Q x for the whole instance (x, out in global memory, x != out); t: shared scratch (p)
 template <int G>
-__device__ void team_qmul(const Team<G>& T, const Pools& P, const Inst& I, const double* F, const double* x,
+__device__ __forceinline__ void team_qmul(const Team<G> T, const Pools& P, const Inst& I, const double* F, const double* x,
                           double* out, double* t) {
   if (I.p) dense_fx(T, F, I.p, I.n, x, nullptr, t, nullptr);
   T.sync();
@@ -243,7 +243,7 @@ __device__ void team_qmul(const Team<G>& T, const Pools& P, const Inst& I, const
 // (A v)_i for all rows i into shared av[m] (and A x1 into ax[m] when x1): per row, the team's
 // threads stride its entries, warps combine their partials in warp order
 template <int G>
-__device__ void team_amul(const Team<G>& T, const Pools& P, const Inst& I, const double* __restrict__ v,
+__device__ __forceinline__ void team_amul(const Team<G> T, const Pools& P, const Inst& I, const double* __restrict__ v,
                           const double* __restrict__ x1, double* av, double* ax, double* wred) {
   const int* rp = P.arp + I.oarp;
   const int* ci = P.aci + I.oann;
@@ -291,8 +291,8 @@ __device__ __forceinline__ double at_row(const Pools& P, const Inst& I, int64_t 
 // power method of Sec. 4.1 on Q (which = 1, R^n) or A A^* (which = 0, R^m); pv, pw, tmp: global
 // scratch of the instance; returns safety * Rayleigh quotient (valid in every thread)
 template <int G>
-__device__ double team_power(const Team<G>& T, const Pools& P, const Inst& I, const double* F, int which, double* pv,
-                             double* pw, double* tmp, TS& S) {
+__device__ __forceinline__ double team_power(const Team<G> T, const Pools& P, const Inst& I, const double* F, int which, double* pv,
+                             double* pw, double* tmp, const TS S) {
   const int64_t dim = which ? I.n : I.m;
   if (dim == 0) return 0.0;
   double s2[1] = {0.0};
@@ -336,8 +336,8 @@ __device__ double team_power(const Team<G>& T, const Pools& P, const Inst& I, co
   return P.power_safety * lam;
 }
 
-template <int G>
-__device__ void solve_one(const Pools& P, int idx, const Team<G>& T, TS& S) {
+template <int G, bool FS>
+__device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G> T, const TS S) {
   const Inst I = P.inst[idx];
   const int64_t n = I.n, m = I.m;
   const int tid = T.tid, nt = T.nt;
@@ -353,11 +353,15 @@ __device__ void solve_one(const Pools& P, int idx, const Team<G>& T, TS& S) {
   double* aqa = P.aqa + I.oaqa;   // [i*m + l]
   Ctrl& C = *S.C();
   // the dense factor: a copy in the team's shared memory when it fits, read every step
+  // FS (whole-block teams only): the team's shared-memory copy, which the schedule offers only
+  // when every instance of the bucket fits; otherwise F is read from global memory (one address
+  // space per instantiation keeps the hot loops' loads plain and unaliased)
   const double* F = P.F + I.oF;
-  if (S.F() && I.p > 0 && I.p * n <= S.fcap) {
-    for (int64_t q = tid; q < I.p * n; q += nt) S.F()[q] = F[q];
+  if constexpr (FS) {
+    double* Fs = S.F();
+    for (int64_t q = tid; q < I.p * n; q += nt) Fs[q] = F[q];
     T.sync();
-    F = S.F();
+    F = Fs;
   }
 
   // ---- set-up (counted in the solve, like the power method): Q A^T, A Q A^T, lambda, sigma0
@@ -685,7 +689,7 @@ struct Sched {
 
 // One bucket with teams of G threads: every team takes instances from the bucket's counter until
 // it is exhausted.
-template <int G>
+template <int G, bool FS>
 __device__ void run_bucket(const Pools& P, const Sched& S, int b, unsigned char* smem_raw) {
   const Team<G> T;
   TS ts = team_state<G>(smem_raw, T, S.pmax[b], S.fcap[b], S.slot);
@@ -698,7 +702,7 @@ __device__ void run_bucket(const Pools& P, const Sched& S, int b, unsigned char*
     T.sync();
     const int idx = *ts.inst();
     if (idx < 0) break;
-    solve_one<G>(P, idx, T, ts);   // ends with a team barrier, so inst is free again
+    solve_one<G, FS>(P, idx, T, ts);   // ends with a team barrier, so inst is free again
   }
 }
 
@@ -709,10 +713,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(Pools P, Sched S) {
   for (int b = 0; b < S.nb; b++) {
     if (S.beg[b + 1] <= S.beg[b]) continue;   // the same for every thread
     switch (S.team[b]) {
-      case 64: run_bucket<64>(P, S, b, smem_raw); break;
-      case 128: run_bucket<128>(P, S, b, smem_raw); break;
-      case 256: run_bucket<256>(P, S, b, smem_raw); break;
-      default: run_bucket<512>(P, S, b, smem_raw); break;
+      case 64: run_bucket<64, false>(P, S, b, smem_raw); break;
+      case 128: run_bucket<128, false>(P, S, b, smem_raw); break;
+      case 256: run_bucket<256, false>(P, S, b, smem_raw); break;
+      default:
+        if (S.fcap[b] > 0) run_bucket<512, true>(P, S, b, smem_raw);
+        else run_bucket<512, false>(P, S, b, smem_raw);
+        break;
     }
   }
 }
@@ -1236,12 +1243,17 @@ static hprqp_status batch_autotune(hprqp_batch* b, int sms) {
     for (int G : {64, 128, 256, 512}) {
       if (G > gmax) continue;
       for (int fs = 0; fs < 2; fs++) {
+        if (fs && G != kBatchThreads) continue;   // F copies for whole-block teams only
         const int64_t fc = fs ? bucket_fcap(S, bk, G) : 0;
         if (fs && fc <= 0) continue;
         if (fs) {
-          // only when F of the bucket's first (largest) instance fits the copy
-          const Inst& I0 = b->hinst[b->horder[S.beg[bk]]];
-          if (I0.p * I0.n > fc) continue;
+          // only when the F of every instance of the bucket fits the copy
+          int64_t need = 0;
+          for (int q = S.beg[bk]; q < S.beg[bk + 1]; q++) {
+            const Inst& Iq = b->hinst[b->horder[q]];
+            need = std::max<int64_t>(need, Iq.p * Iq.n);
+          }
+          if (need == 0 || need > fc) continue;
         }
         T.team[0] = G;
         T.fcap[0] = fc;

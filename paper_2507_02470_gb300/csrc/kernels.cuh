@@ -1059,8 +1059,10 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
 
 template <int G, int KIND, int VAR>
 // plain steps keep six blocks per SM resident (at most 40 registers): their passes are
-// latency-bound gathers, so occupancy matters more than a few extra registers
-__global__ void __launch_bounds__(kThreads, (VAR == VAR_PLAIN || KIND == K_ATH || KIND == K_Q2H) ? 6 : 1)
+// latency-bound gathers, so occupancy matters more than a few extra registers; the variants that
+// reduce (R~ and stopping tests) keep four (at most 64 registers: unbounded they took 80-112
+// registers and ran at a quarter of the SM's warps, twice as long as the plain passes)
+__global__ void __launch_bounds__(kThreads, (VAR == VAR_PLAIN || KIND == K_ATH || KIND == K_Q2H) ? 6 : 4)
     k_rows(Args a, Handles hd) {
   pdl_enter();
   rows_body<G, KIND, VAR>(a, hd);

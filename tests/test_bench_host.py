@@ -140,3 +140,18 @@ def test_l2_note_states_which_timing_rule_applies():
     assert big > 129e6 > 1e6 > small
     assert bench.l2_note(big).startswith("inputs larger than L2")
     assert "fits in L2" in bench.l2_note(small) and "whole solve" in bench.l2_note(small)
+
+
+def test_committed_network_matches_the_learned_configuration():
+    """The network that the default line's 'learned' key evaluates: MLP 512-1024-1024-257 for
+    the n = 1e5, m = 5e4 family, trained on the configured 20,000 members, weights as BF16 bits,
+    the mean training solution over all n + m coordinates."""
+    z = np.load(bench.NETWORK)
+    assert list(z["dims"]) == [512, 1024, 1024, 257]
+    assert int(z["n"]) == 100_000 and int(z["m"]) == 50_000
+    assert int(z["meta_train"]) == 20_000 and int(z["meta_epochs"]) == 30
+    assert z["mu"].shape == (150_000,) and np.all(np.isfinite(z["mu"]))
+    for li, (o, i) in enumerate(((1024, 512), (1024, 1024), (257, 1024))):
+        W = (z[f"W{li}"].astype(np.uint32) << 16).view(np.float32)
+        assert W.shape == (o, i) and np.all(np.isfinite(W)) and z[f"b{li}"].shape == (o,)
+    assert float(z["meta_lambda_A"]) > 0 and float(z["meta_lambda_Q"]) > 0
