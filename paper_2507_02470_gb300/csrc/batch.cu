@@ -102,9 +102,9 @@ struct Team {
   int tid, id, lane, warp;
   __device__ __forceinline__ Team() : tid(threadIdx.x % G), id(threadIdx.x / G), lane(threadIdx.x & 31),
                                       warp((threadIdx.x % G) >> 5) {}
-  __device__ __forceinline__ void sync() const {
-    asm volatile("bar.sync %0, %1;" ::"r"(kIdBase + id), "r"(G) : "memory");
-  }
+  // the named-barrier intrinsic (not inline assembly): the compiler knows it for a barrier
+  // and keeps values it can prove unchanged in registers across it
+  __device__ __forceinline__ void sync() const { __barrier_sync_count(kIdBase + id, G); }
 };
 
 // ------------------------------------------------------------------------------------ the solve
@@ -196,7 +196,25 @@ __device__ __forceinline__ void dense_fx(const Team<G> T, const double* __restri
   for (int64_t r = T.warp; r < p; r += T.nw) {
     const double* Fr = F + r * n;
     double s0 = 0.0, s1 = 0.0;
-    for (int64_t j = T.lane; j < n; j += 32) {
+    // four strides of the row per round, every load issued before the FMAs (the sums keep the
+    // order of the one-at-a-time loop): the pass is bound by load latency, not FP64 issue
+    int64_t j = T.lane;
+    for (; j + 96 < n; j += 128) {
+      const double f0 = Fr[j], f1 = Fr[j + 32], f2 = Fr[j + 64], f3 = Fr[j + 96];
+      const double a0 = x0[j], a1 = x0[j + 32], a2 = x0[j + 64], a3 = x0[j + 96];
+      s0 = fma(f0, a0, s0);
+      s0 = fma(f1, a1, s0);
+      s0 = fma(f2, a2, s0);
+      s0 = fma(f3, a3, s0);
+      if (x1) {
+        const double b0 = x1[j], b1 = x1[j + 32], b2 = x1[j + 64], b3 = x1[j + 96];
+        s1 = fma(f0, b0, s1);
+        s1 = fma(f1, b1, s1);
+        s1 = fma(f2, b2, s1);
+        s1 = fma(f3, b3, s1);
+      }
+    }
+    for (; j < n; j += 32) {
       const double f = Fr[j];
       s0 = fma(f, x0[j], s0);
       if (x1) s1 = fma(f, x1[j], s1);
@@ -218,8 +236,23 @@ __device__ __forceinline__ void dense_fx(const Team<G> T, const double* __restri
 __device__ __forceinline__ double q_row(const Pools& P, const Inst& I, const double* F, int64_t j,
                                         const double* __restrict__ x, const double* t) {
   double acc = 0.0;
-  if (I.p)
-    for (int64_t r = 0; r < I.p; r++) acc = fma(F[r * I.n + j], t[r], acc);
+  if (I.p) {
+    // column j of F, eight entries per round with their loads ahead of the FMAs (same order of
+    // the sum as one entry at a time)
+    const int64_t p = I.p, n = I.n;
+    const double* Fj = F + j;
+    int64_t r = 0;
+    for (; r + 8 <= p; r += 8, Fj += 8 * n) {
+      double f[8], tv[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) f[q] = Fj[q * n];
+#pragma unroll
+      for (int q = 0; q < 8; q++) tv[q] = t[r + q];
+#pragma unroll
+      for (int q = 0; q < 8; q++) acc = fma(f[q], tv[q], acc);
+    }
+    for (; r < p; r++, Fj += n) acc = fma(*Fj, t[r], acc);
+  }
   if (I.has_diag) acc = fma(P.d[I.on + j], x[j], acc);
   if (I.oqrp >= 0) {
     const int* rp = P.qrp + I.oqrp;

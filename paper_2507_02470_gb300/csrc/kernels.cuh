@@ -914,7 +914,11 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
     } else if (KIND == K_APPLY_AT_P) {
       csr_chunk<G, 1>(a.AT, row0, V.pv, nullptr, rs0, rs1, false);
     }
-    __syncthreads();
+    // With one lane per row (G = 1) every part of phase 1 leaves row r's sum to thread r, the
+    // thread that reads it in phase 2 and overwrites it in the next chunk: no barrier is needed,
+    // and a warp whose rows are short does not wait for the block's slowest row.  The staged and
+    // SELL forms (G = 0, -1) and groups of G > 1 lanes write sums of other threads' rows.
+    if constexpr (G != 1) __syncthreads();
     // ---- phase 2: thread per row, full warps
     const int64_t j = row0 + threadIdx.x;
     if (j < rows) {
@@ -1013,7 +1017,7 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
         pw[1] = fma(wv, wv, pw[1]);
       }
     }
-    __syncthreads();
+    if constexpr (G != 1) __syncthreads();   // rs0 / rs1 are reused by the next chunk
   }
 
   // ---- block reductions / controllers
