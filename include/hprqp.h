@@ -120,7 +120,8 @@ typedef struct hprqp_params {
                                 form for every CSR pass; 3: the SELL-32 copy for the A and
                                 A^T passes (rows sorted by length inside each 256-row chunk,
                                 one row per lane), one lane per row elsewhere */
-  int32_t verbose;           /* 0: silent; 2: wall time of each phase of hprqp_create on stderr */
+  int32_t verbose;           /* 0: silent; 2: wall time of each phase of hprqp_create, and the
+                                batched autotuner's timings, on stderr */
   hprqp_alloc_fn alloc;      /* optional allocator hooks (see above) */
   hprqp_free_fn free;
   void* alloc_ctx;
@@ -178,7 +179,7 @@ typedef struct hprqp_params {
                                 gives up with HPRQP_TIMEOUT; 0 (default): about a second */
   int32_t batch_team;        /* batched solver: 0 (default) threads per instance chosen per bucket
                                 of n (autotune 1: timed on the batch; 0: 512/256/128/64 from the
-                                largest n down); 64, 128, 256 or 512: that team size for all */
+                                largest n down); 64, 128, 256 or 512: that block size for all */
 } hprqp_params;
 
 /* Residuals at the returned bar iterate (Sec. 4.1) and solve statistics. */
@@ -336,10 +337,12 @@ hprqp_status hprqp_fp64_rate(int32_t op, int32_t lanes, double* lanes_per_clk, d
 
 /* ------------------------------------------------------------------------------------------
  * Batched solver: many independent instances of eq. (1.1), each run through Algorithm 4 with
- * its own sigma, restart and termination state, in one persistent kernel launch.  Instances are
- * bucketed by n; in each bucket a team of threads (64 to 512, chosen per bucket by an autotuner
- * that times the candidates on the batch itself) solves one instance at a time, taking the next
- * from the bucket's work queue (largest estimated cost first).
+ * its own sigma, restart and termination state.  Instances are bucketed by n, and each bucket
+ * runs as one persistent kernel launch in which a thread block (64 to 512 threads, chosen per
+ * bucket by an autotuner that times the candidates on the batch itself, as is a shared-memory
+ * copy of the instance's dense factor) solves one instance at a time, taking the next from the
+ * bucket's work queue (largest estimated cost first).  The launches of the buckets overlap on
+ * internal streams forked from and joined back to the batch's stream.
  * Supported Q terms per instance: at most one DIAG, one DENSE_FACTOR (p <= 1024) and one CSR.
  * m <= HPRQP_BATCH_MAX_M rows per instance (the second Q product of a step and the theta
  * terms of eqs. (2.12), (3.11) use Q A^T and A Q A^T, formed once per solve).
@@ -365,8 +368,8 @@ typedef struct hprqp_problem {
 typedef struct hprqp_batch hprqp_batch;
 
 /* Copies `count` (>= 1) problems (host or device pointers) to the device.  params: as for
- * hprqp_create (stream, alphas, periods, power method, autotune; NULL = defaults).  The
- * autotuner times the persistent kernel's block size on a sample of the batch at the first
+ * hprqp_create (stream, alphas, periods, power method, autotune, batch_team; NULL = defaults).
+ * The autotuner times each bucket's block size and F copy on a sample of the bucket at the first
  * solve.  Batched instances are solved without the Sec. 4.1 preconditioning (params.scaling
  * is ignored). */
 hprqp_status hprqp_batch_create(hprqp_batch** b, int32_t count, const hprqp_problem* probs,
@@ -385,9 +388,9 @@ hprqp_status hprqp_batch_get(hprqp_batch* b, int32_t i, double* x, double* y, do
 hprqp_status hprqp_batch_stats(hprqp_batch* b, double* seconds, int64_t* kernel_launches);
 /* Bookkeeping, with no counterpart in the paper: the schedule the autotuner chose at the first
  * hprqp_batch_solve.  Instances are bucketed by n (largest first); for each of the 4 buckets,
- * out[5*k .. 5*k+4] = smallest n of the bucket, instances in it, threads per instance (a team of
- * 64..512 threads of a 512-thread block), 1 if a team keeps its instance's dense factor F in
- * shared memory (else 0), and that copy's capacity in doubles.  Host pointer to 20 int64. */
+ * out[5*k .. 5*k+4] = smallest n of the bucket, instances in it, threads per instance (the block
+ * size, 64..512), 1 if a block keeps its instance's dense factor F in shared memory (else 0),
+ * and that copy's capacity in doubles.  Host pointer to 20 int64. */
 hprqp_status hprqp_batch_schedule(const hprqp_batch* b, int64_t* out);
 void hprqp_batch_destroy(hprqp_batch* b);
 const char* hprqp_batch_last_error(const hprqp_batch* b);

@@ -509,7 +509,8 @@ class BatchSolver:
         return {"seconds": sec.value, "kernel_launches": n.value}
 
     def schedule(self):
-        """Per bucket of instances (by n): the autotuner's team size and shared-memory F copy."""
+        """Per bucket of instances (by n): the autotuner's block size (threads per instance) and
+        shared-memory F copy."""
         out = np.zeros(20, np.int64)
         self._check(lib().hprqp_batch_schedule(self.h, _ptr(out)))
         return [{"n_from": int(out[5 * k]), "instances": int(out[5 * k + 1]), "threads": int(out[5 * k + 2]),

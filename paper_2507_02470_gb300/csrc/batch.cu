@@ -1,8 +1,12 @@
-// Batched HPR-QP: many independent instances of eq. (1.1) in one persistent kernel.
+// Batched HPR-QP: many independent instances of eq. (1.1), one persistent launch per bucket of n.
 //
 // One thread block owns one instance at a time and runs Algorithm 4 on it to the end, with its
 // own sigma, restart and termination state (Sec. 3.2-3.3, Sec. 4.1); blocks take instances from
-// an atomic work queue ordered by estimated cost, largest first.  No block ever waits on another.
+// their bucket's atomic work queue, ordered by estimated cost, largest first.  No block ever
+// waits on another.  The buckets' launches are queued on parallel streams, largest n first, so
+// an SM whose block leaves an exhausted bucket starts blocks of the next one.  Per bucket the
+// autotuner picks the block size (64 to 512 threads per instance) and whether a block keeps its
+// instance's dense factor F in shared memory for the whole solve.
 //
 // Per inner step the only work of order k*n is Q xbar-type products through the dense factor
 // (t = F v, then F^T t); everything else is elementwise or of order m*n with m <= 32:
@@ -79,142 +83,32 @@ struct Pools {
   int halpern_total, restart_off, sigma_fixed, sigma_golden;
 };
 
-// ------------------------------------------------------------------------------------ teams
-// A block of kBatchThreads threads works as teams of 64, 128, 256 or 512 consecutive threads; a
-// team solves one instance at a time and synchronises on its own named barrier.  Buckets of
-// instances (by n, largest first) run in order with non-increasing team sizes: a team that finds
-// its bucket exhausted splits into the next bucket's smaller teams at once, without waiting for
-// the other teams of its block.  Barrier ids are assigned by size and position (512: id 1; 256:
-// 2-3; 128: 4-7; 64: 8-15), so a team and the sub-teams of another never share an id, and the
-// shared memory of a team is the kSlotBytes slots of its 64-thread groups.
-constexpr int kBatchThreads = 512;
-constexpr int kMaxBuckets = 4;
-// Shared memory per 64 threads: at most kMaxSlot, and in a launch only what its schedule needs
-// (shared memory and L1 share one array per SM: every byte not reserved caches the teams'
-// vectors and F)
-constexpr size_t kMaxSlot = 25 * 1024;
-constexpr size_t kBatchSmemMax = kMaxSlot * (kBatchThreads / 64);
-
-template <int G>
-struct Team {
-  static constexpr int nt = G, nw = G / 32;
-  static constexpr int kIdBase = kBatchThreads / G;   // 1, 2, 4, 8 for 512, 256, 128, 64
-  int tid, id, lane, warp;
-  __device__ __forceinline__ Team() : tid(threadIdx.x % G), id(threadIdx.x / G), lane(threadIdx.x & 31),
-                                      warp((threadIdx.x % G) >> 5) {}
-  // the named-barrier intrinsic (not inline assembly): the compiler knows it for a barrier
-  // and keeps values it can prove unchanged in registers across it
-  __device__ __forceinline__ void sync() const { __barrier_sync_count(kIdBase + id, G); }
-};
-
-// ------------------------------------------------------------------------------------ the solve
-constexpr int kTerms = 20;   // team-reduced terms of one step
-// 0..4  R~: sum dx^2, dw.Qdw, Qdw.A*dy, (unused), dx.(A*dy - Qdw)
-// 5..11 eta: max rd, max |A*ybar|, max |Qxbar|, xbar.Qxbar, c.xbar, |xbar|_1, phi*(-zbar)
-// 12..15 theta~ (restart candidates): |xbar-x0|^2, (wbar-w0).(Qwbar-Qw0), (Qwbar-Qw0).(A*ybar-A*y0), (unused)
-constexpr unsigned kMaxMask = (1u << 5) | (1u << 6) | (1u << 7);
-
-// Shared-memory state of one team (carved from the block's dynamic shared memory): the
-// m-vectors (m <= 32) and the controller scalars at fixed offsets, then the dense factor's
-// intermediate t = F v (pmax entries, twice), per-warp partial sums, and optionally a copy of
-// the instance's F.  Addresses are computed from the base on use, so they take no registers.
-constexpr int kFixedD = 11 * kMaxM;   // av, ax, y, yb, y0, lo, hi, pm0, pm1 and 2 spare
-struct TS {
-  double* base;
-  int64_t pmax, fcap;
-  int nw;
-  __device__ __forceinline__ double* av() const { return base; }
-  __device__ __forceinline__ double* ax() const { return base + kMaxM; }
-  __device__ __forceinline__ double* y() const { return base + 2 * kMaxM; }
-  __device__ __forceinline__ double* yb() const { return base + 3 * kMaxM; }
-  __device__ __forceinline__ double* y0() const { return base + 4 * kMaxM; }
-  __device__ __forceinline__ double* lo() const { return base + 5 * kMaxM; }
-  __device__ __forceinline__ double* hi() const { return base + 6 * kMaxM; }
-  __device__ __forceinline__ double* pm0() const { return base + 7 * kMaxM; }
-  __device__ __forceinline__ double* pm1() const { return base + 8 * kMaxM; }
-  __device__ __forceinline__ Ctrl* C() const { return reinterpret_cast<Ctrl*>(base + kFixedD); }
-  __device__ __forceinline__ int* inst() const {
-    return reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(base + kFixedD) + sizeof(Ctrl));
+// ------------------------------------------------------------------------------------ block helpers
+template <int NT>
+__device__ __forceinline__ void bsum(double (&v)[NT], unsigned maxmask, double* red) {
+  block_reduce<NT>(v, maxmask, red);
+  // thread 0 holds the result; broadcast through shared memory
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NT; i++) red[i] = v[i];
   }
-  __device__ __forceinline__ double* t0() const { return base + kFixedD + kCtrlD; }
-  __device__ __forceinline__ double* t1() const { return t0() + pmax; }
-  __device__ __forceinline__ double* wred() const { return t0() + 2 * pmax; }             // 2 kMaxM x nw
-  __device__ __forceinline__ double* red() const { return wred() + 2 * kMaxM * nw; }      // kTerms x nw + kTerms
-  __device__ __forceinline__ double* F() const { return fcap > 0 ? red() + kTerms * nw + kTerms : nullptr; }
-  static constexpr int kCtrlD = (int)((sizeof(Ctrl) + sizeof(int) + 15) / 16 * 2);   // Ctrl + inst, in doubles
-};
-
-__host__ __device__ inline size_t team_bytes(int nw, int64_t pmax, int64_t fcap) {
-  const size_t d = (size_t)(kFixedD + TS::kCtrlD + 2 * pmax + 2 * kMaxM * nw + kTerms * nw + kTerms + fcap);
-  return (d * sizeof(double) + 15) / 16 * 16;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NT; i++) v[i] = red[i];
+  __syncthreads();
 }
 
-template <int G>
-__device__ inline TS team_state(unsigned char* base, const Team<G> T, int64_t pmax, int64_t fcap, size_t slot) {
-  TS s;
-  s.base = reinterpret_cast<double*>(base + (size_t)T.id * (G / 64) * slot);
-  s.pmax = pmax;
-  s.fcap = fcap;
-  s.nw = T.nw;
-  return s;
-}
-
-// Sum (or max, per bit of maxmask) of every thread's v[i] over the team, in a fixed order
-// (warp shuffles, then the warps' partials in warp order); every thread receives the result.
-template <int NT, int G>
-__device__ __forceinline__ void team_reduce(const Team<G> T, double (&v)[NT], unsigned maxmask, double* red) {
-#pragma unroll
-  for (int i = 0; i < NT; i++) {
-    double a = v[i];
-    const bool mx = (maxmask >> i) & 1u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double b = __shfl_down_sync(0xffffffffu, a, o);
-      a = mx ? imax(a, b) : a + b;
-    }
-    if (T.lane == 0) red[i * T.nw + T.warp] = a;
-  }
-  T.sync();
-  if (T.tid < NT) {
-    const int i = T.tid;
-    const bool mx = (maxmask >> i) & 1u;
-    double a = red[i * T.nw];
-    for (int q = 1; q < T.nw; q++) a = mx ? imax(a, red[i * T.nw + q]) : a + red[i * T.nw + q];
-    red[NT * T.nw + i] = a;
-  }
-  T.sync();
-#pragma unroll
-  for (int i = 0; i < NT; i++) v[i] = red[NT * T.nw + i];
-  T.sync();
-}
-
-// t[r] = sum_j F[r][j] x[j] (and F x1 when x1), one warp of the team per row; into t0/t1
-template <int G>
-__device__ __forceinline__ void dense_fx(const Team<G> T, const double* __restrict__ F, int64_t p, int64_t n,
+// t[r] = sum_j F[r][j] x[j] (and F x1 when x1), one warp per row; result in shared t0/t1.  A
+// warp streams one row at a time (consecutive addresses); wider forms that interleave several
+// rows or unroll across rows measured slower on the large instances, whose F comes from HBM.
+__device__ __forceinline__ void dense_fx(const double* __restrict__ F, int64_t p, int64_t n,
                                         const double* __restrict__ x0, const double* __restrict__ x1, double* t0,
                                         double* t1) {
-  for (int64_t r = T.warp; r < p; r += T.nw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t r = warp; r < p; r += nw) {
     const double* Fr = F + r * n;
     double s0 = 0.0, s1 = 0.0;
-    // four strides of the row per round, every load issued before the FMAs (the sums keep the
-    // order of the one-at-a-time loop): the pass is bound by load latency, not FP64 issue
-    int64_t j = T.lane;
-    for (; j + 96 < n; j += 128) {
-      const double f0 = Fr[j], f1 = Fr[j + 32], f2 = Fr[j + 64], f3 = Fr[j + 96];
-      const double a0 = x0[j], a1 = x0[j + 32], a2 = x0[j + 64], a3 = x0[j + 96];
-      s0 = fma(f0, a0, s0);
-      s0 = fma(f1, a1, s0);
-      s0 = fma(f2, a2, s0);
-      s0 = fma(f3, a3, s0);
-      if (x1) {
-        const double b0 = x1[j], b1 = x1[j + 32], b2 = x1[j + 64], b3 = x1[j + 96];
-        s1 = fma(f0, b0, s1);
-        s1 = fma(f1, b1, s1);
-        s1 = fma(f2, b2, s1);
-        s1 = fma(f3, b3, s1);
-      }
-    }
-    for (; j < n; j += 32) {
+    for (int64_t j = lane; j < n; j += 32) {
       const double f = Fr[j];
       s0 = fma(f, x0[j], s0);
       if (x1) s1 = fma(f, x1[j], s1);
@@ -224,34 +118,33 @@ __device__ __forceinline__ void dense_fx(const Team<G> T, const double* __restri
       s0 += __shfl_down_sync(0xffffffffu, s0, o);
       if (x1) s1 += __shfl_down_sync(0xffffffffu, s1, o);
     }
-    if (T.lane == 0) {
+    if (lane == 0) {
       t0[r] = s0;
       if (x1) t1[r] = s1;
     }
   }
 }
 
-// (Q x)_j = sum_r F[r][j] t[r] + d_j x_j + (Q_csr x)_j for one coordinate (F: the instance's
-// factor, in global memory or the team's shared copy)
-__device__ __forceinline__ double q_row(const Pools& P, const Inst& I, const double* F, int64_t j,
-                                        const double* __restrict__ x, const double* t) {
+extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int PC>
+struct Shared;
+
+// The instance's dense factor F (p x n, row-major): in global memory, or (FS) the block's copy
+// in shared memory after its Shared state.
+template <bool FS, int PC>
+__device__ __forceinline__ const double* fac(const Pools& P, const Inst& I) {
+  if constexpr (FS) return reinterpret_cast<const double*>(smem_raw + sizeof(Shared<PC>));
+  else return P.F + I.oF;
+}
+
+// (Q x)_j = sum_r F[r][j] t[r] + d_j x_j + (Q_csr x)_j for one coordinate
+template <bool FS, int PC>
+__device__ __forceinline__ double q_row(const Pools& P, const Inst& I, int64_t j, const double* __restrict__ x,
+                                        const double* t) {
   double acc = 0.0;
   if (I.p) {
-    // column j of F, eight entries per round with their loads ahead of the FMAs (same order of
-    // the sum as one entry at a time)
-    const int64_t p = I.p, n = I.n;
-    const double* Fj = F + j;
-    int64_t r = 0;
-    for (; r + 8 <= p; r += 8, Fj += 8 * n) {
-      double f[8], tv[8];
-#pragma unroll
-      for (int q = 0; q < 8; q++) f[q] = Fj[q * n];
-#pragma unroll
-      for (int q = 0; q < 8; q++) tv[q] = t[r + q];
-#pragma unroll
-      for (int q = 0; q < 8; q++) acc = fma(f[q], tv[q], acc);
-    }
-    for (; r < p; r++, Fj += n) acc = fma(*Fj, t[r], acc);
+    const double* F = fac<FS, PC>(P, I);
+    for (int64_t r = 0; r < I.p; r++) acc = fma(F[r * I.n + j], t[r], acc);
   }
   if (I.has_diag) acc = fma(P.d[I.on + j], x[j], acc);
   if (I.oqrp >= 0) {
@@ -264,26 +157,25 @@ __device__ __forceinline__ double q_row(const Pools& P, const Inst& I, const dou
 }
 
 // out = Q x for the whole instance (x, out in global memory, x != out); t: shared scratch (p)
-template <int G>
-__device__ __forceinline__ void team_qmul(const Team<G> T, const Pools& P, const Inst& I, const double* F, const double* x,
-                          double* out, double* t) {
-  if (I.p) dense_fx(T, F, I.p, I.n, x, nullptr, t, nullptr);
-  T.sync();
-  for (int64_t j = T.tid; j < I.n; j += T.nt) out[j] = q_row(P, I, F, j, x, t);
-  T.sync();
+template <bool FS, int PC>
+__device__ void block_qmul(const Pools& P, const Inst& I, const double* x, double* out, double* t) {
+  if (I.p) dense_fx(fac<FS, PC>(P, I), I.p, I.n, x, nullptr, t, nullptr);
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x) out[j] = q_row<FS, PC>(P, I, j, x, t);
+  __syncthreads();
 }
 
-// (A v)_i for all rows i into shared av[m] (and A x1 into ax[m] when x1): per row, the team's
-// threads stride its entries, warps combine their partials in warp order
-template <int G>
-__device__ __forceinline__ void team_amul(const Team<G> T, const Pools& P, const Inst& I, const double* __restrict__ v,
-                          const double* __restrict__ x1, double* av, double* ax, double* wred) {
+// (A v)_i for all rows i into shared av[m] (and A x1 into ax[m] when x1); block pass over the
+// rows of A: per row, lanes stride its entries, warps combine in shared memory (fixed order)
+__device__ void block_amul(const Pools& P, const Inst& I, const double* __restrict__ v, const double* __restrict__ x1,
+                           double* av, double* ax, double* wred) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int* rp = P.arp + I.oarp;
   const int* ci = P.aci + I.oann;
   const double* a = P.av + I.oann;
   for (int64_t i = 0; i < I.m; i++) {
     double s0 = 0.0, s1 = 0.0;
-    for (int k = rp[i] + T.tid; k < rp[i + 1]; k += T.nt) {
+    for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) {
       const double aik = a[k];
       s0 = fma(aik, v[ci[k]], s0);
       if (x1) s1 = fma(aik, x1[ci[k]], s1);
@@ -293,22 +185,22 @@ __device__ __forceinline__ void team_amul(const Team<G> T, const Pools& P, const
       s0 += __shfl_down_sync(0xffffffffu, s0, o);
       if (x1) s1 += __shfl_down_sync(0xffffffffu, s1, o);
     }
-    if (T.lane == 0) {
-      wred[i * T.nw + T.warp] = s0;
-      if (x1) wred[(kMaxM + i) * T.nw + T.warp] = s1;
+    if (lane == 0) {
+      wred[i * 32 + warp] = s0;
+      if (x1) wred[(kMaxM + i) * 32 + warp] = s1;
     }
   }
-  T.sync();
-  if (T.tid < I.m) {
+  __syncthreads();
+  if (threadIdx.x < I.m) {
     double s0 = 0.0, s1 = 0.0;
-    for (int q = 0; q < T.nw; q++) {
-      s0 += wred[T.tid * T.nw + q];
-      if (x1) s1 += wred[(kMaxM + T.tid) * T.nw + q];
+    for (int q = 0; q < nw; q++) {
+      s0 += wred[threadIdx.x * 32 + q];
+      if (x1) s1 += wred[(kMaxM + threadIdx.x) * 32 + q];
     }
-    av[T.tid] = s0;
-    if (x1) ax[T.tid] = s1;
+    av[threadIdx.x] = s0;
+    if (x1) ax[threadIdx.x] = s1;
   }
-  T.sync();
+  __syncthreads();
 }
 
 // (A^T y)_j with y in shared memory
@@ -323,42 +215,43 @@ __device__ __forceinline__ double at_row(const Pools& P, const Inst& I, int64_t 
 
 // power method of Sec. 4.1 on Q (which = 1, R^n) or A A^* (which = 0, R^m); pv, pw, tmp: global
 // scratch of the instance; returns safety * Rayleigh quotient (valid in every thread)
-template <int G>
-__device__ __forceinline__ double team_power(const Team<G> T, const Pools& P, const Inst& I, const double* F, int which, double* pv,
-                             double* pw, double* tmp, const TS S) {
+template <bool FS, int PC>
+__device__ double block_power(const Pools& P, const Inst& I, int which, double* pv, double* pw, double* tmp,
+                              double* t, double* av, double* wred, double* red) {
   const int64_t dim = which ? I.n : I.m;
   if (dim == 0) return 0.0;
   double s2[1] = {0.0};
-  for (int64_t i = T.tid; i < dim; i += T.nt) {
+  for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) {
     const uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761u);
     const double val = 0.5 + (double)h / 4294967296.0;
     pw[i] = val;
     s2[0] = fma(val, val, s2[0]);
   }
-  team_reduce<1, G>(T, s2, 0u, S.red());
+  bsum<1>(s2, 0u, red);
   double scale = 1.0 / sqrt(s2[0]), lam = 0.0;
+  __syncthreads();
   for (long long it = 0; it < P.power_max_iter; it++) {
-    for (int64_t i = T.tid; i < dim; i += T.nt) pv[i] = pw[i] * scale;
-    T.sync();
+    for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) pv[i] = pw[i] * scale;
+    __syncthreads();
     double acc[2] = {0.0, 0.0};
     if (which) {
-      team_qmul(T, P, I, F, pv, pw, S.t0());
-      for (int64_t i = T.tid; i < dim; i += T.nt) {
+      block_qmul<FS, PC>(P, I, pv, pw, t);
+      for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) {
         acc[0] = fma(pv[i], pw[i], acc[0]);
         acc[1] = fma(pw[i], pw[i], acc[1]);
       }
     } else {
       // w = A (A^T v): A^T v from the stored transpose, then the row pass of A
-      for (int64_t j = T.tid; j < I.n; j += T.nt) tmp[j] = at_row(P, I, j, pv);
-      T.sync();
-      team_amul(T, P, I, tmp, nullptr, S.av(), nullptr, S.wred());
-      for (int64_t i = T.tid; i < dim; i += T.nt) {
-        pw[i] = S.av()[i];
-        acc[0] = fma(pv[i], S.av()[i], acc[0]);
-        acc[1] = fma(S.av()[i], S.av()[i], acc[1]);
+      for (int64_t j = threadIdx.x; j < I.n; j += blockDim.x) tmp[j] = at_row(P, I, j, pv);
+      __syncthreads();
+      block_amul(P, I, tmp, nullptr, av, nullptr, wred);
+      for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) {
+        pw[i] = av[i];
+        acc[0] = fma(pv[i], av[i], acc[0]);
+        acc[1] = fma(av[i], av[i], acc[1]);
       }
     }
-    team_reduce<2, G>(T, acc, 0u, S.red());
+    bsum<2>(acc, 0u, red);
     const double nw = sqrt(acc[1]);
     if (nw == 0.0 || !isfinite(nw)) return 0.0;
     const bool conv = it > 0 && fabs(acc[0] - lam) <= P.power_tol * fabs(acc[0]);
@@ -369,11 +262,34 @@ __device__ __forceinline__ double team_power(const Team<G> T, const Pools& P, co
   return P.power_safety * lam;
 }
 
-template <int G, bool FS>
-__device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G> T, const TS S) {
+// ------------------------------------------------------------------------------------ the solve
+constexpr int kTerms = 20;   // block-reduced terms of one step
+// 0..4  R~: sum dx^2, dw.Qdw, Qdw.A*dy, (unused), dx.(A*dy - Qdw)
+// 5..11 eta: max rd, max |A*ybar|, max |Qxbar|, xbar.Qxbar, c.xbar, |xbar|_1, phi*(-zbar)
+// 12..15 theta~ (restart candidates): |xbar-x0|^2, (wbar-w0).(Qwbar-Qw0), (Qwbar-Qw0).(A*ybar-A*y0), (unused)
+constexpr unsigned kMaxMask = (1u << 5) | (1u << 6) | (1u << 7);
+
+// Block state in shared memory, at fixed offsets (the hot loops address it with constants):
+// t = F v for up to PC factor rows (PC = 256 or HPRQP_BATCH_MAX_P), the m-vectors, the warp
+// partials of a block of at most 16 warps, the controller.  With FS the block's copy of F
+// follows it (dynamic shared memory).
+template <int PC>
+struct __align__(16) Shared {
+  double t0[PC], t1[PC];
+  double av[kMaxM], ax[kMaxM];
+  double y[kMaxM], yb[kMaxM], y0[kMaxM], lo[kMaxM], hi[kMaxM];
+  double wred[2 * kMaxM * 32];
+  double red[kTerms * 32];
+  double pm[2][kMaxM];   // power-method vectors on R^m
+  Ctrl C;
+  int inst;
+};
+
+template <bool FS, int PC>
+__device__ void solve_one(const Pools& P, int idx, Shared<PC>& S) {
   const Inst I = P.inst[idx];
   const int64_t n = I.n, m = I.m;
-  const int tid = T.tid, nt = T.nt;
+  const int tid = threadIdx.x, nt = blockDim.x;
   // instance views
   const double *c = P.c + I.on, *L = P.L + I.on, *U = P.U + I.on;
   double *x = P.x + I.on, *w = P.w + I.on, *Qw = P.Qw + I.on, *ATy = P.ATy + I.on;
@@ -384,49 +300,45 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
   double* ybg = P.yb + I.om;
   double* qat = P.qat + I.oqat;   // [j*m + i] = (Q A^T)_{j i}
   double* aqa = P.aqa + I.oaqa;   // [i*m + l]
-  Ctrl& C = *S.C();
-  // the dense factor: a copy in the team's shared memory when it fits, read every step
-  // FS (whole-block teams only): the team's shared-memory copy, which the schedule offers only
-  // when every instance of the bucket fits; otherwise F is read from global memory (one address
-  // space per instantiation keeps the hot loops' loads plain and unaliased)
-  const double* F = P.F + I.oF;
+  Ctrl& C = S.C;
   if constexpr (FS) {
-    double* Fs = S.F();
-    for (int64_t q = tid; q < I.p * n; q += nt) Fs[q] = F[q];
-    T.sync();
-    F = Fs;
+    // the block's copy of F, read by every product of the solve
+    double* Fs = reinterpret_cast<double*>(smem_raw + sizeof(Shared<PC>));
+    const double* Fg = P.F + I.oF;
+    for (int64_t q = tid; q < I.p * n; q += nt) Fs[q] = Fg[q];
+    __syncthreads();
   }
 
   // ---- set-up (counted in the solve, like the power method): Q A^T, A Q A^T, lambda, sigma0
   for (int64_t i = 0; i < m; i++) {
     // column i of A^T = row i of A, scattered into s1
     for (int64_t j = tid; j < n; j += nt) s1[j] = 0.0;
-    T.sync();
+    __syncthreads();
     {
       const int* rp = P.arp + I.oarp;
       const int* ci = P.aci + I.oann;
       const double* a = P.av + I.oann;
       for (int k = rp[i] + tid; k < rp[i + 1]; k += nt) s1[ci[k]] = a[k];  // distinct columns per row
     }
-    T.sync();
-    team_qmul(T, P, I, F, s1, s2, S.t0());
+    __syncthreads();
+    block_qmul<FS, PC>(P, I, s1, s2, S.t0);
     for (int64_t j = tid; j < n; j += nt) qat[j * m + i] = s2[j];
-    T.sync();
+    __syncthreads();
   }
   for (int64_t i = 0; i < m; i++) {
     // row i of A Q A^T: A applied to column i of Q A^T
     for (int64_t j = tid; j < n; j += nt) s1[j] = qat[j * m + i];
-    T.sync();
-    team_amul(T, P, I, s1, nullptr, S.av(), nullptr, S.wred());
-    if (tid < m) aqa[tid * m + i] = S.av()[tid];
-    T.sync();
+    __syncthreads();
+    block_amul(P, I, s1, nullptr, S.av, nullptr, S.wred);
+    if (tid < m) aqa[tid * m + i] = S.av[tid];
+    __syncthreads();
   }
   double lamA = I.lamA, lamQ = I.lamQ;
-  if (m > 0 && !(lamA > 0.0)) lamA = team_power(T, P, I, F, 0, S.pm0(), S.pm1(), v, S);
+  if (m > 0 && !(lamA > 0.0)) lamA = block_power<FS, PC>(P, I, 0, S.pm[0], S.pm[1], v, S.t0, S.av, S.wred, S.red);
   if (m > 0 && !(lamA > 0.0)) lamA = 1.0;
   if (m == 0) lamA = 0.0;
   const bool HQ = I.p || I.has_diag || I.oqrp >= 0;
-  if (HQ && !(lamQ > 0.0)) lamQ = team_power(T, P, I, F, 1, s1, s2, v, S);
+  if (HQ && !(lamQ > 0.0)) lamQ = block_power<FS, PC>(P, I, 1, s1, s2, v, S.t0, S.av, S.wred, S.red);
   if (!HQ) lamQ = 0.0;
   double sigma = I.sigma0;
   if (!(sigma > 0.0)) {
@@ -443,21 +355,21 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
   }
   if (tid < m) {
     const double yv = I.has_ws ? P.y0in[I.om + tid] : 0.0;
-    S.y()[tid] = yv;
-    S.y0()[tid] = yv;
-    S.yb()[tid] = 0.0;
-    S.lo()[tid] = P.l[I.om + tid];
-    S.hi()[tid] = P.u[I.om + tid];
+    S.y[tid] = yv;
+    S.y0[tid] = yv;
+    S.yb[tid] = 0.0;
+    S.lo[tid] = P.l[I.om + tid];
+    S.hi[tid] = P.u[I.om + tid];
   }
-  T.sync();
+  __syncthreads();
   if (I.has_ws) {
-    team_qmul(T, P, I, F, x, Qw, S.t0());
+    block_qmul<FS, PC>(P, I, x, Qw, S.t0);
   } else {
     for (int64_t j = tid; j < n; j += nt) Qw[j] = 0.0;
   }
   for (int64_t j = tid; j < n; j += nt) {
     Qw0[j] = Qw[j];
-    const double a = m > 0 ? at_row(P, I, j, S.y()) : 0.0;
+    const double a = m > 0 ? at_row(P, I, j, S.y) : 0.0;
     ATy[j] = a;
     ATy0[j] = a;
   }
@@ -490,7 +402,7 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
     C.status = 1;
     set_sigma(C, sigma);
   }
-  T.sync();
+  __syncthreads();
 
   // ---- Algorithm 4
   while (!C.done) {
@@ -550,51 +462,51 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
     }
     if (tid < m) {
       // Halpern / restart on y (m <= 32: one thread per row)
-      double yv = S.y()[tid];
-      if (mode == 1) yv = fma(hb, fma(2.0, S.yb()[tid], -yv), ha * S.y0()[tid]);
+      double yv = S.y[tid];
+      if (mode == 1) yv = fma(hb, fma(2.0, S.yb[tid], -yv), ha * S.y0[tid]);
       else if (mode == 2) {
-        yv = S.yb()[tid];
-        S.y0()[tid] = yv;
+        yv = S.yb[tid];
+        S.y0[tid] = yv;
       }
-      S.y()[tid] = yv;
+      S.y[tid] = yv;
     }
-    T.sync();
+    __syncthreads();
     // P2-P3: Q wbar_{1/2} (+ Q xbar), v = what + sigma (Q w - Q wbar_{1/2})
     if (HQ) {
-      if (I.p) dense_fx(T, F, I.p, n, wh, ttest ? xb : nullptr, S.t0(), S.t1());
-      T.sync();
+      if (I.p) dense_fx(fac<FS, PC>(P, I), I.p, n, wh, ttest ? xb : nullptr, S.t0, S.t1);
+      __syncthreads();
       for (int64_t j = tid; j < n; j += nt) {
-        const double qwh = q_row(P, I, F, j, wh, S.t0());
+        const double qwh = q_row<FS, PC>(P, I, j, wh, S.t0);
         Qwh[j] = qwh;
-        if (ttest) Qxb[j] = q_row(P, I, F, j, xb, S.t1());
+        if (ttest) Qxb[j] = q_row<FS, PC>(P, I, j, xb, S.t1);
         if (m > 0) v[j] = fma(sg, Qw[j] - qwh, v[j]);
       }
-      T.sync();
+      __syncthreads();
     }
-    double R[kTerms];
+    double T[kTerms];
 #pragma unroll
-    for (int q = 0; q < kTerms; q++) R[q] = 0.0;
+    for (int q = 0; q < kTerms; q++) T[q] = 0.0;
     // P4: A v (+ A xbar), eq. (3.5) on the m rows
     if (m > 0) {
-      team_amul(T, P, I, v, ttest ? xb : nullptr, S.av(), S.ax(), S.wred());
+      block_amul(P, I, v, ttest ? xb : nullptr, S.av, S.ax, S.wred);
       if (tid < m) {
-        const double yv = S.y()[tid], lo = S.lo()[tid], hi = S.hi()[tid];
-        const double ry = fma(-slA, yv, S.av()[tid]);
+        const double yv = S.y[tid], lo = S.lo[tid], hi = S.hi[tid];
+        const double ry = fma(-slA, yv, S.av[tid]);
         const double ybv = (iclamp(ry, lo, hi) - ry) * islA;
-        S.yb()[tid] = ybv;
+        S.yb[tid] = ybv;
         ybg[tid] = ybv;
       }
-      T.sync();
+      __syncthreads();
     }
     // P5: A^* ybar, wbar (eq. (3.3)), Q wbar by linearity, the R~ / eta / theta~ sums
     for (int64_t j = tid; j < n; j += nt) {
       double atyb = 0.0, dq = 0.0;
       if (m > 0) {
-        atyb = at_row(P, I, j, S.yb());
+        atyb = at_row(P, I, j, S.yb);
         ATyb[j] = atyb;
         if (HQ) {
           const double* qa = qat + j * m;
-          for (int64_t i = 0; i < m; i++) dq = fma(qa[i], S.yb()[i] - S.y()[i], dq);
+          for (int64_t i = 0; i < m; i++) dq = fma(qa[i], S.yb[i] - S.y[i], dq);
         }
       }
       double wbv = 0.0, qwb = 0.0;
@@ -609,46 +521,46 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
         const double dx = x[j] - xbj;
         const double qdw = HQ ? Qw[j] - qwb : 0.0;
         const double ady = m > 0 ? ATy[j] - atyb : 0.0;
-        R[0] = fma(dx, dx, R[0]);
-        if (HQ) R[1] = fma(w[j] - wbv, qdw, R[1]);
-        R[2] = fma(qdw, ady, R[2]);
-        R[4] = fma(dx, ady - qdw, R[4]);
+        T[0] = fma(dx, dx, T[0]);
+        if (HQ) T[1] = fma(w[j] - wbv, qdw, T[1]);
+        T[2] = fma(qdw, ady, T[2]);
+        T[4] = fma(dx, ady - qdw, T[4]);
         // theta~ candidates from ubar - u^{r,0} (used only if this step restarts)
         const double ex = xbj - x0[j];
-        R[12] = fma(ex, ex, R[12]);
+        T[12] = fma(ex, ex, T[12]);
         if (HQ) {
           const double qe = qwb - Qw0[j];
-          R[13] = fma(wbv - w0[j], qe, R[13]);
-          R[14] = fma(qe, atyb - ATy0[j], R[14]);
+          T[13] = fma(wbv - w0[j], qe, T[13]);
+          T[14] = fma(qe, atyb - ATy0[j], T[14]);
         }
       }
       if (ttest) {
         const double xbj = xb[j], qxb = HQ ? Qxb[j] : 0.0, cj = c[j];
-        R[5] = imax(R[5], iabs(atyb - qxb + zb[j] - cj));
-        R[6] = imax(R[6], iabs(atyb));
-        R[7] = imax(R[7], iabs(qxb));
-        R[8] = fma(xbj, qxb, R[8]);
-        R[9] = fma(cj, xbj, R[9]);
-        if (I.phi != PHI_BOX) R[10] += iabs(xbj);
-        R[11] += conj_phi_term(I.phi, zb[j], L[j], U[j], I.lambda);
+        T[5] = imax(T[5], iabs(atyb - qxb + zb[j] - cj));
+        T[6] = imax(T[6], iabs(atyb));
+        T[7] = imax(T[7], iabs(qxb));
+        T[8] = fma(xbj, qxb, T[8]);
+        T[9] = fma(cj, xbj, T[9]);
+        if (I.phi != PHI_BOX) T[10] += iabs(xbj);
+        T[11] += conj_phi_term(I.phi, zb[j], L[j], U[j], I.lambda);
       }
     }
-    if (rtest || ttest) team_reduce<kTerms, G>(T, R, kMaxMask, S.red());
-    T.sync();
+    if (rtest || ttest) block_reduce<kTerms>(T, kMaxMask, S.red);
+    __syncthreads();
     // P6: controller (one thread)
     if (tid == 0) {
       double Ls[kWL], P3[kW3];
 #pragma unroll
-      for (int q = 0; q < kWL; q++) Ls[q] = R[q];
+      for (int q = 0; q < kWL; q++) Ls[q] = T[q];
       P3[0] = P3[1] = P3[2] = P3[3] = 0.0;
       double th3 = 0.0, th3r = 0.0, dyr2 = 0.0;
       for (int64_t i = 0; i < m; i++) {
-        const double dy = S.y()[i] - S.yb()[i];
-        const double dr = S.yb()[i] - S.y0()[i];
+        const double dy = S.y[i] - S.yb[i];
+        const double dr = S.yb[i] - S.y0[i];
         P3[0] = fma(dy, dy, P3[0]);
         dyr2 = fma(dr, dr, dyr2);
         if (ttest) {
-          const double ax = S.ax()[i], lo = S.lo()[i], hi = S.hi()[i], ybv = S.yb()[i];
+          const double ax = S.ax[i], lo = S.lo[i], hi = S.hi[i], ybv = S.yb[i];
           P3[1] = fmax(P3[1], fabs(ax - fmin(fmax(ax, lo), hi)));
           P3[2] = fmax(P3[2], fabs(ax));
           if (ybv > 0.0) P3[3] += lo * ybv;
@@ -657,8 +569,8 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
         if (HQ) {
           double qd = 0.0, qr = 0.0;
           for (int64_t l2 = 0; l2 < m; l2++) {
-            qd = fma(aqa[i * m + l2], S.y()[l2] - S.yb()[l2], qd);
-            qr = fma(aqa[i * m + l2], S.yb()[l2] - S.y0()[l2], qr);
+            qd = fma(aqa[i * m + l2], S.y[l2] - S.yb[l2], qd);
+            qr = fma(aqa[i * m + l2], S.yb[l2] - S.y0[l2], qr);
           }
           th3 = fma(dy, qd, th3);
           th3r = fma(dr, qr, th3r);
@@ -666,11 +578,12 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
       }
       // the single-instance controller expects s * theta_3 in Ls[3]
       Ls[3] = C.s * th3;
+      const long long r_before = C.r;
       controller(C, Ls, P3);
       if (C.restart_pending) {
         // Algorithm 5 with theta~ of eq. (3.11) from ubar^{r,tau_r} - u^{r,0}
-        double t1 = C.lamA * dyr2 + C.lamQ * R[13] - 2.0 * R[14];
-        double t2 = R[12];
+        double t1 = C.lamA * dyr2 + C.lamQ * T[13] - 2.0 * T[14];
+        double t2 = T[12];
         t1 = fmax(t1, 1e-12);
         t2 = fmax(t2, 1e-12);
         double snew;
@@ -685,77 +598,65 @@ __device__ __forceinline__ void solve_one(const Pools& P, int idx, const Team<G>
         }
         C.restart_pending = 0;
       }
+      (void)r_before;
     }
-    T.sync();
+    __syncthreads();
   }
   // ---- results
   if (tid == 0) {
-    Res Rs;
-    Rs.eta_p = C.eta_p;
-    Rs.eta_d = C.eta_d;
-    Rs.eta_gap = C.eta_gap;
-    Rs.pobj = C.pobj;
-    Rs.dobj = C.dobj;
-    Rs.sigma = C.sigma;
-    Rs.lamA = C.lamA;
-    Rs.lamQ = C.lamQ;
-    Rs.iters = C.k;
-    Rs.restarts = C.r;
-    Rs.status = C.status;
-    Rs.pad = 0;
-    P.res[idx] = Rs;
+    Res R;
+    R.eta_p = C.eta_p;
+    R.eta_d = C.eta_d;
+    R.eta_gap = C.eta_gap;
+    R.pobj = C.pobj;
+    R.dobj = C.dobj;
+    R.sigma = C.sigma;
+    R.lamA = C.lamA;
+    R.lamQ = C.lamQ;
+    R.iters = C.k;
+    R.restarts = C.r;
+    R.status = C.status;
+    R.pad = 0;
+    P.res[idx] = R;
   }
-  T.sync();
+  __syncthreads();
 }
 
-// Schedule of one launch: buckets of instances (order[beg[b] .. beg[b+1]), each with its own
-// work counter), and per bucket the team size and the team's F copy capacity (doubles).
-struct Sched {
-  int nb;
-  unsigned slot;                 // shared-memory bytes per 64 threads in this launch
-  int team[kMaxBuckets];
-  int64_t pmax[kMaxBuckets];
-  int64_t fcap[kMaxBuckets];
-  int beg[kMaxBuckets + 1];
-  unsigned* heads;
+// One bucket of instances: order[beg .. beg + count), taken from the work counter *head.
+struct Bucket {
+  int beg, count;
+  unsigned* head;
 };
 
-// One bucket with teams of G threads: every team takes instances from the bucket's counter until
-// it is exhausted.
-template <int G, bool FS>
-__device__ void run_bucket(const Pools& P, const Sched& S, int b, unsigned char* smem_raw) {
-  const Team<G> T;
-  TS ts = team_state<G>(smem_raw, T, S.pmax[b], S.fcap[b], S.slot);
-  const unsigned cnt = (unsigned)(S.beg[b + 1] - S.beg[b]);
+// One block per instance at a time, blocks of any size from 64 to 512 threads (the autotuner's
+// choice for the bucket); a block that finds the bucket's counter exhausted exits, and its SM
+// takes blocks of the next bucket's launch (launched behind this one on another stream).
+// Registers are capped at 64 so that 32 warps fit an SM (two 512-thread blocks): the dense-factor
+// passes wait on memory, and twice the warps in flight outweigh the few spilled values (on the
+// 4096-instance batch: 13.7 s against 14.9 s at 128 registers and 16 warps).
+template <bool FS, int PC>
+__global__ void __launch_bounds__(512, 2) k_batch(Pools P, Bucket B) {
+  Shared<PC>& S = *reinterpret_cast<Shared<PC>*>(smem_raw);
   for (;;) {
-    if (T.tid == 0) {
-      const unsigned q = atomicAdd(S.heads + b, 1u);
-      *ts.inst() = q < cnt ? P.order[S.beg[b] + q] : -1;
+    if (threadIdx.x == 0) {
+      const unsigned q = atomicAdd(B.head, 1u);
+      S.inst = q < (unsigned)B.count ? P.order[B.beg + q] : -1;
     }
-    T.sync();
-    const int idx = *ts.inst();
+    __syncthreads();
+    const int idx = S.inst;
     if (idx < 0) break;
-    solve_one<G, FS>(P, idx, T, ts);   // ends with a team barrier, so inst is free again
+    solve_one<FS, PC>(P, idx, S);
   }
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 1) k_batch(Pools P, Sched S) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // team sizes do not grow from one bucket to the next (the schedule guarantees it), so the
-  // threads of a team that leaves a bucket together form whole teams of the next one
-  for (int b = 0; b < S.nb; b++) {
-    if (S.beg[b + 1] <= S.beg[b]) continue;   // the same for every thread
-    switch (S.team[b]) {
-      case 64: run_bucket<64, false>(P, S, b, smem_raw); break;
-      case 128: run_bucket<128, false>(P, S, b, smem_raw); break;
-      case 256: run_bucket<256, false>(P, S, b, smem_raw); break;
-      default:
-        if (S.fcap[b] > 0) run_bucket<512, true>(P, S, b, smem_raw);
-        else run_bucket<512, false>(P, S, b, smem_raw);
-        break;
-    }
-  }
+// The four instantiations: the capacity of t (factor rows) and the shared-memory F copy.
+constexpr int kSmallP = 256;
+using KFn = void (*)(Pools, Bucket);
+inline KFn batch_kernel(bool fs, bool small_p) {
+  return small_p ? (fs ? k_batch<true, kSmallP> : k_batch<false, kSmallP>)
+                 : (fs ? k_batch<true, kMaxP> : k_batch<false, kMaxP>);
 }
+inline size_t shared_bytes(bool small_p) { return small_p ? sizeof(Shared<kSmallP>) : sizeof(Shared<kMaxP>); }
 
 }  // namespace batch
 }  // namespace hprqp
@@ -763,6 +664,17 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(Pools P, Sched S) {
 // ======================================================================================= host side
 using namespace hprqp;
 using namespace hprqp::batch;
+
+// Instances are bucketed by n, largest first; each bucket runs as its own launch, with the block
+// size and the shared-memory F copy the autotuner chose for it.
+constexpr int kMaxBuckets = 4;
+struct Sched {
+  int beg[kMaxBuckets + 1];    // bucket k: order[beg[k] .. beg[k+1])
+  int64_t pmax[kMaxBuckets];   // largest p of the bucket
+  int64_t fmax[kMaxBuckets];   // largest p*n of the bucket
+  int threads[kMaxBuckets];    // block size (threads per instance)
+  bool fs[kMaxBuckets];        // F copied to shared memory
+};
 
 struct hprqp_batch {
   int dev = 0;
@@ -774,11 +686,11 @@ struct hprqp_batch {
   std::vector<int64_t> n_of, m_of;
   Pools P;
   std::vector<void*> allocs;
-  // schedule: instances bucketed by n (order sorted by bucket, then cost); per bucket the team
+  // schedule: instances bucketed by n (order sorted by bucket, then cost); per bucket the block
   // size and the shared-memory F copy, chosen by the autotuner at the first solve
   Sched sched;
-  int grid = 0;
-  size_t smem = 0;
+  cudaStream_t side[kMaxBuckets - 1] = {};    // buckets 1.. run on these, behind bucket 0
+  cudaEvent_t fork = nullptr, join[kMaxBuckets - 1] = {};
   std::vector<int> bucket_lo;   // smallest n of each bucket
   std::vector<int> horder;      // host copy of the work order
   bool tuned = false;
@@ -787,8 +699,6 @@ struct hprqp_batch {
   double seconds = 0.0;
   int64_t launches = 0;
   bool solved = false;
-  cudaGraphExec_t gexec = nullptr;
-  int gblock = 0;
 };
 
 static thread_local std::string g_batch_err;
@@ -878,7 +788,14 @@ static hprqp_status bzeros(hprqp_batch* b, double** out, size_t cnt) {
 static void brelease(hprqp_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (int k = 0; k < kMaxBuckets - 1; k++) {
+    if (b->side[k]) {
+      cudaStreamSynchronize(b->side[k]);
+      cudaStreamDestroy(b->side[k]);
+    }
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   for (void* p : b->allocs) {
     if (b->prm.free) b->prm.free(p, 0, b->prm.alloc_ctx, b->stream);
     else cudaFree(p);
@@ -1061,7 +978,7 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
     b->m_of.push_back(m);
   }
   // buckets by n (largest first), and inside a bucket the largest estimated cost first (dense
-  // factor passes, else n): every team takes the next instance of its bucket from a counter
+  // factor passes, else n): every block takes the next instance of its bucket from a counter
   static const int64_t kBucketLo[kMaxBuckets] = {3000, 1500, 600, 0};
   auto bucket_of = [](int64_t n) {
     int bk = 0;
@@ -1081,18 +998,20 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
   {
     Sched& S = b->sched;
     S = Sched();
-    S.nb = kMaxBuckets;
     int pos = 0;
     for (int bk = 0; bk < kMaxBuckets; bk++) {
       S.beg[bk] = pos;
-      int64_t pm = 1;
+      int64_t pm = 0, fm = 0;
       while (pos < count && bucket_of(b->hinst[order[pos]].n) == bk) {
-        pm = std::max<int64_t>(pm, b->hinst[order[pos]].p);
+        const Inst& I = b->hinst[order[pos]];
+        pm = std::max<int64_t>(pm, I.p);
+        fm = std::max<int64_t>(fm, I.p * I.n);
         pos++;
       }
       S.pmax[bk] = pm;
-      S.team[bk] = kBatchThreads;
-      S.fcap[bk] = 0;
+      S.fmax[bk] = fm;
+      S.threads[bk] = 256;
+      S.fs[bk] = false;
       b->bucket_lo.push_back((int)kBucketLo[bk]);
     }
     S.beg[kMaxBuckets] = pos;
@@ -1166,8 +1085,11 @@ static hprqp_status batch_create_impl(hprqp_batch* b, int32_t count, const hprqp
   P.qv = tmp;
   BCU(b, cudaStreamSynchronize(b->stream));
   BCU(b, cudaGetDevice(&b->dev));
-  b->sched.heads = P.head;
-  BCU(b, cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax));
+  for (int k = 0; k < kMaxBuckets - 1; k++) {
+    BCU(b, cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+    BCU(b, cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+  }
+  BCU(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
   b->hres.resize(count);
   return HPRQP_OK;
 }
@@ -1209,52 +1131,56 @@ extern "C" hprqp_status hprqp_batch_create(hprqp_batch** out, int32_t count, con
   return HPRQP_OK;
 }
 
-// Shared memory per 64 threads that a team of G threads needs for bucket bk's state (and an F
-// copy of fcap doubles), rounded to 128 bytes.
-static size_t bucket_slot(const Sched& S, int bk, int G, int64_t fcap) {
-  const size_t per = (team_bytes(G / 32, S.pmax[bk], fcap) + (size_t)(G / 64) - 1) / (size_t)(G / 64);
-  return (per + 127) / 128 * 128;
+// Dynamic shared memory of a block of bucket bk: its Shared state (t sized for the bucket's
+// largest p) and, with the F copy, the bucket's largest F.
+static bool small_p(const Sched& S, int bk) { return S.pmax[bk] <= kSmallP; }
+static size_t bucket_smem(const Sched& S, int bk, bool fs) {
+  return shared_bytes(small_p(S, bk)) + (fs ? (size_t)S.fmax[bk] * sizeof(double) : 0);
 }
 
-// The largest F copy that a team of G threads can hold next to its state (0 if none fits).
-static int64_t bucket_fcap(const Sched& S, int bk, int G) {
-  const size_t base = team_bytes(G / 32, S.pmax[bk], 0), room = (size_t)(G / 64) * kMaxSlot;
-  if (base >= room) return 0;
-  return (int64_t)((room - base) / sizeof(double)) / 2 * 2;
-}
-
-static cudaError_t batch_launch(hprqp_batch* b, const Sched& S, int grid, size_t smem) {
-  cudaError_t e = cudaMemsetAsync(b->P.head, 0, sizeof(unsigned) * kMaxBuckets, b->stream);
+// One launch: the instances order[beg .. beg + cnt) of bucket bk with the given block size and F
+// copy, at most one wave of resident blocks (each takes instances from the bucket's counter).
+static cudaError_t launch_bucket(hprqp_batch* b, int bk, int beg, int cnt, int threads, bool fs, int sms,
+                                 cudaStream_t s) {
+  const Sched& S = b->sched;
+  const KFn k = batch_kernel(fs, small_p(S, bk));
+  const size_t smem = bucket_smem(S, bk, fs);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
   if (e != cudaSuccess) return e;
-  k_batch<<<grid, kBatchThreads, smem, b->stream>>>(b->P, S);
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::max(1, std::min(cnt, sms * occ));
+  k<<<grid, threads, smem, s>>>(b->P, Bucket{beg, cnt, b->P.head + bk});
   return cudaGetLastError();
 }
 
-// The launch's slot: the largest that any bucket with instances needs.
-static unsigned sched_slot(const Sched& S) {
-  size_t sl = 128;
-  for (int bk = 0; bk < S.nb; bk++)
-    if (S.beg[bk + 1] > S.beg[bk]) sl = std::max(sl, bucket_slot(S, bk, S.team[bk], S.fcap[bk]));
-  return (unsigned)sl;
+// Whether a bucket's F copies fit a block's shared memory.
+static bool fs_fits(hprqp_batch* b, int bk) {
+  const Sched& S = b->sched;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return S.fmax[bk] > 0 && bucket_smem(S, bk, true) <= (size_t)optin;
 }
 
-// Autotuner (row a10): per bucket of instances, largest n first, time the candidate schedules on
-// a sample of the bucket's own instances (the first 100 iterations of up to 1216 of them, one
-// launch each) and keep the fastest: teams of 64, 128, 256 or 512 threads per instance (never
-// larger than the previous bucket's, so teams only split), and for each, whether the team keeps
-// its instance's dense factor F in shared memory (when F fits the team's slots).
+// Autotuner (row a10): per bucket of instances, time the candidate schedules on a sample of the
+// bucket's own instances (the first 100 iterations of up to 4 per SM of them, one launch each)
+// and keep the fastest: blocks of 512, 256, 128 or 64 threads per instance, each with and
+// without a shared-memory copy of the instance's dense factor F (where every F of the bucket
+// fits).  batch_team fixes the block size of every bucket (no F copy); autotune = 0 takes
+// 512, 256, 128 and 64 threads from the largest n down (no F copy).
 static hprqp_status batch_autotune(hprqp_batch* b, int sms) {
   Sched& S = b->sched;
   Pools& P = b->P;
-  if (b->prm.batch_team) {
-    // one team size for every bucket, no F copies
-    for (int bk = 0; bk < kMaxBuckets; bk++) S.team[bk] = b->prm.batch_team;
-    return HPRQP_OK;
-  }
-  if (!b->prm.autotune) {
-    // fixed schedule: team size from the bucket's n, no F copies
+  if (b->prm.batch_team || !b->prm.autotune) {
     const int fixed[kMaxBuckets] = {512, 256, 128, 64};
-    for (int bk = 0; bk < kMaxBuckets; bk++) S.team[bk] = fixed[bk];
+    for (int bk = 0; bk < kMaxBuckets; bk++) {
+      S.threads[bk] = b->prm.batch_team ? b->prm.batch_team : fixed[bk];
+      S.fs[bk] = false;
+    }
     return HPRQP_OK;
   }
   cudaEvent_t e0, e1;
@@ -1262,56 +1188,37 @@ static hprqp_status batch_autotune(hprqp_batch* b, int sms) {
   BCU(b, cudaEventCreate(&e1));
   const long long keep = P.max_iter;
   P.max_iter = std::min<long long>(keep, 100);
-  int gmax = kBatchThreads;
   for (int bk = 0; bk < kMaxBuckets; bk++) {
     const int cnt = S.beg[bk + 1] - S.beg[bk];
     if (cnt <= 0) continue;
-    Sched T = S;
-    T.nb = 1;
-    T.beg[0] = S.beg[bk];
-    T.beg[1] = S.beg[bk] + std::min(cnt, sms * (kBatchThreads / 64));
-    T.pmax[0] = S.pmax[bk];
+    const int sample = std::min(cnt, sms * 4);
     float best = 1e30f;
-    S.team[bk] = gmax;
-    for (int G : {64, 128, 256, 512}) {
-      if (G > gmax) continue;
-      for (int fs = 0; fs < 2; fs++) {
-        if (fs && G != kBatchThreads) continue;   // F copies for whole-block teams only
-        const int64_t fc = fs ? bucket_fcap(S, bk, G) : 0;
-        if (fs && fc <= 0) continue;
-        if (fs) {
-          // only when the F of every instance of the bucket fits the copy
-          int64_t need = 0;
-          for (int q = S.beg[bk]; q < S.beg[bk + 1]; q++) {
-            const Inst& Iq = b->hinst[b->horder[q]];
-            need = std::max<int64_t>(need, Iq.p * Iq.n);
-          }
-          if (need == 0 || need > fc) continue;
-        }
-        T.team[0] = G;
-        T.fcap[0] = fc;
-        const size_t sl = bucket_slot(S, bk, G, fc);
-        if (sl > kMaxSlot) continue;
-        T.slot = (unsigned)sl;
-        const size_t smem = sl * (kBatchThreads / 64);
-        int occ = 0;
-        BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, smem));
-        if (occ < 1) continue;
-        const int grid = sms * occ;
+    for (int fs = 0; fs < 2; fs++) {
+      if (fs && !fs_fits(b, bk)) continue;
+      // largest blocks first; smaller ones only while they stay within 25 % of the best so far
+      // (time per instance grows steadily as blocks shrink past the best size)
+      for (int G : {512, 256, 128, 64}) {
+        BCU(b, cudaMemsetAsync(P.head + bk, 0, sizeof(unsigned), b->stream));
         BCU(b, cudaEventRecord(e0, b->stream));
-        BCU(b, batch_launch(b, T, grid, smem));
+        const cudaError_t le = launch_bucket(b, bk, S.beg[bk], sample, G, fs != 0, sms, b->stream);
+        if (le == cudaErrorInvalidConfiguration) continue;   // no block of this shape fits an SM
+        BCU(b, le);
         BCU(b, cudaEventRecord(e1, b->stream));
         BCU(b, cudaEventSynchronize(e1));
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        if (b->prm.verbose >= 2)
+          std::fprintf(stderr, "hprqp batch autotune: bucket %d (n >= %d, %d instances): %d threads%s: %.3f ms\n",
+                       bk, b->bucket_lo[bk], sample, G, fs ? ", F in shared memory" : "", ms);
         if (ms < best) {
           best = ms;
-          S.team[bk] = G;
-          S.fcap[bk] = fc;
+          S.threads[bk] = G;
+          S.fs[bk] = fs != 0;
+        } else if (ms > 1.25f * best) {
+          break;
         }
       }
     }
-    gmax = S.team[bk];
   }
   P.max_iter = keep;
   cudaEventDestroy(e0);
@@ -1347,15 +1254,33 @@ extern "C" hprqp_status hprqp_batch_solve(hprqp_batch* b, double tol, int64_t ma
     b->tuned = true;
     hprqp_status st = batch_autotune(b, sms);
     if (st != HPRQP_OK) return st;
-    b->sched.slot = sched_slot(b->sched);
-    b->smem = (size_t)b->sched.slot * (kBatchThreads / 64);
-    int occ = 0;
-    BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, b->smem));
-    b->grid = std::max(1, std::min(b->count, sms * std::max(occ, 1)));
   }
+  const Sched& S = b->sched;
   auto t0 = std::chrono::steady_clock::now();
-  BCU(b, batch_launch(b, b->sched, b->grid, b->smem));
-  b->launches = 1;
+  // bucket 0 on the caller's stream, the others on side streams forked from it: each launch
+  // fills the SMs its blocks fit, and the next bucket's blocks start on an SM as the previous
+  // bucket's blocks leave it (largest instances first, no idle SM between buckets)
+  BCU(b, cudaMemsetAsync(P.head, 0, sizeof(unsigned) * kMaxBuckets, b->stream));
+  BCU(b, cudaEventRecord(b->fork, b->stream));
+  b->launches = 0;
+  bool joined[kMaxBuckets] = {};
+  for (int bk = 0; bk < kMaxBuckets; bk++) {
+    const int cnt = S.beg[bk + 1] - S.beg[bk];
+    if (cnt <= 0) continue;
+    cudaStream_t s = b->stream;
+    if (b->launches > 0) {
+      s = b->side[bk - 1];
+      BCU(b, cudaStreamWaitEvent(s, b->fork, 0));
+    }
+    BCU(b, launch_bucket(b, bk, S.beg[bk], cnt, S.threads[bk], S.fs[bk], sms, s));
+    if (s != b->stream) {
+      BCU(b, cudaEventRecord(b->join[bk - 1], s));
+      joined[bk] = true;
+    }
+    b->launches++;
+  }
+  for (int bk = 1; bk < kMaxBuckets; bk++)
+    if (joined[bk]) BCU(b, cudaStreamWaitEvent(b->stream, b->join[bk - 1], 0));
   BCU(b, cudaMemcpyAsync(b->hres.data(), P.res, sizeof(Res) * b->count, cudaMemcpyDeviceToHost, b->stream));
   BCU(b, cudaStreamSynchronize(b->stream));
   b->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1374,9 +1299,9 @@ extern "C" hprqp_status hprqp_batch_schedule(const hprqp_batch* b, int64_t* out)
     int64_t* o = out + 5 * bk;
     o[0] = b->bucket_lo[bk];
     o[1] = b->sched.beg[bk + 1] - b->sched.beg[bk];
-    o[2] = b->sched.team[bk];
-    o[3] = b->sched.fcap[bk] > 0 ? 1 : 0;
-    o[4] = b->sched.fcap[bk];
+    o[2] = b->sched.threads[bk];
+    o[3] = b->sched.fs[bk] ? 1 : 0;
+    o[4] = b->sched.fs[bk] ? b->sched.fmax[bk] : 0;
   }
   return HPRQP_OK;
 }

@@ -41,7 +41,7 @@ def mixed_batch():
 @pytest.mark.parametrize("autotune", [1, 0])
 def test_batch_first_iterates(pkg, autotune):
     """autotune = 0 runs the fixed schedule, which gives the four buckets of this batch (n >= 3000,
-    1500..2999, 600..1499, below 600) teams of 512, 256, 128 and 64 threads: every team size
+    1500..2999, 600..1499, below 600) blocks of 512, 256, 128 and 64 threads: every block size
     reproduces the oracle's iterates."""
     probs = mixed_batch()
     K = 40
@@ -74,7 +74,7 @@ def test_batch_converged(pkg):
 
 def test_batch_schedule_is_reported(pkg):
     """The autotuner's choice per bucket of n (threads per instance, F in shared memory): every
-    bucket with instances gets a team of 64..512 threads, an F copy only where it fits."""
+    bucket with instances gets a block of 64..512 threads, an F copy only where it fits."""
     probs = mixed_batch()
     with pkg.BatchSolver(probs) as b:
         assert b.solve(tol=1e-8, max_iter=400000) == "converged"
