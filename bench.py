@@ -92,8 +92,8 @@ def _oracle_one(args):
 
 
 def run_batched(args, rank, world, dist=None):
-    """The batch of portfolio CQPs (n from 50 to 5000, m = 11) in one persistent launch, against
-    the plain solver."""
+    """The batch of portfolio CQPs (n from 50 to 5000, m = 11), one persistent launch per
+    n-bucket, against the plain solver."""
     import torch
     import paper_2507_02470_gb300 as pkg
     count = args.c3_count
@@ -171,9 +171,9 @@ def measure_learned(args, rank):
 
 def measure_batched(pkg, torch, count, seed0, steps, warmup, plain_sample, dist=None):
     """The batch of `count` portfolio CQPs (seeds seed0.., n from 50 to 5000, m = 11) solved to
-    1e-8 in one persistent launch per solve (warm-up solves first: the first one runs the
-    autotuner), timed with CUDA events on its stream; then the plain single-instance solver on a
-    sample of the same instances (create + solve each), scaled to the batch."""
+    1e-8, one persistent launch per bucket of n per solve (warm-up solves first: the first one
+    runs the autotuner), timed with CUDA events on its stream; then the plain single-instance
+    solver on a sample of the same instances (create + solve each), scaled to the batch."""
     probs = portfolio_batch(count, seed0)
     stream = torch.cuda.Stream()
     b = pkg.BatchSolver(probs, stream=stream.cuda_stream)
@@ -218,7 +218,7 @@ def measure_batched(pkg, torch, count, seed0, steps, warmup, plain_sample, dist=
     buckets = b.schedule()
     b.close()
     return {"workload": f"batched portfolio CQPs x{count}: n~U{{50..5000}} (sum n={nsum}), "
-                        "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch",
+                        "Q=F^T F+diag, F k x n dense, k=max(5,n/20), m=11, one persistent launch per n-bucket",
             "l2": (f"inputs larger than L2: the dense factors F take {fpool / 1e9:.2f} GB, no flush needed"
                    if fpool > L2_BYTES else
                    f"dense factors F {fpool / 1e6:.1f} MB fit in L2 (129 MB), not flushed between timed steps: "
