@@ -1249,7 +1249,8 @@ static hprqp_status build_pw_graph(hprqp_handle* h, int which) {
   cudaGraph_t g;
   CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
-  for (int i = 0; i < h->pw_chunk && le == cudaSuccess; i++) le = launch_power_iter(h->args, h->plan, which, h->stream);
+  // an even number of iterations per graph, so that every launch starts reading pv
+  for (int i = 0; i < h->pw_chunk && le == cudaSuccess; i++) le = launch_power_iter(h->args, h->plan, which, i, h->stream);
   cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
   if (le != cudaSuccess || ce != cudaSuccess) {
     cudaGetLastError();

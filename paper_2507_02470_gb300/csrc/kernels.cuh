@@ -570,9 +570,10 @@ __device__ __forceinline__ void pre_body(const Args& a, int which) {
       int term = 0;
       if (r < ffac)
         while (term + 1 < Q.nfac && r >= Q.toff[term + 1]) term++;
-      // one-vector products of a tiled factor are formed by the tiled kernels; the step's
-      // products of a thin factor are formed inside the row pass (q_csr_chunk)
-      const bool step_src = which == PRE_WH || which == PRE_WB || which == PRE_W;
+      // one-vector products of a tiled factor are formed by the tiled kernels; the products of
+      // a thin factor for an inner step or the power method are formed inside the row pass
+      // (q_csr_chunk)
+      const bool step_src = which == PRE_WH || which == PRE_WB || which == PRE_W || which == PRE_PV;
       const bool mine = r < ffac && !(Q.tiled[term] && !two) && !(Q.inl[term] && step_src);
       if (mine) {
         const Csr& B = Q.fac[term];
@@ -899,7 +900,7 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
     } else if (KIND == K_APPLY_Q) {
       q_csr_chunk<G, 1>(Q, row0, V.ain, nullptr, V.t1, nullptr, rs0, rs1);
     } else if (KIND == K_POWER_Q) {
-      q_csr_chunk<G, 1>(Q, row0, V.pv, nullptr, V.t1, nullptr, rs0, rs1);
+      q_csr_chunk<G, 1>(Q, row0, V.pv, nullptr, V.t1, nullptr, rs0, rs1, true);
     } else if (KIND == K_A1) {
       if (RED && ttest) csr_chunk<G, 2>(a.A, row0, V.v, V.xb, rs0, rs1, false);
       else csr_chunk<G, 1>(a.A, row0, V.v, nullptr, rs0, rs1, false);
@@ -1011,9 +1012,12 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
       } else if (KIND == K_APPLY_AT_P) {
         V.ptmp[j] = r0;
       } else if (KIND == K_POWER_Q || KIND == K_POWER_A) {
-        const double wv = KIND == K_POWER_Q ? r0 + q_local(Q, j, V.pv, V.t1, true, true) : r0;
+        // the source is the previous product w, unnormalised: v = w / ||w|| = pw_scale w, and
+        // the operator is linear, so Q v = pw_scale (Q w) (A A^* likewise)
+        const double sc = C->pw_scale;
+        const double wv = sc * (KIND == K_POWER_Q ? r0 + q_local(Q, j, V.pv, V.t1, true, true) : r0);
         V.pw[j] = wv;
-        pw[0] = fma(V.pv[j], wv, pw[0]);
+        pw[0] = fma(sc * V.pv[j], wv, pw[0]);
         pw[1] = fma(wv, wv, pw[1]);
       }
     }
@@ -1054,7 +1058,7 @@ __device__ __forceinline__ void rows_body(const Args& a, const Handles& hd) {
           C->pw_lam = lnew;
           C->pw_scale = 1.0 / nw;
           C->pw_it++;
-          if (conv || C->pw_it >= C->pw_max) C->pw_done = 2;  // 2: normalise once more, then stop
+          if (conv || C->pw_it >= C->pw_max) C->pw_done = 1;
         }
       }
     }

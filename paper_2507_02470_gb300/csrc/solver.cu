@@ -127,7 +127,7 @@ struct Seq {
 static bool pre_has_work(const Args& a, int which, int tt) {
   if (!a.Q.has_fd()) return false;
   if (a.Q.ndense) return true;
-  const bool step = which == PRE_WH || which == PRE_WB || which == PRE_W;
+  const bool step = which == PRE_WH || which == PRE_WB || which == PRE_W || which == PRE_PV;
   bool tiled = false;
   for (int f = 0; f < a.Q.nfac; f++) {
     if (!a.Q.tiled[f] && !(step && a.Q.inl[f])) return true;
@@ -531,23 +531,13 @@ cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// v <- w / ||w|| (power method); dim elements
-__global__ void k_pw_norm(Args a, int64_t dim) {
-  Ctrl* C = a.C;
-  if (C->pw_done == 1) return;
-  const double sc = C->pw_scale;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < dim; j += stride) a.V.pv[j] = a.V.pw[j] * sc;
-}
-__global__ void k_pw_flag(Args a) {
-  if (a.C->pw_done == 2) a.C->pw_done = 1;
-}
 __global__ void k_pw_start(Args a, int64_t dim) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += stride) {
-    // 0.5 + (hash(i) mod 2^32) / 2^32, a fixed pseudo-random start vector
+    // 0.5 + (hash(i) mod 2^32) / 2^32, a fixed pseudo-random start vector (the w that the
+    // first iteration reads, from pv)
     const uint32_t h = (uint32_t)((uint64_t)(i + 1) * 2654435761u);
-    a.V.pw[i] = 0.5 + (double)h / 4294967296.0;
+    a.V.pv[i] = 0.5 + (double)h / 4294967296.0;
   }
 }
 
@@ -559,16 +549,18 @@ cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStrea
 }
 
 int kernels_per_power_iter(const Args& a, int which) {
-  if (which == 0) return 4;
-  return 3 + (pre_has_work(a, 4, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 2 : 0);
+  if (which == 0) return 2;
+  return 1 + (pre_has_work(a, 4, 0) ? 1 : 0) + 3 * tiled_terms(a) + (a.Q.qap_d ? 2 : 0);
 }
 
-cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s) {
-  const int64_t dim = which == 0 ? a.m : a.n;
+// One power iteration, Sec. 4.1: w_{i+1} = M v_i with v_i = w_i / ||w_i||, M = Q or A A^*.  The
+// normalisation is folded into the product (M v = pw_scale M w, the scale of the previous w set
+// by the last block of the previous product), so w_i and w_{i+1} alternate between pv and pw:
+// iteration i reads V.pv and writes V.pw of an Args whose two are swapped when i is odd.
+cudaError_t launch_power_iter(const Args& a0, const Plan& p, int which, int i, cudaStream_t s) {
+  Args a = a0;
+  if (i & 1) std::swap(a.V.pv, a.V.pw);
   const Handles none;
-  // normalise the previous w into v (the first call normalises the start vector)
-  k_pw_norm<<<p.gridE, kThreads, 0, s>>>(a, dim);
-  k_pw_flag<<<1, 1, 0, s>>>(a);
   if (which == 0) {
     rowk(K_APPLY_AT_P, 0, p.gAT)<<<p.gridN, kThreads, 0, s>>>(a, none);
     rowk(K_POWER_A, 0, p.gA)<<<p.gridM, kThreads, 0, s>>>(a, none);

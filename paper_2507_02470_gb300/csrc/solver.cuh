@@ -124,7 +124,7 @@ int kernels_per_step(const Args& a);
 int kernels_per_restart(const Args& a);
 int kernels_per_iteration(const Args& a);
 cudaError_t launch_apply(const Args& a, const Plan& p, int op, cudaStream_t s);
-cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, cudaStream_t s);
+cudaError_t launch_power_iter(const Args& a, const Plan& p, int which, int i, cudaStream_t s);
 int kernels_per_power_iter(const Args& a, int which);
 cudaError_t launch_power_init(const Args& a, const Plan& p, int which, cudaStream_t s);
 cudaError_t launch_zbar(const Args& a, const Plan& p, cudaStream_t s);
