@@ -5,7 +5,10 @@ error of FP32 accumulation over K terms is bounded by K 2^-24 sum|a||b|, taken w
 margin of 4); conversions must match the oracle's BF16 rounding bit for bit; the network's
 forward pass, gradients and Adam steps, the warm-start loss and the decoder must match the
 oracle run on the same BF16 values (normwise 1e-3: both sides round activations to BF16 at
-the same points, so only accumulation order differs, which flips a rounding rarely).
+the same points, so only accumulation order differs, which flips a rounding rarely; the
+forward output and the gradients also element by element: within worst-case bounds derived
+from the FP32 accumulation and BF16 rounding of every layer, and within 1e-2 of the largest
+magnitude).
 The last test trains the warm start on a small family and checks that held-out members
 converge in fewer iterations than from the origin, to the same objective.
 """
@@ -43,6 +46,52 @@ def bf16_tensor(torch, a, ld=None):
 
 def normrel(a, b):
     return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+U16 = 2.0 ** -8    # unit roundoff of BF16 (8 significant bits)
+U32 = 2.0 ** -24   # unit roundoff of FP32, the GEMMs' accumulators
+
+
+def mlp_bounds(Ws, bs, hs, dY, B):
+    """Element-wise bounds on |GPU - oracle| for the forward output and the gradients, from the
+    arithmetic alone: both sides take the same BF16 inputs and weights; a GEMM over K terms in
+    FP32 differs from the exact sum by at most 4 K U32 sum|a||b|; a value rounded to BF16 on both
+    sides from inputs e apart differs by at most e + U16 (|a| + |b|); ReLU is 1-Lipschitz.  A
+    ReLU mask may differ only where the oracle's input is within its bound of 0 (there the whole
+    value counts as error).  Loose on purpose: a rounding that flips rarely stays far inside."""
+    L = len(Ws)
+    Wb = [np.abs(OL.bf16_round(w)) for w in Ws]
+    e = np.zeros_like(hs[0])
+    eh = [e]
+    ez = None
+    for l in range(L):
+        K = Ws[l].shape[1]
+        # the GEMM's accumulation, then the FP32 bias add (and, for the output, its FP32 store)
+        az = (np.abs(hs[l]) + e) @ Wb[l].T
+        ez = e @ Wb[l].T + 4 * K * U32 * az + 2 * U32 * (az + np.abs(bs[l]))
+        if l + 1 < L:
+            e = ez + U16 * (2 * hs[l + 1] + ez)
+            eh.append(e)
+    eY = ez
+    # backward: dZ of the last layer is the same BF16 rounding of the same dY on both sides
+    dZ = OL.bf16_round(dY)
+    edZ = np.zeros_like(dZ)
+    eW, eb = [None] * L, [None] * L
+    for l in range(L - 1, -1, -1):
+        aZ, aH = np.abs(dZ), np.abs(hs[l])
+        eW[l] = edZ.T @ (aH + eh[l]) + aZ.T @ eh[l] + 4 * B * U32 * ((aZ + edZ).T @ (aH + eh[l]))
+        eb[l] = edZ.sum(axis=0) + 4 * B * U32 * (aZ + edZ).sum(axis=0)
+        if l == 0:
+            break
+        K = Ws[l].shape[0]
+        dX = dZ @ OL.bf16_round(Ws[l])
+        edX = edZ @ Wb[l] + 4 * K * U32 * ((aZ + edZ) @ Wb[l])
+        unsure = hs[l] <= eh[l]
+        dZn = OL.bf16_round(dX * (hs[l] > 0))
+        edZ = np.where(unsure, np.abs(dX) + edX + U16 * (np.abs(dX) + edX),
+                       edX + U16 * (2 * np.abs(dZn) + edX))
+        dZ = dZn
+    return eY, eW, eb
 
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (256, 384, 1024, 1), (200, 100, 150, 1),
@@ -132,11 +181,23 @@ def test_mlp_forward_backward_adam_match_oracle(env, dims, B):
     assert normrel(Y.cpu().numpy(), Yref) <= 1e-3
     dY = rng.standard_normal((B, dims[-1])) / B
     net.backward(torch.from_numpy(dY.astype(np.float32)).cuda())
-    gW, gb = OL.mlp_backward(Ws, hs, dY.astype(np.float32).astype(np.float64))
+    dY64 = dY.astype(np.float32).astype(np.float64)
+    gW, gb = OL.mlp_backward(Ws, hs, dY64)
+    eY, eW, eb = mlp_bounds(Ws, bs, hs, dY64, B)
+    Yg = Y.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(Yg - Yref) <= eY), np.max(np.abs(Yg - Yref) / (eY + 1e-300))
+    # the worst-case bound above assumes every rounding flips; in fact few do, so every output
+    # element also stays within 1e-2 of the output's largest magnitude
+    assert np.max(np.abs(Yg - Yref)) <= 1e-2 * np.max(np.abs(Yref))
     for l in range(len(Ws)):
         w, b = net.get_grad(l)
         assert normrel(w, gW[l]) <= 1e-3, l
         assert normrel(b, gb[l]) <= 1e-3, l
+        w, b = np.asarray(w, dtype=np.float64), np.asarray(b, dtype=np.float64)
+        assert np.all(np.abs(w - gW[l]) <= eW[l]), (l, np.max(np.abs(w - gW[l]) / (eW[l] + 1e-300)))
+        assert np.all(np.abs(b - gb[l]) <= eb[l]), (l, np.max(np.abs(b - gb[l]) / (eb[l] + 1e-300)))
+        assert np.max(np.abs(w - gW[l])) <= 1e-2 * np.max(np.abs(gW[l])), l
+        assert np.max(np.abs(b - gb[l])) <= 1e-2 * np.max(np.abs(gb[l])), l
     # three Adam steps on the same gradients
     Wr = [w.copy() for w in Ws]
     br = [b.copy() for b in bs]
