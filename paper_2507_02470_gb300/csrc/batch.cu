@@ -1166,11 +1166,11 @@ static bool fs_fits(hprqp_batch* b, int bk) {
   return S.fmax[bk] > 0 && bucket_smem(S, bk, true) <= (size_t)optin;
 }
 
-// Autotuner (row a10): per bucket of instances, time the candidate schedules on a sample of the
-// bucket's own instances (the first 100 iterations of up to 4 per SM of them, one launch each)
-// and keep the fastest: blocks of 512, 256, 128 or 64 threads per instance, each with and
-// without a shared-memory copy of the instance's dense factor F (where every F of the bucket
-// fits).  batch_team fixes the block size of every bucket (no F copy); autotune = 0 takes
+// Autotuner (row a10): per bucket of instances, time the candidate schedules on the bucket's own
+// instances (the first 100 iterations of one wave of them, one launch each) and keep the one
+// with the highest rate of estimated work: blocks of 512, 256, 128 or 64 threads per instance,
+// each with and without a shared-memory copy of the instance's dense factor F (where every F of
+// the bucket fits).  batch_team fixes the block size of every bucket (no F copy); autotune = 0 takes
 // 512, 256, 128 and 64 threads from the largest n down (no F copy).
 static hprqp_status batch_autotune(hprqp_batch* b, int sms) {
   Sched& S = b->sched;
@@ -1191,30 +1191,43 @@ static hprqp_status batch_autotune(hprqp_batch* b, int sms) {
   for (int bk = 0; bk < kMaxBuckets; bk++) {
     const int cnt = S.beg[bk + 1] - S.beg[bk];
     if (cnt <= 0) continue;
-    const int sample = std::min(cnt, sms * 4);
-    float best = 1e30f;
+    double best = 0.0;   // estimated work per millisecond of the best candidate
     for (int fs = 0; fs < 2; fs++) {
       if (fs && !fs_fits(b, bk)) continue;
-      // largest blocks first; smaller ones only while they stay within 25 % of the best so far
-      // (time per instance grows steadily as blocks shrink past the best size)
+      // largest blocks first; smaller ones only while they stay within 15 % of the best so far
+      // (the rate falls steadily as blocks shrink past the best size)
       for (int G : {512, 256, 128, 64}) {
+        // one wave: as many of the bucket's instances (largest first) as blocks of this shape fit
+        // the GPU at once, so that no candidate is timed on a partial last wave; rates compare
+        // the instances' estimated work (the work order's cost) per millisecond
+        const KFn k = batch_kernel(fs != 0, small_p(S, bk));
+        const size_t smem = bucket_smem(S, bk, fs != 0);
+        int occ = 0;
+        BCU(b, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BCU(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, G, smem));
+        if (occ < 1) continue;   // no block of this shape fits an SM
+        const int sample = std::min(cnt, sms * occ);
+        double work = 0.0;
+        for (int q = S.beg[bk]; q < S.beg[bk] + sample; q++) {
+          const Inst& I = b->hinst[b->horder[q]];
+          work += (double)I.n * (2.0 * I.p + 30.0);
+        }
         BCU(b, cudaMemsetAsync(P.head + bk, 0, sizeof(unsigned), b->stream));
         BCU(b, cudaEventRecord(e0, b->stream));
-        const cudaError_t le = launch_bucket(b, bk, S.beg[bk], sample, G, fs != 0, sms, b->stream);
-        if (le == cudaErrorInvalidConfiguration) continue;   // no block of this shape fits an SM
-        BCU(b, le);
+        BCU(b, launch_bucket(b, bk, S.beg[bk], sample, G, fs != 0, sms, b->stream));
         BCU(b, cudaEventRecord(e1, b->stream));
         BCU(b, cudaEventSynchronize(e1));
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = work / std::max(1e-3, (double)ms);
         if (b->prm.verbose >= 2)
-          std::fprintf(stderr, "hprqp batch autotune: bucket %d (n >= %d, %d instances): %d threads%s: %.3f ms\n",
-                       bk, b->bucket_lo[bk], sample, G, fs ? ", F in shared memory" : "", ms);
-        if (ms < best) {
-          best = ms;
+          std::fprintf(stderr, "hprqp batch autotune: bucket %d (n >= %d): %d threads%s, %d instances: %.3f ms, "
+                       "%.4g work/ms\n", bk, b->bucket_lo[bk], G, fs ? ", F in shared memory" : "", sample, ms, rate);
+        if (rate > best) {
+          best = rate;
           S.threads[bk] = G;
           S.fs[bk] = fs != 0;
-        } else if (ms > 1.25f * best) {
+        } else if (rate * 1.15 < best) {
           break;
         }
       }
