@@ -49,6 +49,14 @@ struct hprqp_handle {
   bool fixed_tried = false;
   cudaGraphExec_t g_pw[2] = {nullptr, nullptr};
   int pw_chunk = 16;
+  // the power method on A A^* runs beside the one on Q (both needed: m > 0 and Q present): its
+  // own controller copy, partials, counters and vectors, on its own stream
+  bool pw_pair = false;
+  Args pwA_args;
+  Ctrl* dctrl2 = nullptr;
+  Ctrl* hctrl2 = nullptr;     // pinned mirror
+  cudaStream_t pstream = nullptr;
+  cudaEvent_t pfork = nullptr, pjoin = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::string err;
   hprqp_kkt kkt;
@@ -379,11 +387,18 @@ static void release(hprqp_handle* h) {
     if (g) cudaGraphExecDestroy(g);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  if (h->pstream) {
+    cudaStreamSynchronize(h->pstream);
+    cudaStreamDestroy(h->pstream);
+  }
+  if (h->pfork) cudaEventDestroy(h->pfork);
+  if (h->pjoin) cudaEventDestroy(h->pjoin);
   for (auto& a : h->allocs) {
     if (h->prm.free) h->prm.free(a.first, a.second, h->prm.alloc_ctx, h->stream);
     else cudaFree(a.first);
   }
   if (h->hctrl) cudaFreeHost(h->hctrl);
+  if (h->hctrl2) cudaFreeHost(h->hctrl2);
   if (h->hflags) cudaFreeHost(h->hflags);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -981,6 +996,29 @@ static hprqp_status create_impl(hprqp_handle* h, int64_t n, int64_t m, const hpr
   }
   CU(h, cudaMallocHost(&h->hctrl, sizeof(Ctrl)));
   std::memset(h->hctrl, 0, sizeof(Ctrl));
+  if (a.Q.present() && m > 0) {
+    // state of the power method on A A^* when it runs beside the one on Q
+    Args& pa = h->pwA_args;
+    pa = a;
+    void* p;
+    if ((st = dalloc(h, &p, sizeof(Ctrl)))) return st;
+    CU(h, cudaMemsetAsync(p, 0, sizeof(Ctrl), h->stream));
+    h->dctrl2 = (Ctrl*)p;
+    pa.C = h->dctrl2;
+    if ((st = dalloc(h, &p, 16 * sizeof(unsigned)))) return st;
+    CU(h, cudaMemsetAsync(p, 0, 16 * sizeof(unsigned), h->stream));
+    pa.counters = (unsigned*)p;
+    if ((st = zeros(h, &pa.partP, (size_t)gmax * kWP))) return st;
+    if ((st = zeros(h, &pa.V.pv, m))) return st;
+    if ((st = zeros(h, &pa.V.pw, m))) return st;
+    if ((st = zeros(h, &pa.V.ptmp, n))) return st;
+    CU(h, cudaMallocHost(&h->hctrl2, sizeof(Ctrl)));
+    std::memset(h->hctrl2, 0, sizeof(Ctrl));
+    CU(h, cudaStreamCreateWithFlags(&h->pstream, cudaStreamNonBlocking));
+    CU(h, cudaEventCreateWithFlags(&h->pfork, cudaEventDisableTiming));
+    CU(h, cudaEventCreateWithFlags(&h->pjoin, cudaEventDisableTiming));
+    h->pw_pair = true;
+  }
   CU(h, cudaMallocHost(&h->hflags, 8 * sizeof(int)));
   CU(h, cudaEventCreate(&h->ev[0]));
   CU(h, cudaEventCreate(&h->ev[1]));
@@ -1244,13 +1282,27 @@ static hprqp_status build_iter_graph(hprqp_handle* h) {
   return HPRQP_OK;
 }
 
+// The arguments of the power method on A A^* when it runs beside the one on Q: the solver's,
+// with its own controller copy, partials, counters and vectors.
+static Args pw_pair_args(const hprqp_handle* h) {
+  Args pa = h->args;
+  pa.C = h->pwA_args.C;
+  pa.counters = h->pwA_args.counters;
+  pa.partP = h->pwA_args.partP;
+  pa.V.pv = h->pwA_args.V.pv;
+  pa.V.pw = h->pwA_args.V.pw;
+  pa.V.ptmp = h->pwA_args.V.ptmp;
+  return pa;
+}
+
 static hprqp_status build_pw_graph(hprqp_handle* h, int which) {
   if (h->g_pw[which]) return HPRQP_OK;
+  const Args pa = (which == 0 && h->pw_pair) ? pw_pair_args(h) : h->args;
   cudaGraph_t g;
   CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   // an even number of iterations per graph, so that every launch starts reading pv
-  for (int i = 0; i < h->pw_chunk && le == cudaSuccess; i++) le = launch_power_iter(h->args, h->plan, which, i, h->stream);
+  for (int i = 0; i < h->pw_chunk && le == cudaSuccess; i++) le = launch_power_iter(pa, h->plan, which, i, h->stream);
   cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
   if (le != cudaSuccess || ce != cudaSuccess) {
     cudaGetLastError();
@@ -1281,7 +1333,13 @@ static hprqp_status power_method(hprqp_handle* h, int which, double* lam) {
     double v = 0.5 + (double)hh / 4294967296.0;
     s2 += v * v;
   }
-  Ctrl& C = *h->hctrl;
+  // with the paired state (m > 0 and Q present), the method on A A^* keeps to its own
+  // controller copy and vectors, as its graph does, also when it runs alone
+  const bool pair = which == 0 && h->pw_pair;
+  Ctrl* hc = pair ? h->hctrl2 : h->hctrl;
+  Ctrl* dc = pair ? h->dctrl2 : h->dctrl;
+  if (pair) std::memcpy(hc, h->hctrl, sizeof(Ctrl));
+  Ctrl& C = *hc;
   C.pw_it = 0;
   C.pw_lam = 0.0;
   C.pw_done = 0;
@@ -1289,8 +1347,8 @@ static hprqp_status power_method(hprqp_handle* h, int which, double* lam) {
   C.pw_max = h->prm.power_max_iter;
   C.pw_tol = h->prm.power_tol;
   C.done = 1;  // keep the iteration kernels idle
-  CU(h, cudaMemcpyAsync(h->dctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
-  CU(h, launch_power_init(h->args, h->plan, which, h->stream));
+  CU(h, cudaMemcpyAsync(dc, hc, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+  CU(h, launch_power_init(pair ? pw_pair_args(h) : h->args, h->plan, which, h->stream));
   const int64_t max_launch = h->prm.power_max_iter / h->pw_chunk + 3;
   int* flag = h->hflags;
   h->launches += 1;
@@ -1298,13 +1356,78 @@ static hprqp_status power_method(hprqp_handle* h, int which, double* lam) {
   for (int64_t i = 0; i < max_launch; i++) {
     CU(h, cudaGraphLaunch(h->g_pw[which], h->stream));
     h->launches += pw_nodes;
-    CU(h, cudaMemcpyAsync(flag, &h->dctrl->pw_done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(flag, &dc->pw_done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
     if (*flag == 1) break;
   }
-  CU(h, cudaMemcpyAsync(h->hctrl, h->dctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(hc, dc, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
-  *lam = h->prm.power_safety * h->hctrl->pw_lam;
+  *lam = h->prm.power_safety * hc->pw_lam;
+  return HPRQP_OK;
+}
+
+// Both power methods of Sec. 4.1 at once (m > 0 and Q present): the one on Q on the solver's
+// stream, the one on A A^* on its own stream with its own state, each chunk of iterations a
+// graph launch; the host polls both done flags after every round of launches.  The two are
+// independent and each product leaves most of the GPU's issue slots idle, so they overlap.
+static hprqp_status power_both(hprqp_handle* h, double* lamA, double* lamQ) {
+  Range rg("hprqp_power_AQ");
+  hprqp_status st;
+  if ((st = build_pw_graph(h, 0))) return st;
+  if ((st = build_pw_graph(h, 1))) return st;
+  const Args pa = pw_pair_args(h);
+  auto start_scale = [](int64_t dim) {
+    // host value of 1/||start||, same start vector and summation order as the CPU reference
+    double s2 = 0.0;
+    for (int64_t i = 0; i < dim; i++) {
+      uint32_t hh = (uint32_t)((uint64_t)(i + 1) * 2654435761u);
+      double v = 0.5 + (double)hh / 4294967296.0;
+      s2 += v * v;
+    }
+    return 1.0 / std::sqrt(s2);
+  };
+  Ctrl* hc[2] = {h->hctrl2, h->hctrl};
+  Ctrl* dc[2] = {h->dctrl2, h->dctrl};
+  cudaStream_t ss[2] = {h->pstream, h->stream};
+  CU(h, cudaEventRecord(h->pfork, h->stream));
+  CU(h, cudaStreamWaitEvent(h->pstream, h->pfork, 0));
+  for (int w = 0; w < 2; w++) {
+    Ctrl& C = *hc[w];
+    if (w == 0) std::memcpy(&C, h->hctrl, sizeof(Ctrl));
+    C.pw_it = 0;
+    C.pw_lam = 0.0;
+    C.pw_done = 0;
+    C.pw_scale = start_scale(w == 0 ? h->m : h->n);
+    C.pw_max = h->prm.power_max_iter;
+    C.pw_tol = h->prm.power_tol;
+    C.done = 1;  // keep the iteration kernels idle
+    CU(h, cudaMemcpyAsync(dc[w], hc[w], sizeof(Ctrl), cudaMemcpyHostToDevice, ss[w]));
+    CU(h, launch_power_init(w == 0 ? pa : h->args, h->plan, w, ss[w]));
+    h->launches += 1;
+  }
+  const int64_t max_launch = h->prm.power_max_iter / h->pw_chunk + 3;
+  int* flag = h->hflags + 2;
+  bool done[2] = {false, false};
+  for (int64_t i = 0; i < max_launch && !(done[0] && done[1]); i++) {
+    for (int w = 0; w < 2; w++) {
+      if (done[w]) continue;
+      CU(h, cudaGraphLaunch(h->g_pw[w], ss[w]));
+      h->launches += (int64_t)h->pw_chunk * kernels_per_power_iter(h->args, w);
+      CU(h, cudaMemcpyAsync(flag + w, &dc[w]->pw_done, sizeof(int), cudaMemcpyDeviceToHost, ss[w]));
+    }
+    for (int w = 0; w < 2; w++) {
+      if (done[w]) continue;
+      CU(h, cudaStreamSynchronize(ss[w]));
+      done[w] = flag[w] == 1;
+    }
+  }
+  for (int w = 0; w < 2; w++) CU(h, cudaMemcpyAsync(hc[w], dc[w], sizeof(Ctrl), cudaMemcpyDeviceToHost, ss[w]));
+  CU(h, cudaEventRecord(h->pjoin, h->pstream));
+  CU(h, cudaStreamWaitEvent(h->stream, h->pjoin, 0));
+  CU(h, cudaStreamSynchronize(h->stream));
+  CU(h, cudaStreamSynchronize(h->pstream));
+  *lamA = h->prm.power_safety * h->hctrl2->pw_lam;
+  *lamQ = h->prm.power_safety * h->hctrl->pw_lam;
   return HPRQP_OK;
 }
 
@@ -1658,14 +1781,19 @@ extern "C" hprqp_status hprqp_solve(hprqp_handle* h, double tol, int64_t max_ite
   h->fixed_steps = 0;
   // ---- lambda_A >= lambda_1(AA^*), lambda_Q >= lambda_1(Q) (Sec. 4.1)
   double lamA = 0.0, lamQ = 0.0;
-  if (HA) {
-    if (h->prm.lambda_A > 0) lamA = h->prm.lambda_A;
-    else if ((st = power_method(h, 0, &lamA))) return st;
+  if (HA && HQ && h->pw_pair && !(h->prm.lambda_A > 0) && !(h->prm.lambda_Q > 0)) {
+    if ((st = power_both(h, &lamA, &lamQ))) return st;
     if (!(lamA > 0.0)) lamA = 1.0;
-  }
-  if (HQ) {
-    if (h->prm.lambda_Q > 0) lamQ = h->prm.lambda_Q;
-    else if ((st = power_method(h, 1, &lamQ))) return st;
+  } else {
+    if (HA) {
+      if (h->prm.lambda_A > 0) lamA = h->prm.lambda_A;
+      else if ((st = power_method(h, 0, &lamA))) return st;
+      if (!(lamA > 0.0)) lamA = 1.0;
+    }
+    if (HQ) {
+      if (h->prm.lambda_Q > 0) lamQ = h->prm.lambda_Q;
+      else if ((st = power_method(h, 1, &lamQ))) return st;
+    }
   }
   auto t1 = std::chrono::steady_clock::now();
   if (h->prm.method != 0) {
