@@ -93,7 +93,9 @@ typedef void* (*hprqp_alloc_fn)(size_t bytes, void* ctx, void* stream);
 typedef void (*hprqp_free_fn)(void* ptr, size_t bytes, void* ctx, void* stream);
 
 typedef struct hprqp_params {
-  void* stream;              /* cudaStream_t for all work; NULL: the handle creates one */
+  void* stream;              /* cudaStream_t for all work (the power method on A A^* runs on
+                                an internal stream forked from and joined back to it); NULL:
+                                the handle creates one */
   int64_t check_every;       /* termination test period, default 100 (Table 1 counts) */
   int64_t restart_every;     /* restart test period (R~ evaluation), default 10 */
   double alpha1, alpha2, alpha3;   /* restart parameters, defaults 0.2, 0.8, 0.5 (Sec. 4.1) */
