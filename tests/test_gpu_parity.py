@@ -128,6 +128,25 @@ def test_power_method(pkg):
     assert abs(k["lambda_Q"] - ref.lambda_Q) <= 1e-5 * ref.lambda_Q
 
 
+def test_power_methods_side_by_side_match_each_alone(pkg):
+    # with A and Q both present the two power methods run at once on two streams, each with its
+    # own state; run alone (the other lambda given) each must give the same value bit for bit,
+    # and a second solve on the same handle must repeat it (the state is reset per solve)
+    qp = PROBLEMS["plain"]
+    with pkg.Solver(qp) as s:
+        s.solve(tol=1e-30, max_iter=1)
+        both = s.kkt()
+        s.solve(tol=1e-30, max_iter=1)
+        again = s.kkt()
+    assert (again["lambda_A"], again["lambda_Q"]) == (both["lambda_A"], both["lambda_Q"])
+    with pkg.Solver(qp, lambda_Q=both["lambda_Q"]) as s:
+        s.solve(tol=1e-30, max_iter=1)
+        assert s.kkt()["lambda_A"] == both["lambda_A"]
+    with pkg.Solver(qp, lambda_A=both["lambda_A"]) as s:
+        s.solve(tol=1e-30, max_iter=1)
+        assert s.kkt()["lambda_Q"] == both["lambda_Q"]
+
+
 def test_default_run_matches_oracle_objective(pkg):
     # both sides estimate lambda themselves (power method), defaults everywhere
     qp = qpgen.plain_cqp()
